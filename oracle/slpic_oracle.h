@@ -1,0 +1,61 @@
+/*
+ * slpic_oracle.h -- declarations of the FP64 CPU oracle (test infrastructure).
+ *
+ * This header belongs to the oracle alone.  The CUDA library has its own
+ * public header and never includes this one; the two implementations share
+ * no code.  Citations are to Werner et al., arXiv 1511.08225.
+ */
+#ifndef SLPIC_ORACLE_H
+#define SLPIC_ORACLE_H
+
+#include <stdint.h>
+
+enum { ORC_BETA_ONE = 0, ORC_BETA_HEAVISIDE = 1, ORC_BETA_RELATIVISTIC = 2 };
+
+/* Sec. II, Eqs. (relativisticBeta), (heavisideBeta) */
+double orc_beta(int kind, double r, double v0);
+
+/* Appendix A, Eq. (slpicIntegrationV): tau* = int beta(|v(t)|) dt over one step */
+double orc_beta_integral(int kind, const double u[3], const double a[3], double dt,
+                         double v0);
+/* the paper's modified-midpoint evaluation, doubling substeps until rel_tol */
+double orc_beta_integral_mmid(int kind, const double u[3], const double a[3], double dt,
+                              double v0, double rel_tol, long *n_used);
+/* pins: closed-form time along the velocity line, and brute-force RK4 */
+double orc_time_closed(int kind, const double u[3], const double a[3], double v0,
+                       double tau);
+double orc_beta_integral_closed(int kind, const double u[3], const double a[3], double dt,
+                                double v0);
+void orc_rk4_limited(int kind, const double u[3], const double a[3], double dt, double v0,
+                     long n_sub, double out[7]);
+
+/* Appendix A, Eq. (LimPtclDynAppendixDotE), 1D nodal Poisson */
+void orc_poisson1d_dirichlet(int n_cells, double dx, double eps0, const double *rho,
+                             double phi_lo, double phi_hi, double *phi);
+void orc_poisson1d_periodic(int n_cells, double dx, double eps0, const double *rho,
+                            double *phi);
+void orc_efield1d(int n_cells, int periodic, double dx, const double *phi, double *E);
+
+/* Appendix A charge assignment (FP64) and the quantised FP32 -> int64 rule */
+void orc_deposit1d(int n_cells, int periodic, double dx, long n, const double *x,
+                   const double *v, const uint8_t *alive, int kind, double v0, double w,
+                   double *dens);
+float orc_beta_f32(int kind, float vx, float vy, float vz, float v0);
+void orc_deposit_q40(int n_cells, int periodic, long n, const int32_t *cell,
+                     const float *offset, const float *v, int kind, float v0,
+                     int64_t *acc);
+
+/* Appendix A gather/push/move with Sec. IV walls */
+void orc_push1d(int n_cells, int periodic, double dx, double dt, const double *E, long n,
+                double *x, double *v, uint8_t *alive, double qm, int kind, double v0,
+                long *flux);
+
+/* counter-based SplitMix64 and the volume source */
+uint64_t orc_splitmix64_at(uint64_t key, uint64_t i);
+uint64_t orc_stream_key(uint64_t seed, uint64_t step, uint32_t species);
+float orc_u24(uint64_t z);
+void orc_inject(uint64_t seed, uint64_t step, uint32_t species, long n_new,
+                float src_lo_cells, float src_len_cells, double dx, double vth,
+                double *x, double *v);
+
+#endif

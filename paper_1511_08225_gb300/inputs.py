@@ -1,0 +1,191 @@
+"""Seeded synthetic inputs for the speed-limited PIC path.
+
+This module builds problem descriptions and draws initial particle states.
+It holds none of the timestep's arithmetic (no push, deposit or field solve),
+so both the CUDA library's tests and the FP64 oracle can take their inputs
+from it.  Everything is drawn from ``numpy.random.Generator(PCG64(seed))``.
+
+Normalised units throughout: electron plasma frequency, electron Debye length,
+electron thermal speed, eps0, e and m_e are all 1, so the reference density
+n0 is 1 and an electron with temperature T_e = 1 has thermal speed 1.
+
+Problem dictionaries (the plain description both implementations accept):
+
+    n_cells, dx, dt, periodic, phi_lo, phi_hi, eps0, seed,
+    species: [{name, q, m, w, v0, kind, T, capacity}],
+    source:  {mode, lo_cells, len_cells, rate, ref_species}
+
+``kind`` is 0 = beta == 1 (plain PIC), 1 = Heaviside, 2 = "relativistic"
+(Sec. II of the paper).  ``T`` is the temperature of the physical source
+Maxwellian (0 = the species is not injected).  ``w`` is the g-weight of one
+macroparticle (real particles per macroparticle per unit area).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import integrate
+
+BETA_ONE, BETA_HEAVISIDE, BETA_RELATIVISTIC = 0, 1, 2
+SRC_NONE, SRC_LOSS_MATCHED, SRC_RATE = 0, 1, 2
+
+SEED = 20151126
+
+
+def make_rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ------------------------------------------------------------------ g loading
+def _g_factor(kind: int, r: np.ndarray, v0: float) -> np.ndarray:
+    """Density ratio g0/f0 of a speed-limited load, i.e. how much more often a
+    macroparticle of speed r must be drawn than a physical particle (Sec. II:
+    f = beta g).  Bounded by 1 + r/v0 for all three kinds."""
+    r = np.asarray(r, dtype=np.float64)
+    if kind == BETA_ONE:
+        return np.ones_like(r)
+    if kind == BETA_HEAVISIDE:
+        return np.maximum(1.0, r / v0)
+    return np.sqrt(r * r + v0 * v0) / v0
+
+
+def mean_g_factor(kind: int, vth: float, v0: float, vdim: int = 3) -> float:
+    """<g0/f0> over a Maxwellian of thermal speed vth (vdim = 1 or 3)."""
+    if kind == BETA_ONE:
+        return 1.0
+    if vdim == 3:
+        def dens(r):
+            return 4.0 * math.pi * r * r * (2 * math.pi * vth * vth) ** -1.5 * math.exp(
+                -r * r / (2 * vth * vth))
+    else:
+        def dens(r):
+            return 2.0 * (2 * math.pi * vth * vth) ** -0.5 * math.exp(-r * r / (2 * vth * vth))
+    top = 40.0 * vth
+    pts = [v0] if v0 < top else None
+    val, _ = integrate.quad(lambda r: dens(r) * float(_g_factor(kind, np.array(r), v0)),
+                            0.0, top, points=pts, limit=400, epsabs=0, epsrel=1e-12)
+    return val
+
+
+def _isotropic(rng, n):
+    z = rng.uniform(-1.0, 1.0, n)
+    ph = rng.uniform(0.0, 2 * math.pi, n)
+    s = np.sqrt(1.0 - z * z)
+    return np.stack([s * np.cos(ph), s * np.sin(ph), z], axis=1)
+
+
+def g_velocities(rng, n: int, vth: float, v0: float, kind: int, vdim: int = 3) -> np.ndarray:
+    """Draw n velocities from g0 = f0 * (g0/f0), f0 a Maxwellian (vth per
+    component), by rejection from the envelope f0 * (1 + r/v0): a mixture of
+    the Maxwellian itself (mass 1) and the Maxwellian weighted by r/v0 (speed
+    drawn from r^2/(2 vth^2) ~ Gamma(2) in 3V, ~ Exp(1) in 1V).  Returns
+    (n, 3) float64; in 1V only the x component is non-zero."""
+    out = np.zeros((n, 3))
+    if kind == BETA_ONE:
+        if vdim == 3:
+            out[:] = rng.normal(0.0, vth, (n, 3))
+        else:
+            out[:, 0] = rng.normal(0.0, vth, n)
+        return out
+    mean_r = vth * (2.0 * math.sqrt(2.0 / math.pi) if vdim == 3 else math.sqrt(2.0 / math.pi))
+    p_weighted = (mean_r / v0) / (1.0 + mean_r / v0)
+    filled = 0
+    while filled < n:
+        m = max(1024, int(1.3 * (n - filled)))
+        pick_w = rng.random(m) < p_weighted
+        r = np.empty(m)
+        if vdim == 3:
+            r[~pick_w] = np.sqrt((rng.normal(0.0, vth, (int((~pick_w).sum()), 3)) ** 2).sum(1))
+            r[pick_w] = vth * np.sqrt(2.0 * rng.gamma(2.0, 1.0, int(pick_w.sum())))
+        else:
+            r[~pick_w] = np.abs(rng.normal(0.0, vth, int((~pick_w).sum())))
+            r[pick_w] = vth * np.sqrt(2.0 * rng.exponential(1.0, int(pick_w.sum())))
+        acc = rng.random(m) * (1.0 + r / v0) <= _g_factor(kind, r, v0)
+        r = r[acc][: n - filled]
+        k = r.size
+        if vdim == 3:
+            out[filled:filled + k] = r[:, None] * _isotropic(rng, k)
+        else:
+            out[filled:filled + k, 0] = r * np.where(rng.random(k) < 0.5, -1.0, 1.0)
+        filled += k
+    return out
+
+
+def uniform_cells(rng, n: int, n_cells: int, lo: float = 0.0, hi: float | None = None):
+    """Positions uniform in [lo, hi) cells, as (int32 cell, float32 offset in [0,1))."""
+    hi = float(n_cells) if hi is None else hi
+    xc = rng.uniform(lo, hi, n)
+    cell = np.floor(xc).astype(np.int64)
+    off = (xc - cell).astype(np.float32)
+    # float32 rounding can turn 0.99999997 into 1.0: move such points into the next cell
+    bump = off >= np.float32(1.0)
+    off[bump] = 0.0
+    cell[bump] += 1
+    cell = np.minimum(cell, n_cells - 1)
+    return cell.astype(np.int32), off
+
+
+# ------------------------------------------------------------------ problems
+def species(name, q, m, T, v0, kind, n0=1.0, ppc=100, dx=0.5, vdim=3, capacity=None,
+            n_load=None, inject_T=None):
+    vth = math.sqrt(T / m)
+    w = n0 * dx * mean_g_factor(kind, vth, v0, vdim) / ppc
+    return {"name": name, "q": float(q), "m": float(m), "w": float(w), "v0": float(v0),
+            "kind": int(kind), "T": float(T if inject_T is None else inject_T),
+            "T_load": float(T), "vth": vth, "ppc": int(ppc), "vdim": int(vdim),
+            "capacity": int(capacity) if capacity is not None else None}
+
+
+def periodic_problem(n_cells=256, dx=0.5, dt=0.2, ppc=100, mass_ratio=100.0, T_e=1.0,
+                     T_i=1.0, v0=0.2, kind=BETA_HEAVISIDE, seed=SEED, vdim=3):
+    """1D periodic electron-ion plasma (the 256-cell, 51,200-particle case when
+    called with defaults).  Velocities Maxwellian (g-loaded), positions uniform."""
+    sp = [species("e", -1.0, 1.0, T_e, v0, kind, ppc=ppc, dx=dx, vdim=vdim),
+          species("i", 1.0, mass_ratio, T_i, v0, kind, ppc=ppc, dx=dx, vdim=vdim)]
+    for s in sp:
+        s["T"] = 0.0  # no source on a periodic grid
+        s["capacity"] = int(ppc * n_cells * 1.0) + 64
+    return {"n_cells": int(n_cells), "dx": float(dx), "dt": float(dt), "periodic": True,
+            "phi_lo": 0.0, "phi_hi": 0.0, "eps0": 1.0, "seed": int(seed), "species": sp,
+            "source": {"mode": SRC_NONE, "lo_cells": 0.0, "len_cells": 0.0, "rate": 0.0,
+                       "ref_species": 1}}
+
+
+def sheath_problem(n_cells=4096, dx=0.5, v0=0.05, ppc=1000, mass_ratio=73440.0, T_e=1.0,
+                   T_i=0.1, kind=BETA_HEAVISIDE, dt=None, seed=SEED, capacity_factor=1.5,
+                   source_mode=SRC_LOSS_MATCHED, rate=0.0):
+    """1D bounded argon-like sheath: absorbing walls at phi = 0, electrons and
+    ions loaded uniformly, a central source band (45%..55% of the domain)
+    re-injecting physical Maxwellian pairs.  dt defaults to dx / v0."""
+    dt = dx / v0 if dt is None else dt
+    sp = [species("e", -1.0, 1.0, T_e, v0, kind, ppc=ppc, dx=dx),
+          species("i", 1.0, mass_ratio, T_i, v0, kind, ppc=ppc, dx=dx)]
+    for s in sp:
+        s["capacity"] = int(capacity_factor * ppc * n_cells) + 1024
+    return {"n_cells": int(n_cells), "dx": float(dx), "dt": float(dt), "periodic": False,
+            "phi_lo": 0.0, "phi_hi": 0.0, "eps0": 1.0, "seed": int(seed), "species": sp,
+            "source": {"mode": int(source_mode), "lo_cells": 0.45 * n_cells,
+                       "len_cells": 0.10 * n_cells, "rate": float(rate), "ref_species": 1}}
+
+
+def load_state(prob: dict, seed: int | None = None):
+    """Initial FP32 particle state for every species: a list of
+    (cell int32[n], offset float32[n], v float32[n,3]) with ppc * n_cells
+    particles per species, positions uniform over the grid, velocities drawn
+    from the speed-limited load g0 of each species."""
+    rng = make_rng(prob["seed"] if seed is None else seed)
+    out = []
+    for sp in prob["species"]:
+        n = int(sp["ppc"]) * int(prob["n_cells"])
+        cell, off = uniform_cells(rng, n, int(prob["n_cells"]))
+        v = g_velocities(rng, n, sp["vth"], sp["v0"], sp["kind"], sp.get("vdim", 3))
+        out.append((cell, off, v.astype(np.float32)))
+    return out
+
+
+def random_state(rng, n: int, n_cells: int, vscale: float = 1.0):
+    """Generic FP32 state for parity cases: uniform cells, Gaussian velocities."""
+    cell, off = uniform_cells(rng, n, n_cells)
+    v = rng.normal(0.0, vscale, (n, 3)).astype(np.float32)
+    return cell, off, v
