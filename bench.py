@@ -1,0 +1,407 @@
+"""Benchmark: SLPIC particle-steps/s on the 1D bounded argon-like sheath.
+
+Workload (one GPU, weak-scaled: every rank runs its own independent sheath):
+4,096 cells, dx = 0.5 lambda_De, electrons + ions with m_i/m_e = 73,440 and
+T_e/T_i = 10, 1,000 macroparticles per cell per species (8.19M at load),
+Heaviside beta with v0 = 0.02 v_te and dt = dx/v0, absorbing phi = 0 walls, a
+central source band re-injecting the ions' losses (LOSS_MATCHED).  A step is
+one full pass of the timestep: gather, push, move, walls, deposit,
+compaction, injection, FP64 Poisson solve.  Inputs are synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank simulates its own
+instance; the timed region is bracketed by a barrier and device
+synchronisation and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SLPIC particle-steps/s incl. deposit+field solve, 1xGB300"
+UNIT = "particle-steps/s"
+BYTES_PER_PARTICLE_STEP = 40  # int32 cell + float4 state, read once and written once
+FALLBACK_HBM_GBS = 6800.0
+V0 = 0.02
+PPC = 1000
+N_CELLS = 4096
+
+
+def workload_config(n_gpus):
+    return {
+        "workload": "1D bounded argon-like sheath (1D3V): 4096 cells, dx=0.5 lambda_De, "
+                    "m_i/m_e=73440, T_e/T_i=10, 1000 ppc/species (8.19M particles at load), "
+                    "Heaviside beta, v0=0.02 v_te, dt=dx/v0, phi=0 absorbing walls, "
+                    "central LOSS_MATCHED source",
+        "n_cells": N_CELLS, "ppc_per_species": PPC, "v0": V0, "species": 2,
+        "precision": "FP32 push, int64 fixed-point deposit, FP64 Poisson",
+        "l2": "state larger than L2 (8.19M x 20 B = 164 MB read + 164 MB written per step)",
+        "parallelism": f"independent instance per GPU x{n_gpus}",
+    }
+
+
+def make_problem(seed):
+    from paper_1511_08225_gb300 import inputs
+    return inputs.sheath_problem(n_cells=N_CELLS, ppc=PPC, v0=V0, seed=seed)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.t_on = self.t_off = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def mark(self, on):
+        if on:
+            self.t_on = time.time()
+        else:
+            self.t_off = time.time()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r for t, r in self.rows if self.t_on and self.t_off and self.t_on <= t <= self.t_off]
+        if not rows:
+            rows = [r for _, r in self.rows]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline inputs
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d and d[k]:
+                    return float(d[k]), "measured"
+        except (ValueError, OSError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "push_math.cuh", "slpic_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1511_08225_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_particles):
+    """DRAM bytes per launch of the particle kernel from the committed ncu
+    summary, scaled to this launch's particle count; None if the kernel source
+    changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "k_particles_sheath.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    per_particle = d["dram_bytes_per_launch"] / d["particles_per_launch"]
+    return per_particle * n_particles
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(prob, state, budget_s, max_particles=None, rng_seed=0):
+    """Time the FP64 oracle on a particle subsample of the same workload until
+    budget_s of CPU time is spent (at least one step); particle-steps/s."""
+    from oracle import oracle as orc
+    rng = np.random.default_rng(rng_seed)
+    o = orc.OracleSim(prob)
+    n_total = sum(s[0].size for s in state)
+    frac = 1.0 if max_particles is None else min(1.0, max_particles / n_total)
+    for s, (c, off, v) in enumerate(state):
+        k = max(1, int(round(c.size * frac)))
+        idx = rng.choice(c.size, size=k, replace=False) if k < c.size else np.arange(c.size)
+        o.load_cells(s, c[idx], off[idx], v[idx])
+    o.start()
+    done, t0 = 0, time.perf_counter()
+    while True:
+        n = sum(x.size for x in o.x)
+        o.step(1)
+        done += n
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, sum(x.size for x in o.x)
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle as it stands, same metric/config."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1511_08225_gb300 import inputs
+    from oracle import oracle as orc
+    orc.build()
+    prob = make_problem(inputs.SEED)
+    state = inputs.load_state(prob)
+    # calibrate the per-particle cost, then size each step's sample so that
+    # warmup + steps end in about two minutes
+    rate, _, _, _ = oracle_rate(prob, state, 0.5, max_particles=20_000)
+    total_steps = max(1, args.steps + args.warmup)
+    per_step_particles = int(max(200, min(8_192_000, rate * 120.0 / total_steps)))
+    rng = np.random.default_rng(1)
+    o = orc.OracleSim(prob)
+    n_total = sum(s[0].size for s in state)
+    frac = per_step_particles / n_total
+    for s, (c, off, v) in enumerate(state):
+        k = max(1, int(round(c.size * frac)))
+        idx = rng.choice(c.size, size=k, replace=False)
+        o.load_cells(s, c[idx], off[idx], v[idx])
+    o.start()
+    for _ in range(args.warmup):
+        o.step(1)
+    done = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        done += sum(x.size for x in o.x)
+        o.step(1)
+    dt = time.perf_counter() - t0
+    value = done / dt
+    sample = (f"each step advances a fixed random subsample of {per_step_particles} "
+              f"particles of the 8.19M-particle workload (same grid, fields, source)")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference", "config": workload_config(args.gpus),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1511_08225_gb300 import binding, inputs
+    from paper_1511_08225_gb300 import build as pkg_build
+    pkg_build.build()
+    binding.load_library()
+
+    seed = inputs.SEED + rank
+    prob = make_problem(seed)
+    state = inputs.load_state(prob)
+    n_load = sum(s[0].size for s in state)
+
+    stream = torch.cuda.Stream()
+    sim = binding.Simulation(prob)
+    binding.slpic_set_stream(sim.h, stream.cuda_stream)
+    sim.load_state(state)
+    sim.prepare()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def live():
+        return sum(sim.count(s) for s in range(2))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    sim.step(args.warmup)
+    sim.synchronize()
+    n0 = live()
+    binding.slpic_enable_kernel_timing(sim.h, args.steps)
+    barrier()
+    clocks.mark(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clocks.mark(False)
+    ms = ev0.elapsed_time(ev1)
+    sim.synchronize()
+    n1 = live()
+    push_ms, field_ms, nrec = binding.slpic_kernel_times(sim.h)
+    kps = binding.slpic_kernels_per_step(sim.h)
+    clocks.stop()
+
+    particle_steps = 0.5 * (n0 + n1) * args.steps
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms, particle_steps], dtype=torch.float64, device="cuda")
+        tt = t.clone()
+        dist.all_reduce(tt[:1], op=dist.ReduceOp.MAX)
+        ps = t[1:].clone()
+        dist.all_reduce(ps, op=dist.ReduceOp.SUM)
+        t_max, particle_steps = float(tt[0]), float(ps[0])
+    value = particle_steps / (t_max * 1e-3)
+
+    # roofline of the particle kernel (dominant kernel)
+    n_mean = 0.5 * (n0 + n1)
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_PARTICLE_STEP * n_mean / (push_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": profiled_traffic(n_mean),
+            "kernel": "k_particles", "kernel_ms": push_ms, "field_kernel_ms": field_ms,
+            "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
+            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+    # end to end through the C ABI with pinned host buffers: load, steps with
+    # a read-back of the fields after every step
+    e2e = None
+    if rank == 0 or world > 1:
+        e2e = run_e2e(prob, state, args, binding, torch, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, done, dt, _ = oracle_rate(prob, state, args.cpu_budget, max_particles=40_000)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} particle-steps of a random 40,000-particle subsample of "
+                         f"the workload (same grid, fields, source), {dt:.1f} s, one thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "impl": "gb300", "config": workload_config(world),
+            "particles_at_load": n_load, "particles_timed_mean": n_mean,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": kps * args.steps, "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(prob, state, args, binding, torch, stream):
+    """Same metric through the public API with pinned host memory: each timed
+    run loads the particles from host, then every step is followed by a
+    device-to-host read of rho, phi and E (the step's result)."""
+    pinned = []
+    for c, o, v in state:
+        tc = torch.from_numpy(c).pin_memory()
+        to = torch.from_numpy(o).pin_memory()
+        tv = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+        pinned.append((tc.numpy(), to.numpy(), tv.numpy()))
+    nn = prob["n_cells"] + 1
+    rho = torch.empty(nn, dtype=torch.float64).pin_memory().numpy()
+    phi = torch.empty(nn, dtype=torch.float64).pin_memory().numpy()
+    E = torch.empty(nn, dtype=torch.float32).pin_memory().numpy()
+    L = binding.load_library()
+    steps = max(1, min(args.steps, args.e2e_steps))
+    sim = binding.Simulation(prob)
+    binding.slpic_set_stream(sim.h, stream.cuda_stream)
+    torch.cuda.synchronize()
+    h2d = sum(a.nbytes + b.nbytes + c.nbytes for a, b, c in pinned)
+    t0 = time.perf_counter()
+    for s, (c, o, v) in enumerate(pinned):
+        sim.load(s, c, o, v)
+    n = 0
+    for _ in range(steps):
+        sim.step(1)
+        rc = L.slpic_fields(sim.h, 0, binding._ptr(rho), binding._ptr(phi), binding._ptr(E))
+        if rc:
+            raise RuntimeError(f"slpic_fields failed: {rc}")
+    t1 = time.perf_counter()
+    d = sim.diagnostics()
+    n_end = sum(d["count"][:2])
+    n_start = sum(c.size for c, _, _ in pinned)
+    sim.close()
+    return {"value": 0.5 * (n_start + n_end) * steps / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": rho.nbytes + phi.nbytes + E.nbytes,
+            "steps": steps, "note": "load from pinned host memory counted once per run, "
+                                    "fields read back after every step"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

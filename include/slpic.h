@@ -1,0 +1,245 @@
+/*
+ * slpic.h -- C ABI of the GB300 speed-limited particle-in-cell library.
+ *
+ * Speed-limited PIC (SLPIC; Werner, Jenkins, Chap & Cary, arXiv 1511.08225)
+ * advances macroparticles that sample g = f / beta along the characteristics
+ * of Sec. II, Eq. (LimPtclDyn):  xdot = beta(|v|) v,  vdot = beta(|v|) q E / m,
+ * with the leapfrog discretisation of Appendix A, Eq. (slpicIntegration):
+ *
+ *   v^{n+1/2} = v^{n-1/2} + (q/m) E^n(x^n) int_{t^{n-1/2}}^{t^{n+1/2}} beta dt
+ *   x^{n+1}   = x^n + beta(|v^{n+1/2}|) v^{n+1/2} dt
+ *   rho^{n+1} = sum_p q w beta(|v^{n+1/2}|) S(x - x^{n+1})
+ *   div E^{n+1} = rho^{n+1} / eps0
+ *
+ * This library runs that loop on one GPU: 1D, 3 velocity components (1D3V,
+ * as in the paper's sheath of Sec. IV), electrostatic, linear (CIC) shape,
+ * absorbing Dirichlet or periodic boundaries, and a volume source.
+ *
+ * Units: whatever the caller uses consistently; the test problems use
+ * normalised units (omega_pe = lambda_De = v_te = eps0 = e = m_e = 1).
+ *
+ * General rules for every entry point
+ *  - Return value: SLPIC_OK (0) or a negative SLPIC_ERR_* code.  After an
+ *    error, slpic_last_error(h) returns a message (valid until the next call).
+ *  - Handles are opaque, created by slpic_create and owned by the caller,
+ *    who must call slpic_destroy.  A handle is not thread-safe.
+ *  - Array arguments belong to the caller.  Host arrays are read or written
+ *    during the call only.  *_dev entry points take device pointers and run
+ *    on the handle's stream (slpic_set_stream); they retain nothing.
+ *  - The handle allocates its device memory (particle store, grid arrays) in
+ *    slpic_create and frees it in slpic_destroy.
+ *  - Work is asynchronous on the handle's stream; entry points that return
+ *    host data synchronise that stream first.  Errors raised by kernels
+ *    (capacity overflow, invalid particles) are reported by the next
+ *    synchronising call.
+ */
+#ifndef SLPIC_H
+#define SLPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SLPIC_OK 0
+#define SLPIC_ERR_INVALID (-1)    /* bad argument or bad particle data        */
+#define SLPIC_ERR_CFL (-2)        /* dt * v0 > dx: more than one cell a step  */
+#define SLPIC_ERR_OOM (-3)        /* device allocation failed                 */
+#define SLPIC_ERR_CAPACITY (-4)   /* particle store full (injection dropped)  */
+#define SLPIC_ERR_NOCONVERGE (-5) /* iterative solve did not converge          */
+#define SLPIC_ERR_TIMEOUT (-6)    /* a bounded device-side wait ran out        */
+#define SLPIC_ERR_CUDA (-7)       /* CUDA runtime error (message has details)  */
+
+/* ---- enumerations -------------------------------------------------------- */
+/* beta of Sec. II: ONE = plain PIC; HEAVISIDE = Eq. (heavisideBeta),
+ * beta = 1 for |v| <= v0 else v0/|v|; RELATIVISTIC = Eq. (relativisticBeta),
+ * beta = v0 / sqrt(|v|^2 + v0^2). */
+#define SLPIC_BETA_ONE 0
+#define SLPIC_BETA_HEAVISIDE 1
+#define SLPIC_BETA_RELATIVISTIC 2
+
+#define SLPIC_BC_DIRICHLET_ABSORB 0 /* phi fixed at both walls; x<0 or x>=L absorbed */
+#define SLPIC_BC_PERIODIC 1         /* x wraps; rho mean removed; mean(phi) = 0       */
+
+#define SLPIC_SRC_NONE 0
+#define SLPIC_SRC_LOSS_MATCHED 1 /* re-inject the physical count of ref-species losses */
+#define SLPIC_SRC_RATE 2         /* inject rate*dt physical pairs per step              */
+
+#define SLPIC_MAX_SPECIES 4
+
+/* ---- configuration (Sec. IV problem statement) ---------------------------- */
+typedef struct {
+    double q;         /* charge per real particle                                  */
+    double m;         /* mass per real particle                                    */
+    double w;         /* g-weight: real particles per macroparticle (per unit area) */
+    double v0;        /* speed limit of beta (ignored for SLPIC_BETA_ONE)          */
+    double T_src;     /* temperature of the physical source Maxwellian; 0 = none   */
+    int64_t capacity; /* maximum macroparticles of this species                    */
+    int32_t beta_kind;/* SLPIC_BETA_*                                               */
+    int32_t reserved;
+} slpic_species;
+
+typedef struct {
+    int32_t ndim;          /* must be 1                                              */
+    int32_t n_cells;       /* N; nodes are 0..N (Dirichlet) or 0..N-1 (periodic)     */
+    double dx;             /* cell size                                              */
+    double dt;             /* timestep                                               */
+    int32_t bc;            /* SLPIC_BC_*                                             */
+    int32_t n_species;     /* 1..SLPIC_MAX_SPECIES                                   */
+    double phi_lo, phi_hi; /* wall potentials (Dirichlet)                            */
+    double eps0;           /* permittivity (1 in normalised units)                   */
+    double max_speed;      /* for SLPIC_BETA_ONE species: the caller's bound on |v|,
+                              checked against dx/dt (0 = unchecked)                 */
+    uint64_t seed;         /* source random stream                                   */
+    int32_t src_mode;      /* SLPIC_SRC_*                                            */
+    int32_t src_ref_species; /* LOSS_MATCHED: species whose losses are re-injected   */
+    double src_lo_cells;   /* source band start, in cells                            */
+    double src_len_cells;  /* source band length, in cells                           */
+    double src_rate;       /* RATE: physical pairs per unit time (per unit area)     */
+    slpic_species species[SLPIC_MAX_SPECIES];
+} slpic_config;
+
+/* ---- diagnostics ----------------------------------------------------------- */
+typedef struct {
+    int64_t step;                       /* steps taken                           */
+    double time;                        /* step * dt                             */
+    int64_t count[SLPIC_MAX_SPECIES];   /* live macroparticles                   */
+    double sum_w[SLPIC_MAX_SPECIES];    /* g-weight sum                          */
+    double sum_wbeta[SLPIC_MAX_SPECIES];/* physical particle count sum(w beta)   */
+    double kinetic[SLPIC_MAX_SPECIES];  /* physical kinetic energy
+                                           sum(1/2 m w beta |v|^2) (f = beta g)  */
+    double field_energy;                /* 1/2 eps0 dx sum_j E_j^2 (walls x 1/2) */
+    int64_t absorbed[SLPIC_MAX_SPECIES][2]; /* macroparticles absorbed at x=0 / x=L,
+                                               cumulative                         */
+    int64_t injected[SLPIC_MAX_SPECIES];    /* macroparticles injected, cumulative */
+} slpic_diag;
+
+typedef struct slpic_sim slpic_t;
+
+/* ---- lifetime -------------------------------------------------------------- */
+
+/* Validate *cfg and allocate a simulation on the current CUDA device.
+ * Checks (Sec. II, "dt <~ dx/v0"): dt * v0_s <= dx for every speed-limited
+ * species, and dt * max_speed <= dx for SLPIC_BETA_ONE species when
+ * max_speed > 0; otherwise SLPIC_ERR_CFL.  Allocates 2 x capacity particle
+ * slots per species (ping-pong) and the grid arrays; SLPIC_ERR_OOM if that
+ * fails.  *out is set only on success. */
+int slpic_create(const slpic_config *cfg, slpic_t **out);
+
+/* Free everything the handle owns.  NULL is accepted. */
+int slpic_destroy(slpic_t *h);
+
+/* Message for the last error on this handle ("" if none).  Owned by h. */
+const char *slpic_last_error(const slpic_t *h);
+
+/* Message for the last slpic_create failure in this thread. */
+const char *slpic_create_error(void);
+
+/* Run all further work on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream).  The handle starts on a private non-blocking stream. */
+int slpic_set_stream(slpic_t *h, void *stream);
+
+/* ---- particles ------------------------------------------------------------- */
+
+/* Append n macroparticles of `species` (Appendix A: the state at load is
+ * x^0 and v^{-1/2}).  Host arrays: cell[n] (int32, 0 <= cell < N), offset[n]
+ * (float32 in [0,1): x = (cell + offset) dx), v[3n] (float32, vx vy vz per
+ * particle).  Invalid data (cell out of range, offset outside [0,1), non-finite
+ * v) gives SLPIC_ERR_INVALID and loads nothing; more than the free capacity
+ * gives SLPIC_ERR_CAPACITY.  After the last load call slpic_prepare (or the
+ * first slpic_step) deposits rho^0 with beta(|v^{-1/2}|) and solves E^0.
+ * `instance` must be 0. */
+int slpic_load_particles(slpic_t *h, int instance, int species, int64_t n,
+                         const int32_t *cell, const float *offset, const float *v);
+
+/* Same, from device pointers (e.g. tensors already on the GPU). */
+int slpic_load_particles_dev(slpic_t *h, int instance, int species, int64_t n,
+                             const int32_t *cell, const float *offset, const float *v);
+
+/* Same, from FP64 host positions x[n] in [0, L) and velocities v[3n]; the
+ * library splits x into (cell, offset) and rounds to FP32. */
+int slpic_load_particles_f64(slpic_t *h, int instance, int species, int64_t n,
+                             const double *x, const double *v);
+
+/* Deposit rho from the current particles (beta of their current velocity,
+ * the quantised rule below) and solve phi and E.  Called implicitly by the
+ * first slpic_step after a load. */
+int slpic_prepare(slpic_t *h);
+
+/* ---- the timestep ---------------------------------------------------------- */
+
+/* Enqueue nsteps timesteps of Appendix A on the handle's stream and return.
+ * One step: gather E^n, push v by the exact beta integral, move x by
+ * beta(|v^{n+1/2}|) v^{n+1/2} dt, absorb at walls (or wrap), deposit
+ * rho^{n+1}; then inject source particles (deposited into rho^{n+1}, first
+ * pushed next step) and solve phi^{n+1}, E^{n+1}.  The steps run as a
+ * captured CUDA graph with no host synchronisation between them. */
+int slpic_step(slpic_t *h, int64_t nsteps);
+
+/* Wait for queued work; report device-side errors raised since the last
+ * report (SLPIC_ERR_CAPACITY, ...). */
+int slpic_synchronize(slpic_t *h);
+
+/* ---- read-back (host, synchronising) -------------------------------------- */
+
+/* Fields of the latest solve, all nodal, n_nodes = N+1 (Dirichlet) or N
+ * (periodic): rho (charge density, the wall nodes carry the half-cell charge
+ * divided by dx), phi, E (the FP32 copy the particles gather).  Any pointer
+ * may be NULL. */
+int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, float *E);
+
+/* Physical number density sum(w beta S)/dx of one species, nodal. */
+int slpic_density(slpic_t *h, int instance, int species, double *n);
+
+/* The raw fixed-point deposit of one species from the latest deposit, int64
+ * per node: every particle adds qT = rint(beta 2^40) split into
+ * rint(beta*offset*2^40) on node cell+1 and the rest on node cell, with
+ * beta = ONE ? 1 : HEAVISIDE ? (|v| <= v0 ? 1 : v0/|v|) : v0/sqrt(|v|^2+v0^2),
+ * |v|^2 = (vx*vx + vy*vy) + vz*vz, every FP32 operation rounded to nearest
+ * (no fused multiply-add).  Integer sums are exact, so the result does not
+ * depend on particle order. */
+int slpic_charge_raw(slpic_t *h, int instance, int species, int64_t *acc);
+
+int slpic_particle_count(slpic_t *h, int instance, int species, int64_t *n);
+
+/* Copy up to `cap` particles of a species to host arrays (layout as in
+ * slpic_load_particles); *n_out = number copied.  Particle order is not
+ * preserved across steps (absorbed particles are compacted out). */
+int slpic_get_particles(slpic_t *h, int instance, int species, int64_t cap,
+                        int32_t *cell, float *offset, float *v, int64_t *n_out);
+
+/* Counts, energies and wall fluxes (see slpic_diag). */
+int slpic_diagnostics(slpic_t *h, int instance, slpic_diag *out);
+
+/* ---- checkpoint ------------------------------------------------------------ */
+
+/* Serialise the complete state (particles, deposit, fields, counters, source
+ * remainders, step index) into a host buffer.  With buf == NULL, *size
+ * receives the bytes needed.  Restoring into a handle created from the same
+ * config continues bit for bit. */
+int slpic_save(slpic_t *h, void *buf, size_t *size);
+int slpic_restore(slpic_t *h, const void *buf, size_t size);
+
+/* ---- timing --------------------------------------------------------------- */
+
+/* Record CUDA events around the particle kernel and the field/source kernel
+ * of every step enqueued by slpic_step from now on (up to max_steps steps;
+ * 0 turns timing off).  The events are recorded on the handle's stream, the
+ * stream the kernels run on. */
+int slpic_enable_kernel_timing(slpic_t *h, int64_t max_steps);
+
+/* Mean device time (ms) of the particle kernel and of the field/source kernel
+ * over the steps recorded since slpic_enable_kernel_timing; synchronising. */
+int slpic_kernel_times(slpic_t *h, double *particle_ms, double *field_ms, int64_t *steps);
+
+/* Number of kernels one slpic_step(h, 1) launches. */
+int slpic_kernels_per_step(slpic_t *h, int *n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLPIC_H */

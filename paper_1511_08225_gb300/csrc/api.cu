@@ -1,0 +1,902 @@
+// api.cu -- the C ABI declared in include/slpic.h.
+//
+// The handle owns all device memory of one simulation; the timestep runs as a
+// captured CUDA graph (particle kernel, then field kernel) whose kernels read
+// the time level from device memory, so one graph serves every step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "slpic.h"
+#include "slpic_internal.cuh"
+
+using namespace slpic;
+
+struct slpic_sim {
+    slpic_config cfg{};
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;     // work stream (caller may replace)
+    cudaStream_t own_stream = nullptr; // created here
+    cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
+    StepParams p{};
+    int nn = 0, ns = 0;
+    int ctas = 1;        // particle-kernel CTAs per species
+    int small_ctas = 1;  // CTAs per species for deposit / diag
+    long long step = 0;  // host mirror of DevState::step
+    bool dirty = true;   // particles loaded since the last deposit/solve
+
+    DevState *d_state = nullptr;
+    unsigned long long *d_acc = nullptr;
+    float *d_E = nullptr;
+    double *d_E64 = nullptr, *d_phi = nullptr, *d_rho = nullptr;
+    int32_t *d_cell[kMaxSpecies][2] = {};
+    float4 *d_pv[kMaxSpecies][2] = {};
+    double *d_diag = nullptr;
+    int *d_bad = nullptr;
+    void *d_stage = nullptr;  // load/read-back staging
+    size_t stage_bytes = 0;
+
+    cudaGraphExec_t g1 = nullptr, gK = nullptr;
+    int K = 8;
+    cudaGraphExec_t gt = nullptr;  // timed one-step graph
+    cudaGraph_t gt_graph = nullptr; // kept alive: its event nodes are retargeted per launch
+    cudaGraphNode_t ev_node[3] = {};
+    std::vector<cudaEvent_t> events;
+    long long t_max = 0, t_used = 0;
+
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+#define CK(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return SLPIC_ERR_CUDA;                                                         \
+        }                                                                                  \
+    } while (0)
+
+static int fail(slpic_t *h, int code, const std::string &msg)
+{
+    h->err = msg;
+    return code;
+}
+
+static int check_handle(slpic_t *h, int instance)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    if (instance != 0)
+        return fail(h, SLPIC_ERR_INVALID, "instance must be 0");
+    h->err.clear();
+    CK(h, cudaSetDevice(h->device));
+    return SLPIC_OK;
+}
+
+// Checks that need no device (the shared-memory fit is checked in slpic_create).
+static int validate_config(const slpic_config *c, std::string &why)
+{
+    if (!c) {
+        why = "cfg is NULL";
+        return SLPIC_ERR_INVALID;
+    }
+    if (c->ndim != 1) {
+        why = "ndim must be 1";
+        return SLPIC_ERR_INVALID;
+    }
+    if (c->n_cells < 2 || !(c->dx > 0) || !(c->dt > 0) || !(c->eps0 > 0)) {
+        why = "need n_cells >= 2 and dx, dt, eps0 > 0";
+        return SLPIC_ERR_INVALID;
+    }
+    if (c->bc != SLPIC_BC_PERIODIC && c->bc != SLPIC_BC_DIRICHLET_ABSORB) {
+        why = "unknown bc";
+        return SLPIC_ERR_INVALID;
+    }
+    if (c->n_species < 1 || c->n_species > SLPIC_MAX_SPECIES) {
+        why = "n_species must be 1..4";
+        return SLPIC_ERR_INVALID;
+    }
+    for (int s = 0; s < c->n_species; ++s) {
+        const slpic_species &sp = c->species[s];
+        if (!(sp.m > 0) || !(sp.w > 0) || sp.capacity <= 0 || !std::isfinite(sp.q)) {
+            why = "species " + std::to_string(s) + ": need m > 0, w > 0, capacity > 0";
+            return SLPIC_ERR_INVALID;
+        }
+        if (sp.beta_kind < SLPIC_BETA_ONE || sp.beta_kind > SLPIC_BETA_RELATIVISTIC) {
+            why = "species " + std::to_string(s) + ": unknown beta_kind";
+            return SLPIC_ERR_INVALID;
+        }
+        if (sp.capacity > (1LL << 31) - 1) {
+            why = "species " + std::to_string(s) + ": capacity above 2^31-1";
+            return SLPIC_ERR_INVALID;
+        }
+        if (sp.beta_kind != SLPIC_BETA_ONE) {
+            if (!(sp.v0 > 0)) {
+                why = "species " + std::to_string(s) + ": v0 must be > 0";
+                return SLPIC_ERR_INVALID;
+            }
+            // |beta v| <= v0, so dt v0 <= dx keeps every move within one cell
+            if (c->dt * sp.v0 > c->dx * (1.0 + 1e-12)) {
+                why = "species " + std::to_string(s) + ": dt * v0 > dx";
+                return SLPIC_ERR_CFL;
+            }
+        } else if (c->max_speed > 0 && c->dt * c->max_speed > c->dx * (1.0 + 1e-12)) {
+            why = "species " + std::to_string(s) + ": dt * max_speed > dx";
+            return SLPIC_ERR_CFL;
+        }
+        if (sp.T_src < 0) {
+            why = "species " + std::to_string(s) + ": T_src < 0";
+            return SLPIC_ERR_INVALID;
+        }
+    }
+    if (c->src_mode != SLPIC_SRC_NONE) {
+        if (c->src_mode != SLPIC_SRC_LOSS_MATCHED && c->src_mode != SLPIC_SRC_RATE) {
+            why = "unknown src_mode";
+            return SLPIC_ERR_INVALID;
+        }
+        if (!(c->src_lo_cells >= 0) || !(c->src_len_cells > 0) ||
+            !(c->src_lo_cells + c->src_len_cells < c->n_cells)) {
+            why = "source band must satisfy 0 <= lo, len > 0, lo + len < n_cells";
+            return SLPIC_ERR_INVALID;
+        }
+        if (c->src_mode == SLPIC_SRC_LOSS_MATCHED &&
+            (c->src_ref_species < 0 || c->src_ref_species >= c->n_species)) {
+            why = "src_ref_species out of range";
+            return SLPIC_ERR_INVALID;
+        }
+        if (c->src_mode == SLPIC_SRC_RATE && !(c->src_rate >= 0)) {
+            why = "src_rate < 0";
+            return SLPIC_ERR_INVALID;
+        }
+    }
+    return SLPIC_OK;
+}
+
+static void free_all(slpic_t *h)
+{
+    cudaSetDevice(h->device);
+    if (h->g1)
+        cudaGraphExecDestroy(h->g1);
+    if (h->gK)
+        cudaGraphExecDestroy(h->gK);
+    if (h->gt)
+        cudaGraphExecDestroy(h->gt);
+    if (h->gt_graph)
+        cudaGraphDestroy(h->gt_graph);
+    for (cudaEvent_t e : h->events)
+        cudaEventDestroy(e);
+    cudaFree(h->d_state);
+    cudaFree(h->d_acc);
+    cudaFree(h->d_E);
+    cudaFree(h->d_E64);
+    cudaFree(h->d_phi);
+    cudaFree(h->d_rho);
+    cudaFree(h->d_diag);
+    cudaFree(h->d_bad);
+    cudaFree(h->d_stage);
+    for (int s = 0; s < kMaxSpecies; ++s)
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(h->d_cell[s][b]);
+            cudaFree(h->d_pv[s][b]);
+        }
+    if (h->own_stream)
+        cudaStreamDestroy(h->own_stream);
+    if (h->cap_stream)
+        cudaStreamDestroy(h->cap_stream);
+}
+
+extern "C" const char *slpic_create_error(void) { return g_create_err.c_str(); }
+
+extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
+{
+    g_create_err.clear();
+    if (!out) {
+        g_create_err = "out is NULL";
+        return SLPIC_ERR_INVALID;
+    }
+    std::string why;
+    int rc = validate_config(cfg, why);
+    if (rc != SLPIC_OK) {
+        g_create_err = why;
+        return rc;
+    }
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) {
+        g_create_err = std::string("no CUDA device: ") + cudaGetErrorString(ce);
+        return SLPIC_ERR_CUDA;
+    }
+    int max_smem = 0, sms = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    {
+        int nn_ = cfg->bc == SLPIC_BC_PERIODIC ? cfg->n_cells : cfg->n_cells + 1;
+        // E (float) + deposit (int64) per node, plus the kernel's static shared memory
+        if ((size_t)nn_ * 12 + 1024 > (size_t)max_smem) {
+            g_create_err = "grid does not fit in shared memory (n_cells too large for the 1D kernel)";
+            return SLPIC_ERR_INVALID;
+        }
+    }
+    slpic_t *h = new slpic_sim();
+    h->cfg = *cfg;
+    h->device = dev;
+    h->num_sms = sms;
+    h->ns = cfg->n_species;
+    h->nn = cfg->bc == SLPIC_BC_PERIODIC ? cfg->n_cells : cfg->n_cells + 1;
+
+    auto bail = [&](int code, const std::string &msg) {
+        g_create_err = msg;
+        free_all(h);
+        delete h;
+        return code;
+    };
+#define CKC(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bail(e_ == cudaErrorMemoryAllocation ? SLPIC_ERR_OOM : SLPIC_ERR_CUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+    CKC(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+    const int nn = h->nn, ns = h->ns;
+    CKC(cudaMalloc(&h->d_state, sizeof(DevState)));
+    CKC(cudaMalloc(&h->d_acc, sizeof(unsigned long long) * 2 * ns * nn));
+    CKC(cudaMalloc(&h->d_E, sizeof(float) * nn));
+    CKC(cudaMalloc(&h->d_E64, sizeof(double) * nn));
+    CKC(cudaMalloc(&h->d_phi, sizeof(double) * nn));
+    CKC(cudaMalloc(&h->d_rho, sizeof(double) * nn));
+    CKC(cudaMalloc(&h->d_diag, sizeof(double) * 2 * kMaxSpecies));
+    CKC(cudaMalloc(&h->d_bad, sizeof(int)));
+    for (int s = 0; s < ns; ++s)
+        for (int b = 0; b < 2; ++b) {
+            CKC(cudaMalloc(&h->d_cell[s][b], sizeof(int32_t) * cfg->species[s].capacity));
+            CKC(cudaMalloc(&h->d_pv[s][b], sizeof(float4) * cfg->species[s].capacity));
+        }
+    CKC(cudaMemset(h->d_state, 0, sizeof(DevState)));
+    CKC(cudaMemset(h->d_acc, 0, sizeof(unsigned long long) * 2 * ns * nn));
+    CKC(cudaMemset(h->d_E, 0, sizeof(float) * nn));
+    CKC(cudaMemset(h->d_E64, 0, sizeof(double) * nn));
+    CKC(cudaMemset(h->d_phi, 0, sizeof(double) * nn));
+    CKC(cudaMemset(h->d_rho, 0, sizeof(double) * nn));
+    CKC(configure_kernels(nn));
+    int occ = 0;
+    CKC(particle_ctas_per_sm(nn, &occ));
+    if (occ < 1)
+        return bail(SLPIC_ERR_INVALID, "particle kernel cannot be resident (shared memory)");
+    // persistent grid: every SM holds `occ` particle CTAs, shared among species
+    h->ctas = std::max(1, sms * occ / ns);
+    h->small_ctas = std::max(1, sms * 2 / ns);
+
+    StepParams &p = h->p;
+    p.n_cells = cfg->n_cells;
+    p.nn = nn;
+    p.periodic = cfg->bc == SLPIC_BC_PERIODIC;
+    p.ns = ns;
+    p.dt = (float)cfg->dt;
+    p.dt_dx = (float)(cfg->dt / cfg->dx);
+    p.dx = cfg->dx;
+    p.dt64 = cfg->dt;
+    p.eps0 = cfg->eps0;
+    p.phi_lo = cfg->phi_lo;
+    p.phi_hi = cfg->phi_hi;
+    p.src_mode = cfg->src_mode;
+    p.src_ref = cfg->src_ref_species;
+    p.src_lo_cells = (float)cfg->src_lo_cells;
+    p.src_len_cells = (float)cfg->src_len_cells;
+    p.src_rate = cfg->src_rate;
+    p.seed = cfg->seed;
+    for (int s = 0; s < ns; ++s) {
+        const slpic_species &sp = cfg->species[s];
+        SpeciesDev &d = p.sp[s];
+        for (int b = 0; b < 2; ++b) {
+            d.cell[b] = h->d_cell[s][b];
+            d.pv[b] = h->d_pv[s][b];
+        }
+        d.capacity = sp.capacity;
+        d.qm = (float)(sp.q / sp.m);
+        d.v0 = sp.beta_kind == SLPIC_BETA_ONE ? INFINITY : (float)sp.v0;
+        d.vth_src = sp.T_src > 0 ? (float)std::sqrt(sp.T_src / sp.m) : 0.0f;
+        d.kind = sp.beta_kind;
+        d.qw_dx = sp.q * sp.w / cfg->dx;
+        d.w = sp.w;
+    }
+    p.acc = h->d_acc;
+    p.E = h->d_E;
+    p.E64 = h->d_E64;
+    p.phi = h->d_phi;
+    p.rho = h->d_rho;
+    p.st = h->d_state;
+#undef CKC
+    *out = h;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_destroy(slpic_t *h)
+{
+    if (!h)
+        return SLPIC_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return SLPIC_OK;
+}
+
+extern "C" const char *slpic_last_error(const slpic_t *h) { return h ? h->err.c_str() : ""; }
+
+extern "C" int slpic_set_stream(slpic_t *h, void *stream)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->stream = (cudaStream_t)stream;
+    return SLPIC_OK;
+}
+
+static int ensure_stage(slpic_t *h, size_t bytes)
+{
+    if (bytes <= h->stage_bytes)
+        return SLPIC_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(h->d_stage);
+    h->d_stage = nullptr;
+    h->stage_bytes = 0;
+    CK(h, cudaMalloc(&h->d_stage, bytes));
+    h->stage_bytes = bytes;
+    return SLPIC_OK;
+}
+
+static int read_state(slpic_t *h, DevState *st)
+{
+    CK(h, cudaMemcpyAsync(st, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return SLPIC_OK;
+}
+
+// Append n particles already on the device (cell, off, v in host layout).
+static int append_dev(slpic_t *h, int s, long long n, const int32_t *cell, const float *off,
+                      const float *v)
+{
+    DevState st;
+    int rc = read_state(h, &st);
+    if (rc)
+        return rc;
+    const int P = (int)(h->step & 1);
+    long long have = (long long)st.count[s][P];
+    if (have + n > h->cfg.species[s].capacity)
+        return fail(h, SLPIC_ERR_CAPACITY, "load exceeds the species capacity");
+    CK(h, cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->stream));
+    launch_validate(cell, off, v, n, h->cfg.n_cells, h->d_bad, h->stream);
+    CK(h, cudaGetLastError());
+    int bad = 0;
+    CK(h, cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (bad)
+        return fail(h, SLPIC_ERR_INVALID,
+                    "particle data out of range (cell not in [0,N), offset not in [0,1), or non-finite v)");
+    launch_pack(cell, off, v, n, h->d_cell[s][P] + have, h->d_pv[s][P] + have, h->stream);
+    CK(h, cudaGetLastError());
+    unsigned long long nc = (unsigned long long)(have + n);
+    CK(h, cudaMemcpyAsync(&h->d_state->count[s][P], &nc, sizeof(nc), cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->dirty = true;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_load_particles(slpic_t *h, int instance, int species, int64_t n,
+                                    const int32_t *cell, const float *offset, const float *v)
+{
+    int rc = check_handle(h, instance);
+    if (rc)
+        return rc;
+    if (species < 0 || species >= h->ns || n < 0 || (n > 0 && (!cell || !offset || !v)))
+        return fail(h, SLPIC_ERR_INVALID, "bad species, count or pointer");
+    if (n == 0)
+        return SLPIC_OK;
+    size_t bc = sizeof(int32_t) * n, bo = sizeof(float) * n, bv = sizeof(float) * 3 * n;
+    rc = ensure_stage(h, bc + bo + bv + 64);
+    if (rc)
+        return rc;
+    char *base = (char *)h->d_stage;
+    int32_t *dc = (int32_t *)base;
+    float *doff = (float *)(base + ((bc + 15) & ~size_t(15)));
+    float *dv = (float *)((char *)doff + ((bo + 15) & ~size_t(15)));
+    CK(h, cudaMemcpyAsync(dc, cell, bc, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(doff, offset, bo, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(dv, v, bv, cudaMemcpyHostToDevice, h->stream));
+    return append_dev(h, species, n, dc, doff, dv);
+}
+
+extern "C" int slpic_load_particles_dev(slpic_t *h, int instance, int species, int64_t n,
+                                        const int32_t *cell, const float *offset,
+                                        const float *v)
+{
+    int rc = check_handle(h, instance);
+    if (rc)
+        return rc;
+    if (species < 0 || species >= h->ns || n < 0 || (n > 0 && (!cell || !offset || !v)))
+        return fail(h, SLPIC_ERR_INVALID, "bad species, count or pointer");
+    if (n == 0)
+        return SLPIC_OK;
+    return append_dev(h, species, n, cell, offset, v);
+}
+
+extern "C" int slpic_load_particles_f64(slpic_t *h, int instance, int species, int64_t n,
+                                        const double *x, const double *v)
+{
+    int rc = check_handle(h, instance);
+    if (rc)
+        return rc;
+    if (species < 0 || species >= h->ns || n < 0 || (n > 0 && (!x || !v)))
+        return fail(h, SLPIC_ERR_INVALID, "bad species, count or pointer");
+    std::vector<int32_t> c(n);
+    std::vector<float> o(n), vf(3 * n);
+    const double L = h->cfg.dx * h->cfg.n_cells;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(x[i] >= 0.0 && x[i] < L))
+            return fail(h, SLPIC_ERR_INVALID, "x outside [0, L)");
+        double xi = x[i] / h->cfg.dx;
+        double cf = std::floor(xi);
+        int ci = (int)cf;
+        float of = (float)(xi - cf);
+        if (of >= 1.0f) {
+            of = 0.0f;
+            ci += 1;
+        }
+        if (ci >= h->cfg.n_cells) {
+            ci = h->cfg.n_cells - 1;
+            of = std::nextafter(1.0f, 0.0f);
+        }
+        c[i] = ci;
+        o[i] = of;
+        for (int k = 0; k < 3; ++k)
+            vf[3 * i + k] = (float)v[3 * i + k];
+    }
+    return slpic_load_particles(h, instance, species, n, c.data(), o.data(), vf.data());
+}
+
+extern "C" int slpic_prepare(slpic_t *h)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    const int P = (int)(h->step & 1);
+    CK(h, cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * 2 * h->ns * h->nn, h->stream));
+    for (int s = 0; s < h->ns; ++s)
+        CK(h, cudaMemsetAsync(&h->d_state->count[s][P ^ 1], 0, sizeof(unsigned long long),
+                              h->stream));
+    launch_deposit(h->p, h->small_ctas, h->stream);
+    CK(h, cudaGetLastError());
+    launch_field(h->p, 0, h->stream);
+    CK(h, cudaGetLastError());
+    h->dirty = false;
+    return SLPIC_OK;
+}
+
+static int capture(slpic_t *h, int nsteps, bool timed, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    cudaEvent_t ev[3] = {};
+    if (timed)
+        for (int i = 0; i < 3; ++i)
+            CK(h, cudaEventCreate(&ev[i]));
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < nsteps; ++k) {
+        // "external" records become event-record nodes of the graph (a plain
+        // record inside a capture only orders streams)
+        if (timed)
+            cudaEventRecordWithFlags(ev[0], h->cap_stream, cudaEventRecordExternal);
+        launch_particles(h->p, h->ctas, h->cap_stream);
+        if (timed)
+            cudaEventRecordWithFlags(ev[1], h->cap_stream, cudaEventRecordExternal);
+        launch_field(h->p, 1, h->cap_stream);
+        if (timed)
+            cudaEventRecordWithFlags(ev[2], h->cap_stream, cudaEventRecordExternal);
+    }
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess) {
+        h->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        return SLPIC_ERR_CUDA;
+    }
+    CK(h, cudaGraphInstantiate(out, g, 0));
+    if (timed) {
+        size_t nnodes = 0;
+        CK(h, cudaGraphGetNodes(g, nullptr, &nnodes));
+        std::vector<cudaGraphNode_t> nodes(nnodes);
+        CK(h, cudaGraphGetNodes(g, nodes.data(), &nnodes));
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            CK(h, cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeEventRecord)
+                continue;
+            cudaEvent_t e2;
+            CK(h, cudaGraphEventRecordNodeGetEvent(nd, &e2));
+            for (int i = 0; i < 3; ++i)
+                if (e2 == ev[i])
+                    h->ev_node[i] = nd;
+        }
+        for (int i = 0; i < 3; ++i)
+            if (!h->ev_node[i]) {
+                h->err = "timed graph: event-record node not found";
+                return SLPIC_ERR_CUDA;
+            }
+        for (int i = 0; i < 3; ++i)
+            cudaEventDestroy(ev[i]);
+        h->gt_graph = g;  // node handles stay valid only while the graph exists
+        return SLPIC_OK;
+    }
+    cudaGraphDestroy(g);
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_step(slpic_t *h, int64_t nsteps)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (nsteps < 0)
+        return fail(h, SLPIC_ERR_INVALID, "nsteps < 0");
+    if (h->dirty && (rc = slpic_prepare(h)))
+        return rc;
+    if (nsteps == 0)
+        return SLPIC_OK;
+    if (h->t_max > 0) {
+        if (!h->gt && (rc = capture(h, 1, true, &h->gt)))
+            return rc;
+        for (int64_t i = 0; i < nsteps; ++i) {
+            if (h->t_used < h->t_max) {
+                for (int k = 0; k < 3; ++k)
+                    CK(h, cudaGraphExecEventRecordNodeSetEvent(h->gt, h->ev_node[k],
+                                                               h->events[3 * h->t_used + k]));
+                h->t_used++;
+                CK(h, cudaGraphLaunch(h->gt, h->stream));
+            } else {
+                if (!h->g1 && (rc = capture(h, 1, false, &h->g1)))
+                    return rc;
+                CK(h, cudaGraphLaunch(h->g1, h->stream));
+            }
+        }
+        h->step += nsteps;
+        return SLPIC_OK;
+    }
+    if (!h->g1 && (rc = capture(h, 1, false, &h->g1)))
+        return rc;
+    if (nsteps >= h->K && !h->gK && (rc = capture(h, h->K, false, &h->gK)))
+        return rc;
+    int64_t left = nsteps;
+    while (left >= h->K) {
+        CK(h, cudaGraphLaunch(h->gK, h->stream));
+        left -= h->K;
+    }
+    while (left-- > 0)
+        CK(h, cudaGraphLaunch(h->g1, h->stream));
+    h->step += nsteps;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_synchronize(slpic_t *h)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    int e = 0;
+    CK(h, cudaMemcpy(&e, &h->d_state->error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        int zero = 0;
+        CK(h, cudaMemcpy(&h->d_state->error, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        return fail(h, e, e == SLPIC_ERR_CAPACITY ? "particle store full: injection truncated"
+                                                  : "device error");
+    }
+    return SLPIC_OK;
+}
+
+static int sync_prepared(slpic_t *h, int instance)
+{
+    int rc = check_handle(h, instance);
+    if (rc)
+        return rc;
+    if (h->dirty && (rc = slpic_prepare(h)))
+        return rc;
+    return slpic_synchronize(h);
+}
+
+extern "C" int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, float *E)
+{
+    int rc = sync_prepared(h, instance);
+    if (rc)
+        return rc;
+    if (rho)
+        CK(h, cudaMemcpy(rho, h->d_rho, sizeof(double) * h->nn, cudaMemcpyDeviceToHost));
+    if (phi)
+        CK(h, cudaMemcpy(phi, h->d_phi, sizeof(double) * h->nn, cudaMemcpyDeviceToHost));
+    if (E)
+        CK(h, cudaMemcpy(E, h->d_E, sizeof(float) * h->nn, cudaMemcpyDeviceToHost));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_charge_raw(slpic_t *h, int instance, int species, int64_t *acc)
+{
+    int rc = sync_prepared(h, instance);
+    if (rc)
+        return rc;
+    if (species < 0 || species >= h->ns || !acc)
+        return fail(h, SLPIC_ERR_INVALID, "bad species or pointer");
+    const int P = (int)(h->step & 1);
+    CK(h, cudaMemcpy(acc, h->d_acc + ((size_t)P * h->ns + species) * h->nn,
+                     sizeof(int64_t) * h->nn, cudaMemcpyDeviceToHost));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_density(slpic_t *h, int instance, int species, double *n)
+{
+    if (!n)
+        return h ? fail(h, SLPIC_ERR_INVALID, "n is NULL") : SLPIC_ERR_INVALID;
+    std::vector<int64_t> acc(h ? h->nn : 0);
+    int rc = slpic_charge_raw(h, instance, species, acc.data());
+    if (rc)
+        return rc;
+    const double f = h->cfg.species[species].w / h->cfg.dx / 1099511627776.0;
+    for (int j = 0; j < h->nn; ++j)
+        n[j] = (double)acc[j] * f;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_particle_count(slpic_t *h, int instance, int species, int64_t *n)
+{
+    int rc = sync_prepared(h, instance);
+    if (rc)
+        return rc;
+    if (species < 0 || species >= h->ns || !n)
+        return fail(h, SLPIC_ERR_INVALID, "bad species or pointer");
+    DevState st;
+    if ((rc = read_state(h, &st)))
+        return rc;
+    *n = (int64_t)st.count[species][h->step & 1];
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_get_particles(slpic_t *h, int instance, int species, int64_t cap,
+                                   int32_t *cell, float *offset, float *v, int64_t *n_out)
+{
+    int64_t n = 0;
+    int rc = slpic_particle_count(h, instance, species, &n);
+    if (rc)
+        return rc;
+    if (cap < 0 || (cap > 0 && (!cell || !offset || !v)))
+        return fail(h, SLPIC_ERR_INVALID, "bad cap or pointer");
+    if (n > cap)
+        n = cap;
+    if (n_out)
+        *n_out = n;
+    if (n == 0)
+        return SLPIC_OK;
+    size_t bc = sizeof(int32_t) * n, bo = sizeof(float) * n, bv = sizeof(float) * 3 * n;
+    if ((rc = ensure_stage(h, bc + bo + bv + 64)))
+        return rc;
+    char *base = (char *)h->d_stage;
+    int32_t *dc = (int32_t *)base;
+    float *doff = (float *)(base + ((bc + 15) & ~size_t(15)));
+    float *dv = (float *)((char *)doff + ((bo + 15) & ~size_t(15)));
+    const int P = (int)(h->step & 1);
+    launch_unpack(h->d_cell[species][P], h->d_pv[species][P], n, dc, doff, dv, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(cell, dc, bc, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(offset, doff, bo, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(v, dv, bv, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_diagnostics(slpic_t *h, int instance, slpic_diag *out)
+{
+    int rc = sync_prepared(h, instance);
+    if (rc)
+        return rc;
+    if (!out)
+        return fail(h, SLPIC_ERR_INVALID, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    CK(h, cudaMemsetAsync(h->d_diag, 0, sizeof(double) * 2 * kMaxSpecies, h->stream));
+    launch_diag(h->p, h->d_diag, h->small_ctas, h->stream);
+    CK(h, cudaGetLastError());
+    double red[2 * kMaxSpecies];
+    CK(h, cudaMemcpyAsync(red, h->d_diag, sizeof(red), cudaMemcpyDeviceToHost, h->stream));
+    DevState st;
+    if ((rc = read_state(h, &st)))
+        return rc;
+    std::vector<double> E(h->nn);
+    CK(h, cudaMemcpy(E.data(), h->d_E64, sizeof(double) * h->nn, cudaMemcpyDeviceToHost));
+    const int P = (int)(h->step & 1);
+    out->step = st.step;
+    out->time = (double)st.step * h->cfg.dt;
+    for (int s = 0; s < h->ns; ++s) {
+        const slpic_species &sp = h->cfg.species[s];
+        out->count[s] = (int64_t)st.count[s][P];
+        out->sum_w[s] = sp.w * (double)st.count[s][P];
+        out->sum_wbeta[s] = sp.w * red[2 * s];
+        out->kinetic[s] = 0.5 * sp.m * sp.w * red[2 * s + 1];
+        out->absorbed[s][0] = st.absorbed_total[s][0];
+        out->absorbed[s][1] = st.absorbed_total[s][1];
+        out->injected[s] = st.injected_total[s];
+    }
+    double fe = 0.0;
+    for (int j = 0; j < h->nn; ++j) {
+        double wgt = (!h->p.periodic && (j == 0 || j == h->nn - 1)) ? 0.5 : 1.0;
+        fe += wgt * E[j] * E[j];
+    }
+    out->field_energy = 0.5 * h->cfg.eps0 * h->cfg.dx * fe;
+    return SLPIC_OK;
+}
+
+// ---- checkpoint -------------------------------------------------------------------
+namespace {
+struct SaveHeader {
+    char magic[8];
+    int32_t version, ns, nn, pad;
+    int64_t step;
+    int64_t count[kMaxSpecies];
+};
+}  // namespace
+
+extern "C" int slpic_save(slpic_t *h, void *buf, size_t *size)
+{
+    int rc = sync_prepared(h, 0);
+    if (rc)
+        return rc;
+    if (!size)
+        return fail(h, SLPIC_ERR_INVALID, "size is NULL");
+    DevState st;
+    if ((rc = read_state(h, &st)))
+        return rc;
+    const int P = (int)(h->step & 1);
+    size_t need = sizeof(SaveHeader) + sizeof(DevState) +
+                  sizeof(unsigned long long) * 2 * h->ns * h->nn + sizeof(float) * h->nn +
+                  3 * sizeof(double) * h->nn;
+    for (int s = 0; s < h->ns; ++s)
+        need += st.count[s][P] * (sizeof(int32_t) + sizeof(float4));
+    if (!buf) {
+        *size = need;
+        return SLPIC_OK;
+    }
+    if (*size < need)
+        return fail(h, SLPIC_ERR_INVALID, "buffer too small");
+    char *o = (char *)buf;
+    SaveHeader hd{};
+    std::memcpy(hd.magic, "SLPIC1D", 8);
+    hd.version = 1;
+    hd.ns = h->ns;
+    hd.nn = h->nn;
+    hd.step = h->step;
+    for (int s = 0; s < h->ns; ++s)
+        hd.count[s] = (int64_t)st.count[s][P];
+    std::memcpy(o, &hd, sizeof(hd));
+    o += sizeof(hd);
+    std::memcpy(o, &st, sizeof(st));
+    o += sizeof(st);
+    auto d2h = [&](const void *src, size_t b) -> int {
+        CK(h, cudaMemcpy(o, src, b, cudaMemcpyDeviceToHost));
+        o += b;
+        return SLPIC_OK;
+    };
+    if ((rc = d2h(h->d_acc, sizeof(unsigned long long) * 2 * h->ns * h->nn)) ||
+        (rc = d2h(h->d_E, sizeof(float) * h->nn)) || (rc = d2h(h->d_E64, sizeof(double) * h->nn)) ||
+        (rc = d2h(h->d_phi, sizeof(double) * h->nn)) || (rc = d2h(h->d_rho, sizeof(double) * h->nn)))
+        return rc;
+    for (int s = 0; s < h->ns; ++s) {
+        size_t n = st.count[s][P];
+        if ((rc = d2h(h->d_cell[s][P], sizeof(int32_t) * n)) ||
+            (rc = d2h(h->d_pv[s][P], sizeof(float4) * n)))
+            return rc;
+    }
+    *size = need;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_restore(slpic_t *h, const void *buf, size_t size)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (!buf || size < sizeof(SaveHeader) + sizeof(DevState))
+        return fail(h, SLPIC_ERR_INVALID, "buffer too small");
+    const char *i = (const char *)buf;
+    SaveHeader hd;
+    std::memcpy(&hd, i, sizeof(hd));
+    i += sizeof(hd);
+    if (std::memcmp(hd.magic, "SLPIC1D", 8) != 0 || hd.version != 1 || hd.ns != h->ns ||
+        hd.nn != h->nn)
+        return fail(h, SLPIC_ERR_INVALID, "checkpoint does not match this configuration");
+    for (int s = 0; s < h->ns; ++s)
+        if (hd.count[s] > h->cfg.species[s].capacity)
+            return fail(h, SLPIC_ERR_CAPACITY, "checkpoint exceeds the species capacity");
+    CK(h, cudaStreamSynchronize(h->stream));
+    DevState st;
+    std::memcpy(&st, i, sizeof(st));
+    i += sizeof(st);
+    const int P = (int)(hd.step & 1);
+    auto h2d = [&](void *dst, size_t b) -> int {
+        CK(h, cudaMemcpy(dst, i, b, cudaMemcpyHostToDevice));
+        i += b;
+        return SLPIC_OK;
+    };
+    CK(h, cudaMemcpy(h->d_state, &st, sizeof(st), cudaMemcpyHostToDevice));
+    if ((rc = h2d(h->d_acc, sizeof(unsigned long long) * 2 * h->ns * h->nn)) ||
+        (rc = h2d(h->d_E, sizeof(float) * h->nn)) || (rc = h2d(h->d_E64, sizeof(double) * h->nn)) ||
+        (rc = h2d(h->d_phi, sizeof(double) * h->nn)) || (rc = h2d(h->d_rho, sizeof(double) * h->nn)))
+        return rc;
+    for (int s = 0; s < h->ns; ++s) {
+        size_t n = (size_t)hd.count[s];
+        if ((rc = h2d(h->d_cell[s][P], sizeof(int32_t) * n)) ||
+            (rc = h2d(h->d_pv[s][P], sizeof(float4) * n)))
+            return rc;
+    }
+    h->step = hd.step;
+    h->dirty = false;
+    return SLPIC_OK;
+}
+
+// ---- timing ----------------------------------------------------------------------
+extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t max_steps)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (max_steps < 0)
+        return fail(h, SLPIC_ERR_INVALID, "max_steps < 0");
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (cudaEvent_t e : h->events)
+        cudaEventDestroy(e);
+    h->events.clear();
+    h->t_used = 0;
+    h->t_max = max_steps;
+    h->events.resize(3 * max_steps);
+    for (auto &e : h->events)
+        CK(h, cudaEventCreate(&e));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_kernel_times(slpic_t *h, double *particle_ms, double *field_ms,
+                                  int64_t *steps)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    double a = 0.0, b = 0.0;
+    for (long long k = 0; k < h->t_used; ++k) {
+        float x = 0.f, y = 0.f;
+        CK(h, cudaEventElapsedTime(&x, h->events[3 * k], h->events[3 * k + 1]));
+        CK(h, cudaEventElapsedTime(&y, h->events[3 * k + 1], h->events[3 * k + 2]));
+        a += x;
+        b += y;
+    }
+    long long n = h->t_used;
+    if (particle_ms)
+        *particle_ms = n ? a / n : 0.0;
+    if (field_ms)
+        *field_ms = n ? b / n : 0.0;
+    if (steps)
+        *steps = n;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_kernels_per_step(slpic_t *h, int *n)
+{
+    if (!h || !n)
+        return SLPIC_ERR_INVALID;
+    *n = 2;
+    return SLPIC_OK;
+}

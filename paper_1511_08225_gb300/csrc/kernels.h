@@ -1,0 +1,31 @@
+// kernels.h -- host-side launchers of the SLPIC kernels (kernels.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "slpic_internal.cuh"
+
+namespace slpic {
+
+constexpr int kParticleThreads = 256;
+constexpr int kFieldThreads = 1024;
+
+size_t particle_smem_bytes(int nn);
+size_t field_smem_bytes(int nn);
+cudaError_t configure_kernels(int nn);
+cudaError_t particle_ctas_per_sm(int nn, int *out);
+
+void launch_particles(const StepParams &p, int ctas_per_species, cudaStream_t st);
+void launch_field(const StepParams &p, int mode, cudaStream_t st);
+void launch_deposit(const StepParams &p, int ctas_per_species, cudaStream_t st);
+void launch_diag(const StepParams &p, double *out, int ctas_per_species, cudaStream_t st);
+void launch_validate(const int32_t *cell, const float *off, const float *v, long long n,
+                     int n_cells, int *bad, cudaStream_t st);
+void launch_pack(const int32_t *cell, const float *off, const float *v, long long n,
+                 int32_t *cdst, float4 *pdst, cudaStream_t st);
+void launch_unpack(const int32_t *csrc, const float4 *psrc, long long n, int32_t *cell,
+                   float *off, float *v, cudaStream_t st);
+
+}  // namespace slpic

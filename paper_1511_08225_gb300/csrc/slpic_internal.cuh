@@ -1,0 +1,79 @@
+// slpic_internal.cuh -- device data layout shared by the kernels and the C ABI.
+//
+// Particle store (per species, ping-pong buffer b = 0/1):
+//   cell[b][i]  int32   cell index c (0 <= c < N)
+//   pv[b][i]    float4  {offset in [0,1), vx, vy, vz}
+// 20 bytes per macroparticle, structure-of-arrays so that one warp reads 512
+// contiguous bytes of float4 and 128 bytes of int32 per access.  The live
+// particles of time level n sit in buffer (n & 1); the particle kernel of step
+// n reads buffer (n & 1) and writes the survivors, compacted, to buffer
+// ((n+1) & 1).
+//
+// Charge deposit: int64 fixed point, 2 time levels x species x nodes; the
+// deposit of rho^n is acc[(n & 1)][s][j].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "slpic.h"
+
+namespace slpic {
+
+constexpr int kMaxSpecies = SLPIC_MAX_SPECIES;
+
+// Counters and bookkeeping that live on the device, so that a captured CUDA
+// graph can run many steps with no host round trip.
+struct DevState {
+    long long step;                                // time level n of the current particles
+    unsigned long long count[kMaxSpecies][2];      // live particles per buffer
+    unsigned long long absorbed_step[kMaxSpecies][2];  // absorbed this step, per wall
+    long long absorbed_total[kMaxSpecies][2];
+    long long injected_total[kMaxSpecies];
+    double src_frac[kMaxSpecies];                  // fractional macroparticles carried over
+    int error;                                     // first SLPIC_ERR_* raised on the device
+    int pad;
+};
+
+struct SpeciesDev {
+    int32_t *cell[2];
+    float4 *pv[2];
+    long long capacity;
+    float qm;        // q/m
+    float v0;        // speed limit
+    float vth_src;   // sqrt(T_src/m) of the source Maxwellian (0 = not injected)
+    int kind;        // SLPIC_BETA_*
+    double qw_dx;    // q * w / dx: charge density of one unit of deposit
+    double w;        // g-weight
+};
+
+// Everything a kernel needs, passed by value (fixed at graph capture; the
+// time level is read from DevState at run time).
+struct StepParams {
+    int n_cells;
+    int nn;           // nodes: N+1 (Dirichlet) or N (periodic)
+    int periodic;
+    int ns;
+    float dt;
+    float dt_dx;      // dt / dx
+    double dx;
+    double dt64;
+    double eps0;
+    double phi_lo, phi_hi;
+    // source
+    int src_mode;
+    int src_ref;
+    float src_lo_cells;
+    float src_len_cells;
+    double src_rate;
+    unsigned long long seed;
+    SpeciesDev sp[kMaxSpecies];
+    unsigned long long *acc;  // [2][ns][nn]
+    float *E;                 // [nn]  FP32 copy gathered by the particle kernel
+    double *E64;              // [nn]
+    double *phi;              // [nn]
+    double *rho;              // [nn]
+    DevState *st;
+};
+
+}  // namespace slpic

@@ -1,0 +1,97 @@
+"""The C ABI without a GPU: the library builds, loads, exports every function
+declared in include/slpic.h, and the ctypes structures match the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1511_08225_gb300 import binding
+from paper_1511_08225_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "slpic.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(slpic_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return ctypes.CDLL(binding.LIB_PATH)
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.EXPORTS) == names
+
+
+def test_binding_loads_and_sets_signatures(lib):
+    L = binding.load_library()
+    assert L.slpic_step.argtypes is not None
+
+
+def test_struct_layout_matches_c(tmp_path):
+    """Compile a host program against slpic.h and compare sizeof/offsetof
+    with the ctypes mirror (a silent mismatch would scramble the config)."""
+    prog = tmp_path / "layout.c"
+    fields_cfg = [f for f, _ in binding.slpic_config._fields_]
+    fields_sp = [f for f, _ in binding.slpic_species._fields_]
+    fields_dg = [f for f, _ in binding.slpic_diag._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slpic.h"', 'int main(void){']
+    for st, fl in (("slpic_config", fields_cfg), ("slpic_species", fields_sp),
+                   ("slpic_diag", fields_dg)):
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fl:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0;}")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    for line in out:
+        if not line.strip():
+            continue
+        parts = line.split()
+        cls = getattr(binding, parts[0])
+        if parts[1] == "size":
+            assert ctypes.sizeof(cls) == int(parts[2]), line
+        else:
+            assert getattr(cls, parts[1]).offset == int(parts[2]), line
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    """With no device, slpic_create returns an error code and a message
+    instead of crashing (on a GPU machine this test is skipped)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1511_08225_gb300 import inputs
+    cfg = binding.config_from_problem(inputs.periodic_problem(n_cells=16, ppc=2))
+    with pytest.raises(binding.SlpicError) as ei:
+        binding.slpic_create(cfg)
+    assert ei.value.code == binding.SLPIC_ERR_CUDA
+
+
+def test_config_errors_need_no_device(lib):
+    """Config validation runs before any device call: CFL violations and bad
+    source bands are refused with their own codes on any machine."""
+    from paper_1511_08225_gb300 import inputs
+    prob = inputs.sheath_problem(n_cells=64, ppc=2, v0=0.1)
+    prob["dt"] = 2 * prob["dx"] / 0.1
+    with pytest.raises(binding.SlpicError) as ei:
+        binding.slpic_create(binding.config_from_problem(prob))
+    assert ei.value.code == binding.SLPIC_ERR_CFL
+    prob = inputs.sheath_problem(n_cells=64, ppc=2, v0=0.1)
+    prob["source"]["len_cells"] = 64.0
+    with pytest.raises(binding.SlpicError) as ei:
+        binding.slpic_create(binding.config_from_problem(prob))
+    assert ei.value.code == binding.SLPIC_ERR_INVALID
