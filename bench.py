@@ -144,20 +144,27 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_particles_sheath4096.md")
+
+
 def profiled_traffic(n_particles):
     """DRAM bytes per launch of the particle kernel from the committed ncu
-    summary, scaled to this launch's particle count; None if the kernel source
-    changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "k_particles_sheath.json")
-    if not os.path.exists(p):
+    summary (its `key: value` lines), scaled to this launch's particle count;
+    None if the summary is missing or the kernel source changed since."""
+    if not os.path.exists(PROFILE_SUMMARY):
         return None
+    kv = {}
+    for line in open(PROFILE_SUMMARY):
+        line = line.strip().lstrip("-").strip()
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip().strip("`")] = v.strip().strip("`")
     try:
-        d = json.load(open(p))
-    except ValueError:
+        if kv.get("source_hash") != kernel_source_hash():
+            return None
+        per_particle = float(kv["dram_bytes_per_launch"]) / float(kv["particles_per_launch"])
+    except (KeyError, ValueError):
         return None
-    if d.get("source_hash") != kernel_source_hash():
-        return None
-    per_particle = d["dram_bytes_per_launch"] / d["particles_per_launch"]
     return per_particle * n_particles
 
 
@@ -277,7 +284,8 @@ def run_gpu(args):
     sim.step(args.warmup)
     sim.synchronize()
     n0 = live()
-    binding.slpic_enable_kernel_timing(sim.h, args.steps)
+    timed_len = max(1, min(args.steps, 256))
+    binding.slpic_enable_kernel_timing(sim.h, timed_len)
     barrier()
     clocks.mark(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -44,11 +44,10 @@ struct slpic_sim {
 
     cudaGraphExec_t g1 = nullptr, gK = nullptr;
     int K = 8;
-    cudaGraphExec_t gt = nullptr;  // timed one-step graph
-    cudaGraph_t gt_graph = nullptr; // kept alive: its event nodes are retargeted per launch
-    cudaGraphNode_t ev_node[3] = {};
-    std::vector<cudaEvent_t> events;
-    long long t_max = 0, t_used = 0;
+    cudaGraphExec_t gt = nullptr;   // timed graph: t_len steps with their own events
+    std::vector<cudaEvent_t> events; // 3 per step of the timed graph
+    long long t_len = 0;             // steps per timed graph (0 = timing off)
+    long long t_launched = 0;        // timed-graph launches since timing was enabled
 
     std::string err;
 };
@@ -169,8 +168,6 @@ static void free_all(slpic_t *h)
         cudaGraphExecDestroy(h->gK);
     if (h->gt)
         cudaGraphExecDestroy(h->gt);
-    if (h->gt_graph)
-        cudaGraphDestroy(h->gt_graph);
     for (cudaEvent_t e : h->events)
         cudaEventDestroy(e);
     cudaFree(h->d_state);
@@ -486,59 +483,33 @@ extern "C" int slpic_prepare(slpic_t *h)
     return SLPIC_OK;
 }
 
+// Capture nsteps timesteps into a graph.  With `timed`, event-record nodes
+// (3 per step, from h->events) bracket the particle and field kernels; every
+// replay re-records them, so the events describe the most recent replay.
 static int capture(slpic_t *h, int nsteps, bool timed, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
-    cudaEvent_t ev[3] = {};
-    if (timed)
-        for (int i = 0; i < 3; ++i)
-            CK(h, cudaEventCreate(&ev[i]));
     CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < nsteps; ++k) {
         // "external" records become event-record nodes of the graph (a plain
         // record inside a capture only orders streams)
         if (timed)
-            cudaEventRecordWithFlags(ev[0], h->cap_stream, cudaEventRecordExternal);
+            cudaEventRecordWithFlags(h->events[3 * k], h->cap_stream, cudaEventRecordExternal);
         launch_particles(h->p, h->ctas, h->cap_stream);
         if (timed)
-            cudaEventRecordWithFlags(ev[1], h->cap_stream, cudaEventRecordExternal);
+            cudaEventRecordWithFlags(h->events[3 * k + 1], h->cap_stream, cudaEventRecordExternal);
         launch_field(h->p, 1, h->cap_stream);
         if (timed)
-            cudaEventRecordWithFlags(ev[2], h->cap_stream, cudaEventRecordExternal);
+            cudaEventRecordWithFlags(h->events[3 * k + 2], h->cap_stream, cudaEventRecordExternal);
     }
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) {
         h->err = std::string("graph capture: ") + cudaGetErrorString(e);
         return SLPIC_ERR_CUDA;
     }
-    CK(h, cudaGraphInstantiate(out, g, 0));
-    if (timed) {
-        size_t nnodes = 0;
-        CK(h, cudaGraphGetNodes(g, nullptr, &nnodes));
-        std::vector<cudaGraphNode_t> nodes(nnodes);
-        CK(h, cudaGraphGetNodes(g, nodes.data(), &nnodes));
-        for (cudaGraphNode_t nd : nodes) {
-            cudaGraphNodeType t;
-            CK(h, cudaGraphNodeGetType(nd, &t));
-            if (t != cudaGraphNodeTypeEventRecord)
-                continue;
-            cudaEvent_t e2;
-            CK(h, cudaGraphEventRecordNodeGetEvent(nd, &e2));
-            for (int i = 0; i < 3; ++i)
-                if (e2 == ev[i])
-                    h->ev_node[i] = nd;
-        }
-        for (int i = 0; i < 3; ++i)
-            if (!h->ev_node[i]) {
-                h->err = "timed graph: event-record node not found";
-                return SLPIC_ERR_CUDA;
-            }
-        for (int i = 0; i < 3; ++i)
-            cudaEventDestroy(ev[i]);
-        h->gt_graph = g;  // node handles stay valid only while the graph exists
-        return SLPIC_OK;
-    }
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
+    CK(h, e);
     return SLPIC_OK;
 }
 
@@ -553,27 +524,22 @@ extern "C" int slpic_step(slpic_t *h, int64_t nsteps)
         return rc;
     if (nsteps == 0)
         return SLPIC_OK;
-    if (h->t_max > 0) {
-        if (!h->gt && (rc = capture(h, 1, true, &h->gt)))
+    if (!h->g1 && (rc = capture(h, 1, false, &h->g1)))
+        return rc;
+    if (h->t_len > 0) {
+        if (!h->gt && (rc = capture(h, (int)h->t_len, true, &h->gt)))
             return rc;
-        for (int64_t i = 0; i < nsteps; ++i) {
-            if (h->t_used < h->t_max) {
-                for (int k = 0; k < 3; ++k)
-                    CK(h, cudaGraphExecEventRecordNodeSetEvent(h->gt, h->ev_node[k],
-                                                               h->events[3 * h->t_used + k]));
-                h->t_used++;
-                CK(h, cudaGraphLaunch(h->gt, h->stream));
-            } else {
-                if (!h->g1 && (rc = capture(h, 1, false, &h->g1)))
-                    return rc;
-                CK(h, cudaGraphLaunch(h->g1, h->stream));
-            }
+        int64_t left = nsteps;
+        while (left >= h->t_len) {
+            CK(h, cudaGraphLaunch(h->gt, h->stream));
+            h->t_launched++;
+            left -= h->t_len;
         }
+        while (left-- > 0)
+            CK(h, cudaGraphLaunch(h->g1, h->stream));
         h->step += nsteps;
         return SLPIC_OK;
     }
-    if (!h->g1 && (rc = capture(h, 1, false, &h->g1)))
-        return rc;
     if (nsteps >= h->K && !h->gK && (rc = capture(h, h->K, false, &h->gK)))
         return rc;
     int64_t left = nsteps;
@@ -849,20 +815,24 @@ extern "C" int slpic_restore(slpic_t *h, const void *buf, size_t size)
 }
 
 // ---- timing ----------------------------------------------------------------------
-extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t max_steps)
+extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
 {
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
-    if (max_steps < 0)
-        return fail(h, SLPIC_ERR_INVALID, "max_steps < 0");
+    if (steps_per_graph < 0 || steps_per_graph > 4096)
+        return fail(h, SLPIC_ERR_INVALID, "steps_per_graph must be in 0..4096");
     CK(h, cudaStreamSynchronize(h->stream));
+    if (h->gt) {
+        cudaGraphExecDestroy(h->gt);
+        h->gt = nullptr;
+    }
     for (cudaEvent_t e : h->events)
         cudaEventDestroy(e);
     h->events.clear();
-    h->t_used = 0;
-    h->t_max = max_steps;
-    h->events.resize(3 * max_steps);
+    h->t_launched = 0;
+    h->t_len = steps_per_graph;
+    h->events.resize(3 * steps_per_graph);
     for (auto &e : h->events)
         CK(h, cudaEventCreate(&e));
     return SLPIC_OK;
@@ -876,14 +846,14 @@ extern "C" int slpic_kernel_times(slpic_t *h, double *particle_ms, double *field
         return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     double a = 0.0, b = 0.0;
-    for (long long k = 0; k < h->t_used; ++k) {
+    long long n = h->t_launched > 0 ? h->t_len : 0;
+    for (long long k = 0; k < n; ++k) {
         float x = 0.f, y = 0.f;
         CK(h, cudaEventElapsedTime(&x, h->events[3 * k], h->events[3 * k + 1]));
         CK(h, cudaEventElapsedTime(&y, h->events[3 * k + 1], h->events[3 * k + 2]));
         a += x;
         b += y;
     }
-    long long n = h->t_used;
     if (particle_ms)
         *particle_ms = n ? a / n : 0.0;
     if (field_ms)
