@@ -225,18 +225,56 @@ int slpic_restore(slpic_t *h, const void *buf, size_t size);
 
 /* ---- timing --------------------------------------------------------------- */
 
-/* Record CUDA events around the particle kernel and the field/source kernel
- * of every step enqueued by slpic_step from now on (up to max_steps steps;
- * 0 turns timing off).  The events are recorded on the handle's stream, the
- * stream the kernels run on. */
-int slpic_enable_kernel_timing(slpic_t *h, int64_t max_steps);
+/* From now on slpic_step runs its steps as graphs of `steps_per_graph` steps
+ * (1..4096; 0 turns timing off) in which CUDA events bracket the particle
+ * kernel and the field/source kernel of every step.  The events are recorded
+ * on the handle's stream, the stream the kernels run on; each graph replay
+ * re-records them.  Steps beyond a multiple of steps_per_graph run untimed. */
+int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph);
 
 /* Mean device time (ms) of the particle kernel and of the field/source kernel
- * over the steps recorded since slpic_enable_kernel_timing; synchronising. */
+ * over the steps of the most recent timed graph replay (*steps of them; 0 if
+ * none ran); synchronising. */
 int slpic_kernel_times(slpic_t *h, double *particle_ms, double *field_ms, int64_t *steps);
 
 /* Number of kernels one slpic_step(h, 1) launches. */
 int slpic_kernels_per_step(slpic_t *h, int *n);
+
+/* ---- allocation-free particle step ------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory: code running inside another framework's step
+ * loop whose memory pool owns the device, services that reserve all memory at
+ * start-up, and loops that cannot afford the device synchronisation that
+ * cudaMalloc/cudaFree may cause.  It needs no handle and calls no allocator.
+ *
+ * One particle step of one species of *cfg (gather, push, move, walls, deposit,
+ * compaction: the same per-particle arithmetic as slpic_step's particle kernel),
+ * on device arrays owned by the caller, on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream):
+ *   cell_in[n] (int32), state_in[4n] (float32 {offset, vx, vy, vz} per particle,
+ *   16-byte aligned): the particles at time level n;
+ *   E[nodes] (float32): the nodal field they gather;
+ *   cell_out[n], state_out[4n]: receive the survivors, compacted (order not kept);
+ *   charge_out[nodes] (int64, device): receives the fixed-point deposit of the
+ *   survivors, the rule of slpic_charge_raw (overwritten, not accumulated);
+ *   *n_out (host): survivors; absorbed[2] (host): losses at x=0 and x=L.
+ * nodes = n_cells + 1 (Dirichlet) or n_cells (periodic).  The call waits for its
+ * work on `stream` to finish before it returns.
+ *
+ * Its only scratch (three counters and the int64 accumulator) is a fixed array in
+ * device memory that every GPU loading the library holds until exit; grids of
+ * more than 16384 nodes return SLPIC_ERR_CAPACITY.  The first call on a device
+ * looks up that array's device address (and sets the kernel's shared-memory
+ * limit); make the first call before any stream capture.  All calls share the
+ * array; each call clears what it uses, so calls that overlap on the GPU
+ * (concurrent streams or threads) race and must be serialised by the caller.
+ * Returns SLPIC_ERR_INVALID for bad arguments or misaligned state arrays,
+ * SLPIC_ERR_CFL if dt * v0 > dx, SLPIC_ERR_CUDA on a runtime error. */
+int slpic_particle_step_noalloc(const slpic_config *cfg, int species, int64_t n,
+                                const int32_t *cell_in, const float *state_in, const float *E,
+                                int32_t *cell_out, float *state_out, int64_t *charge_out,
+                                int64_t *n_out, int64_t *absorbed, void *stream);
 
 #ifdef __cplusplus
 }

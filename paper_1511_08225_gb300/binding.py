@@ -39,6 +39,7 @@ EXPORTS = (
     "slpic_fields", "slpic_density", "slpic_charge_raw", "slpic_particle_count",
     "slpic_get_particles", "slpic_diagnostics", "slpic_save", "slpic_restore",
     "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernels_per_step",
+    "slpic_particle_step_noalloc",
 )
 
 
@@ -117,6 +118,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "slpic_kernel_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D),
                                    ctypes.POINTER(I64)]),
         "slpic_kernels_per_step": (I, [P, ctypes.POINTER(I)]),
+        "slpic_particle_step_noalloc": (I, [ctypes.POINTER(slpic_config), I, I64, P, P, P, P, P,
+                                            P, ctypes.POINTER(I64), P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -311,6 +314,24 @@ def slpic_kernels_per_step(h) -> int:
     n = ctypes.c_int()
     _check(h, load_library().slpic_kernels_per_step(h, ctypes.byref(n)), "slpic_kernels_per_step")
     return n.value
+
+
+def slpic_particle_step_noalloc(cfg: slpic_config, species: int, cell_in, state_in, E,
+                                cell_out, state_out, charge_out, stream: int = 0):
+    """Allocation-free particle step on torch CUDA tensors (see slpic.h).
+    Returns (n_out, [absorbed_lo, absorbed_hi])."""
+    n = int(cell_in.numel())
+    n_out = ctypes.c_int64()
+    absorbed = (ctypes.c_int64 * 2)()
+    rc = load_library().slpic_particle_step_noalloc(
+        ctypes.byref(cfg), species, n, ctypes.c_void_p(cell_in.data_ptr()),
+        ctypes.c_void_p(state_in.data_ptr()), ctypes.c_void_p(E.data_ptr()),
+        ctypes.c_void_p(cell_out.data_ptr()), ctypes.c_void_p(state_out.data_ptr()),
+        ctypes.c_void_p(charge_out.data_ptr()), ctypes.byref(n_out), absorbed,
+        ctypes.c_void_p(stream))
+    if rc != SLPIC_OK:
+        raise SlpicError(rc, "slpic_particle_step_noalloc", "")
+    return n_out.value, [absorbed[0], absorbed[1]]
 
 
 # ---------------------------------------------------------------- convenience wrapper
