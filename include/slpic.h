@@ -226,7 +226,8 @@ int slpic_restore(slpic_t *h, const void *buf, size_t size);
 /* ---- timing --------------------------------------------------------------- */
 
 /* From now on slpic_step runs its steps as graphs of `steps_per_graph` steps
- * (1..4096; 0 turns timing off) in which CUDA events bracket the particle
+ * (1..4096, rounded up to a multiple of 16, the interval of the compacting
+ * particle step; 0 turns timing off) in which CUDA events bracket the particle
  * kernel and the field/source kernel of every step.  The events are recorded
  * on the handle's stream, the stream the kernels run on; each graph replay
  * re-records them.  Steps beyond a multiple of steps_per_graph run untimed. */

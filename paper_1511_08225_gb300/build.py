@@ -52,7 +52,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+    # --fmad=false: no implicit multiply-add contraction, so an inlined device
+    # function gives the same bits in every kernel; the multiply-adds the kernels
+    # want are written explicitly (__fmaf_rn / fma).
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",
              "-I", INCLUDE, "-I", CSRC]
     if verbose:
         flags += ["-Xptxas", "-v"]

@@ -42,9 +42,10 @@ struct slpic_sim {
     void *d_stage = nullptr;  // load/read-back staging
     size_t stage_bytes = 0;
 
-    cudaGraphExec_t g1 = nullptr, gK = nullptr;
-    int K = 8;
-    cudaGraphExec_t gt = nullptr;   // timed graph: t_len steps with their own events
+    cudaGraphExec_t g1 = nullptr;   // one in-place step
+    cudaGraphExec_t gc = nullptr;   // one compacting step
+    cudaGraphExec_t gK = nullptr;   // one cycle: kCompactEvery - 1 in-place steps, 1 compacting
+    cudaGraphExec_t gt = nullptr;   // timed graph: t_len steps (whole cycles) with their own events
     std::vector<cudaEvent_t> events; // 3 per step of the timed graph
     long long t_len = 0;             // steps per timed graph (0 = timing off)
     long long t_launched = 0;        // timed-graph launches since timing was enabled
@@ -164,6 +165,8 @@ static void free_all(slpic_t *h)
     cudaSetDevice(h->device);
     if (h->g1)
         cudaGraphExecDestroy(h->g1);
+    if (h->gc)
+        cudaGraphExecDestroy(h->gc);
     if (h->gK)
         cudaGraphExecDestroy(h->gK);
     if (h->gt)
@@ -216,8 +219,8 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     {
         int nn_ = cfg->bc == SLPIC_BC_PERIODIC ? cfg->n_cells : cfg->n_cells + 1;
-        // E (float) + deposit (int64) per node, plus the kernel's static shared memory
-        if ((size_t)nn_ * 12 + 1024 > (size_t)max_smem) {
+        // the particle kernel's queue, E and deposit, plus its static shared memory
+        if (particle_kernel_smem_bytes(nn_) + 1024 > (size_t)max_smem || nn_ > field_max_nodes()) {
             g_create_err = "grid does not fit in shared memory (n_cells too large for the 1D kernel)";
             return SLPIC_ERR_INVALID;
         }
@@ -287,6 +290,9 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     p.eps0 = cfg->eps0;
     p.phi_lo = cfg->phi_lo;
     p.phi_hi = cfg->phi_hi;
+    p.inv_n = 1.0 / cfg->n_cells;
+    p.inv_dx = 1.0 / cfg->dx;
+    p.k2 = cfg->dx * cfg->dx / cfg->eps0;
     p.src_mode = cfg->src_mode;
     p.src_ref = cfg->src_ref_species;
     p.src_lo_cells = (float)cfg->src_lo_cells;
@@ -306,6 +312,7 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
         d.vth_src = sp.T_src > 0 ? (float)std::sqrt(sp.T_src / sp.m) : 0.0f;
         d.kind = sp.beta_kind;
         d.qw_dx = sp.q * sp.w / cfg->dx;
+        d.rho_unit = d.qw_dx / 1099511627776.0;
         d.w = sp.w;
     }
     p.acc = h->d_acc;
@@ -472,9 +479,12 @@ extern "C" int slpic_prepare(slpic_t *h)
         return rc;
     const int P = (int)(h->step & 1);
     CK(h, cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * 2 * h->ns * h->nn, h->stream));
-    for (int s = 0; s < h->ns; ++s)
+    for (int s = 0; s < h->ns; ++s) {
         CK(h, cudaMemsetAsync(&h->d_state->count[s][P ^ 1], 0, sizeof(unsigned long long),
                               h->stream));
+        CK(h, cudaMemsetAsync(&h->d_state->holes[s][P ^ 1], 0, sizeof(unsigned long long),
+                              h->stream));
+    }
     launch_deposit(h->p, h->small_ctas, h->stream);
     CK(h, cudaGetLastError());
     launch_field(h->p, 0, h->stream);
@@ -483,22 +493,26 @@ extern "C" int slpic_prepare(slpic_t *h)
     return SLPIC_OK;
 }
 
-// Capture nsteps timesteps into a graph.  With `timed`, event-record nodes
-// (3 per step, from h->events) bracket the particle and field kernels; every
-// replay re-records them, so the events describe the most recent replay.
-static int capture(slpic_t *h, int nsteps, bool timed, cudaGraphExec_t *out)
+// Capture the timesteps first_step .. first_step + nsteps - 1 into a graph: an
+// in-place particle step, or a compacting one on every kCompactEvery-th step, each
+// followed by the field kernel.  With `timed`, event-record nodes (3 per step, from
+// h->events) bracket the particle and field kernels; every replay re-records them,
+// so the events describe the most recent replay.
+static int capture(slpic_t *h, long long first_step, int nsteps, bool timed,
+                   cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
     CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < nsteps; ++k) {
+        const bool compact = (first_step + k) % kCompactEvery == kCompactEvery - 1;
         // "external" records become event-record nodes of the graph (a plain
         // record inside a capture only orders streams)
         if (timed)
             cudaEventRecordWithFlags(h->events[3 * k], h->cap_stream, cudaEventRecordExternal);
-        launch_particles(h->p, h->ctas, h->cap_stream);
+        launch_particles(h->p, h->ctas, compact, h->cap_stream);
         if (timed)
             cudaEventRecordWithFlags(h->events[3 * k + 1], h->cap_stream, cudaEventRecordExternal);
-        launch_field(h->p, 1, h->cap_stream);
+        launch_field(h->p, compact ? 2 : 1, h->cap_stream);
         if (timed)
             cudaEventRecordWithFlags(h->events[3 * k + 2], h->cap_stream, cudaEventRecordExternal);
     }
@@ -524,32 +538,33 @@ extern "C" int slpic_step(slpic_t *h, int64_t nsteps)
         return rc;
     if (nsteps == 0)
         return SLPIC_OK;
-    if (!h->g1 && (rc = capture(h, 1, false, &h->g1)))
+    // graphs: steps whose index is 0 mod kCompactEvery start a cycle
+    if (!h->g1 && (rc = capture(h, 0, 1, false, &h->g1)))
         return rc;
-    if (h->t_len > 0) {
-        if (!h->gt && (rc = capture(h, (int)h->t_len, true, &h->gt)))
-            return rc;
-        int64_t left = nsteps;
-        while (left >= h->t_len) {
-            CK(h, cudaGraphLaunch(h->gt, h->stream));
-            h->t_launched++;
-            left -= h->t_len;
-        }
-        while (left-- > 0)
-            CK(h, cudaGraphLaunch(h->g1, h->stream));
-        h->step += nsteps;
-        return SLPIC_OK;
-    }
-    if (nsteps >= h->K && !h->gK && (rc = capture(h, h->K, false, &h->gK)))
+    if (!h->gc && (rc = capture(h, kCompactEvery - 1, 1, false, &h->gc)))
         return rc;
     int64_t left = nsteps;
-    while (left >= h->K) {
-        CK(h, cudaGraphLaunch(h->gK, h->stream));
-        left -= h->K;
+    while (left > 0) {
+        const long long phase = h->step % kCompactEvery;
+        if (phase == 0 && h->t_len > 0 && left >= h->t_len) {
+            if (!h->gt && (rc = capture(h, 0, (int)h->t_len, true, &h->gt)))
+                return rc;
+            CK(h, cudaGraphLaunch(h->gt, h->stream));
+            h->t_launched++;
+            h->step += h->t_len;
+            left -= h->t_len;
+        } else if (phase == 0 && left >= kCompactEvery) {
+            if (!h->gK && (rc = capture(h, 0, kCompactEvery, false, &h->gK)))
+                return rc;
+            CK(h, cudaGraphLaunch(h->gK, h->stream));
+            h->step += kCompactEvery;
+            left -= kCompactEvery;
+        } else {
+            CK(h, cudaGraphLaunch(phase == kCompactEvery - 1 ? h->gc : h->g1, h->stream));
+            h->step += 1;
+            left -= 1;
+        }
     }
-    while (left-- > 0)
-        CK(h, cudaGraphLaunch(h->g1, h->stream));
-    h->step += nsteps;
     return SLPIC_OK;
 }
 
@@ -585,6 +600,12 @@ extern "C" int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, 
     int rc = sync_prepared(h, instance);
     if (rc)
         return rc;
+    if (rho || phi) {
+        // the step computes E only; rho and phi of the latest deposit on demand
+        launch_potential(h->p, h->stream);
+        CK(h, cudaGetLastError());
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     if (rho)
         CK(h, cudaMemcpy(rho, h->d_rho, sizeof(double) * h->nn, cudaMemcpyDeviceToHost));
     if (phi)
@@ -631,39 +652,57 @@ extern "C" int slpic_particle_count(slpic_t *h, int instance, int species, int64
     DevState st;
     if ((rc = read_state(h, &st)))
         return rc;
-    *n = (int64_t)st.count[species][h->step & 1];
+    const int P = (int)(h->step & 1);
+    *n = (int64_t)(st.count[species][P] - st.holes[species][P]);
     return SLPIC_OK;
 }
 
 extern "C" int slpic_get_particles(slpic_t *h, int instance, int species, int64_t cap,
                                    int32_t *cell, float *offset, float *v, int64_t *n_out)
 {
-    int64_t n = 0;
-    int rc = slpic_particle_count(h, instance, species, &n);
+    int64_t n_live = 0;
+    int rc = slpic_particle_count(h, instance, species, &n_live);
     if (rc)
         return rc;
     if (cap < 0 || (cap > 0 && (!cell || !offset || !v)))
         return fail(h, SLPIC_ERR_INVALID, "bad cap or pointer");
-    if (n > cap)
-        n = cap;
     if (n_out)
-        *n_out = n;
-    if (n == 0)
+        *n_out = 0;
+    DevState st;
+    if ((rc = read_state(h, &st)))
+        return rc;
+    const int P = (int)(h->step & 1);
+    const int64_t slots = (int64_t)st.count[species][P];
+    if (slots == 0 || cap == 0)
         return SLPIC_OK;
-    size_t bc = sizeof(int32_t) * n, bo = sizeof(float) * n, bv = sizeof(float) * 3 * n;
+    size_t bc = sizeof(int32_t) * slots, bo = sizeof(float) * slots, bv = sizeof(float) * 3 * slots;
     if ((rc = ensure_stage(h, bc + bo + bv + 64)))
         return rc;
     char *base = (char *)h->d_stage;
     int32_t *dc = (int32_t *)base;
     float *doff = (float *)(base + ((bc + 15) & ~size_t(15)));
     float *dv = (float *)((char *)doff + ((bo + 15) & ~size_t(15)));
-    const int P = (int)(h->step & 1);
-    launch_unpack(h->d_cell[species][P], h->d_pv[species][P], n, dc, doff, dv, h->stream);
+    launch_unpack(h->d_cell[species][P], h->d_pv[species][P], slots, dc, doff, dv, h->stream);
     CK(h, cudaGetLastError());
-    CK(h, cudaMemcpyAsync(cell, dc, bc, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaMemcpyAsync(offset, doff, bo, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaMemcpyAsync(v, dv, bv, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<int32_t> hc(slots);
+    std::vector<float> ho(slots), hv(3 * slots);
+    CK(h, cudaMemcpyAsync(hc.data(), dc, bc, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(ho.data(), doff, bo, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(hv.data(), dv, bv, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    int64_t k = 0;
+    for (int64_t i = 0; i < slots && k < cap; ++i) {
+        if (hc[i] < 0)
+            continue;  // hole left by an absorbed particle
+        cell[k] = hc[i];
+        offset[k] = ho[i];
+        v[3 * k] = hv[3 * i];
+        v[3 * k + 1] = hv[3 * i + 1];
+        v[3 * k + 2] = hv[3 * i + 2];
+        ++k;
+    }
+    if (n_out)
+        *n_out = k;
     return SLPIC_OK;
 }
 
@@ -690,8 +729,9 @@ extern "C" int slpic_diagnostics(slpic_t *h, int instance, slpic_diag *out)
     out->time = (double)st.step * h->cfg.dt;
     for (int s = 0; s < h->ns; ++s) {
         const slpic_species &sp = h->cfg.species[s];
-        out->count[s] = (int64_t)st.count[s][P];
-        out->sum_w[s] = sp.w * (double)st.count[s][P];
+        const int64_t live = (int64_t)(st.count[s][P] - st.holes[s][P]);
+        out->count[s] = live;
+        out->sum_w[s] = sp.w * (double)live;
         out->sum_wbeta[s] = sp.w * red[2 * s];
         out->kinetic[s] = 0.5 * sp.m * sp.w * red[2 * s + 1];
         out->absorbed[s][0] = st.absorbed_total[s][0];
@@ -742,7 +782,7 @@ extern "C" int slpic_save(slpic_t *h, void *buf, size_t *size)
     char *o = (char *)buf;
     SaveHeader hd{};
     std::memcpy(hd.magic, "SLPIC1D", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.ns = h->ns;
     hd.nn = h->nn;
     hd.step = h->step;
@@ -782,7 +822,7 @@ extern "C" int slpic_restore(slpic_t *h, const void *buf, size_t size)
     SaveHeader hd;
     std::memcpy(&hd, i, sizeof(hd));
     i += sizeof(hd);
-    if (std::memcmp(hd.magic, "SLPIC1D", 8) != 0 || hd.version != 1 || hd.ns != h->ns ||
+    if (std::memcmp(hd.magic, "SLPIC1D", 8) != 0 || hd.version != 2 || hd.ns != h->ns ||
         hd.nn != h->nn)
         return fail(h, SLPIC_ERR_INVALID, "checkpoint does not match this configuration");
     for (int s = 0; s < h->ns; ++s)
@@ -822,6 +862,7 @@ extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
         return rc;
     if (steps_per_graph < 0 || steps_per_graph > 4096)
         return fail(h, SLPIC_ERR_INVALID, "steps_per_graph must be in 0..4096");
+    steps_per_graph = (steps_per_graph + kCompactEvery - 1) / kCompactEvery * kCompactEvery;
     CK(h, cudaStreamSynchronize(h->stream));
     if (h->gt) {
         cudaGraphExecDestroy(h->gt);

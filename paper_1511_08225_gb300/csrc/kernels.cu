@@ -1,12 +1,14 @@
 // kernels.cu -- the GPU kernels of one SLPIC timestep (1D3V, electrostatic).
 //
 //   k_particles  gather + push + move + walls + deposit + compaction   (HBM-bound)
-//   k_field      source injection, Poisson solve, E, bookkeeping       (one CTA)
+//   k_field      source injection, Poisson solve for E, bookkeeping (one 8-CTA cluster)
+//   k_potential  rho and phi on demand for read-back                  (one CTA)
 //   k_deposit    deposit of the current particles (after a load)
 //   k_diag       reductions for slpic_diagnostics
 //   k_validate   range checks of device-side particle loads
 //
 // Citations: Werner et al., arXiv 1511.08225, Appendix A, Eq. (slpicIntegration).
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -18,29 +20,95 @@
 namespace slpic {
 
 // ---------------------------------------------------------------------------------
-// Particle kernel: one launch advances every live particle of every species by one
-// step.  Grid (ctas_per_species, n_species); CTA b of species s owns a contiguous
-// range of tiles of the input buffer.  The whole 1D grid (E as float, the deposit
-// as int64) is staged in shared memory: the gather and the deposit never touch
-// global memory, so the kernel streams 20 B in and 20 B out per particle.
-// Survivors are compacted into the other buffer: per tile, a ballot per warp, one
-// warp scanning the (item, warp) counts, and one atomicAdd to reserve the tile's
-// output range (order inside a tile is kept; tile order is not).
+// Particle kernels: one launch advances every particle of every species by one step.
+// Grid (ctas_per_species, n_species); CTA b of species s owns a contiguous range of
+// the input buffer.  The whole 1D grid (E as float, the deposit as two 32-bit words
+// per node) is staged in shared memory: the gather and the deposit never touch
+// global memory, so a step streams 20 B in and 20 B out per particle.
+//
+// Divergence: most particles take the iteration-free push (push_vx_easy).  The few
+// that need the piece walk and Newton (strong field against a slow particle, band
+// crossings) would stall their whole warp, so they are queued in shared memory and
+// pushed later in full warps of queued particles.
+//
+// k_particles (most steps) writes each particle back to its own slot of the other
+// buffer and a hole (cell = -1) where one is absorbed; its warps never wait for one
+// another.  k_particles_compact (every kCompactEvery-th step) packs the survivors:
+// per batch, a ballot per warp, one warp scanning the (item, warp) counts, and one
+// atomicAdd to reserve the batch's output range (order inside a batch is kept;
+// batch order is not).
 // ---------------------------------------------------------------------------------
 constexpr int kPB = kParticleThreads;  // threads per CTA
 constexpr int kPI = 4;                 // particles per thread per tile
 constexpr int kPT = kPB * kPI;         // particles per tile
 constexpr int kNW = kPB / 32;
+constexpr int kQCap = kPT + kPB;       // queue: < kPB left + one tile
 static_assert(kPI * kNW == 32, "one warp scans the per-(item, warp) counts");
 
-__global__ void __launch_bounds__(kPB, 3) k_particles(StepParams p)
+// Compact the live items of NI per thread into out[] (block-wide; all threads call).
+template <int NI>
+__device__ __forceinline__ void compact_store(const bool (&live)[NI], const int (&c)[NI],
+                                              const float4 (&q)[NI], int *s_off,
+                                              unsigned long long *s_base,
+                                              unsigned long long *cnt_out, int32_t *cout,
+                                              float4 *vout)
+{
+    static_assert(NI * kNW <= 32, "scan fits one warp");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned mask[NI];
+#pragma unroll
+    for (int k = 0; k < NI; ++k) {
+        mask[k] = __ballot_sync(0xffffffffu, live[k]);
+        if (lane == 0)
+            s_off[k * kNW + warp] = __popc(mask[k]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < NI * kNW ? s_off[lane] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane < NI * kNW)
+            s_off[lane] = incl - v;
+        if (lane == 31)
+            *s_base = incl ? atomicAdd(cnt_out, (unsigned long long)incl) : 0ULL;
+    }
+    __syncthreads();
+    const unsigned long long ob = *s_base;
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < NI; ++k) {
+        if (live[k]) {
+            unsigned long long o = ob + (unsigned long long)s_off[k * kNW + warp] +
+                                   (unsigned long long)__popc(mask[k] & lt);
+            __stcs(cout + o, c[k]);
+            __stcs(vout + o, q[k]);
+        }
+    }
+    __syncthreads();
+}
+
+size_t particle_kernel_smem_bytes(int nn)
+{
+    return (size_t)kQCap * (sizeof(float4) + sizeof(int)) + (size_t)nn * 3 * sizeof(unsigned);
+}
+
+__global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long *s_hist = reinterpret_cast<unsigned long long *>(smem);
-    float *s_E = reinterpret_cast<float *>(s_hist + p.nn);
+    float4 *s_qv = reinterpret_cast<float4 *>(smem);            // [kQCap] queued states
+    unsigned *s_lo = reinterpret_cast<unsigned *>(s_qv + kQCap);  // [nn] deposit, low words
+    unsigned *s_hi = s_lo + p.nn;                                 // [nn] deposit, high words
+    float *s_E = reinterpret_cast<float *>(s_hi + p.nn);          // [nn]
+    int *s_qc = reinterpret_cast<int *>(s_E + p.nn);              // [kQCap] queued cells
     __shared__ int s_off[32];
     __shared__ unsigned long long s_base;
     __shared__ unsigned int s_abs[2];
+    __shared__ int s_qn;
 
     const int s = blockIdx.y;
     const SpeciesDev &sp = p.sp[s];
@@ -55,17 +123,44 @@ __global__ void __launch_bounds__(kPB, 3) k_particles(StepParams p)
     unsigned long long *acc = p.acc + ((size_t)(P ^ 1) * p.ns + s) * p.nn;
 
     for (int j = threadIdx.x; j < p.nn; j += kPB) {
-        s_hist[j] = 0ULL;
+        s_lo[j] = 0u;
+        s_hi[j] = 0u;
         s_E[j] = p.E[j];
     }
     if (threadIdx.x < 2)
         s_abs[threadIdx.x] = 0u;
+    if (threadIdx.x == 0)
+        s_qn = 0;
     __syncthreads();
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    DepositSplit32 dep{s_lo, s_hi};
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const long long ntiles = (n + kPT - 1) / kPT;
     const long long t0 = ntiles * blockIdx.x / gridDim.x;
     const long long t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+
+    // push the last m queued particles in full warps, then store the survivors
+    auto drain = [&](int m) {
+        const int base = s_qn - m;
+        bool live[1] = {(int)threadIdx.x < m};
+        int c[1] = {0};
+        float4 q[1] = {make_float4(0.f, 0.f, 0.f, 0.f)};
+        if (live[0]) {
+            c[0] = s_qc[base + threadIdx.x];
+            q[0] = s_qv[base + threadIdx.x];
+            float ax = gather_ax(p, sp, s_E, c[0], q[0].x);
+            float vx = push_vx_walk(sp.kind, q[0].y, q[0].z, q[0].w, ax, p.dt, sp.v0);
+            int wall = 0;
+            live[0] = move_and_deposit(p, sp, dep, c[0], q[0], vx, wall);
+            if (!live[0])
+                atomicAdd(&s_abs[wall], 1u);
+        }
+        __syncthreads();  // every queued entry read before the queue shrinks
+        if (threadIdx.x == 0)
+            s_qn = base;
+        compact_store<1>(live, c, q, s_off, &s_base, cnt_out, cout, vout);
+    };
 
     for (long long t = t0; t < t1; ++t) {
         const long long base = t * kPT;
@@ -78,56 +173,196 @@ __global__ void __launch_bounds__(kPB, 3) k_particles(StepParams p)
             live[k] = i < n;
             if (live[k]) {
                 c[k] = __ldcs(cin + i);
-                q[k] = __ldcs(vin + i);
+                live[k] = c[k] >= 0;  // holes are dropped here
+                if (live[k])
+                    q[k] = __ldcs(vin + i);
             }
         }
 #pragma unroll
         for (int k = 0; k < kPI; ++k) {
+            bool hard = false;
             if (live[k]) {
-                int wall = 0;
-                live[k] = advance(p, sp, s_E, s_hist, c[k], q[k], wall);
-                if (!live[k])
-                    atomicAdd(&s_abs[wall], 1u);
+                float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
+                float vx;
+                if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, sp.v0, vx)) {
+                    int wall = 0;
+                    live[k] = move_and_deposit(p, sp, dep, c[k], q[k], vx, wall);
+                    if (!live[k])
+                        atomicAdd(&s_abs[wall], 1u);
+                } else {
+                    hard = true;
+                    live[k] = false;  // stored later by drain()
+                }
+            }
+            unsigned hm = __ballot_sync(0xffffffffu, hard);
+            if (hm) {
+                int qb = 0;
+                if (lane == 0)
+                    qb = atomicAdd(&s_qn, __popc(hm));
+                qb = __shfl_sync(0xffffffffu, qb, 0);
+                if (hard) {
+                    int slot = qb + __popc(hm & lt);
+                    s_qc[slot] = c[k];
+                    s_qv[slot] = q[k];
+                }
             }
         }
-        unsigned mask[kPI];
-#pragma unroll
-        for (int k = 0; k < kPI; ++k) {
-            mask[k] = __ballot_sync(0xffffffffu, live[k]);
-            if (lane == 0)
-                s_off[k * kNW + warp] = __popc(mask[k]);
+        compact_store<kPI>(live, c, q, s_off, &s_base, cnt_out, cout, vout);
+        while (s_qn >= kPB)
+            drain(kPB);
+    }
+    while (s_qn > 0)
+        drain(min(s_qn, kPB));
+
+    for (int j = threadIdx.x; j < p.nn; j += kPB) {
+        unsigned long long v = ((unsigned long long)s_hi[j] << 32) + s_lo[j];
+        if (v)
+            atomicAdd(acc + j, v);
+    }
+    if (threadIdx.x < 2 && s_abs[threadIdx.x])
+        atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
+}
+
+constexpr int kWI = 4;           // particles per lane per warp-tile
+constexpr int kWT = 32 * kWI;    // particles per warp-tile
+constexpr int kWQ = 64;          // per-warp queue: < 32 waiting + up to 32 new
+
+size_t particle_inplace_smem_bytes(int nn)
+{
+    return (size_t)kNW * kWQ * sizeof(int) + (size_t)nn * 3 * sizeof(unsigned);
+}
+
+__global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *s_qi = reinterpret_cast<int *>(smem);                       // [kNW][kWQ] queued slots
+    unsigned *s_lo = reinterpret_cast<unsigned *>(s_qi + kNW * kWQ);  // [nn]
+    unsigned *s_hi = s_lo + p.nn;                                // [nn]
+    float *s_E = reinterpret_cast<float *>(s_hi + p.nn);         // [nn]
+    __shared__ unsigned int s_abs[2];
+
+    const int s = blockIdx.y;
+    const SpeciesDev &sp = p.sp[s];
+    const long long step = *(volatile long long *)&p.st->step;
+    const int P = (int)(step & 1);
+    const long long n = (long long)*(volatile unsigned long long *)&p.st->count[s][P];
+    const int32_t *__restrict__ cin = sp.cell[P];
+    const float4 *__restrict__ vin = sp.pv[P];
+    int32_t *__restrict__ cout = sp.cell[P ^ 1];
+    float4 *__restrict__ vout = sp.pv[P ^ 1];
+    unsigned long long *acc = p.acc + ((size_t)(P ^ 1) * p.ns + s) * p.nn;
+
+    for (int j = threadIdx.x; j < p.nn; j += kPB) {
+        s_lo[j] = 0u;
+        s_hi[j] = 0u;
+        s_E[j] = p.E[j];
+    }
+    if (threadIdx.x < 2)
+        s_abs[threadIdx.x] = 0u;
+    __syncthreads();
+
+    DepositSplit32 dep{s_lo, s_hi};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int *qi = s_qi + warp * kWQ;
+    int qn = 0;  // queue length, the same in every lane
+    unsigned nabs0 = 0u, nabs1 = 0u;
+
+    // move, deposit and store one particle whose new vx is known
+    auto finish = [&](long long i, int c, float4 q, float vx) {
+        int wall = 0;
+        if (move_and_deposit(p, sp, dep, c, q, vx, wall)) {
+            __stcs(cout + i, c);
+            __stcs(vout + i, q);
+        } else {
+            __stcs(cout + i, -1);
+            if (wall)
+                ++nabs1;
+            else
+                ++nabs0;
         }
-        __syncthreads();
-        if (warp == 0) {
-            int v = s_off[lane];
-            int incl = v;
+    };
+    // the general push for the particles queued at [from, from + m), one per lane;
+    // the queue holds slot numbers only, the particle is read again (from L2)
+    auto push_queued = [&](int from, int m) {
+        int ii = 0;
+        if (lane < m)
+            ii = qi[from + lane];
+        __syncwarp();  // slots read before they are refilled
+        if (lane < m) {
+            int c = cin[ii];
+            float4 q = vin[ii];
+            float ax = gather_ax(p, sp, s_E, c, q.x);
+            float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
+            finish(ii, c, q, vx);
+        }
+    };
+
+    // warp-tiles of kWT consecutive particles: the CTA owns a contiguous range of
+    // them and its warps take every kNW-th
+    const long long nwt = (n + kWT - 1) / kWT;
+    const long long w0 = nwt * blockIdx.x / gridDim.x;
+    const long long w1 = nwt * (blockIdx.x + 1) / gridDim.x;
+    for (long long t = w0 + warp; t < w1; t += kNW) {
+        const long long base = t * kWT;
+        int c[kWI];
+        float4 q[kWI];
+        bool act[kWI];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o)
-                    incl += y;
+        for (int k = 0; k < kWI; ++k) {
+            long long i = base + k * 32 + lane;
+            act[k] = i < n;
+            c[k] = -1;
+            if (act[k]) {
+                c[k] = __ldcs(cin + i);
+                if (c[k] >= 0)
+                    q[k] = __ldcs(vin + i);
             }
-            s_off[lane] = incl - v;
-            if (lane == 31)
-                s_base = incl ? atomicAdd(cnt_out, (unsigned long long)incl) : 0ULL;
         }
-        __syncthreads();
-        const unsigned long long ob = s_base;
-        const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-        for (int k = 0; k < kPI; ++k) {
-            if (live[k]) {
-                unsigned long long o = ob + (unsigned long long)s_off[k * kNW + warp] +
-                                       (unsigned long long)__popc(mask[k] & lt);
-                __stcs(cout + o, c[k]);
-                __stcs(vout + o, q[k]);
+        for (int k = 0; k < kWI; ++k) {
+            const long long i = base + k * 32 + lane;
+            bool hard = false;
+            if (act[k]) {
+                if (c[k] < 0) {
+                    __stcs(cout + i, -1);  // a hole stays a hole
+                } else {
+                    float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
+                    float vx;
+                    if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, sp.v0, vx))
+                        finish(i, c[k], q[k], vx);
+                    else
+                        hard = true;
+                }
+            }
+            unsigned hm = __ballot_sync(0xffffffffu, hard);
+            if (hm) {
+                if (hard)
+                    qi[qn + __popc(hm & lt)] = (int)i;
+                qn += __popc(hm);
+                __syncwarp();
+                if (qn >= 32) {
+                    qn -= 32;
+                    push_queued(qn, 32);
+                }
             }
         }
-        __syncthreads();
+    }
+    __syncwarp();
+    if (qn > 0)
+        push_queued(0, qn);
+
+    unsigned a0 = __reduce_add_sync(0xffffffffu, nabs0);
+    unsigned a1 = __reduce_add_sync(0xffffffffu, nabs1);
+    if (lane == 0) {
+        if (a0)
+            atomicAdd(&s_abs[0], a0);
+        if (a1)
+            atomicAdd(&s_abs[1], a1);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < p.nn; j += kPB) {
-        unsigned long long v = s_hist[j];
+        unsigned long long v = ((unsigned long long)s_hi[j] << 32) + s_lo[j];
         if (v)
             atomicAdd(acc + j, v);
     }
@@ -154,6 +389,8 @@ __global__ void __launch_bounds__(256) k_deposit(StepParams p)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         int c = sp.cell[P][i];
+        if (c < 0)
+            continue;  // hole
         float4 q = sp.pv[P][i];
         int c1 = c + 1;
         if (p.periodic && c1 == N)
@@ -261,60 +498,18 @@ __device__ void inject_species(const StepParams &p, int s, long long step, long 
     }
 }
 
-__global__ void __launch_bounds__(kFT) k_field(StepParams p, int mode)
+// On demand (slpic_fields): rho and phi of the latest deposit acc[step & 1], one CTA.
+// The particle step needs only E, which k_field computes; phi is read back rarely.
+__global__ void __launch_bounds__(kFT) k_potential(StepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     double *s_P = reinterpret_cast<double *>(smem);  // [nn]
     __shared__ double s_w[32];
-    __shared__ long long s_ninj[kMaxSpecies], s_base[kMaxSpecies];
     __shared__ double s_D0, s_shift;
 
-    DevState *st = p.st;
-    const long long step = st->step;
-    const int P = (int)(step & 1);
-    const int Q = mode ? (P ^ 1) : P;  // deposit to solve from
+    const long long step = p.st->step;
+    const int Q = (int)(step & 1);
     const int N = p.n_cells, nn = p.nn;
-
-    if (mode == 1) {
-        // ---- source injection (Sec. IV; counts as in the LOSS_MATCHED / RATE readings)
-        if (threadIdx.x == 0) {
-            double S = 0.0;
-            if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
-                int r = p.src_ref;
-                S = (double)(st->absorbed_step[r][0] + st->absorbed_step[r][1]) * p.sp[r].w;
-            } else if (p.src_mode == SLPIC_SRC_RATE) {
-                S = p.src_rate * p.dt64;
-            }
-            for (int s = 0; s < p.ns; ++s) {
-                long long k = 0;
-                if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
-                    double f = st->src_frac[s] + S / p.sp[s].w;
-                    k = (long long)floor(f);
-                    st->src_frac[s] = f - (double)k;
-                }
-                long long have = (long long)st->count[s][P ^ 1];
-                long long room = p.sp[s].capacity - have;
-                if (k > room) {
-                    k = room;
-                    atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
-                }
-                s_ninj[s] = k;
-                s_base[s] = have;
-                st->count[s][P ^ 1] = (unsigned long long)(have + k);
-                st->injected_total[s] += k;
-                st->absorbed_total[s][0] += (long long)st->absorbed_step[s][0];
-                st->absorbed_total[s][1] += (long long)st->absorbed_step[s][1];
-                st->absorbed_step[s][0] = 0ULL;
-                st->absorbed_step[s][1] = 0ULL;
-            }
-        }
-        __syncthreads();
-        for (int s = 0; s < p.ns; ++s)
-            if (s_ninj[s] > 0)
-                inject_species(p, s, step, s_base[s], s_ninj[s], Q);
-        __threadfence();
-        __syncthreads();
-    }
 
     // ---- rho_j from the fixed-point deposits (FP64)
     const double scale = 1.0 / 1099511627776.0;  // 2^-40
@@ -329,7 +524,8 @@ __global__ void __launch_bounds__(kFT) k_field(StepParams p, int mode)
         }
         p.rho[j] = r;
         s_P[j] = r;
-        rsum += r;
+        if (j < N)
+            rsum += r;
     }
     const double k2 = p.dx * p.dx / p.eps0;
     double mean = 0.0;
@@ -385,33 +581,228 @@ __global__ void __launch_bounds__(kFT) k_field(StepParams p, int mode)
         for (int j = j0; j < j1; ++j)
             p.phi[j] -= s_shift;
     }
-    // E from D_j = D0 - P_j
-    const double inv2dx = 0.5 / p.dx;
-    for (int j = j0; j < j1; ++j) {
+}
+
+// ---------------------------------------------------------------------------------
+// Field kernel: one thread-block cluster of kFC CTAs (one per SM), so that the FP64
+// work is spread over kFC SMs.  mode 0: E from acc[step&1] (after a load).
+// mode 1 / 2 (end of a step, after k_particles / k_particles_compact): CTA 0
+// injects this step's source particles after the output buffer's slots and deposits
+// them; then E from acc[(step+1)&1]; the consumed deposit and counters are cleared
+// and the step advances.
+//
+// With r_j = (dx^2/eps0)(rho_j - mean) for j = 1..N-1 and P_j = sum_{i=1..j} r_i,
+// D_j = phi_{j+1} - phi_j = D_0 - P_j and
+//   sum_{j=0}^{N-1} P_j = sum_{i=1}^{N-1} (N - i) r_i,
+// so one exchange of per-CTA sums (sum rho, sum r, sum (N-i) r) between the CTAs of
+// the cluster, through distributed shared memory, gives every CTA its prefix offset,
+// the periodic mean and D_0 (from phi_N - phi_0, or from sum_j D_j = 0 on a periodic
+// grid).  E_j = -(D_{j-1} + D_j)/(2 dx), one-sided at Dirichlet walls.
+// ---------------------------------------------------------------------------------
+constexpr int kFC = kFieldClusterCtas;
+constexpr int kFCT = kFieldClusterThreads;
+constexpr int kFCW = kFCT / 32;
+constexpr int kFMaxChunk = 16;  // nodes per thread: nn <= kFC * kFCT * kFMaxChunk
+
+template <int NV>
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double (*s_w)[32])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+            v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if (lane == 0)
+            s_w[k][warp] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double t = 0.0;
+        for (int w = 0; w < kFCW; ++w)
+            t += s_w[k][w];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
+    k_field(StepParams p, int mode)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ double s_w[3][32];
+    __shared__ double s_tot[3];  // this CTA's: sum rho, sum r, sum (N-i) r
+    __shared__ double s_scan[kFCW];
+    __shared__ long long s_ninj[kMaxSpecies], s_base[kMaxSpecies];
+
+    DevState *st = p.st;
+    const long long step = st->step;
+    const int P = (int)(step & 1);
+    const int Q = mode ? (P ^ 1) : P;  // deposit to solve from
+    const int N = p.n_cells, nn = p.nn;
+
+    if (mode >= 1 && rank == 0) {
+        // ---- source injection (Sec. IV; counts as in the LOSS_MATCHED / RATE readings)
+        if (threadIdx.x == 0) {
+            double S = 0.0;
+            if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
+                int r = p.src_ref;
+                S = (double)(st->absorbed_step[r][0] + st->absorbed_step[r][1]) * p.sp[r].w;
+            } else if (p.src_mode == SLPIC_SRC_RATE) {
+                S = p.src_rate * p.dt64;
+            }
+            for (int s = 0; s < p.ns; ++s) {
+                long long k = 0;
+                if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
+                    double f = st->src_frac[s] + S / p.sp[s].w;
+                    k = (long long)floor(f);
+                    st->src_frac[s] = f - (double)k;
+                }
+                // after an in-place step the output uses the input's slots (holes
+                // included); after a compacting step its count was reserved by atomics
+                long long have = (long long)(mode == 1 ? st->count[s][P] : st->count[s][P ^ 1]);
+                st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + st->absorbed_step[s][0] +
+                                                      st->absorbed_step[s][1]
+                                                : 0ULL;
+                long long room = p.sp[s].capacity - have;
+                if (k > room) {
+                    k = room;
+                    atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
+                }
+                s_ninj[s] = k;
+                s_base[s] = have;
+                st->count[s][P ^ 1] = (unsigned long long)(have + k);
+                st->injected_total[s] += k;
+                st->absorbed_total[s][0] += (long long)st->absorbed_step[s][0];
+                st->absorbed_total[s][1] += (long long)st->absorbed_step[s][1];
+                st->absorbed_step[s][0] = 0ULL;
+                st->absorbed_step[s][1] = 0ULL;
+            }
+        }
+        __syncthreads();
+        for (int s = 0; s < p.ns; ++s)
+            if (s_ninj[s] > 0)
+                inject_species(p, s, step, s_base[s], s_ninj[s], Q);
+        __threadfence();
+    }
+    cl.sync();  // the injected particles' deposit is complete before anyone reads acc
+
+    // ---- this thread's nodes: CTA rank owns [c0, c1), the thread a chunk of it
+    const int per_cta = (nn + kFC - 1) / kFC;
+    const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
+    const int chunk = (per_cta + kFCT - 1) / kFCT;
+    const int j0 = min(c1, c0 + (int)threadIdx.x * chunk), j1 = min(c1, j0 + chunk);
+    double rho[kFMaxChunk], pre[kFMaxChunk];
+    double v3[3] = {0.0, 0.0, 0.0};  // sum rho (j < N), sum rho (1 <= j <= N-1), sum (N-j) rho
+    double run = 0.0;
+#pragma unroll
+    for (int k = 0; k < kFMaxChunk; ++k) {
+        int j = j0 + k;
+        double r = 0.0;
+        if (j < j1) {
+            for (int s = 0; s < p.ns; ++s) {
+                long long a = (long long)__ldcg(p.acc + ((size_t)Q * p.ns + s) * nn + j);
+                r = fma(p.sp[s].rho_unit, (double)a, r);
+            }
+            p.rho[j] = r;
+            if (j < N)
+                v3[0] += r;
+            if (j >= 1 && j < N) {
+                run += r;
+                v3[1] += r;
+                v3[2] = fma((double)(N - j), r, v3[2]);
+            }
+        }
+        rho[k] = r;
+        pre[k] = run;  // chunk-local inclusive prefix of rho over 1..N-1
+    }
+    // exclusive prefix of the chunk sums within the CTA
+    double thread_run = run;
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        double incl = thread_run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            double y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            s_scan[warp] = incl;
+        __syncthreads();
+        double before = 0.0;
+        for (int w = 0; w < warp; ++w)
+            before += s_scan[w];
+        thread_run = before + incl - thread_run;  // exclusive
+    }
+    block_sum_n<3>(v3, s_w);
+    if (threadIdx.x == 0) {
+        s_tot[0] = v3[0];
+        s_tot[1] = v3[1];
+        s_tot[2] = v3[2];
+    }
+    cl.sync();
+    // one thread gathers the other CTAs' sums (distributed shared memory) and forms
+    // the step's scalars; FP64 is narrow on this GPU, so nothing is computed twice
+    __shared__ double s_c[5];  // cta offset, mean, D0, P_{N-1}, k2 * mean
+    if (threadIdx.x == 0) {
+        double tot_rho = 0.0, tot_r = 0.0, tot_w = 0.0, cta_off = 0.0;
+        for (int r = 0; r < kFC; ++r) {
+            const double *t = cl.map_shared_rank(s_tot, r);
+            tot_rho += t[0];
+            tot_r += t[1];
+            tot_w += t[2];
+            if (r < rank)
+                cta_off += t[1];
+        }
+        const double mean = p.periodic ? tot_rho * p.inv_n : 0.0;
+        // sum_{j=0}^{N-1} P_j with the mean removed: k2 (sum (N-i) rho_i - mean N(N-1)/2)
+        const double sumP = p.k2 * (tot_w - mean * 0.5 * (double)N * (double)(N - 1));
+        s_c[0] = cta_off;
+        s_c[1] = mean;
+        s_c[2] = p.periodic ? sumP * p.inv_n : (p.phi_hi - p.phi_lo + sumP) * p.inv_n;
+        s_c[3] = p.k2 * (tot_r - mean * (double)(N - 1));  // P_{N-1}
+        s_c[4] = p.k2 * mean;
+    }
+    cl.sync();  // no CTA leaves (or reuses s_tot) while others still read it
+    const double cta_off = s_c[0], mean = s_c[1], D0 = s_c[2], P_last = s_c[3];
+    const double k2 = p.k2, k2mean = s_c[4];
+    const double inv2dx = 0.5 * p.inv_dx;
+    const double base_run = cta_off + thread_run;
+#pragma unroll
+    for (int k = 0; k < kFMaxChunk; ++k) {
+        int j = j0 + k;
+        if (j >= j1)
+            break;
+        // P_j = k2 (sum_{i=1..j} rho_i - mean j)
+        double Pj = (j < N) ? fma(k2, base_run + pre[k], -k2mean * (double)j) : P_last;
         double e;
-        if (p.periodic) {
-            int jm = (j == 0) ? N - 1 : j - 1;
-            e = -((D0 - s_P[jm]) + (D0 - s_P[j])) * inv2dx;
-        } else if (j == 0) {
-            e = -(D0 - s_P[0]) / p.dx;
-        } else if (j == N) {
-            e = -(D0 - s_P[N - 1]) / p.dx;
+        if (j == 0) {
+            e = p.periodic ? ((P_last - D0) - D0) * inv2dx : -D0 * p.inv_dx;
+        } else if (!p.periodic && j == N) {
+            e = (P_last - D0) * p.inv_dx;
         } else {
-            e = -((D0 - s_P[j - 1]) + (D0 - s_P[j])) * inv2dx;
+            double Pm = Pj - fma(k2, rho[k], -k2mean);  // P_{j-1}
+            e = ((Pm + Pj) - 2.0 * D0) * inv2dx;
         }
         p.E64[j] = e;
         p.E[j] = (float)e;
     }
 
-    if (mode == 1) {
-        // the deposit of rho^n and the input count are consumed: clear them for
-        // the next step's particle kernel, then advance the time level
-        for (int idx = threadIdx.x; idx < p.ns * nn; idx += kFT)
-            p.acc[(size_t)P * p.ns * nn + idx] = 0ULL;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int s = 0; s < p.ns; ++s)
+    if (mode >= 1) {
+        // the deposit of rho^n and the input buffer are consumed: clear them for the
+        // next step's particle kernel, then advance the time level
+        const int total = p.ns * nn;
+        for (int idx = rank * kFCT + threadIdx.x; idx < total; idx += kFC * kFCT)
+            p.acc[(size_t)P * total + idx] = 0ULL;
+        if (rank == 0 && threadIdx.x == 0) {
+            for (int s = 0; s < p.ns; ++s) {
                 st->count[s][P] = 0ULL;
+                st->holes[s][P] = 0ULL;
+            }
             st->step = step + 1;
         }
     }
@@ -431,6 +822,8 @@ __global__ void __launch_bounds__(256) k_diag(StepParams p, double *out)
     double a = 0.0, b = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
+        if (sp.cell[P][i] < 0)
+            continue;  // hole
         float4 q = sp.pv[P][i];
         double bt = (double)beta_q(sp.kind, q.y, q.z, q.w, sp.v0);
         double v2 = (double)q.y * q.y + (double)q.z * q.z + (double)q.w * q.w;
@@ -505,36 +898,58 @@ __global__ void k_unpack(const int32_t *csrc, const float4 *psrc, long long n, i
 // ---------------------------------------------------------------------------------
 size_t particle_smem_bytes(int nn) { return (size_t)nn * (sizeof(unsigned long long) + sizeof(float)); }
 size_t field_smem_bytes(int nn) { return (size_t)nn * sizeof(double); }
+int field_max_nodes() { return kFC * kFCT * kFMaxChunk; }
 
 cudaError_t configure_kernels(int nn)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_particles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)particle_smem_bytes(nn));
+    cudaError_t e = cudaFuncSetAttribute(k_particles_compact,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)particle_kernel_smem_bytes(nn));
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(k_particles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)particle_inplace_smem_bytes(nn));
     if (e != cudaSuccess)
         return e;
     e = cudaFuncSetAttribute(k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(nn * sizeof(unsigned long long)));
     if (e != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)field_smem_bytes(nn));
 }
 
 cudaError_t particle_ctas_per_sm(int nn, int *out)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_particles, kPB,
-                                                         particle_smem_bytes(nn));
+    // one grid size serves both particle kernels: the smaller occupancy of the two
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_particles, kPB,
+                                                                  particle_inplace_smem_bytes(nn));
+    if (e != cudaSuccess)
+        return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particles_compact, kPB,
+                                                      particle_kernel_smem_bytes(nn));
+    *out = a < b ? a : b;
+    return e;
 }
 
-void launch_particles(const StepParams &p, int ctas_per_species, cudaStream_t st)
+void launch_particles(const StepParams &p, int ctas_per_species, bool compact, cudaStream_t st)
 {
     dim3 grid(ctas_per_species, p.ns);
-    k_particles<<<grid, kPB, particle_smem_bytes(p.nn), st>>>(p);
+    if (compact)
+        k_particles_compact<<<grid, kPB, particle_kernel_smem_bytes(p.nn), st>>>(p);
+    else
+        k_particles<<<grid, kPB, particle_inplace_smem_bytes(p.nn), st>>>(p);
 }
 
 void launch_field(const StepParams &p, int mode, cudaStream_t st)
 {
-    k_field<<<1, kFT, field_smem_bytes(p.nn), st>>>(p, mode);
+    k_field<<<kFC, kFCT, 0, st>>>(p, mode);
+}
+
+void launch_potential(const StepParams &p, cudaStream_t st)
+{
+    k_potential<<<1, kFT, field_smem_bytes(p.nn), st>>>(p);
 }
 
 void launch_deposit(const StepParams &p, int ctas_per_species, cudaStream_t st)

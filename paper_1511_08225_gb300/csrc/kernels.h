@@ -10,15 +10,22 @@
 namespace slpic {
 
 constexpr int kParticleThreads = 256;
-constexpr int kFieldThreads = 1024;
+constexpr int kFieldThreads = 1024;        // k_potential (one CTA)
+constexpr int kFieldClusterCtas = 8;       // k_field: one cluster of 8 CTAs
+constexpr int kFieldClusterThreads = 128;
 
-size_t particle_smem_bytes(int nn);
+size_t particle_smem_bytes(int nn);         // E + one int64 per node (allocation-free kernel)
+size_t particle_kernel_smem_bytes(int nn);  // k_particles_compact: queue + E + split deposit
+size_t particle_inplace_smem_bytes(int nn); // k_particles: per-warp queues + E + split deposit
+constexpr int kCompactEvery = 16;           // one compacting particle step per this many
 size_t field_smem_bytes(int nn);
+int field_max_nodes();
 cudaError_t configure_kernels(int nn);
 cudaError_t particle_ctas_per_sm(int nn, int *out);
 
-void launch_particles(const StepParams &p, int ctas_per_species, cudaStream_t st);
+void launch_particles(const StepParams &p, int ctas_per_species, bool compact, cudaStream_t st);
 void launch_field(const StepParams &p, int mode, cudaStream_t st);
+void launch_potential(const StepParams &p, cudaStream_t st);
 void launch_deposit(const StepParams &p, int ctas_per_species, cudaStream_t st);
 void launch_diag(const StepParams &p, double *out, int ctas_per_species, cudaStream_t st);
 void launch_validate(const int32_t *cell, const float *off, const float *v, long long n,

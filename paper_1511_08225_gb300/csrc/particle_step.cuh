@@ -16,25 +16,28 @@ __device__ __forceinline__ void deposit_node(unsigned long long *hist, int c, in
     atomicAdd(hist + c1, qR);
 }
 
-// Push one particle (Appendix A): returns false if absorbed (wall = 0 at x=0,
-// 1 at x=L).  c, q updated in place.
-__device__ __forceinline__ bool advance(const StepParams &p, const SpeciesDev &sp,
-                                        const float *sE, unsigned long long *hist, int &c,
-                                        float4 &q, int &wall)
+// Gather (Sec. II): linear interpolation of the nodal field at the particle.
+__device__ __forceinline__ float gather_ax(const StepParams &p, const SpeciesDev &sp,
+                                           const float *sE, int c, float d)
+{
+    int c1 = c + 1;
+    if (p.periodic && c1 == p.n_cells)
+        c1 = 0;
+    // explicit roundings: every kernel that inlines this gets the same bits
+    float Ep = __fmaf_rn(d, sE[c1], __fmul_rn(1.0f - d, sE[c]));
+    return __fmul_rn(sp.qm, Ep);
+}
+
+// After the velocity push (new vx): x^{n+1} = x^n + beta(|v^{n+1/2}|) v^{n+1/2} dt in
+// cell units, walls or wrap, and rho^{n+1} += q w beta S(x - x^{n+1}) through
+// dep(c, c+1, beta, offset).  Returns false if absorbed (wall = 0 at x=0, 1 at x=L).
+template <typename Dep>
+__device__ __forceinline__ bool move_and_deposit(const StepParams &p, const SpeciesDev &sp,
+                                                 Dep &dep, int &c, float4 &q, float vx, int &wall)
 {
     const int N = p.n_cells;
-    float d = q.x;
-    int c1 = c + 1;
-    if (p.periodic && c1 == N)
-        c1 = 0;
-    // gather: linear interpolation of the nodal field (Sec. II scatter/gather)
-    float Ep = (1.0f - d) * sE[c] + d * sE[c1];
-    float ax = sp.qm * Ep;
-    // v^{n+1/2} = v^{n-1/2} + a int beta dt
-    float vx = push_vx(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
-    // x^{n+1} = x^n + beta(|v^{n+1/2}|) v^{n+1/2} dt, in cell units
     float b = beta_q(sp.kind, vx, q.z, q.w, sp.v0);
-    float xn = d + b * vx * p.dt_dx;
+    float xn = __fmaf_rn(__fmul_rn(b, vx), p.dt_dx, q.x);
     float fl = floorf(xn);
     int cn = c + (int)fl;
     float dn = xn - fl;
@@ -56,12 +59,55 @@ __device__ __forceinline__ bool advance(const StepParams &p, const SpeciesDev &s
     int cn1 = cn + 1;
     if (p.periodic && cn1 == N)
         cn1 = 0;
-    // rho^{n+1} += q w beta(|v^{n+1/2}|) S(x - x^{n+1})
-    deposit_node(hist, cn, cn1, b, dn);
+    dep(cn, cn1, b, dn);
     c = cn;
     q.x = dn;
     q.y = vx;
     return true;
+}
+
+// int64 shared-memory histogram
+struct DepositU64 {
+    unsigned long long *hist;
+    __device__ __forceinline__ void operator()(int c, int c1, float b, float off)
+    {
+        deposit_node(hist, c, c1, b, off);
+    }
+};
+
+// The same integers kept as two 32-bit words per node (value = hi 2^32 + lo):
+// 32-bit shared-memory atomics are native; the carry out of lo is detected from
+// the old value the atomic returns and added to hi, so the sum stays exact.
+struct DepositSplit32 {
+    unsigned *lo, *hi;
+    __device__ __forceinline__ void add(int c, unsigned long long v)
+    {
+        unsigned vl = (unsigned)v, vh = (unsigned)(v >> 32);
+        unsigned old = atomicAdd(lo + c, vl);
+        vh += (old + vl < old) ? 1u : 0u;
+        if (vh)
+            atomicAdd(hi + c, vh);
+    }
+    __device__ __forceinline__ void operator()(int c, int c1, float b, float off)
+    {
+        unsigned long long qL, qR;
+        quantise(b, off, qL, qR);
+        add(c, qL);
+        add(c1, qR);
+    }
+};
+
+// Push one particle (Appendix A): returns false if absorbed (wall = 0 at x=0,
+// 1 at x=L).  c, q updated in place.
+__device__ __forceinline__ bool advance(const StepParams &p, const SpeciesDev &sp,
+                                        const float *sE, unsigned long long *hist, int &c,
+                                        float4 &q, int &wall)
+{
+    float ax = gather_ax(p, sp, sE, c, q.x);
+    // v^{n+1/2} = v^{n-1/2} + a int beta dt
+    float vx = push_vx(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
+    DepositU64 dep{hist};
+    return move_and_deposit(p, sp, dep, c, q, vx, wall);
 }
 
 }  // namespace slpic

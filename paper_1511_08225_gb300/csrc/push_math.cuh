@@ -13,14 +13,15 @@
 //
 //     F(w) = (w sqrt(w^2+D') + D' asinh(w / sqrt(D'))) / 2.
 //
-// The push walks the pieces the line crosses (fast w < 0, slow band, fast
-// w > 0), spending the budget |a| dt of (*), and solves the last piece for
-// w_end.  Differences of F are formed without cancellation (see seg_integral),
-// and w_end itself is returned, so the new velocity keeps full FP32
-// precision even when |a| dt << |v|.  Small steps in a fast piece use the
-// series reversion of (*) to 4th order; larger ones use Newton from a
+// Most particles need no iteration (push_vx_easy): plain leapfrog inside the
+// band, or the 8th-order series reversion of (*) when the step is small
+// against the speed.  The rest walk the pieces the line crosses (fast w < 0,
+// slow band, fast w > 0), spending the budget |a| dt of (*), and solve the
+// last piece for w_end (push_vx_walk): by the series, or by Newton from a
 // one-sided bound (the piece integrand is convex for w > 0, concave for
-// w < 0, so Newton converges monotonically).
+// w < 0, so Newton converges monotonically).  Differences of F are formed
+// without cancellation (see seg_integral), and w_end itself is returned, so
+// the new velocity keeps full FP32 precision even when |a| dt << |v|.
 //
 // Quantised deposit: the bit-exact rule declared with slpic_charge_raw in
 // slpic.h; every FP32 operation uses an explicit round-to-nearest intrinsic
@@ -48,16 +49,31 @@ __device__ __forceinline__ float beta_q(int kind, float vx, float vy, float vz, 
     return __fdiv_rn(v0, __fsqrt_rn(__fadd_rn(s2, __fmul_rn(v0, v0))));
 }
 
+// rint(x) as an unsigned 64-bit integer, for 0 <= x < 2^41, from the bits of
+// rintf(x): the rounded value is an integer with at most 24 significant bits,
+// i.e. its mantissa (hidden bit included) shifted by exponent - 23.  Integer
+// shifts only: a float -> int64 conversion would run on the FP64 pipe, which is
+// narrow on this GPU.  Same value as llrintf (round to nearest, ties to even).
+__device__ __forceinline__ unsigned long long rint_u64(float x)
+{
+    unsigned bits = __float_as_uint(rintf(x));
+    if (bits == 0u)
+        return 0ULL;
+    int e = (int)(bits >> 23) - 127;  // unbiased exponent, 0 <= e <= 40
+    unsigned long long m = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
+    return e >= 23 ? (m << (e - 23)) : (m >> (23 - e));
+}
+
 // qT = rint(beta 2^40), qR = rint((beta*offset) 2^40); node c gets qT - qR,
 // node c+1 gets qR.
 __device__ __forceinline__ void quantise(float beta, float offset, unsigned long long &qL,
                                          unsigned long long &qR)
 {
     const float two40 = 1099511627776.0f;
-    long long r = __float2ll_rn(__fmul_rn(__fmul_rn(beta, offset), two40));
-    long long t = __float2ll_rn(__fmul_rn(beta, two40));
-    qR = (unsigned long long)r;
-    qL = (unsigned long long)(t - r);
+    unsigned long long r = rint_u64(__fmul_rn(__fmul_rn(beta, offset), two40));
+    unsigned long long t = rint_u64(__fmul_rn(beta, two40));
+    qR = r;
+    qL = t - r;
 }
 
 // int_{wa}^{wa+d} sqrt(w^2 + D) dw for a segment that does not cross w = 0
@@ -82,6 +98,40 @@ __device__ __forceinline__ float seg_integral(float wa, float ra, float d, float
     return t1 + t2;
 }
 
+// Series reversion of int_{wa}^{wa+d} sqrt(w^2 + D) dw = y about wa.  With
+// ra = sqrt(wa^2 + D), om = wa/ra and k = y/ra^2 (so D/ra^2 = 1 - om^2),
+//   d / ra = k (1 + b2 k + b3 k^2 + ... + b8 k^7) + O(k^9),
+// the b_i below (derived symbolically; b2..b4 by hand).  The truncation error is
+// below 6 k^9 ra for every om in [-1, 1], i.e. < 3e-8 ra for k <= 0.12.  The
+// integrand is analytic within |w - wa| < ra, so the series holds across w = 0
+// when D > 0; it must not be used across the Heaviside band edge.
+constexpr float kSeriesMax = 0.12f;
+
+__device__ __forceinline__ float series_poly(float om, float k)
+{
+    // explicit fused multiply-adds: every kernel that inlines this gets the same bits
+    const float o2 = om * om;
+    const float b2 = -0.5f * om;
+    const float b3 = __fmaf_rn(4.0f, o2, -1.0f) * (1.0f / 6.0f);
+    const float b4 = -om * __fmaf_rn(28.0f, o2, -13.0f) * (1.0f / 24.0f);
+    const float b5 = __fmaf_rn(__fmaf_rn(280.0f, o2, -188.0f), o2, 13.0f) * (1.0f / 120.0f);
+    const float b6 = -om * __fmaf_rn(__fmaf_rn(3640.0f, o2, -3188.0f), o2, 493.0f) * (1.0f / 720.0f);
+    const float b7 =
+        __fmaf_rn(__fmaf_rn(__fmaf_rn(58240.0f, o2, -62832.0f), o2, 15480.0f), o2, -493.0f) *
+        (1.0f / 5040.0f);
+    const float b8 =
+        -om * __fmaf_rn(__fmaf_rn(__fmaf_rn(1106560.0f, o2, -1417584.0f), o2, 483528.0f), o2,
+                        -37369.0f) *
+        (1.0f / 40320.0f);
+    float poly = __fmaf_rn(b8, k, b7);
+    poly = __fmaf_rn(poly, k, b6);
+    poly = __fmaf_rn(poly, k, b5);
+    poly = __fmaf_rn(poly, k, b4);
+    poly = __fmaf_rn(poly, k, b3);
+    poly = __fmaf_rn(poly, k, b2);
+    return __fmaf_rn(poly, k, 1.0f);
+}
+
 // Solve int_{wa}^{wa+d} sqrt(w^2 + D) dw = y for d in [0, dmax], on a piece
 // where w keeps the sign of wa (wa >= 0: convex; wa < 0: concave).
 __device__ __forceinline__ float solve_seg(float wa, float D, float y, float dmax)
@@ -89,15 +139,8 @@ __device__ __forceinline__ float solve_seg(float wa, float D, float y, float dma
     float ra = sqrtf(wa * wa + D);
     float inv_ra = 1.0f / ra;
     float kap = y * inv_ra * inv_ra;  // y / ra^2
-    if (kap <= 0.03f) {
-        // d/ra = k - (om/2) k^2 + ((4om^2-1)/6) k^3 + (om(13-28om^2)/24) k^4 + O(k^5),
-        // om = wa/ra: series reversion of ra d + (wa/2ra) d^2 + (D/6ra^3) d^3 - (D wa/8ra^5) d^4
-        float om = wa * inv_ra;
-        float om2 = om * om;
-        float c2 = -0.5f * om;
-        float c3 = (4.0f * om2 - 1.0f) * (1.0f / 6.0f);
-        float c4 = om * (13.0f - 28.0f * om2) * (1.0f / 24.0f);
-        float d = y * inv_ra * (1.0f + kap * (c2 + kap * (c3 + kap * c4)));
+    if (kap <= kSeriesMax) {
+        float d = y * inv_ra * series_poly(wa * inv_ra, kap);
         return fminf(d, dmax);
     }
     float d;
@@ -122,8 +165,8 @@ __device__ __forceinline__ float solve_seg(float wa, float D, float y, float dma
     return d;
 }
 
-// New vx of a 1D3V particle (E along x, so vy and vz are unchanged).
-__device__ __forceinline__ float push_vx(int kind, float ux, float uy, float uz, float ax,
+// The general walk over the pieces of (*) for the particles push_vx_easy leaves.
+__device__ __forceinline__ float push_vx_walk(int kind, float ux, float uy, float uz, float ax,
                                          float dt, float v0)
 {
     if (kind == SLPIC_BETA_ONE)
@@ -182,6 +225,76 @@ __device__ __forceinline__ float push_vx(int kind, float ux, float uy, float uz,
         w = hi;
     }
     return sg * (w + solve_seg(w, D, rem * v0, CUDART_INF_F));
+}
+
+// New vx of a 1D3V particle (E along x, so vy and vz are unchanged): the cases
+// that need no iteration.  Returns false (vx untouched) for the rest, which
+// push_vx handles; for every particle it accepts, push_vx gives the same bits.
+//   - beta == 1, or no field;
+//   - Heaviside with both ends of the step in the band |v| <= v0 (plain leapfrog);
+//   - a single smooth piece of (*) with k = |a| dt v0 / |v|^2 <= kSeriesMax
+//     (the series).  Without a band (relativistic beta, or |v_perp| >= v0) the
+//     integrand is analytic along the whole line; with a band the step must
+//     start above it, or start below it and provably end below it.
+__device__ __forceinline__ bool push_vx_easy(int kind, float ux, float uy, float uz, float ax,
+                                             float dt, float v0, float &vx)
+{
+    if (kind == SLPIC_BETA_ONE) {
+        vx = __fadd_rn(ux, __fmul_rn(ax, dt));  // plain leapfrog: int beta dt = dt
+        return true;
+    }
+    float A = fabsf(ax);
+    if (A == 0.0f) {
+        vx = ux;
+        return true;
+    }
+    float sg = (ax > 0.0f) ? 1.0f : -1.0f;
+    float wa = sg * ux;
+    float Dp = __fadd_rn(__fmul_rn(uy, uy), __fmul_rn(uz, uz));
+    float rem = __fmul_rn(A, dt);
+    float v02 = v0 * v0;
+    float D = Dp;
+    if (kind == SLPIC_BETA_HEAVISIDE) {
+        float wb = __fadd_rn(wa, rem);
+        // |v| is convex along the line: both ends in the band => beta = 1 all
+        // step and the push is plain leapfrog, bit for bit
+        if (__fadd_rn(__fmul_rn(wa, wa), Dp) <= v02 && __fadd_rn(__fmul_rn(wb, wb), Dp) <= v02) {
+            vx = sg * wb;
+            return true;
+        }
+        if (Dp < v02) {
+            float hi = sqrtf(v02 - Dp);
+            // above the band, or below it with a budget too small to reach it:
+            // below the band 1/beta = |v|/v0 >= 1, so reaching -hi costs >= -hi - wa
+            bool ok = wa >= hi || (wa < -hi && -hi - wa >= rem);
+            if (!ok)
+                return false;
+        }
+    } else {
+        D = Dp + v02;
+    }
+    float y = __fmul_rn(rem, v0);
+    float ra2 = __fmaf_rn(wa, wa, D);
+    // one reciprocal square root gives 1/ra, wa/ra and y/ra^2 (its ~2 ulp error
+    // moves d, already a small correction to wa, by ~1e-7 of itself)
+    float rs = rsqrtf(ra2);
+    float yr = __fmul_rn(y, rs);       // y / ra
+    float kap = __fmul_rn(yr, rs);     // y / ra^2
+    if (!(kap <= kSeriesMax))
+        return false;
+    vx = sg * __fmaf_rn(yr, series_poly(__fmul_rn(wa, rs), kap), wa);
+    return true;
+}
+
+// New vx, any particle: the easy cases above, else walk the pieces of (*) and
+// solve the last one (series or Newton, see solve_seg).
+__device__ __forceinline__ float push_vx(int kind, float ux, float uy, float uz, float ax,
+                                         float dt, float v0)
+{
+    float vx;
+    if (push_vx_easy(kind, ux, uy, uz, ax, dt, v0, vx))
+        return vx;
+    return push_vx_walk(kind, ux, uy, uz, ax, dt, v0);
 }
 
 // ---- counter-based SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) ---------------

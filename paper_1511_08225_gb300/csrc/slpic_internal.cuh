@@ -1,13 +1,15 @@
 // slpic_internal.cuh -- device data layout shared by the kernels and the C ABI.
 //
 // Particle store (per species, ping-pong buffer b = 0/1):
-//   cell[b][i]  int32   cell index c (0 <= c < N)
+//   cell[b][i]  int32   cell index c (0 <= c < N), or -1 for a hole (a particle
+//                       absorbed since the last compacting step)
 //   pv[b][i]    float4  {offset in [0,1), vx, vy, vz}
 // 20 bytes per macroparticle, structure-of-arrays so that one warp reads 512
-// contiguous bytes of float4 and 128 bytes of int32 per access.  The live
-// particles of time level n sit in buffer (n & 1); the particle kernel of step
-// n reads buffer (n & 1) and writes the survivors, compacted, to buffer
-// ((n+1) & 1).
+// contiguous bytes of float4 and 128 bytes of int32 per access.  The particles
+// of time level n sit in slots [0, count) of buffer (n & 1); the particle kernel
+// of step n reads buffer (n & 1) and writes buffer ((n+1) & 1).  Most steps write
+// every particle back to its own slot and leave a hole where one was absorbed;
+// every compaction interval a compacting step packs the survivors.
 //
 // Charge deposit: int64 fixed point, 2 time levels x species x nodes; the
 // deposit of rho^n is acc[(n & 1)][s][j].
@@ -26,11 +28,12 @@ constexpr int kMaxSpecies = SLPIC_MAX_SPECIES;
 // graph can run many steps with no host round trip.
 struct DevState {
     long long step;                                // time level n of the current particles
-    unsigned long long count[kMaxSpecies][2];      // live particles per buffer
+    unsigned long long count[kMaxSpecies][2];      // slots in use per buffer (live + holes)
     unsigned long long absorbed_step[kMaxSpecies][2];  // absorbed this step, per wall
     long long absorbed_total[kMaxSpecies][2];
     long long injected_total[kMaxSpecies];
     double src_frac[kMaxSpecies];                  // fractional macroparticles carried over
+    unsigned long long holes[kMaxSpecies][2];      // absorbed slots (cell < 0) per buffer
     int error;                                     // first SLPIC_ERR_* raised on the device
     int pad;
 };
@@ -43,7 +46,8 @@ struct SpeciesDev {
     float v0;        // speed limit
     float vth_src;   // sqrt(T_src/m) of the source Maxwellian (0 = not injected)
     int kind;        // SLPIC_BETA_*
-    double qw_dx;    // q * w / dx: charge density of one unit of deposit
+    double qw_dx;    // q * w / dx: charge density of one whole particle's deposit
+    double rho_unit; // q * w / dx * 2^-40: charge density of one fixed-point unit
     double w;        // g-weight
 };
 
@@ -60,6 +64,9 @@ struct StepParams {
     double dt64;
     double eps0;
     double phi_lo, phi_hi;
+    double inv_n;     // 1 / n_cells
+    double inv_dx;    // 1 / dx
+    double k2;        // dx^2 / eps0
     // source
     int src_mode;
     int src_ref;

@@ -169,12 +169,28 @@ def sheath_problem(n_cells=4096, dx=0.5, v0=0.05, ppc=1000, mass_ratio=73440.0, 
                        "len_cells": 0.10 * n_cells, "rate": float(rate), "ref_species": 1}}
 
 
-def load_state(prob: dict, seed: int | None = None):
+def load_state(prob: dict, seed: int | None = None, quiet: bool = False):
     """Initial FP32 particle state for every species: a list of
     (cell int32[n], offset float32[n], v float32[n,3]) with ppc * n_cells
-    particles per species, positions uniform over the grid, velocities drawn
-    from the speed-limited load g0 of each species."""
+    particles per species, velocities drawn from the speed-limited load g0.
+
+    quiet=False: positions uniform over the grid (independent draws).
+    quiet=True: every cell holds the same ppc velocities at offsets (k+1/2)/ppc,
+    and each species' weight w is reset so that sum(w beta) over a cell is
+    exactly n0 dx: the load is neutral cell by cell, with no noise field."""
     rng = make_rng(prob["seed"] if seed is None else seed)
+    if quiet:
+        out = []
+        N = int(prob["n_cells"])
+        for sp in prob["species"]:
+            ppc = int(sp["ppc"])
+            v = g_velocities(rng, ppc, sp["vth"], sp["v0"], sp["kind"], sp.get("vdim", 3))
+            r = np.sqrt((v * v).sum(1))
+            sp["w"] = float(prob["dx"] / (1.0 / _g_factor(sp["kind"], r, sp["v0"])).sum())
+            cell = np.repeat(np.arange(N, dtype=np.int32), ppc)
+            off = np.tile(((np.arange(ppc) + 0.5) / ppc).astype(np.float32), N)
+            out.append((cell, off, np.tile(v.astype(np.float32), (N, 1))))
+        return out
     out = []
     for sp in prob["species"]:
         n = int(sp["ppc"]) * int(prob["n_cells"])

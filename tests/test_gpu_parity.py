@@ -343,9 +343,9 @@ def test_empty_species_and_device_load():
 def test_kernel_timing_records_both_kernels():
     prob = _problem(N=64)
     sim = _sim(prob, _state(prob, (10_000, 10_000)))
-    binding.slpic_enable_kernel_timing(sim.h, 4)
-    sim.step(10)  # two timed replays of 4 steps, then 2 untimed steps
+    binding.slpic_enable_kernel_timing(sim.h, 4)  # rounded up to one 16-step cycle
+    sim.step(40)  # two timed replays of 16 steps, then 8 untimed steps
     pm, fm, n = binding.slpic_kernel_times(sim.h)
-    assert n == 4 and pm > 0 and fm > 0
+    assert n == 16 and pm > 0 and fm > 0
     assert binding.slpic_kernels_per_step(sim.h) == 2
     sim.close()
