@@ -462,8 +462,15 @@ __device__ double block_sum(double v, double *s_w)
     return t;
 }
 
+// Source particles k_inj of species s for this step (Sec. IV source, the readings of
+// LOSS_MATCHED / RATE): macroparticle i takes uniforms u_j = u24(SplitMix64(key, 8i+j))
+// for its position in the band (FP32, pinned operations) and a physical Maxwellian
+// velocity (Box-Muller): the g-source equals the f-source.  With `store` the
+// particle is written to slot base + i of buffer Q; its deposit is added to the
+// nodes in [n0, n1) only, so that every CTA of the field cluster can deposit the
+// part of the source that falls in its own nodes.
 __device__ void inject_species(const StepParams &p, int s, long long step, long long base,
-                               long long k, int Q)
+                               long long k, int Q, bool store, int n0, int n1)
 {
     const SpeciesDev &sp = p.sp[s];
     const int N = p.n_cells;
@@ -472,29 +479,36 @@ __device__ void inject_species(const StepParams &p, int s, long long step, long 
     for (long long i = threadIdx.x; i < k; i += blockDim.x) {
         unsigned long long b8 = 8ULL * (unsigned long long)i;
         float u0 = u24(sm64_at(key, b8 + 0));
+        float xc = __fadd_rn(p.src_lo_cells, __fmul_rn(u0, p.src_len_cells));
+        float fc = floorf(xc);
+        int c = (int)fc;
+        int c1 = c + 1;
+        if (p.periodic && c1 == N)
+            c1 = 0;
+        const bool mine0 = c >= n0 && c < n1, mine1 = c1 >= n0 && c1 < n1;
+        if (!store && !mine0 && !mine1)
+            continue;
+        float off = xc - fc;
         float u1 = u24(sm64_at(key, b8 + 1));
         float u2 = u24(sm64_at(key, b8 + 2));
         float u3 = u24(sm64_at(key, b8 + 3));
         float u4 = u24(sm64_at(key, b8 + 4));
-        float xc = __fadd_rn(p.src_lo_cells, __fmul_rn(u0, p.src_len_cells));
-        float fc = floorf(xc);
-        int c = (int)fc;
-        float off = xc - fc;
         // physical Maxwellian (Box-Muller); the g-source equals the f-source
         float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
         float s2, c2;
         sincospif(2.0f * u2, &s2, &c2);
         float4 q = make_float4(off, sp.vth_src * r1 * c2, sp.vth_src * r1 * s2,
                                sp.vth_src * r2 * cospif(2.0f * u4));
-        sp.cell[Q][base + i] = c;
-        sp.pv[Q][base + i] = q;
-        int c1 = c + 1;
-        if (p.periodic && c1 == N)
-            c1 = 0;
+        if (store) {
+            sp.cell[Q][base + i] = c;
+            sp.pv[Q][base + i] = q;
+        }
         unsigned long long qL, qR;
         quantise(beta_q(sp.kind, q.y, q.z, q.w, sp.v0), off, qL, qR);
-        atomicAdd(acc + c, qL);
-        atomicAdd(acc + c1, qR);
+        if (mine0)
+            atomicAdd(acc + c, qL);
+        if (mine1)
+            atomicAdd(acc + c1, qR);
     }
 }
 
@@ -602,7 +616,7 @@ __global__ void __launch_bounds__(kFT) k_potential(StepParams p)
 constexpr int kFC = kFieldClusterCtas;
 constexpr int kFCT = kFieldClusterThreads;
 constexpr int kFCW = kFCT / 32;
-constexpr int kFMaxChunk = 16;  // nodes per thread: nn <= kFC * kFCT * kFMaxChunk
+constexpr int kFMaxChunk = 8;   // nodes per thread: nn <= kFC * kFCT * kFMaxChunk
 
 template <int NV>
 __device__ __forceinline__ void block_sum_n(double (&v)[NV], double (*s_w)[32])
@@ -636,16 +650,25 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     __shared__ double s_w[3][32];
     __shared__ double s_tot[3];  // this CTA's: sum rho, sum r, sum (N-i) r
     __shared__ double s_scan[kFCW];
+    __shared__ double s_c[5];    // cta offset, mean, D0, P_{N-1}, k2 * mean
     __shared__ long long s_ninj[kMaxSpecies], s_base[kMaxSpecies];
+    __shared__ double s_frac[kMaxSpecies];
 
     DevState *st = p.st;
     const long long step = st->step;
     const int P = (int)(step & 1);
     const int Q = mode ? (P ^ 1) : P;  // deposit to solve from
     const int N = p.n_cells, nn = p.nn;
+    // this CTA's nodes [c0, c1); the thread's chunk of them
+    const int per_cta = (nn + kFC - 1) / kFC;
+    const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
+    const int chunk = (per_cta + kFCT - 1) / kFCT;
+    const int j0 = min(c1, c0 + (int)threadIdx.x * chunk), j1 = min(c1, j0 + chunk);
 
-    if (mode >= 1 && rank == 0) {
-        // ---- source injection (Sec. IV; counts as in the LOSS_MATCHED / RATE readings)
+    if (mode >= 1) {
+        // ---- source injection (Sec. IV; LOSS_MATCHED / RATE readings).  Every CTA
+        // derives the same counts from the same state; CTA 0 alone writes the
+        // particles and (after the exchange below) the bookkeeping.
         if (threadIdx.x == 0) {
             double S = 0.0;
             if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
@@ -656,45 +679,30 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
             }
             for (int s = 0; s < p.ns; ++s) {
                 long long k = 0;
+                double f = st->src_frac[s];
                 if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
-                    double f = st->src_frac[s] + S / p.sp[s].w;
+                    f += S / p.sp[s].w;
                     k = (long long)floor(f);
-                    st->src_frac[s] = f - (double)k;
+                    f -= (double)k;
                 }
                 // after an in-place step the output uses the input's slots (holes
                 // included); after a compacting step its count was reserved by atomics
                 long long have = (long long)(mode == 1 ? st->count[s][P] : st->count[s][P ^ 1]);
-                st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + st->absorbed_step[s][0] +
-                                                      st->absorbed_step[s][1]
-                                                : 0ULL;
                 long long room = p.sp[s].capacity - have;
-                if (k > room) {
-                    k = room;
-                    atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
-                }
-                s_ninj[s] = k;
+                s_ninj[s] = k > room ? -room - 1 : k;  // negative: truncated
                 s_base[s] = have;
-                st->count[s][P ^ 1] = (unsigned long long)(have + k);
-                st->injected_total[s] += k;
-                st->absorbed_total[s][0] += (long long)st->absorbed_step[s][0];
-                st->absorbed_total[s][1] += (long long)st->absorbed_step[s][1];
-                st->absorbed_step[s][0] = 0ULL;
-                st->absorbed_step[s][1] = 0ULL;
+                s_frac[s] = f;
             }
         }
         __syncthreads();
-        for (int s = 0; s < p.ns; ++s)
-            if (s_ninj[s] > 0)
-                inject_species(p, s, step, s_base[s], s_ninj[s], Q);
-        __threadfence();
+        for (int s = 0; s < p.ns; ++s) {
+            long long k = s_ninj[s] < 0 ? -s_ninj[s] - 1 : s_ninj[s];
+            if (k > 0)
+                inject_species(p, s, step, s_base[s], k, Q, rank == 0, c0, c1);
+        }
+        __syncthreads();  // this CTA's source deposits are in acc before it reads acc
     }
-    cl.sync();  // the injected particles' deposit is complete before anyone reads acc
 
-    // ---- this thread's nodes: CTA rank owns [c0, c1), the thread a chunk of it
-    const int per_cta = (nn + kFC - 1) / kFC;
-    const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
-    const int chunk = (per_cta + kFCT - 1) / kFCT;
-    const int j0 = min(c1, c0 + (int)threadIdx.x * chunk), j1 = min(c1, j0 + chunk);
     double rho[kFMaxChunk], pre[kFMaxChunk];
     double v3[3] = {0.0, 0.0, 0.0};  // sum rho (j < N), sum rho (1 <= j <= N-1), sum (N-j) rho
     double run = 0.0;
@@ -747,7 +755,6 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     cl.sync();
     // one thread gathers the other CTAs' sums (distributed shared memory) and forms
     // the step's scalars; FP64 is narrow on this GPU, so nothing is computed twice
-    __shared__ double s_c[5];  // cta offset, mean, D0, P_{N-1}, k2 * mean
     if (threadIdx.x == 0) {
         double tot_rho = 0.0, tot_r = 0.0, tot_w = 0.0, cta_off = 0.0;
         for (int r = 0; r < kFC; ++r) {
@@ -767,9 +774,13 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
         s_c[3] = p.k2 * (tot_r - mean * (double)(N - 1));  // P_{N-1}
         s_c[4] = p.k2 * mean;
     }
-    cl.sync();  // no CTA leaves (or reuses s_tot) while others still read it
-    const double cta_off = s_c[0], mean = s_c[1], D0 = s_c[2], P_last = s_c[3];
+    // this CTA's reads of the others' shared memory are done; the matching wait
+    // before exit keeps every CTA alive until all of them have read
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    __syncthreads();
+    const double cta_off = s_c[0], D0 = s_c[2], P_last = s_c[3];
     const double k2 = p.k2, k2mean = s_c[4];
+
     const double inv2dx = 0.5 * p.inv_dx;
     const double base_run = cta_off + thread_run;
 #pragma unroll
@@ -793,19 +804,35 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     }
 
     if (mode >= 1) {
-        // the deposit of rho^n and the input buffer are consumed: clear them for the
-        // next step's particle kernel, then advance the time level
-        const int total = p.ns * nn;
-        for (int idx = rank * kFCT + threadIdx.x; idx < total; idx += kFC * kFCT)
-            p.acc[(size_t)P * total + idx] = 0ULL;
+        // the deposit of rho^n is consumed: clear this CTA's nodes of it for the next
+        // step's particle kernel
+        for (int s = 0; s < p.ns; ++s)
+            for (int j = c0 + (int)threadIdx.x; j < c1; j += kFCT)
+                p.acc[((size_t)P * p.ns + s) * nn + j] = 0ULL;
+        // every CTA has read the step's state (before the exchange): CTA 0 updates it
         if (rank == 0 && threadIdx.x == 0) {
             for (int s = 0; s < p.ns; ++s) {
+                const bool cut = s_ninj[s] < 0;
+                const long long k = cut ? -s_ninj[s] - 1 : s_ninj[s];
+                if (cut)
+                    atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
+                st->src_frac[s] = s_frac[s];
+                st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + st->absorbed_step[s][0] +
+                                                      st->absorbed_step[s][1]
+                                                : 0ULL;
+                st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + k);
+                st->injected_total[s] += k;
+                st->absorbed_total[s][0] += (long long)st->absorbed_step[s][0];
+                st->absorbed_total[s][1] += (long long)st->absorbed_step[s][1];
+                st->absorbed_step[s][0] = 0ULL;
+                st->absorbed_step[s][1] = 0ULL;
                 st->count[s][P] = 0ULL;
                 st->holes[s][P] = 0ULL;
             }
             st->step = step + 1;
         }
     }
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------------

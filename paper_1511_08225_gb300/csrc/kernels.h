@@ -12,7 +12,7 @@ namespace slpic {
 constexpr int kParticleThreads = 256;
 constexpr int kFieldThreads = 1024;        // k_potential (one CTA)
 constexpr int kFieldClusterCtas = 8;       // k_field: one cluster of 8 CTAs
-constexpr int kFieldClusterThreads = 128;
+constexpr int kFieldClusterThreads = 256;
 
 size_t particle_smem_bytes(int nn);         // E + one int64 per node (allocation-free kernel)
 size_t particle_kernel_smem_bytes(int nn);  // k_particles_compact: queue + E + split deposit

@@ -166,7 +166,9 @@ __device__ __forceinline__ float solve_seg(float wa, float D, float y, float dma
 }
 
 // The general walk over the pieces of (*) for the particles push_vx_easy leaves.
-__device__ __forceinline__ float push_vx_walk(int kind, float ux, float uy, float uz, float ax,
+// Not inlined: it is long (asinh, Newton) and rare, and inlining it at every
+// call site overflows the instruction cache of the particle kernels.
+static __device__ __noinline__ float push_vx_walk(int kind, float ux, float uy, float uz, float ax,
                                          float dt, float v0)
 {
     if (kind == SLPIC_BETA_ONE)
