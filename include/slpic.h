@@ -227,16 +227,18 @@ int slpic_restore(slpic_t *h, const void *buf, size_t size);
 
 /* From now on slpic_step runs its steps as graphs of `steps_per_graph` steps
  * (1..4096, rounded up to a multiple of 16, the interval of the compacting
- * particle step; 0 turns timing off) in which CUDA events bracket the particle
- * kernel and the field/source kernel of every step.  The events are recorded
+ * particle step; 0 turns timing off) in which CUDA events bracket the kernels of
+ * every step.  The events are recorded
  * on the handle's stream, the stream the kernels run on; each graph replay
  * re-records them.  Steps beyond a multiple of steps_per_graph run untimed. */
 int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph);
 
-/* Mean device time (ms) of the particle kernel and of the field/source kernel
- * over the steps of the most recent timed graph replay (*steps of them; 0 if
- * none ran); synchronising. */
-int slpic_kernel_times(slpic_t *h, double *particle_ms, double *field_ms, int64_t *steps);
+/* Mean device time (ms) per step of the streaming particle kernel, of the kernel
+ * that pushes the particles needing iteration, and of the field/source kernel,
+ * over the steps of the most recent timed graph replay (*steps of them; 0 if none
+ * ran); synchronising.  Any pointer may be NULL. */
+int slpic_kernel_times(slpic_t *h, double *particle_ms, double *hard_ms, double *field_ms,
+                       int64_t *steps);
 
 /* Number of kernels one slpic_step(h, 1) launches. */
 int slpic_kernels_per_step(slpic_t *h, int *n);

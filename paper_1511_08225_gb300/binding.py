@@ -115,7 +115,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "slpic_save": (I, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "slpic_restore": (I, [P, P, ctypes.c_size_t]),
         "slpic_enable_kernel_timing": (I, [P, I64]),
-        "slpic_kernel_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D),
+        "slpic_kernel_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                    ctypes.POINTER(I64)]),
         "slpic_kernels_per_step": (I, [P, ctypes.POINTER(I)]),
         "slpic_particle_step_noalloc": (I, [ctypes.POINTER(slpic_config), I, I64, P, P, P, P, P,
@@ -304,10 +304,12 @@ def slpic_enable_kernel_timing(h, max_steps: int):
 
 
 def slpic_kernel_times(h):
-    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    """(particle_ms, hard_ms, field_ms, steps) per step of the last timed replay."""
+    a, b, c, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
     _check(h, load_library().slpic_kernel_times(h, ctypes.byref(a), ctypes.byref(b),
-                                                ctypes.byref(n)), "slpic_kernel_times")
-    return a.value, b.value, n.value
+                                                ctypes.byref(c), ctypes.byref(n)),
+           "slpic_kernel_times")
+    return a.value, b.value, c.value, n.value
 
 
 def slpic_kernels_per_step(h) -> int:

@@ -26,7 +26,9 @@ struct slpic_sim {
     cudaStream_t cap_stream = nullptr; // private stream used only for graph capture
     StepParams p{};
     int nn = 0, ns = 0;
-    int ctas = 1;        // particle-kernel CTAs per species
+    int ctas = 1;        // in-place particle-kernel CTAs per species
+    int ctas_c = 1;      // compacting particle-kernel CTAs per species
+    int hard_ctas = 1;   // k_hard CTAs
     int small_ctas = 1;  // CTAs per species for deposit / diag
     long long step = 0;  // host mirror of DevState::step
     bool dirty = true;   // particles loaded since the last deposit/solve
@@ -37,6 +39,7 @@ struct slpic_sim {
     double *d_E64 = nullptr, *d_phi = nullptr, *d_rho = nullptr;
     int32_t *d_cell[kMaxSpecies][2] = {};
     float4 *d_pv[kMaxSpecies][2] = {};
+    int32_t *d_hard[kMaxSpecies] = {};
     double *d_diag = nullptr;
     int *d_bad = nullptr;
     void *d_stage = nullptr;  // load/read-back staging
@@ -182,11 +185,13 @@ static void free_all(slpic_t *h)
     cudaFree(h->d_diag);
     cudaFree(h->d_bad);
     cudaFree(h->d_stage);
-    for (int s = 0; s < kMaxSpecies; ++s)
+    for (int s = 0; s < kMaxSpecies; ++s) {
         for (int b = 0; b < 2; ++b) {
             cudaFree(h->d_cell[s][b]);
             cudaFree(h->d_pv[s][b]);
         }
+        cudaFree(h->d_hard[s]);
+    }
     if (h->own_stream)
         cudaStreamDestroy(h->own_stream);
     if (h->cap_stream)
@@ -258,11 +263,13 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     CKC(cudaMalloc(&h->d_rho, sizeof(double) * nn));
     CKC(cudaMalloc(&h->d_diag, sizeof(double) * 2 * kMaxSpecies));
     CKC(cudaMalloc(&h->d_bad, sizeof(int)));
-    for (int s = 0; s < ns; ++s)
+    for (int s = 0; s < ns; ++s) {
         for (int b = 0; b < 2; ++b) {
             CKC(cudaMalloc(&h->d_cell[s][b], sizeof(int32_t) * cfg->species[s].capacity));
             CKC(cudaMalloc(&h->d_pv[s][b], sizeof(float4) * cfg->species[s].capacity));
         }
+        CKC(cudaMalloc(&h->d_hard[s], sizeof(int32_t) * cfg->species[s].capacity));
+    }
     CKC(cudaMemset(h->d_state, 0, sizeof(DevState)));
     CKC(cudaMemset(h->d_acc, 0, sizeof(unsigned long long) * 2 * ns * nn));
     CKC(cudaMemset(h->d_E, 0, sizeof(float) * nn));
@@ -270,13 +277,15 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     CKC(cudaMemset(h->d_phi, 0, sizeof(double) * nn));
     CKC(cudaMemset(h->d_rho, 0, sizeof(double) * nn));
     CKC(configure_kernels(nn));
-    int occ = 0;
-    CKC(particle_ctas_per_sm(nn, &occ));
-    if (occ < 1)
+    int occ = 0, occ_c = 0;
+    CKC(particle_ctas_per_sm(nn, &occ, &occ_c));
+    if (occ < 1 || occ_c < 1)
         return bail(SLPIC_ERR_INVALID, "particle kernel cannot be resident (shared memory)");
-    // persistent grid: every SM holds `occ` particle CTAs, shared among species
+    // persistent grids: every SM holds `occ` particle CTAs, shared among species
     h->ctas = std::max(1, sms * occ / ns);
+    h->ctas_c = std::max(1, sms * occ_c / ns);
     h->small_ctas = std::max(1, sms * 2 / ns);
+    h->hard_ctas = sms * 8;
 
     StepParams &p = h->p;
     p.n_cells = cfg->n_cells;
@@ -306,6 +315,7 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
             d.cell[b] = h->d_cell[s][b];
             d.pv[b] = h->d_pv[s][b];
         }
+        d.hard = h->d_hard[s];
         d.capacity = sp.capacity;
         d.qm = (float)(sp.q / sp.m);
         d.v0 = sp.beta_kind == SLPIC_BETA_ONE ? INFINITY : (float)sp.v0;
@@ -495,9 +505,9 @@ extern "C" int slpic_prepare(slpic_t *h)
 
 // Capture the timesteps first_step .. first_step + nsteps - 1 into a graph: an
 // in-place particle step, or a compacting one on every kCompactEvery-th step, each
-// followed by the field kernel.  With `timed`, event-record nodes (3 per step, from
-// h->events) bracket the particle and field kernels; every replay re-records them,
-// so the events describe the most recent replay.
+// followed by k_hard and the field kernel.  With `timed`, event-record nodes (4 per
+// step, from h->events) bracket the three kernels; every replay re-records them, so
+// the events describe the most recent replay.
 static int capture(slpic_t *h, long long first_step, int nsteps, bool timed,
                    cudaGraphExec_t *out)
 {
@@ -508,13 +518,16 @@ static int capture(slpic_t *h, long long first_step, int nsteps, bool timed,
         // "external" records become event-record nodes of the graph (a plain
         // record inside a capture only orders streams)
         if (timed)
-            cudaEventRecordWithFlags(h->events[3 * k], h->cap_stream, cudaEventRecordExternal);
-        launch_particles(h->p, h->ctas, compact, h->cap_stream);
+            cudaEventRecordWithFlags(h->events[4 * k], h->cap_stream, cudaEventRecordExternal);
+        launch_particles(h->p, compact ? h->ctas_c : h->ctas, compact, h->cap_stream);
         if (timed)
-            cudaEventRecordWithFlags(h->events[3 * k + 1], h->cap_stream, cudaEventRecordExternal);
+            cudaEventRecordWithFlags(h->events[4 * k + 1], h->cap_stream, cudaEventRecordExternal);
+        launch_hard(h->p, h->hard_ctas, compact, h->cap_stream);
+        if (timed)
+            cudaEventRecordWithFlags(h->events[4 * k + 2], h->cap_stream, cudaEventRecordExternal);
         launch_field(h->p, compact ? 2 : 1, h->cap_stream);
         if (timed)
-            cudaEventRecordWithFlags(h->events[3 * k + 2], h->cap_stream, cudaEventRecordExternal);
+            cudaEventRecordWithFlags(h->events[4 * k + 3], h->cap_stream, cudaEventRecordExternal);
     }
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) {
@@ -873,32 +886,36 @@ extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
     h->events.clear();
     h->t_launched = 0;
     h->t_len = steps_per_graph;
-    h->events.resize(3 * steps_per_graph);
+    h->events.resize(4 * steps_per_graph);
     for (auto &e : h->events)
         CK(h, cudaEventCreate(&e));
     return SLPIC_OK;
 }
 
-extern "C" int slpic_kernel_times(slpic_t *h, double *particle_ms, double *field_ms,
-                                  int64_t *steps)
+extern "C" int slpic_kernel_times(slpic_t *h, double *particle_ms, double *hard_ms,
+                                  double *field_ms, int64_t *steps)
 {
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
     CK(h, cudaStreamSynchronize(h->stream));
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0, c = 0.0;
     long long n = h->t_launched > 0 ? h->t_len : 0;
     for (long long k = 0; k < n; ++k) {
-        float x = 0.f, y = 0.f;
-        CK(h, cudaEventElapsedTime(&x, h->events[3 * k], h->events[3 * k + 1]));
-        CK(h, cudaEventElapsedTime(&y, h->events[3 * k + 1], h->events[3 * k + 2]));
+        float x = 0.f, y = 0.f, z = 0.f;
+        CK(h, cudaEventElapsedTime(&x, h->events[4 * k], h->events[4 * k + 1]));
+        CK(h, cudaEventElapsedTime(&y, h->events[4 * k + 1], h->events[4 * k + 2]));
+        CK(h, cudaEventElapsedTime(&z, h->events[4 * k + 2], h->events[4 * k + 3]));
         a += x;
         b += y;
+        c += z;
     }
     if (particle_ms)
         *particle_ms = n ? a / n : 0.0;
+    if (hard_ms)
+        *hard_ms = n ? b / n : 0.0;
     if (field_ms)
-        *field_ms = n ? b / n : 0.0;
+        *field_ms = n ? c / n : 0.0;
     if (steps)
         *steps = n;
     return SLPIC_OK;
@@ -908,6 +925,6 @@ extern "C" int slpic_kernels_per_step(slpic_t *h, int *n)
 {
     if (!h || !n)
         return SLPIC_ERR_INVALID;
-    *n = 2;
+    *n = 3;
     return SLPIC_OK;
 }

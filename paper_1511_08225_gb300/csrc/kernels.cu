@@ -28,8 +28,8 @@ namespace slpic {
 //
 // Divergence: most particles take the iteration-free push (push_vx_easy).  The few
 // that need the piece walk and Newton (strong field against a slow particle, band
-// crossings) would stall their whole warp, so they are queued in shared memory and
-// pushed later in full warps of queued particles.
+// crossings) would stall their whole warp, so their slots are listed and k_hard
+// pushes them afterwards, spread over the whole GPU.
 //
 // k_particles (most steps) writes each particle back to its own slot of the other
 // buffer and a hole (cell = -1) where one is absorbed; its warps never wait for one
@@ -42,7 +42,6 @@ constexpr int kPB = kParticleThreads;  // threads per CTA
 constexpr int kPI = 4;                 // particles per thread per tile
 constexpr int kPT = kPB * kPI;         // particles per tile
 constexpr int kNW = kPB / 32;
-constexpr int kQCap = kPT + kPB;       // queue: < kPB left + one tile
 static_assert(kPI * kNW == 32, "one warp scans the per-(item, warp) counts");
 
 // Compact the live items of NI per thread into out[] (block-wide; all threads call).
@@ -92,23 +91,34 @@ __device__ __forceinline__ void compact_store(const bool (&live)[NI], const int 
     __syncthreads();
 }
 
-size_t particle_kernel_smem_bytes(int nn)
+size_t particle_kernel_smem_bytes(int nn) { return (size_t)nn * 3 * sizeof(unsigned); }
+
+// Append the slots of this warp's hard particles to the species' list for k_hard
+// (one atomicAdd per warp).
+__device__ __forceinline__ void list_hard(bool hard, long long i, const SpeciesDev &sp,
+                                          unsigned long long *hard_n)
 {
-    return (size_t)kQCap * (sizeof(float4) + sizeof(int)) + (size_t)nn * 3 * sizeof(unsigned);
+    const unsigned hm = __ballot_sync(0xffffffffu, hard);
+    if (!hm)
+        return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long b = 0;
+    if (lane == 0)
+        b = atomicAdd(hard_n, (unsigned long long)__popc(hm));
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (hard)
+        sp.hard[b + __popc(hm & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
 __global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    float4 *s_qv = reinterpret_cast<float4 *>(smem);            // [kQCap] queued states
-    unsigned *s_lo = reinterpret_cast<unsigned *>(s_qv + kQCap);  // [nn] deposit, low words
-    unsigned *s_hi = s_lo + p.nn;                                 // [nn] deposit, high words
-    float *s_E = reinterpret_cast<float *>(s_hi + p.nn);          // [nn]
-    int *s_qc = reinterpret_cast<int *>(s_E + p.nn);              // [kQCap] queued cells
+    unsigned *s_lo = reinterpret_cast<unsigned *>(smem);  // [nn] deposit, low words
+    unsigned *s_hi = s_lo + p.nn;                         // [nn] deposit, high words
+    float *s_E = reinterpret_cast<float *>(s_hi + p.nn);  // [nn]
     __shared__ int s_off[32];
     __shared__ unsigned long long s_base;
     __shared__ unsigned int s_abs[2];
-    __shared__ int s_qn;
 
     const int s = blockIdx.y;
     const SpeciesDev &sp = p.sp[s];
@@ -129,38 +139,12 @@ __global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
     }
     if (threadIdx.x < 2)
         s_abs[threadIdx.x] = 0u;
-    if (threadIdx.x == 0)
-        s_qn = 0;
     __syncthreads();
 
     DepositSplit32 dep{s_lo, s_hi};
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
     const long long ntiles = (n + kPT - 1) / kPT;
     const long long t0 = ntiles * blockIdx.x / gridDim.x;
     const long long t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
-
-    // push the last m queued particles in full warps, then store the survivors
-    auto drain = [&](int m) {
-        const int base = s_qn - m;
-        bool live[1] = {(int)threadIdx.x < m};
-        int c[1] = {0};
-        float4 q[1] = {make_float4(0.f, 0.f, 0.f, 0.f)};
-        if (live[0]) {
-            c[0] = s_qc[base + threadIdx.x];
-            q[0] = s_qv[base + threadIdx.x];
-            float ax = gather_ax(p, sp, s_E, c[0], q[0].x);
-            float vx = push_vx_walk(sp.kind, q[0].y, q[0].z, q[0].w, ax, p.dt, sp.v0);
-            int wall = 0;
-            live[0] = move_and_deposit(p, sp, dep, c[0], q[0], vx, wall);
-            if (!live[0])
-                atomicAdd(&s_abs[wall], 1u);
-        }
-        __syncthreads();  // every queued entry read before the queue shrinks
-        if (threadIdx.x == 0)
-            s_qn = base;
-        compact_store<1>(live, c, q, s_off, &s_base, cnt_out, cout, vout);
-    };
 
     for (long long t = t0; t < t1; ++t) {
         const long long base = t * kPT;
@@ -191,28 +175,13 @@ __global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
                         atomicAdd(&s_abs[wall], 1u);
                 } else {
                     hard = true;
-                    live[k] = false;  // stored later by drain()
+                    live[k] = false;  // pushed, deposited and stored by k_hard
                 }
             }
-            unsigned hm = __ballot_sync(0xffffffffu, hard);
-            if (hm) {
-                int qb = 0;
-                if (lane == 0)
-                    qb = atomicAdd(&s_qn, __popc(hm));
-                qb = __shfl_sync(0xffffffffu, qb, 0);
-                if (hard) {
-                    int slot = qb + __popc(hm & lt);
-                    s_qc[slot] = c[k];
-                    s_qv[slot] = q[k];
-                }
-            }
+            list_hard(hard, base + k * kPB + threadIdx.x, sp, &p.st->hard_n[s]);
         }
         compact_store<kPI>(live, c, q, s_off, &s_base, cnt_out, cout, vout);
-        while (s_qn >= kPB)
-            drain(kPB);
     }
-    while (s_qn > 0)
-        drain(min(s_qn, kPB));
 
     for (int j = threadIdx.x; j < p.nn; j += kPB) {
         unsigned long long v = ((unsigned long long)s_hi[j] << 32) + s_lo[j];
@@ -225,20 +194,15 @@ __global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
 
 constexpr int kWI = 4;           // particles per lane per warp-tile
 constexpr int kWT = 32 * kWI;    // particles per warp-tile
-constexpr int kWQ = 64;          // per-warp queue: < 32 waiting + up to 32 new
 
-size_t particle_inplace_smem_bytes(int nn)
-{
-    return (size_t)kNW * kWQ * sizeof(int) + (size_t)nn * 3 * sizeof(unsigned);
-}
+size_t particle_inplace_smem_bytes(int nn) { return (size_t)nn * 3 * sizeof(unsigned); }
 
 __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    int *s_qi = reinterpret_cast<int *>(smem);                       // [kNW][kWQ] queued slots
-    unsigned *s_lo = reinterpret_cast<unsigned *>(s_qi + kNW * kWQ);  // [nn]
-    unsigned *s_hi = s_lo + p.nn;                                // [nn]
-    float *s_E = reinterpret_cast<float *>(s_hi + p.nn);         // [nn]
+    unsigned *s_lo = reinterpret_cast<unsigned *>(smem);  // [nn] deposit, low words
+    unsigned *s_hi = s_lo + p.nn;                         // [nn] deposit, high words
+    float *s_E = reinterpret_cast<float *>(s_hi + p.nn);  // [nn]
     __shared__ unsigned int s_abs[2];
 
     const int s = blockIdx.y;
@@ -263,40 +227,7 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
 
     DepositSplit32 dep{s_lo, s_hi};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    int *qi = s_qi + warp * kWQ;
-    int qn = 0;  // queue length, the same in every lane
     unsigned nabs0 = 0u, nabs1 = 0u;
-
-    // move, deposit and store one particle whose new vx is known
-    auto finish = [&](long long i, int c, float4 q, float vx) {
-        int wall = 0;
-        if (move_and_deposit(p, sp, dep, c, q, vx, wall)) {
-            __stcs(cout + i, c);
-            __stcs(vout + i, q);
-        } else {
-            __stcs(cout + i, -1);
-            if (wall)
-                ++nabs1;
-            else
-                ++nabs0;
-        }
-    };
-    // the general push for the particles queued at [from, from + m), one per lane;
-    // the queue holds slot numbers only, the particle is read again (from L2)
-    auto push_queued = [&](int from, int m) {
-        int ii = 0;
-        if (lane < m)
-            ii = qi[from + lane];
-        __syncwarp();  // slots read before they are refilled
-        if (lane < m) {
-            int c = cin[ii];
-            float4 q = vin[ii];
-            float ax = gather_ax(p, sp, s_E, c, q.x);
-            float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
-            finish(ii, c, q, vx);
-        }
-    };
 
     // warp-tiles of kWT consecutive particles: the CTA owns a contiguous range of
     // them and its warps take every kNW-th
@@ -329,28 +260,26 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
                 } else {
                     float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
                     float vx;
-                    if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, sp.v0, vx))
-                        finish(i, c[k], q[k], vx);
-                    else
-                        hard = true;
+                    if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, sp.v0, vx)) {
+                        int wall = 0;
+                        if (move_and_deposit(p, sp, dep, c[k], q[k], vx, wall)) {
+                            __stcs(cout + i, c[k]);
+                            __stcs(vout + i, q[k]);
+                        } else {
+                            __stcs(cout + i, -1);
+                            if (wall)
+                                ++nabs1;
+                            else
+                                ++nabs0;
+                        }
+                    } else {
+                        hard = true;  // k_hard pushes it and writes its slot
+                    }
                 }
             }
-            unsigned hm = __ballot_sync(0xffffffffu, hard);
-            if (hm) {
-                if (hard)
-                    qi[qn + __popc(hm & lt)] = (int)i;
-                qn += __popc(hm);
-                __syncwarp();
-                if (qn >= 32) {
-                    qn -= 32;
-                    push_queued(qn, 32);
-                }
-            }
+            list_hard(hard, i, sp, &p.st->hard_n[s]);
         }
     }
-    __syncwarp();
-    if (qn > 0)
-        push_queued(0, qn);
 
     unsigned a0 = __reduce_add_sync(0xffffffffu, nabs0);
     unsigned a1 = __reduce_add_sync(0xffffffffu, nabs1);
@@ -368,6 +297,72 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
     }
     if (threadIdx.x < 2 && s_abs[threadIdx.x])
         atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------------
+// k_hard: the particles the particle kernel listed (those needing the piece walk and
+// Newton).  They cluster (strong fields, the source band), and each needs a long
+// serial computation, so one warp holding many of them would become the critical
+// path; spread over a grid-stride loop of the whole GPU their latency hides.  The
+// field is gathered from global memory and the deposit goes straight to the global
+// int64 accumulator.  After an in-place step a particle returns to its slot (a hole
+// if absorbed); after a compacting step survivors are appended to the output.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_hard(StepParams p, int compact)
+{
+    __shared__ unsigned int s_abs[kMaxSpecies][2];
+    if (threadIdx.x < 2 * kMaxSpecies)
+        s_abs[threadIdx.x >> 1][threadIdx.x & 1] = 0u;
+    __syncthreads();
+    const long long step = *(volatile long long *)&p.st->step;
+    const int P = (int)(step & 1);
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int s = 0; s < p.ns; ++s) {
+        const SpeciesDev &sp = p.sp[s];
+        const long long nh = (long long)*(volatile unsigned long long *)&p.st->hard_n[s];
+        DepositU64 dep{p.acc + ((size_t)(P ^ 1) * p.ns + s) * p.nn};
+        for (long long b = gwarp * 32; b < nh; b += nwarps * 32) {
+            const long long t = b + lane;
+            bool live = false;
+            int c = 0, slot = 0;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < nh) {
+                slot = sp.hard[t];
+                c = sp.cell[P][slot];
+                q = sp.pv[P][slot];
+                float ax = gather_ax(p, sp, p.E, c, q.x);
+                float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
+                int wall = 0;
+                live = move_and_deposit(p, sp, dep, c, q, vx, wall);
+                if (!live)
+                    atomicAdd(&s_abs[s][wall], 1u);
+            }
+            if (compact) {
+                const unsigned m = __ballot_sync(0xffffffffu, live);
+                unsigned long long o = 0;
+                if (lane == 0 && m)
+                    o = atomicAdd(&p.st->count[s][P ^ 1], (unsigned long long)__popc(m));
+                o = __shfl_sync(0xffffffffu, o, 0);
+                if (live) {
+                    o += __popc(m & ((1u << lane) - 1u));
+                    sp.cell[P ^ 1][o] = c;
+                    sp.pv[P ^ 1][o] = q;
+                }
+            } else if (t < nh) {
+                sp.cell[P ^ 1][slot] = live ? c : -1;
+                if (live)
+                    sp.pv[P ^ 1][slot] = q;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kMaxSpecies) {
+        const int s = threadIdx.x >> 1, w = threadIdx.x & 1;
+        if (s < p.ns && s_abs[s][w])
+            atomicAdd(&p.st->absorbed_step[s][w], (unsigned long long)s_abs[s][w]);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -828,6 +823,7 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
                 st->absorbed_step[s][1] = 0ULL;
                 st->count[s][P] = 0ULL;
                 st->holes[s][P] = 0ULL;
+                st->hard_n[s] = 0ULL;
             }
             st->step = step + 1;
         }
@@ -946,18 +942,14 @@ cudaError_t configure_kernels(int nn)
                                 (int)field_smem_bytes(nn));
 }
 
-cudaError_t particle_ctas_per_sm(int nn, int *out)
+cudaError_t particle_ctas_per_sm(int nn, int *inplace, int *compacting)
 {
-    // one grid size serves both particle kernels: the smaller occupancy of the two
-    int a = 0, b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_particles, kPB,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(inplace, k_particles, kPB,
                                                                   particle_inplace_smem_bytes(nn));
     if (e != cudaSuccess)
         return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_particles_compact, kPB,
-                                                      particle_kernel_smem_bytes(nn));
-    *out = a < b ? a : b;
-    return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(compacting, k_particles_compact, kPB,
+                                                         particle_kernel_smem_bytes(nn));
 }
 
 void launch_particles(const StepParams &p, int ctas_per_species, bool compact, cudaStream_t st)
@@ -967,6 +959,11 @@ void launch_particles(const StepParams &p, int ctas_per_species, bool compact, c
         k_particles_compact<<<grid, kPB, particle_kernel_smem_bytes(p.nn), st>>>(p);
     else
         k_particles<<<grid, kPB, particle_inplace_smem_bytes(p.nn), st>>>(p);
+}
+
+void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st)
+{
+    k_hard<<<ctas, 256, 0, st>>>(p, compact ? 1 : 0);
 }
 
 void launch_field(const StepParams &p, int mode, cudaStream_t st)

@@ -15,15 +15,16 @@ constexpr int kFieldClusterCtas = 8;       // k_field: one cluster of 8 CTAs
 constexpr int kFieldClusterThreads = 256;
 
 size_t particle_smem_bytes(int nn);         // E + one int64 per node (allocation-free kernel)
-size_t particle_kernel_smem_bytes(int nn);  // k_particles_compact: queue + E + split deposit
-size_t particle_inplace_smem_bytes(int nn); // k_particles: per-warp queues + E + split deposit
+size_t particle_kernel_smem_bytes(int nn);  // k_particles_compact: E + split deposit
+size_t particle_inplace_smem_bytes(int nn); // k_particles: E + split deposit
 constexpr int kCompactEvery = 16;           // one compacting particle step per this many
 size_t field_smem_bytes(int nn);
 int field_max_nodes();
 cudaError_t configure_kernels(int nn);
-cudaError_t particle_ctas_per_sm(int nn, int *out);
+cudaError_t particle_ctas_per_sm(int nn, int *inplace, int *compacting);
 
 void launch_particles(const StepParams &p, int ctas_per_species, bool compact, cudaStream_t st);
+void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st);
 void launch_field(const StepParams &p, int mode, cudaStream_t st);
 void launch_potential(const StepParams &p, cudaStream_t st);
 void launch_deposit(const StepParams &p, int ctas_per_species, cudaStream_t st);

@@ -34,6 +34,7 @@ struct DevState {
     long long injected_total[kMaxSpecies];
     double src_frac[kMaxSpecies];                  // fractional macroparticles carried over
     unsigned long long holes[kMaxSpecies][2];      // absorbed slots (cell < 0) per buffer
+    unsigned long long hard_n[kMaxSpecies];        // particles listed for k_hard this step
     int error;                                     // first SLPIC_ERR_* raised on the device
     int pad;
 };
@@ -41,6 +42,7 @@ struct DevState {
 struct SpeciesDev {
     int32_t *cell[2];
     float4 *pv[2];
+    int32_t *hard;   // slots of this step's particles that need the iterative push
     long long capacity;
     float qm;        // q/m
     float v0;        // speed limit

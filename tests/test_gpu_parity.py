@@ -345,7 +345,7 @@ def test_kernel_timing_records_both_kernels():
     sim = _sim(prob, _state(prob, (10_000, 10_000)))
     binding.slpic_enable_kernel_timing(sim.h, 4)  # rounded up to one 16-step cycle
     sim.step(40)  # two timed replays of 16 steps, then 8 untimed steps
-    pm, fm, n = binding.slpic_kernel_times(sim.h)
-    assert n == 16 and pm > 0 and fm > 0
-    assert binding.slpic_kernels_per_step(sim.h) == 2
+    pm, hm, fm, n = binding.slpic_kernel_times(sim.h)
+    assert n == 16 and pm > 0 and hm > 0 and fm > 0
+    assert binding.slpic_kernels_per_step(sim.h) == 3
     sim.close()
