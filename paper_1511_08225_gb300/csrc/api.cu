@@ -324,6 +324,7 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
         d.qw_dx = sp.q * sp.w / cfg->dx;
         d.rho_unit = d.qw_dx / 1099511627776.0;
         d.w = sp.w;
+        d.inv_w = 1.0 / sp.w;
     }
     p.acc = h->d_acc;
     p.E = h->d_E;

@@ -593,47 +593,55 @@ __global__ void __launch_bounds__(kFT) k_potential(StepParams p)
 }
 
 // ---------------------------------------------------------------------------------
-// Field kernel: one thread-block cluster of kFC CTAs (one per SM), so that the FP64
-// work is spread over kFC SMs.  mode 0: E from acc[step&1] (after a load).
-// mode 1 / 2 (end of a step, after k_particles / k_particles_compact): CTA 0
-// injects this step's source particles after the output buffer's slots and deposits
-// them; then E from acc[(step+1)&1]; the consumed deposit and counters are cleared
-// and the step advances.
+// Field kernel: one thread-block cluster of kFC CTAs (one per SM).  mode 0: E from
+// acc[step&1] (after a load).  mode 1 / 2 (end of a step, after k_particles /
+// k_particles_compact and k_hard): CTA 0 writes this step's source particles after
+// the output buffer's slots, every CTA deposits the part of them in its own nodes;
+// then E from acc[(step+1)&1]; the consumed deposit and counters are cleared and
+// the step advances.
 //
-// With r_j = (dx^2/eps0)(rho_j - mean) for j = 1..N-1 and P_j = sum_{i=1..j} r_i,
-// D_j = phi_{j+1} - phi_j = D_0 - P_j and
-//   sum_{j=0}^{N-1} P_j = sum_{i=1}^{N-1} (N - i) r_i,
-// so one exchange of per-CTA sums (sum rho, sum r, sum (N-i) r) between the CTAs of
-// the cluster, through distributed shared memory, gives every CTA its prefix offset,
-// the periodic mean and D_0 (from phi_N - phi_0, or from sum_j D_j = 0 on a periodic
-// grid).  E_j = -(D_{j-1} + D_j)/(2 dx), one-sided at Dirichlet walls.
+// Poisson (Appendix A, Eq. LimPtclDynAppendixDotE), nodal 3-point stencil, solved
+// exactly by prefix sums instead of a sequential Thomas sweep.  With
+// D_j = phi_{j+1} - phi_j the stencil reads D_j - D_{j-1} = -(dx^2/eps0) rho_j, so
+//   D_j = D_0 - P_j,   P_j = k2 (sum_{i=1..j} rho_i - mean j),   k2 = dx^2/eps0,
+//   sum_{j=0}^{N-1} P_j = k2 (sum_{i=1}^{N-1} (N - i) rho_i - mean N(N-1)/2),
+// D_0 from phi_N - phi_0 = sum_j D_j (Dirichlet) or sum_j D_j = 0 with the mean of
+// rho removed (periodic), and E_j = -(D_{j-1} + D_j)/(2 dx), one-sided at walls.
+// Because rho_j = sum_s c_s acc_s[j] with integer deposits, every sum above is a sum
+// of integers: the prefix sums A_s[j] = sum_{i=1..j} acc_s[i], the weighted sum
+// W_s = sum (N-i) acc_s[i] and the total T_s are formed exactly in 128-bit integers
+// (one exchange of per-CTA totals through distributed shared memory), and FP64 -
+// narrow on this GPU - is used only to combine them into E.
 // ---------------------------------------------------------------------------------
 constexpr int kFC = kFieldClusterCtas;
 constexpr int kFCT = kFieldClusterThreads;
 constexpr int kFCW = kFCT / 32;
-constexpr int kFMaxChunk = 8;   // nodes per thread: nn <= kFC * kFCT * kFMaxChunk
 
-template <int NV>
-__device__ __forceinline__ void block_sum_n(double (&v)[NV], double (*s_w)[32])
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int o)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1)
-            v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        if (lane == 0)
-            s_w[k][warp] = v[k];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double t = 0.0;
-        for (int w = 0; w < kFCW; ++w)
-            t += s_w[k][w];
-        v[k] = t;
-    }
-    __syncthreads();
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    lo = __shfl_up_sync(0xffffffffu, lo, o);
+    hi = __shfl_up_sync(0xffffffffu, hi, o);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int o)
+{
+    unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+    lo = __shfl_down_sync(0xffffffffu, lo, o);
+    hi = __shfl_down_sync(0xffffffffu, hi, o);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ double u128_to_double(u128 v)
+{
+    unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;
+    double d = (double)lo;
+    if (hi)
+        d = fma((double)hi, 18446744073709551616.0, d);  // 2^64
+    return d;
 }
 
 __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
@@ -642,10 +650,13 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    __shared__ double s_w[3][32];
-    __shared__ double s_tot[3];  // this CTA's: sum rho, sum r, sum (N-i) r
-    __shared__ double s_scan[kFCW];
-    __shared__ double s_c[5];    // cta offset, mean, D0, P_{N-1}, k2 * mean
+    // per species: this CTA's sum over its rows 1..N-1 (R), weighted sum (W), total
+    // over nodes j < N (T)
+    __shared__ u128 s_tot[kMaxSpecies][3];
+    __shared__ u128 s_warp[kMaxSpecies][kFCW];
+    __shared__ u128 s_wpart[kMaxSpecies][kFCW][2];
+    __shared__ double s_c[4];  // D0, P_{N-1}, mean, (unused)
+    __shared__ u128 s_off[kMaxSpecies];
     __shared__ long long s_ninj[kMaxSpecies], s_base[kMaxSpecies];
     __shared__ double s_frac[kMaxSpecies];
 
@@ -653,7 +664,8 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     const long long step = st->step;
     const int P = (int)(step & 1);
     const int Q = mode ? (P ^ 1) : P;  // deposit to solve from
-    const int N = p.n_cells, nn = p.nn;
+    const int N = p.n_cells, nn = p.nn, ns = p.ns;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this CTA's nodes [c0, c1); the thread's chunk of them
     const int per_cta = (nn + kFC - 1) / kFC;
     const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
@@ -672,11 +684,11 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
             } else if (p.src_mode == SLPIC_SRC_RATE) {
                 S = p.src_rate * p.dt64;
             }
-            for (int s = 0; s < p.ns; ++s) {
+            for (int s = 0; s < ns; ++s) {
                 long long k = 0;
                 double f = st->src_frac[s];
                 if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
-                    f += S / p.sp[s].w;
+                    f = fma(S, p.sp[s].inv_w, f);
                     k = (long long)floor(f);
                     f -= (double)k;
                 }
@@ -690,7 +702,7 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
             }
         }
         __syncthreads();
-        for (int s = 0; s < p.ns; ++s) {
+        for (int s = 0; s < ns; ++s) {
             long long k = s_ninj[s] < 0 ? -s_ninj[s] - 1 : s_ninj[s];
             if (k > 0)
                 inject_species(p, s, step, s_base[s], k, Q, rank == 0, c0, c1);
@@ -698,101 +710,134 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
         __syncthreads();  // this CTA's source deposits are in acc before it reads acc
     }
 
-    double rho[kFMaxChunk], pre[kFMaxChunk];
-    double v3[3] = {0.0, 0.0, 0.0};  // sum rho (j < N), sum rho (1 <= j <= N-1), sum (N-j) rho
-    double run = 0.0;
+    // ---- integer sums over this thread's nodes, one species at a time: the rows'
+    // inclusive sum R (rows 1..N-1), the weighted sum W = sum (N-j) acc[j] and the
+    // total T (nodes j < N); then R's exclusive prefix over the CTA's threads.  The
+    // deposits are kept in shared memory for the E pass.
+    extern __shared__ __align__(16) unsigned char fsmem[];
+    unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(fsmem);  // [ns][per_cta]
+    u128 before[kMaxSpecies];
 #pragma unroll
-    for (int k = 0; k < kFMaxChunk; ++k) {
-        int j = j0 + k;
-        double r = 0.0;
-        if (j < j1) {
-            for (int s = 0; s < p.ns; ++s) {
-                long long a = (long long)__ldcg(p.acc + ((size_t)Q * p.ns + s) * nn + j);
-                r = fma(p.sp[s].rho_unit, (double)a, r);
-            }
-            p.rho[j] = r;
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        before[s] = 0;
+        if (s >= ns)
+            continue;
+        const unsigned long long *acc = p.acc + ((size_t)Q * ns + s) * nn;
+        u128 run = 0, wsum = 0, tsum = 0;
+        for (int j = j0; j < j1; ++j) {
+            const unsigned long long v = __ldcg(acc + j);
+            s_acc[s * per_cta + (j - c0)] = v;
             if (j < N)
-                v3[0] += r;
+                tsum += v;
             if (j >= 1 && j < N) {
-                run += r;
-                v3[1] += r;
-                v3[2] = fma((double)(N - j), r, v3[2]);
+                run += v;
+                wsum += (u128)v * (unsigned)(N - j);
             }
         }
-        rho[k] = r;
-        pre[k] = run;  // chunk-local inclusive prefix of rho over 1..N-1
-    }
-    // exclusive prefix of the chunk sums within the CTA
-    double thread_run = run;
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        double incl = thread_run;
+        u128 incl = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            double y = __shfl_up_sync(0xffffffffu, incl, o);
+            u128 y = shfl_up_u128(incl, o);
             if (lane >= o)
                 incl += y;
         }
         if (lane == 31)
-            s_scan[warp] = incl;
-        __syncthreads();
-        double before = 0.0;
-        for (int w = 0; w < warp; ++w)
-            before += s_scan[w];
-        thread_run = before + incl - thread_run;  // exclusive
+            s_warp[s][warp] = incl;
+        before[s] = incl - run;
+        // W and T: warp sums (integers, so order-free), one partial per warp
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            wsum += shfl_down_u128(wsum, o);
+            tsum += shfl_down_u128(tsum, o);
+        }
+        if (lane == 0) {
+            s_wpart[s][warp][0] = wsum;
+            s_wpart[s][warp][1] = tsum;
+        }
     }
-    block_sum_n<3>(v3, s_w);
-    if (threadIdx.x == 0) {
-        s_tot[0] = v3[0];
-        s_tot[1] = v3[1];
-        s_tot[2] = v3[2];
+    __syncthreads();
+    if (threadIdx.x < ns) {
+        u128 r = 0, w2 = 0, t2 = 0;
+        for (int w = 0; w < kFCW; ++w) {
+            r += s_warp[threadIdx.x][w];
+            w2 += s_wpart[threadIdx.x][w][0];
+            t2 += s_wpart[threadIdx.x][w][1];
+        }
+        s_tot[threadIdx.x][0] = r;
+        s_tot[threadIdx.x][1] = w2;
+        s_tot[threadIdx.x][2] = t2;
+    }
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        if (s >= ns)
+            break;
+        u128 wp = 0;
+        for (int w = 0; w < warp; ++w)
+            wp += s_warp[s][w];
+        before[s] += wp;
     }
     cl.sync();
-    // one thread gathers the other CTAs' sums (distributed shared memory) and forms
-    // the step's scalars; FP64 is narrow on this GPU, so nothing is computed twice
+    // gather the CTAs' totals (distributed shared memory), one remote load per
+    // thread, then one thread forms the step's scalars
+    __shared__ u128 s_all[kMaxSpecies][kFC][3];
+    if (threadIdx.x < ns * kFC * 3) {
+        const int s = threadIdx.x / (kFC * 3), r = (threadIdx.x / 3) % kFC, q = threadIdx.x % 3;
+        s_all[s][r][q] = *cl.map_shared_rank(&s_tot[s][q], r);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double tot_rho = 0.0, tot_r = 0.0, tot_w = 0.0, cta_off = 0.0;
-        for (int r = 0; r < kFC; ++r) {
-            const double *t = cl.map_shared_rank(s_tot, r);
-            tot_rho += t[0];
-            tot_r += t[1];
-            tot_w += t[2];
-            if (r < rank)
-                cta_off += t[1];
+        double sumW = 0.0, sumR = 0.0, sumT = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            u128 R = 0, W = 0, T = 0, off = 0;
+            for (int r = 0; r < kFC; ++r) {
+                R += s_all[s][r][0];
+                W += s_all[s][r][1];
+                T += s_all[s][r][2];
+                if (r < rank)
+                    off += s_all[s][r][0];
+            }
+            s_off[s] = off;
+            const double cs = p.sp[s].rho_unit;
+            sumR = fma(cs, u128_to_double(R), sumR);
+            sumW = fma(cs, u128_to_double(W), sumW);
+            sumT = fma(cs, u128_to_double(T), sumT);
         }
-        const double mean = p.periodic ? tot_rho * p.inv_n : 0.0;
-        // sum_{j=0}^{N-1} P_j with the mean removed: k2 (sum (N-i) rho_i - mean N(N-1)/2)
-        const double sumP = p.k2 * (tot_w - mean * 0.5 * (double)N * (double)(N - 1));
-        s_c[0] = cta_off;
-        s_c[1] = mean;
-        s_c[2] = p.periodic ? sumP * p.inv_n : (p.phi_hi - p.phi_lo + sumP) * p.inv_n;
-        s_c[3] = p.k2 * (tot_r - mean * (double)(N - 1));  // P_{N-1}
-        s_c[4] = p.k2 * mean;
+        const double mean = p.periodic ? sumT * p.inv_n : 0.0;
+        const double sumP = p.k2 * (sumW - mean * 0.5 * (double)N * (double)(N - 1));
+        s_c[0] = p.periodic ? sumP * p.inv_n : (p.phi_hi - p.phi_lo + sumP) * p.inv_n;  // D0
+        s_c[1] = p.k2 * (sumR - mean * (double)(N - 1));                                // P_{N-1}
+        s_c[2] = mean;
     }
     // this CTA's reads of the others' shared memory are done; the matching wait
     // before exit keeps every CTA alive until all of them have read
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     __syncthreads();
-    const double cta_off = s_c[0], D0 = s_c[2], P_last = s_c[3];
-    const double k2 = p.k2, k2mean = s_c[4];
+    const double D0 = s_c[0], P_last = s_c[1], mean = s_c[2];
+    const double k2 = p.k2, inv2dx = 0.5 * p.inv_dx;
 
-    const double inv2dx = 0.5 * p.inv_dx;
-    const double base_run = cta_off + thread_run;
+    // ---- E on this thread's nodes: P_{j-1} + P_j = k2 (sum_s c_s (A_s[j-1] + A_s[j])
+    //      - mean (2j - 1)), the integer pair sum converted once per species
+    u128 A[kMaxSpecies];  // A_s[j0 - 1] (prefix before the chunk's first row)
 #pragma unroll
-    for (int k = 0; k < kFMaxChunk; ++k) {
-        int j = j0 + k;
-        if (j >= j1)
-            break;
-        // P_j = k2 (sum_{i=1..j} rho_i - mean j)
-        double Pj = (j < N) ? fma(k2, base_run + pre[k], -k2mean * (double)j) : P_last;
+    for (int s = 0; s < kMaxSpecies; ++s)
+        A[s] = (s < ns) ? s_off[s] + before[s] : (u128)0;
+    for (int j = j0; j < j1; ++j) {
         double e;
         if (j == 0) {
-            e = p.periodic ? ((P_last - D0) - D0) * inv2dx : -D0 * p.inv_dx;
+            e = p.periodic ? ((P_last + 0.0) - 2.0 * D0) * inv2dx : -D0 * p.inv_dx;
         } else if (!p.periodic && j == N) {
             e = (P_last - D0) * p.inv_dx;
         } else {
-            double Pm = Pj - fma(k2, rho[k], -k2mean);  // P_{j-1}
-            e = ((Pm + Pj) - 2.0 * D0) * inv2dx;
+            double pair = 0.0;
+#pragma unroll
+            for (int s = 0; s < kMaxSpecies; ++s) {
+                if (s >= ns)
+                    break;
+                const u128 prev = A[s];
+                A[s] += s_acc[s * per_cta + (j - c0)];  // row j (1 <= j <= N-1)
+                pair = fma(p.sp[s].rho_unit, u128_to_double(prev + A[s]), pair);
+            }
+            e = (k2 * (pair - mean * (double)(2 * j - 1)) - 2.0 * D0) * inv2dx;
         }
         p.E64[j] = e;
         p.E[j] = (float)e;
@@ -801,12 +846,12 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     if (mode >= 1) {
         // the deposit of rho^n is consumed: clear this CTA's nodes of it for the next
         // step's particle kernel
-        for (int s = 0; s < p.ns; ++s)
+        for (int s = 0; s < ns; ++s)
             for (int j = c0 + (int)threadIdx.x; j < c1; j += kFCT)
-                p.acc[((size_t)P * p.ns + s) * nn + j] = 0ULL;
+                p.acc[((size_t)P * ns + s) * nn + j] = 0ULL;
         // every CTA has read the step's state (before the exchange): CTA 0 updates it
         if (rank == 0 && threadIdx.x == 0) {
-            for (int s = 0; s < p.ns; ++s) {
+            for (int s = 0; s < ns; ++s) {
                 const bool cut = s_ninj[s] < 0;
                 const long long k = cut ? -s_ninj[s] - 1 : s_ninj[s];
                 if (cut)
@@ -921,7 +966,7 @@ __global__ void k_unpack(const int32_t *csrc, const float4 *psrc, long long n, i
 // ---------------------------------------------------------------------------------
 size_t particle_smem_bytes(int nn) { return (size_t)nn * (sizeof(unsigned long long) + sizeof(float)); }
 size_t field_smem_bytes(int nn) { return (size_t)nn * sizeof(double); }
-int field_max_nodes() { return kFC * kFCT * kFMaxChunk; }
+int field_max_nodes() { return 1 << 16; }
 
 cudaError_t configure_kernels(int nn)
 {
@@ -936,6 +981,10 @@ cudaError_t configure_kernels(int nn)
         return e;
     e = cudaFuncSetAttribute(k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(nn * sizeof(unsigned long long)));
+    if (e != cudaSuccess)
+        return e;
+    e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)field_cluster_smem_bytes(nn, kMaxSpecies));
     if (e != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(k_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -966,9 +1015,14 @@ void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st)
     k_hard<<<ctas, 256, 0, st>>>(p, compact ? 1 : 0);
 }
 
+size_t field_cluster_smem_bytes(int nn, int ns)
+{
+    return (size_t)ns * ((nn + kFC - 1) / kFC) * sizeof(unsigned long long);
+}
+
 void launch_field(const StepParams &p, int mode, cudaStream_t st)
 {
-    k_field<<<kFC, kFCT, 0, st>>>(p, mode);
+    k_field<<<kFC, kFCT, field_cluster_smem_bytes(p.nn, p.ns), st>>>(p, mode);
 }
 
 void launch_potential(const StepParams &p, cudaStream_t st)

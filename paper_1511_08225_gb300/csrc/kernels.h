@@ -19,6 +19,7 @@ size_t particle_kernel_smem_bytes(int nn);  // k_particles_compact: E + split de
 size_t particle_inplace_smem_bytes(int nn); // k_particles: E + split deposit
 constexpr int kCompactEvery = 16;           // one compacting particle step per this many
 size_t field_smem_bytes(int nn);
+size_t field_cluster_smem_bytes(int nn, int ns);
 int field_max_nodes();
 cudaError_t configure_kernels(int nn);
 cudaError_t particle_ctas_per_sm(int nn, int *inplace, int *compacting);

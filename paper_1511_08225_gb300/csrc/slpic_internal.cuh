@@ -51,6 +51,7 @@ struct SpeciesDev {
     double qw_dx;    // q * w / dx: charge density of one whole particle's deposit
     double rho_unit; // q * w / dx * 2^-40: charge density of one fixed-point unit
     double w;        // g-weight
+    double inv_w;    // 1 / w
 };
 
 // Everything a kernel needs, passed by value (fixed at graph capture; the
