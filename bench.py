@@ -139,7 +139,7 @@ def hbm_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cu", "push_math.cuh", "slpic_internal.cuh"):
+    for f in ("kernels.cu", "particle_step.cuh", "push_math.cuh", "slpic_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1511_08225_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -457,53 +457,46 @@ __device__ double block_sum(double v, double *s_w)
     return t;
 }
 
-// Source particles k_inj of species s for this step (Sec. IV source, the readings of
+// Source particles of species s for this step (Sec. IV source, the readings of
 // LOSS_MATCHED / RATE): macroparticle i takes uniforms u_j = u24(SplitMix64(key, 8i+j))
 // for its position in the band (FP32, pinned operations) and a physical Maxwellian
-// velocity (Box-Muller): the g-source equals the f-source.  With `store` the
-// particle is written to slot base + i of buffer Q; its deposit is added to the
-// nodes in [n0, n1) only, so that every CTA of the field cluster can deposit the
-// part of the source that falls in its own nodes.
+// velocity (Box-Muller): the g-source equals the f-source.  This CTA makes the
+// particles i = first, first + stride, ... < k, writes them to slots base + i of
+// buffer Q and adds their deposit to acc[Q].
 __device__ void inject_species(const StepParams &p, int s, long long step, long long base,
-                               long long k, int Q, bool store, int n0, int n1)
+                               long long k, int Q, int first, int stride)
 {
     const SpeciesDev &sp = p.sp[s];
     const int N = p.n_cells;
     const unsigned long long key = sm64_stream(p.seed, (unsigned long long)step, (unsigned)s);
     unsigned long long *acc = p.acc + ((size_t)Q * p.ns + s) * p.nn;
-    for (long long i = threadIdx.x; i < k; i += blockDim.x) {
+    for (long long i = first + (long long)threadIdx.x * stride; i < k;
+         i += (long long)blockDim.x * stride) {
         unsigned long long b8 = 8ULL * (unsigned long long)i;
         float u0 = u24(sm64_at(key, b8 + 0));
-        float xc = __fadd_rn(p.src_lo_cells, __fmul_rn(u0, p.src_len_cells));
-        float fc = floorf(xc);
-        int c = (int)fc;
-        int c1 = c + 1;
-        if (p.periodic && c1 == N)
-            c1 = 0;
-        const bool mine0 = c >= n0 && c < n1, mine1 = c1 >= n0 && c1 < n1;
-        if (!store && !mine0 && !mine1)
-            continue;
-        float off = xc - fc;
         float u1 = u24(sm64_at(key, b8 + 1));
         float u2 = u24(sm64_at(key, b8 + 2));
         float u3 = u24(sm64_at(key, b8 + 3));
         float u4 = u24(sm64_at(key, b8 + 4));
+        float xc = __fadd_rn(p.src_lo_cells, __fmul_rn(u0, p.src_len_cells));
+        float fc = floorf(xc);
+        int c = (int)fc;
+        float off = xc - fc;
         // physical Maxwellian (Box-Muller); the g-source equals the f-source
         float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
         float s2, c2;
         sincospif(2.0f * u2, &s2, &c2);
         float4 q = make_float4(off, sp.vth_src * r1 * c2, sp.vth_src * r1 * s2,
                                sp.vth_src * r2 * cospif(2.0f * u4));
-        if (store) {
-            sp.cell[Q][base + i] = c;
-            sp.pv[Q][base + i] = q;
-        }
+        sp.cell[Q][base + i] = c;
+        sp.pv[Q][base + i] = q;
+        int c1 = c + 1;
+        if (p.periodic && c1 == N)
+            c1 = 0;
         unsigned long long qL, qR;
         quantise(beta_q(sp.kind, q.y, q.z, q.w, sp.v0), off, qL, qR);
-        if (mine0)
-            atomicAdd(acc + c, qL);
-        if (mine1)
-            atomicAdd(acc + c1, qR);
+        atomicAdd(acc + c, qL);
+        atomicAdd(acc + c1, qR);
     }
 }
 
@@ -595,10 +588,10 @@ __global__ void __launch_bounds__(kFT) k_potential(StepParams p)
 // ---------------------------------------------------------------------------------
 // Field kernel: one thread-block cluster of kFC CTAs (one per SM).  mode 0: E from
 // acc[step&1] (after a load).  mode 1 / 2 (end of a step, after k_particles /
-// k_particles_compact and k_hard): CTA 0 writes this step's source particles after
-// the output buffer's slots, every CTA deposits the part of them in its own nodes;
-// then E from acc[(step+1)&1]; the consumed deposit and counters are cleared and
-// the step advances.
+// k_particles_compact and k_hard): the CTAs make this step's source particles (every
+// kFC-th each), write them after the output buffer's slots and deposit them; then E
+// from acc[(step+1)&1]; the consumed deposit and counters are cleared and the step
+// advances.
 //
 // Poisson (Appendix A, Eq. LimPtclDynAppendixDotE), nodal 3-point stencil, solved
 // exactly by prefix sums instead of a sequential Thomas sweep.  With
@@ -674,9 +667,11 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
 
     if (mode >= 1) {
         // ---- source injection (Sec. IV; LOSS_MATCHED / RATE readings).  Every CTA
-        // derives the same counts from the same state; CTA 0 alone writes the
-        // particles and (after the exchange below) the bookkeeping.
-        if (threadIdx.x == 0) {
+        // derives the same counts from the same state (thread s for species s) and
+        // makes every kFC-th particle; CTA 0 writes the bookkeeping after the
+        // exchange below, when every CTA has read the state.
+        const int s = threadIdx.x;
+        if (s < ns) {
             double S = 0.0;
             if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
                 int r = p.src_ref;
@@ -684,30 +679,30 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
             } else if (p.src_mode == SLPIC_SRC_RATE) {
                 S = p.src_rate * p.dt64;
             }
-            for (int s = 0; s < ns; ++s) {
-                long long k = 0;
-                double f = st->src_frac[s];
-                if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
-                    f = fma(S, p.sp[s].inv_w, f);
-                    k = (long long)floor(f);
-                    f -= (double)k;
-                }
-                // after an in-place step the output uses the input's slots (holes
-                // included); after a compacting step its count was reserved by atomics
-                long long have = (long long)(mode == 1 ? st->count[s][P] : st->count[s][P ^ 1]);
-                long long room = p.sp[s].capacity - have;
-                s_ninj[s] = k > room ? -room - 1 : k;  // negative: truncated
-                s_base[s] = have;
-                s_frac[s] = f;
+            long long k = 0;
+            double f = st->src_frac[s];
+            if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
+                f = fma(S, p.sp[s].inv_w, f);
+                k = (long long)floor(f);
+                f -= (double)k;
             }
+            // after an in-place step the output uses the input's slots (holes
+            // included); after a compacting step its count was reserved by atomics
+            long long have = (long long)(mode == 1 ? st->count[s][P] : st->count[s][P ^ 1]);
+            long long room = p.sp[s].capacity - have;
+            s_ninj[s] = k > room ? -room - 1 : k;  // negative: truncated
+            s_base[s] = have;
+            s_frac[s] = f;
         }
         __syncthreads();
-        for (int s = 0; s < ns; ++s) {
-            long long k = s_ninj[s] < 0 ? -s_ninj[s] - 1 : s_ninj[s];
+        for (int sp_ = 0; sp_ < ns; ++sp_) {
+            long long k = s_ninj[sp_] < 0 ? -s_ninj[sp_] - 1 : s_ninj[sp_];
             if (k > 0)
-                inject_species(p, s, step, s_base[s], k, Q, rank == 0, c0, c1);
+                inject_species(p, sp_, step, s_base[sp_], k, Q, rank, kFC);
         }
-        __syncthreads();  // this CTA's source deposits are in acc before it reads acc
+        // every CTA's source deposits are in acc before any CTA reads acc
+        __threadfence();
+        cl.sync();
     }
 
     // ---- integer sums over this thread's nodes, one species at a time: the rows'
@@ -849,29 +844,31 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
         for (int s = 0; s < ns; ++s)
             for (int j = c0 + (int)threadIdx.x; j < c1; j += kFCT)
                 p.acc[((size_t)P * ns + s) * nn + j] = 0ULL;
-        // every CTA has read the step's state (before the exchange): CTA 0 updates it
-        if (rank == 0 && threadIdx.x == 0) {
-            for (int s = 0; s < ns; ++s) {
-                const bool cut = s_ninj[s] < 0;
-                const long long k = cut ? -s_ninj[s] - 1 : s_ninj[s];
-                if (cut)
-                    atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
-                st->src_frac[s] = s_frac[s];
-                st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + st->absorbed_step[s][0] +
-                                                      st->absorbed_step[s][1]
-                                                : 0ULL;
-                st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + k);
-                st->injected_total[s] += k;
-                st->absorbed_total[s][0] += (long long)st->absorbed_step[s][0];
-                st->absorbed_total[s][1] += (long long)st->absorbed_step[s][1];
-                st->absorbed_step[s][0] = 0ULL;
-                st->absorbed_step[s][1] = 0ULL;
-                st->count[s][P] = 0ULL;
-                st->holes[s][P] = 0ULL;
-                st->hard_n[s] = 0ULL;
-            }
-            st->step = step + 1;
+        // every CTA has read the step's state (before the exchange): CTA 0 updates it,
+        // thread s for species s
+        if (rank == 0 && threadIdx.x < ns) {
+            const int s = threadIdx.x;
+            const bool cut = s_ninj[s] < 0;
+            const long long k = cut ? -s_ninj[s] - 1 : s_ninj[s];
+            if (cut)
+                atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
+            const unsigned long long ab0 = st->absorbed_step[s][0], ab1 = st->absorbed_step[s][1];
+            st->src_frac[s] = s_frac[s];
+            st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + ab0 + ab1 : 0ULL;
+            st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + k);
+            st->injected_total[s] += k;
+            st->absorbed_total[s][0] += (long long)ab0;
+            st->absorbed_total[s][1] += (long long)ab1;
+            st->absorbed_step[s][0] = 0ULL;
+            st->absorbed_step[s][1] = 0ULL;
+            st->count[s][P] = 0ULL;
+            st->holes[s][P] = 0ULL;
+            st->hard_n[s] = 0ULL;
         }
+        // the step index is read at the start of every CTA: advance it last
+        __syncthreads();
+        if (rank == 0 && threadIdx.x == 0)
+            st->step = step + 1;
     }
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
