@@ -98,6 +98,22 @@ def lib():
         L.orc_inject.restype = None
         L.orc_inject.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _L,
                                  ctypes.c_float, ctypes.c_float, _D, _D, _P, _P]
+        L.orc_poisson2d_direct.restype = None
+        L.orc_poisson2d_direct.argtypes = [_I, _I, _D, _D, _P, _D, _D, _P]
+        L.orc_poisson2d_cg.restype = _I
+        L.orc_poisson2d_cg.argtypes = [_I, _I, _D, _D, _P, _D, _D, _D, _I, _P,
+                                       ctypes.POINTER(_D)]
+        L.orc_efield2d.restype = None
+        L.orc_efield2d.argtypes = [_I, _I, _D, _P, _P, _P]
+        L.orc_deposit2d.restype = None
+        L.orc_deposit2d.argtypes = [_I, _I, _D, _L, _P, _P, _P, _P, _I, _D, _D, _P]
+        L.orc_deposit2d_q40.restype = None
+        L.orc_deposit2d_q40.argtypes = [_I, _I, _L, _P, _P, _P, _I, ctypes.c_float, _P]
+        L.orc_push2d.restype = None
+        L.orc_push2d.argtypes = [_I, _I, _D, _D, _P, _P, _L, _P, _P, _P, _P, _D, _I, _D, _P]
+        L.orc_inject2d.restype = None
+        L.orc_inject2d.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _L,
+                                   ctypes.c_float, ctypes.c_float, _I, _D, _D, _P, _P, _P]
     return _lib
 
 
@@ -200,6 +216,51 @@ def splitmix64_at(key: int, i: int) -> int:
 
 def stream_key(seed: int, step: int, species: int) -> int:
     return lib().orc_stream_key(seed, step, species)
+
+
+# ---------------------------------------------------------------- 2D grid pieces
+# Node (i, j) of an nx x (ny+1) grid is entry [j, i] (periodic in x, plates at j = 0, ny).
+def poisson2d_direct(rho: np.ndarray, dx: float, phi_lo=0.0, phi_hi=0.0, eps0=1.0):
+    """5-point Poisson (Appendix A, Eq. LimPtclDynAppendixDotE, in 2D) solved
+    directly: DFT in x, Thomas per mode in y.  rho, phi: (ny+1, nx)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = rho.shape[0] - 1, rho.shape[1]
+    phi = np.zeros_like(rho)
+    lib().orc_poisson2d_direct(nx, ny, dx, eps0, _ptr(rho), phi_lo, phi_hi, _ptr(phi))
+    return phi
+
+
+def poisson2d_cg(rho: np.ndarray, dx: float, phi0=None, phi_lo=0.0, phi_hi=0.0, eps0=1.0,
+                 rtol=1e-8, maxit=100000):
+    """Jacobi-preconditioned CG on the same system from the guess phi0;
+    returns (phi, iterations (-1: not converged), relative residual)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = rho.shape[0] - 1, rho.shape[1]
+    phi = np.zeros_like(rho) if phi0 is None else np.array(phi0, dtype=np.float64)
+    res = ctypes.c_double(0.0)
+    it = lib().orc_poisson2d_cg(nx, ny, dx, eps0, _ptr(rho), phi_lo, phi_hi, rtol, maxit,
+                                _ptr(phi), ctypes.byref(res))
+    return phi, it, res.value
+
+
+def efield2d(phi: np.ndarray, dx: float):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ny, nx = phi.shape[0] - 1, phi.shape[1]
+    Ex, Ey = np.zeros_like(phi), np.zeros_like(phi)
+    lib().orc_efield2d(nx, ny, dx, _ptr(phi), _ptr(Ex), _ptr(Ey))
+    return Ex, Ey
+
+
+def deposit2d_q40(nx, ny, cell, offset, v, kind, v0) -> np.ndarray:
+    """The quantised 2D deposit rule (bit-exact contract, see the C file);
+    offset (n, 2) = (dx_, dy_); returns int64 (ny+1, nx)."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    offset = np.ascontiguousarray(offset, dtype=np.float32).reshape(-1, 2)
+    v = np.ascontiguousarray(v, dtype=np.float32).reshape(-1, 3)
+    acc = np.zeros((ny + 1, nx), dtype=np.int64)
+    lib().orc_deposit2d_q40(nx, ny, cell.size, _ptr(cell), _ptr(offset), _ptr(v), kind,
+                            np.float32(v0), _ptr(acc))
+    return acc
 
 
 # ---------------------------------------------------------------- the simulation
@@ -364,3 +425,126 @@ def _beta_vec(kind, r, v0):
     if kind == BETA_HEAVISIDE:
         return np.where(r <= v0, 1.0, v0 / np.maximum(r, 1e-300))
     return v0 / np.sqrt(r * r + v0 * v0)
+
+
+class OracleSim2D:
+    """Plain FP64 SLPIC in 2D3V: periodic in x, absorbing plates in y (the 2D
+    form of Appendix A with bilinear weighting).  The field is solved directly
+    (DFT x Thomas) unless ``cg=True``, which uses the Jacobi-PCG of the C file
+    warm-started from the previous potential.
+
+    ``prob``: nx, ny, dx, dt, phi_lo, phi_hi, eps0, seed, species (as in 1D),
+    source {mode, lo_cells, len_cells (in y), rate, ref_species}, cg_rtol.
+    """
+
+    def __init__(self, prob: dict, cg: bool = False):
+        self.prob = prob
+        self.nx, self.ny = int(prob["nx"]), int(prob["ny"])
+        self.dx, self.dt = float(prob["dx"]), float(prob["dt"])
+        self.eps0 = float(prob.get("eps0", 1.0))
+        self.cg = cg
+        self.sp = prob["species"]
+        ns = len(self.sp)
+        self.x = [np.zeros(0) for _ in range(ns)]
+        self.y = [np.zeros(0) for _ in range(ns)]
+        self.v = [np.zeros((0, 3)) for _ in range(ns)]
+        self.step_index = 0
+        self.frac = [0.0] * ns
+        self.flux = np.zeros((ns, 2), dtype=np.int64)
+        self.last_absorbed = np.zeros((ns, 2), dtype=np.int64)
+        shape = (self.ny + 1, self.nx)
+        self.dens = np.zeros((ns,) + shape)
+        self.rho = np.zeros(shape)
+        self.phi = np.zeros(shape)
+        self.Ex = np.zeros(shape)
+        self.Ey = np.zeros(shape)
+        self.cg_iters = 0
+
+    def load(self, s, x, y, v):
+        self.x[s] = np.concatenate([self.x[s], np.asarray(x, dtype=np.float64)])
+        self.y[s] = np.concatenate([self.y[s], np.asarray(y, dtype=np.float64)])
+        self.v[s] = np.concatenate([self.v[s], np.asarray(v, dtype=np.float64).reshape(-1, 3)])
+
+    def load_cells(self, s, cell, offset, v):
+        """FP32 (cell = cy*nx + cx, offset (dx_, dy_), v) -> FP64 positions."""
+        cell = np.asarray(cell, dtype=np.int64)
+        off = np.asarray(offset, dtype=np.float32).reshape(-1, 2).astype(np.float64)
+        x = ((cell % self.nx) + off[:, 0]) * self.dx
+        y = ((cell // self.nx) + off[:, 1]) * self.dx
+        self.load(s, x, y, np.asarray(v, dtype=np.float32).astype(np.float64))
+
+    def start(self):
+        self.deposit()
+        self.solve()
+
+    def deposit(self):
+        L = lib()
+        self.dens = np.zeros((len(self.sp), self.ny + 1, self.nx))
+        for s, sp in enumerate(self.sp):
+            x, y = np.ascontiguousarray(self.x[s]), np.ascontiguousarray(self.y[s])
+            v = np.ascontiguousarray(self.v[s])
+            L.orc_deposit2d(self.nx, self.ny, self.dx, x.size, _ptr(x), _ptr(y), _ptr(v), None,
+                            int(sp["kind"]), float(sp["v0"]), float(sp["w"]),
+                            _ptr(self.dens[s]))
+        self.rho = sum(float(sp["q"]) * self.dens[s] for s, sp in enumerate(self.sp))
+
+    def solve(self):
+        p = self.prob
+        lo, hi = p.get("phi_lo", 0.0), p.get("phi_hi", 0.0)
+        if self.cg:
+            self.phi, self.cg_iters, _ = poisson2d_cg(
+                self.rho, self.dx, self.phi, lo, hi, self.eps0, p.get("cg_rtol", 1e-8))
+        else:
+            self.phi = poisson2d_direct(self.rho, self.dx, lo, hi, self.eps0)
+        self.Ex, self.Ey = efield2d(self.phi, self.dx)
+
+    def push(self):
+        L = lib()
+        Ex, Ey = np.ascontiguousarray(self.Ex), np.ascontiguousarray(self.Ey)
+        for s, sp in enumerate(self.sp):
+            n = self.x[s].size
+            x, y = np.ascontiguousarray(self.x[s]), np.ascontiguousarray(self.y[s])
+            v = np.ascontiguousarray(self.v[s])
+            alive = np.ones(n, dtype=np.uint8)
+            flux = np.zeros(2, dtype=np.int64)
+            L.orc_push2d(self.nx, self.ny, self.dx, self.dt, _ptr(Ex), _ptr(Ey), n, _ptr(x),
+                         _ptr(y), _ptr(v), _ptr(alive), float(sp["q"]) / float(sp["m"]),
+                         int(sp["kind"]), float(sp["v0"]), _ptr(flux))
+            keep = alive.astype(bool)
+            self.x[s], self.y[s], self.v[s] = x[keep], y[keep], v[keep]
+            self.last_absorbed[s] = flux
+            self.flux[s] += flux
+
+    def inject(self):
+        src = self.prob.get("source", {"mode": SRC_NONE})
+        mode = int(src.get("mode", SRC_NONE))
+        if mode == SRC_NONE:
+            return
+        if mode == SRC_LOSS_MATCHED:
+            ref = int(src["ref_species"])
+            S = float(self.last_absorbed[ref].sum()) * float(self.sp[ref]["w"])
+        else:
+            S = float(src["rate"]) * self.dt
+        L = lib()
+        for s, sp in enumerate(self.sp):
+            if float(sp.get("T", 0.0)) <= 0.0:
+                continue
+            self.frac[s] += S / float(sp["w"])
+            k = int(np.floor(self.frac[s]))
+            self.frac[s] -= k
+            if k == 0:
+                continue
+            x, y, v = np.zeros(k), np.zeros(k), np.zeros((k, 3))
+            vth = np.sqrt(float(sp["T"]) / float(sp["m"]))
+            L.orc_inject2d(int(self.prob["seed"]), self.step_index, s, k,
+                           np.float32(src["lo_cells"]), np.float32(src["len_cells"]), self.nx,
+                           self.dx, vth, _ptr(x), _ptr(y), _ptr(v))
+            self.load(s, x, y, v)
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            self.push()
+            self.inject()
+            self.deposit()
+            self.solve()
+            self.step_index += 1

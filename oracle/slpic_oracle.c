@@ -596,3 +596,358 @@ double orc_beta_integral_closed(int kind, const double u[3], const double a[3], 
     }
     return 0.5 * (lo + hi);
 }
+
+/* ======================================================================== */
+/* 2D electrostatic SLPIC (2D3V), the same method on a rectangular grid:    */
+/* periodic in x, absorbing plates at fixed potential in y (Sec. IV walls). */
+/* Nodes (i, j), i = 0..nx-1 (node nx is node 0), j = 0..ny; node (i, j) is */
+/* entry j*nx + i.  Cell size dx in both directions.                        */
+/* ======================================================================== */
+
+/* Poisson, Appendix A Eq. (LimPtclDynAppendixDotE) with the 5-point        */
+/* stencil: -(sum of the 4 neighbours - 4 phi_ij)/dx^2 = rho_ij/eps0 on     */
+/* rows j = 1..ny-1; phi_{i,0} = phi_lo, phi_{i,ny} = phi_hi.               */
+/* Direct solve, written for checking rather than speed: a plain DFT in x   */
+/* turns the system into one tridiagonal system in y per Fourier mode k,    */
+/*   -P_{j-1} + (2 + lambda_k) P_j - P_{j+1} = dx^2 R_j / eps0,            */
+/*   lambda_k = 4 sin^2(pi k / nx),                                         */
+/* each solved by the Thomas algorithm; then the inverse DFT.               */
+static void thomas_const(int m, double diag, const double *d, double *x)
+{
+    /* -x_{i-1} + diag x_i - x_{i+1} = d_i, i = 0..m-1, x_{-1} = x_m = 0 */
+    if (m <= 0)
+        return;
+    double *cp = (double *)malloc(sizeof(double) * m);
+    double *dp = (double *)malloc(sizeof(double) * m);
+    for (int i = 0; i < m; ++i) {
+        double den = (i == 0) ? diag : diag + cp[i - 1];
+        cp[i] = -1.0 / den;
+        dp[i] = (i == 0) ? d[i] / den : (d[i] + dp[i - 1]) / den;
+    }
+    x[m - 1] = dp[m - 1];
+    for (int i = m - 2; i >= 0; --i)
+        x[i] = dp[i] - cp[i] * x[i + 1];
+    free(cp);
+    free(dp);
+}
+
+void orc_poisson2d_direct(int nx, int ny, double dx, double eps0, const double *rho,
+                          double phi_lo, double phi_hi, double *phi)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    int m = ny - 1; /* unknown rows j = 1..ny-1 */
+    double *cs = (double *)malloc(sizeof(double) * nx);
+    double *sn = (double *)malloc(sizeof(double) * nx);
+    for (int t = 0; t < nx; ++t) {
+        cs[t] = cos(two_pi * t / nx);
+        sn[t] = sin(two_pi * t / nx);
+    }
+    /* cosine and sine transforms of the right-hand side, per mode k and row */
+    double *ra = (double *)calloc((size_t)nx * m, sizeof(double));
+    double *rb = (double *)calloc((size_t)nx * m, sizeof(double));
+    for (int r = 0; r < m; ++r) {
+        int j = r + 1;
+        for (int k = 0; k < nx; ++k) {
+            double a = 0.0, b = 0.0;
+            for (int i = 0; i < nx; ++i) {
+                double f = dx * dx * rho[(size_t)j * nx + i] / eps0;
+                int t = (int)(((long)k * i) % nx);
+                a += f * cs[t];
+                b += f * sn[t];
+            }
+            /* boundary rows: constant in x, so only mode 0 sees them */
+            if (k == 0) {
+                if (j == 1)
+                    a += nx * phi_lo;
+                if (j == ny - 1)
+                    a += nx * phi_hi;
+            }
+            ra[(size_t)k * m + r] = a;
+            rb[(size_t)k * m + r] = b;
+        }
+    }
+    double *pa = (double *)malloc(sizeof(double) * (size_t)nx * m);
+    double *pb = (double *)malloc(sizeof(double) * (size_t)nx * m);
+    for (int k = 0; k < nx; ++k) {
+        double s = sin(0.5 * two_pi * k / nx);
+        double diag = 2.0 + 4.0 * s * s;
+        thomas_const(m, diag, ra + (size_t)k * m, pa + (size_t)k * m);
+        thomas_const(m, diag, rb + (size_t)k * m, pb + (size_t)k * m);
+    }
+    for (int i = 0; i < nx; ++i) {
+        phi[i] = phi_lo;
+        phi[(size_t)ny * nx + i] = phi_hi;
+    }
+    for (int r = 0; r < m; ++r) {
+        int j = r + 1;
+        for (int i = 0; i < nx; ++i) {
+            double f = 0.0;
+            for (int k = 0; k < nx; ++k) {
+                int t = (int)(((long)k * i) % nx);
+                f += pa[(size_t)k * m + r] * cs[t] + pb[(size_t)k * m + r] * sn[t];
+            }
+            phi[(size_t)j * nx + i] = f / nx;
+        }
+    }
+    free(cs);
+    free(sn);
+    free(ra);
+    free(rb);
+    free(pa);
+    free(pb);
+}
+
+/* The same system solved by conjugate gradients with the Jacobi (diagonal) */
+/* preconditioner, FP64, from the initial guess in phi (its rows 1..ny-1),  */
+/* until ||b - A phi||_2 <= rtol ||b||_2 or maxit iterations.  A is the    */
+/* stencil scaled by dx^2 (diagonal 4), b = dx^2 rho/eps0 plus the plates'  */
+/* potentials on rows 1 and ny-1.  Returns the iterations used (-1 if not  */
+/* converged); *rel_res gets the final relative residual.  The paper names */
+/* no 2D solver; this is the textbook preconditioned CG.                   */
+static void apply_A(int nx, int ny, const double *u, double *out)
+{
+    /* u, out: rows 1..ny-1 stored as r = j-1; rows 0 and ny are zero */
+    int m = ny - 1;
+    for (int r = 0; r < m; ++r)
+        for (int i = 0; i < nx; ++i) {
+            int ip = (i + 1) % nx, im = (i + nx - 1) % nx;
+            double s = u[(size_t)r * nx + ip] + u[(size_t)r * nx + im];
+            if (r > 0)
+                s += u[(size_t)(r - 1) * nx + i];
+            if (r < m - 1)
+                s += u[(size_t)(r + 1) * nx + i];
+            out[(size_t)r * nx + i] = 4.0 * u[(size_t)r * nx + i] - s;
+        }
+}
+
+static double dot(long n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long i = 0; i < n; ++i)
+        s += a[i] * b[i];
+    return s;
+}
+
+int orc_poisson2d_cg(int nx, int ny, double dx, double eps0, const double *rho,
+                     double phi_lo, double phi_hi, double rtol, int maxit, double *phi,
+                     double *rel_res)
+{
+    int m = ny - 1;
+    long n = (long)nx * m;
+    double *b = (double *)malloc(sizeof(double) * n);
+    double *x = (double *)malloc(sizeof(double) * n);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *z = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *q = (double *)malloc(sizeof(double) * n);
+    for (int rr = 0; rr < m; ++rr)
+        for (int i = 0; i < nx; ++i) {
+            int j = rr + 1;
+            double v = dx * dx * rho[(size_t)j * nx + i] / eps0;
+            if (j == 1)
+                v += phi_lo;
+            if (j == ny - 1)
+                v += phi_hi;
+            b[(size_t)rr * nx + i] = v;
+            x[(size_t)rr * nx + i] = phi[(size_t)j * nx + i];
+        }
+    apply_A(nx, ny, x, q);
+    for (long k = 0; k < n; ++k)
+        r[k] = b[k] - q[k];
+    double bn = sqrt(dot(n, b, b));
+    if (bn == 0.0)
+        bn = 1.0;
+    int it = 0, done = 0;
+    double res = sqrt(dot(n, r, r)) / bn;
+    if (res <= rtol)
+        done = 1;
+    for (long k = 0; k < n; ++k) {
+        z[k] = r[k] / 4.0; /* Jacobi: the diagonal of A is 4 */
+        p[k] = z[k];
+    }
+    double rz = dot(n, r, z);
+    while (!done && it < maxit) {
+        apply_A(nx, ny, p, q);
+        double alpha = rz / dot(n, p, q);
+        for (long k = 0; k < n; ++k) {
+            x[k] += alpha * p[k];
+            r[k] -= alpha * q[k];
+        }
+        ++it;
+        res = sqrt(dot(n, r, r)) / bn;
+        if (res <= rtol) {
+            done = 1;
+            break;
+        }
+        for (long k = 0; k < n; ++k)
+            z[k] = r[k] / 4.0;
+        double rz1 = dot(n, r, z);
+        double beta = rz1 / rz;
+        rz = rz1;
+        for (long k = 0; k < n; ++k)
+            p[k] = z[k] + beta * p[k];
+    }
+    for (int i = 0; i < nx; ++i) {
+        phi[i] = phi_lo;
+        phi[(size_t)ny * nx + i] = phi_hi;
+    }
+    for (int rr = 0; rr < m; ++rr)
+        for (int i = 0; i < nx; ++i)
+            phi[(size_t)(rr + 1) * nx + i] = x[(size_t)rr * nx + i];
+    if (rel_res)
+        *rel_res = res;
+    free(b);
+    free(x);
+    free(r);
+    free(z);
+    free(p);
+    free(q);
+    return done ? it : -1;
+}
+
+/* Nodal E = -grad phi: centred differences (periodic in x), one-sided at   */
+/* the plates in y.                                                          */
+void orc_efield2d(int nx, int ny, double dx, const double *phi, double *Ex, double *Ey)
+{
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t k = (size_t)j * nx + i;
+            int ip = (i + 1) % nx, im = (i + nx - 1) % nx;
+            Ex[k] = -(phi[(size_t)j * nx + ip] - phi[(size_t)j * nx + im]) / (2.0 * dx);
+            if (j == 0)
+                Ey[k] = -(phi[k + nx] - phi[k]) / dx;
+            else if (j == ny)
+                Ey[k] = -(phi[k] - phi[k - nx]) / dx;
+            else
+                Ey[k] = -(phi[k + nx] - phi[k - nx]) / (2.0 * dx);
+        }
+}
+
+/* Bilinear (area) charge assignment, the 2D form of the Appendix A deposit: */
+/* number density w beta S / dx^2 on the 4 nodes of the particle's cell.    */
+void orc_deposit2d(int nx, int ny, double dx, long n, const double *x, const double *y,
+                   const double *v, const uint8_t *alive, int kind, double v0, double w,
+                   double *dens)
+{
+    (void)ny;
+    for (long p = 0; p < n; ++p) {
+        if (alive && !alive[p])
+            continue;
+        double xi = x[p] / dx, yi = y[p] / dx;
+        int cx = (int)floor(xi), cy = (int)floor(yi);
+        double fx = xi - cx, fy = yi - cy;
+        double r = sqrt(v[3 * p] * v[3 * p] + v[3 * p + 1] * v[3 * p + 1] +
+                        v[3 * p + 2] * v[3 * p + 2]);
+        double q = w * orc_beta(kind, r, v0) / (dx * dx);
+        int cx1 = (cx + 1) % nx;
+        dens[(size_t)cy * nx + cx] += q * (1.0 - fx) * (1.0 - fy);
+        dens[(size_t)cy * nx + cx1] += q * fx * (1.0 - fy);
+        dens[(size_t)(cy + 1) * nx + cx] += q * (1.0 - fx) * fy;
+        dens[(size_t)(cy + 1) * nx + cx1] += q * fx * fy;
+    }
+}
+
+/* The quantised deposit rule in 2D: with beta as in orc_beta_f32 and FP32   */
+/* offsets (dx_, dy_) in [0,1), round-to-nearest each FP32 operation:        */
+/*   qT = rint(beta 2^40), qX = rint((beta dx_) 2^40), qY = rint((beta dy_) 2^40), */
+/*   qXY = rint(((beta dx_) dy_) 2^40);                                      */
+/*   node (c+1, c+1) += qXY, (c+1, c) += qX - qXY, (c, c+1) += qY - qXY,    */
+/*   (c, c) += qT - qX - qY + qXY          (int64; the four sum to qT).     */
+/* cell = cy*nx + cx; offsets interleaved (dx_, dy_) per particle.           */
+void orc_deposit2d_q40(int nx, int ny, long n, const int32_t *cell, const float *offset,
+                       const float *v, int kind, float v0, int64_t *acc)
+{
+    (void)ny;
+    const float scale = 1099511627776.0f; /* 2^40 */
+    for (long p = 0; p < n; ++p) {
+        int c = cell[p];
+        if (c < 0)
+            continue;
+        int cx = c % nx, cy = c / nx;
+        float b = orc_beta_f32(kind, v[3 * p], v[3 * p + 1], v[3 * p + 2], v0);
+        float bx = b * offset[2 * p];
+        float by = b * offset[2 * p + 1];
+        float bxy = bx * offset[2 * p + 1];
+        int64_t qT = llrintf(b * scale), qX = llrintf(bx * scale);
+        int64_t qY = llrintf(by * scale), qXY = llrintf(bxy * scale);
+        int cx1 = (cx + 1) % nx;
+        acc[(size_t)cy * nx + cx] += qT - qX - qY + qXY;
+        acc[(size_t)cy * nx + cx1] += qX - qXY;
+        acc[(size_t)(cy + 1) * nx + cx] += qY - qXY;
+        acc[(size_t)(cy + 1) * nx + cx1] += qXY;
+    }
+}
+
+/* Gather + push + move + walls, 2D: bilinear E at the particle, then        */
+/* Eq. (slpicIntegration) with a = (q/m)(Ex, Ey, 0); x wraps, a particle    */
+/* with y < 0 or y >= Ly is absorbed (flux[0] / flux[1]).                   */
+void orc_push2d(int nx, int ny, double dx, double dt, const double *Ex, const double *Ey,
+                long n, double *x, double *y, double *v, uint8_t *alive, double qm, int kind,
+                double v0, long *flux)
+{
+    double Lx = dx * nx, Ly = dx * ny;
+    for (long p = 0; p < n; ++p) {
+        if (!alive[p])
+            continue;
+        double xi = x[p] / dx, yi = y[p] / dx;
+        int cx = (int)floor(xi), cy = (int)floor(yi);
+        double fx = xi - cx, fy = yi - cy;
+        int cx1 = (cx + 1) % nx;
+        size_t k00 = (size_t)cy * nx + cx, k10 = (size_t)cy * nx + cx1;
+        size_t k01 = (size_t)(cy + 1) * nx + cx, k11 = (size_t)(cy + 1) * nx + cx1;
+        double w00 = (1.0 - fx) * (1.0 - fy), w10 = fx * (1.0 - fy);
+        double w01 = (1.0 - fx) * fy, w11 = fx * fy;
+        double ex = w00 * Ex[k00] + w10 * Ex[k10] + w01 * Ex[k01] + w11 * Ex[k11];
+        double ey = w00 * Ey[k00] + w10 * Ey[k10] + w01 * Ey[k01] + w11 * Ey[k11];
+        double a[3] = {qm * ex, qm * ey, 0.0};
+        double *vp = v + 3 * p;
+        double tau = orc_beta_integral(kind, vp, a, dt, v0);
+        for (int i = 0; i < 3; ++i)
+            vp[i] += a[i] * tau;
+        double r = sqrt(vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]);
+        double b = orc_beta(kind, r, v0);
+        double xn = x[p] + b * vp[0] * dt, yn = y[p] + b * vp[1] * dt;
+        xn -= Lx * floor(xn / Lx);
+        if (xn >= Lx)
+            xn -= Lx;
+        x[p] = xn;
+        y[p] = yn;
+        if (yn < 0.0) {
+            alive[p] = 0;
+            flux[0] += 1;
+        } else if (yn >= Ly) {
+            alive[p] = 0;
+            flux[1] += 1;
+        }
+    }
+}
+
+/* 2D volume source: the 1D source with the band across y and x uniform.   */
+/* Macroparticle k takes u_j = u24(SplitMix64(key, 8k + j)): y in cells =  */
+/* lo + u_0 len (FP32), x in cells = u_5 nx (FP32), velocity from          */
+/* (u_1..u_4) as in orc_inject.                                            */
+void orc_inject2d(uint64_t seed, uint64_t step, uint32_t species, long n_new,
+                  float src_lo_cells, float src_len_cells, int nx, double dx, double vth,
+                  double *x, double *y, double *v)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    uint64_t key = orc_stream_key(seed, step, species);
+    for (long k = 0; k < n_new; ++k) {
+        float u0 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 0));
+        double u1 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 1));
+        double u2 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 2));
+        double u3 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 3));
+        double u4 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 4));
+        float u5 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 5));
+        float yc = src_lo_cells + u0 * src_len_cells;
+        float xc = u5 * (float)nx;
+        if (xc >= (float)nx)
+            xc = 0.0f; /* u_5 = 1 is the periodic image of x = 0 */
+        x[k] = (double)xc * dx;
+        y[k] = (double)yc * dx;
+        double r1 = sqrt(-2.0 * log(u1)), r2 = sqrt(-2.0 * log(u3));
+        v[3 * k + 0] = vth * r1 * cos(two_pi * u2);
+        v[3 * k + 1] = vth * r1 * sin(two_pi * u2);
+        v[3 * k + 2] = vth * r2 * cos(two_pi * u4);
+    }
+}

@@ -58,4 +58,23 @@ void orc_inject(uint64_t seed, uint64_t step, uint32_t species, long n_new,
                 float src_lo_cells, float src_len_cells, double dx, double vth,
                 double *x, double *v);
 
+/* 2D: periodic x, plates in y; node (i, j) at j*nx + i, j = 0..ny */
+void orc_poisson2d_direct(int nx, int ny, double dx, double eps0, const double *rho,
+                          double phi_lo, double phi_hi, double *phi);
+int orc_poisson2d_cg(int nx, int ny, double dx, double eps0, const double *rho,
+                     double phi_lo, double phi_hi, double rtol, int maxit, double *phi,
+                     double *rel_res);
+void orc_efield2d(int nx, int ny, double dx, const double *phi, double *Ex, double *Ey);
+void orc_deposit2d(int nx, int ny, double dx, long n, const double *x, const double *y,
+                   const double *v, const uint8_t *alive, int kind, double v0, double w,
+                   double *dens);
+void orc_deposit2d_q40(int nx, int ny, long n, const int32_t *cell, const float *offset,
+                       const float *v, int kind, float v0, int64_t *acc);
+void orc_push2d(int nx, int ny, double dx, double dt, const double *Ex, const double *Ey,
+                long n, double *x, double *y, double *v, uint8_t *alive, double qm, int kind,
+                double v0, long *flux);
+void orc_inject2d(uint64_t seed, uint64_t step, uint32_t species, long n_new,
+                  float src_lo_cells, float src_len_cells, int nx, double dx, double vth,
+                  double *x, double *y, double *v);
+
 #endif

@@ -205,3 +205,42 @@ def random_state(rng, n: int, n_cells: int, vscale: float = 1.0):
     cell, off = uniform_cells(rng, n, n_cells)
     v = rng.normal(0.0, vscale, (n, 3)).astype(np.float32)
     return cell, off, v
+
+
+# ------------------------------------------------------------------ 2D problems
+def plasma2d_problem(nx=1024, ny=1024, dx=1.0, v0=0.1, ppc=64, mass_ratio=1836.0, T_e=1.0,
+                     T_i=0.1, kind=BETA_HEAVISIDE, dt=None, seed=SEED, capacity_factor=1.25,
+                     source_mode=SRC_LOSS_MATCHED, rate=0.0, cg_rtol=1e-8, cg_maxit=20000):
+    """2D3V electron-ion plasma between two absorbing plates at phi = 0 (y = 0 and
+    y = ny dx), periodic in x, loaded uniformly (ppc per species per cell), with a
+    central source band (45%..55% of y) re-injecting physical Maxwellian pairs.
+    dt defaults to dx / v0.  Weights are per unit length in z: w = n0 dx^2 <1/beta> / ppc."""
+    dt = dx / v0 if dt is None else dt
+    sp = []
+    for name, q, m, T in (("e", -1.0, 1.0, T_e), ("i", 1.0, mass_ratio, T_i)):
+        s = species(name, q, m, T, v0, kind, ppc=ppc, dx=dx)
+        s["w"] *= dx  # area weighting: n0 dx^2 <1/beta> / ppc
+        s["capacity"] = int(capacity_factor * ppc * nx * ny) + 4096
+        sp.append(s)
+    return {"ndim": 2, "nx": int(nx), "ny": int(ny), "dx": float(dx), "dt": float(dt),
+            "phi_lo": 0.0, "phi_hi": 0.0, "eps0": 1.0, "seed": int(seed), "species": sp,
+            "source": {"mode": int(source_mode), "lo_cells": 0.45 * ny, "len_cells": 0.10 * ny,
+                       "rate": float(rate), "ref_species": 1},
+            "cg_rtol": float(cg_rtol), "cg_maxit": int(cg_maxit)}
+
+
+def load_state2d(prob: dict, seed: int | None = None):
+    """Initial FP32 2D state per species: (cell int32 = cy*nx + cx, offset float32
+    (n, 2), v float32 (n, 3)), ppc * nx * ny particles per species, positions
+    uniform over the domain, velocities from the speed-limited load g0."""
+    rng = make_rng(prob["seed"] if seed is None else seed)
+    nx, ny = int(prob["nx"]), int(prob["ny"])
+    out = []
+    for sp in prob["species"]:
+        n = int(sp["ppc"]) * nx * ny
+        cx, ox = uniform_cells(rng, n, nx)
+        cy, oy = uniform_cells(rng, n, ny)
+        v = g_velocities(rng, n, sp["vth"], sp["v0"], sp["kind"], 3)
+        cell = (cy.astype(np.int64) * nx + cx).astype(np.int32)
+        out.append((cell, np.stack([ox, oy], axis=1).astype(np.float32), v.astype(np.float32)))
+    return out
