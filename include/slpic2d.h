@@ -1,0 +1,127 @@
+/*
+ * slpic2d.h -- C ABI of the 2D (2D3V) speed-limited PIC path.
+ *
+ * The same method as slpic.h (Appendix A, Eq. (slpicIntegration) of Werner
+ * et al., arXiv 1511.08225) on a rectangular grid of nx x ny square cells of
+ * side dx: periodic in x, absorbing plates at fixed potential in y (the Sec. IV
+ * walls turned into planes), bilinear (2D cloud-in-cell) gather and deposit,
+ * and the 5-point Poisson equation of Eq. (LimPtclDynAppendixDotE) solved each
+ * step by Jacobi-preconditioned conjugate gradients (the paper names no 2D
+ * solver; CG is the reading taken here) to a relative residual
+ * ||b - A phi||_2 / ||b||_2 <= cg_rtol, warm-started from the previous step's
+ * potential.
+ *
+ * Grid: nodes (i, j), i = 0..nx-1 (node nx is node 0), j = 0..ny; node (i, j)
+ * is entry j*nx + i of every nodal array (rho, phi, Ex, Ey, charge).  The
+ * plates are rows j = 0 (phi_lo) and j = ny (phi_hi).
+ * Particles: cell = cy*nx + cx (int32), offsets (ox, oy) in [0,1) (FP32),
+ * velocity (vx, vy, vz) (FP32); position ((cx + ox) dx, (cy + oy) dx).
+ *
+ * Deposit precision: int64 fixed point, 2^40 per unit of beta, with the 2D
+ * quantised rule (bit-exact across implementations that agree on the FP32
+ * particle state; every FP32 operation rounded to nearest, none fused):
+ *   beta as in slpic_charge_raw;  bx = beta*ox,  by = beta*oy,  bxy = bx*oy;
+ *   qT = rint(beta 2^40), qX = rint(bx 2^40), qY = rint(by 2^40),
+ *   qXY = rint(bxy 2^40);
+ *   node (cx+1, cy+1) += qXY, (cx+1, cy) += qX - qXY, (cx, cy+1) += qY - qXY,
+ *   (cx, cy) += qT - qX - qY + qXY            (the four sum to qT).
+ * rho_ij = sum_s q_s w_s / dx^2 * acc_s[ij] * 2^-40.
+ *
+ * General rules (return codes, handle ownership, host/device arrays,
+ * asynchrony) are those stated at the top of slpic.h.
+ */
+#ifndef SLPIC2D_H
+#define SLPIC2D_H
+
+#include "slpic.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t nx, ny;          /* cells in x (periodic) and in y (between the plates)   */
+    double dx;               /* cell side                                             */
+    double dt;               /* timestep; dt * v0_s <= dx required (SLPIC_ERR_CFL)     */
+    double phi_lo, phi_hi;   /* plate potentials at y = 0 and y = ny dx               */
+    double eps0;             /* permittivity                                          */
+    double max_speed;        /* SLPIC_BETA_ONE species: caller's bound on |v| (0 = unchecked) */
+    uint64_t seed;           /* source random stream                                  */
+    int32_t n_species;       /* 1..SLPIC_MAX_SPECIES                                  */
+    int32_t src_mode;        /* SLPIC_SRC_*                                           */
+    int32_t src_ref_species; /* LOSS_MATCHED: species whose losses are re-injected    */
+    int32_t cg_maxit;        /* iteration cap per solve (SLPIC_ERR_NOCONVERGE beyond) */
+    double src_lo_cells;     /* source band in y: start, in cells                     */
+    double src_len_cells;    /* source band in y: length, in cells (x: whole period)  */
+    double src_rate;         /* RATE: physical pairs per unit time                    */
+    double cg_rtol;          /* relative residual target of each solve (e.g. 1e-8)    */
+    slpic_species species[SLPIC_MAX_SPECIES];
+} slpic2d_config;
+
+typedef struct {
+    int64_t step;
+    double time;
+    int64_t count[SLPIC_MAX_SPECIES];       /* live macroparticles                      */
+    int64_t absorbed[SLPIC_MAX_SPECIES][2]; /* cumulative, at y = 0 / y = Ly            */
+    int64_t injected[SLPIC_MAX_SPECIES];    /* cumulative                               */
+    int32_t cg_iterations;                  /* iterations of the last solve             */
+    int32_t reserved;
+    int64_t cg_iterations_total;            /* over every solve since creation          */
+    double cg_rel_residual;                 /* ||b - A phi|| / ||b|| after the last solve */
+} slpic2d_diag;
+
+typedef struct slpic2d_sim slpic2d_t;
+
+/* Validate *cfg (nx >= 2, ny >= 2, dx > 0, dt > 0, 0 < cg_rtol < 1,
+ * cg_maxit > 0, species as in slpic_create, CFL as in slpic_create) and
+ * allocate on the current device: 2 x capacity particle slots per species
+ * (24 bytes each), nodal int64 deposits, and the FP64 CG vectors.
+ * *out is set only on success; slpic_create_error() explains a failure. */
+int slpic2d_create(const slpic2d_config *cfg, slpic2d_t **out);
+int slpic2d_destroy(slpic2d_t *h);
+const char *slpic2d_last_error(const slpic2d_t *h);
+/* Run subsequent work on this CUDA stream (cudaStream_t cast to void*; NULL =
+ * the legacy default stream). */
+int slpic2d_set_stream(slpic2d_t *h, void *stream);
+
+/* Append n particles of species s from host arrays: cell[n] (cy*nx + cx),
+ * offset[2n] interleaved (ox, oy) in [0,1), v[3n] interleaved (vx, vy, vz),
+ * the velocity being v^{-1/2}.  Checks every particle (SLPIC_ERR_INVALID)
+ * and the capacity (SLPIC_ERR_CAPACITY) before anything is stored. */
+int slpic2d_load_particles(slpic2d_t *h, int s, int64_t n, const int32_t *cell,
+                           const float *offset, const float *v);
+
+/* Deposit rho^0 from the loaded particles (beta of v^{-1/2}) and solve for
+ * phi^0, E^0.  Required once after loading, before slpic2d_step. */
+int slpic2d_prepare(slpic2d_t *h);
+
+/* Advance nsteps steps of Appendix A (per step: gather/push/move/absorb and
+ * deposit of rho^{n+1}; source injection; CG solve; E^{n+1}).  Asynchronous;
+ * the status of earlier device work is returned. */
+int slpic2d_step(slpic2d_t *h, int64_t nsteps);
+int slpic2d_synchronize(slpic2d_t *h);
+
+/* Current fields, host arrays of (ny+1)*nx entries; any pointer may be NULL. */
+int slpic2d_fields(slpic2d_t *h, double *rho, double *phi, float *Ex, float *Ey);
+/* The int64 deposit of species s for the current time level ((ny+1)*nx). */
+int slpic2d_charge_raw(slpic2d_t *h, int s, int64_t *acc);
+int slpic2d_particle_count(slpic2d_t *h, int s, int64_t *n);
+/* Copy out species s (capacity *n on entry, count on return; order is not
+ * preserved across steps). */
+int slpic2d_get_particles(slpic2d_t *h, int s, int32_t *cell, float *offset, float *v,
+                          int64_t *n);
+int slpic2d_diagnostics(slpic2d_t *h, slpic2d_diag *out);
+
+/* The field solve alone, for a given charge density: rho and phi host arrays
+ * of (ny+1)*nx entries (phi's rows 0 and ny are set to the plate potentials,
+ * its other rows are the initial guess on entry and the solution on return).
+ * Same CG kernel and tolerance as slpic2d_step; *iterations and *rel_residual
+ * (may be NULL) report the solve.  Leaves the simulation's own fields alone. */
+int slpic2d_solve_poisson(slpic2d_t *h, const double *rho, double *phi, int32_t *iterations,
+                          double *rel_residual);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -200,6 +200,11 @@ static void free_all(slpic_t *h)
 
 extern "C" const char *slpic_create_error(void) { return g_create_err.c_str(); }
 
+namespace slpic {
+// slpic2d_create reports its failures through slpic_create_error too
+void set_create_error(const std::string &msg) { g_create_err = msg; }
+}  // namespace slpic
+
 extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
 {
     g_create_err.clear();

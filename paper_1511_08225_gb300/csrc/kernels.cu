@@ -157,9 +157,8 @@ __global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
             live[k] = i < n;
             if (live[k]) {
                 c[k] = __ldcs(cin + i);
-                live[k] = c[k] >= 0;  // holes are dropped here
-                if (live[k])
-                    q[k] = __ldcs(vin + i);
+                q[k] = __ldcs(vin + i);  // not behind the cell: no dependent round trip
+                live[k] = c[k] >= 0;     // holes are dropped here
             }
         }
 #pragma unroll
@@ -245,9 +244,10 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
             act[k] = i < n;
             c[k] = -1;
             if (act[k]) {
+                // both loads issued together: a hole's stale float4 is read and
+                // ignored rather than waiting for its cell before the load
                 c[k] = __ldcs(cin + i);
-                if (c[k] >= 0)
-                    q[k] = __ldcs(vin + i);
+                q[k] = __ldcs(vin + i);
             }
         }
 #pragma unroll

@@ -1,0 +1,1153 @@
+// slpic2d.cu -- the 2D3V speed-limited PIC path behind include/slpic2d.h.
+//
+// Per step (Appendix A, Eq. slpicIntegration, on an nx x ny grid, periodic in x,
+// absorbing plates in y):
+//   k_particles2d  gather E (bilinear) -> push v (the same speed-limited solve as
+//                  1D, along the direction of a) -> move -> plates/wrap -> deposit
+//                  rho^{n+1} (quantised int64, bilinear) into the nodal arrays by
+//                  global atomics.  Absorbed particles leave holes (cell = -1); every
+//                  kCompact2d-th step the kernel writes the survivors packed instead.
+//   k_inject2d     one CTA: source particles appended and deposited; bookkeeping.
+//   k_cg2d         cooperative kernel: b from the deposits, Jacobi-PCG on the
+//                  5-point system (FP64 vectors, FP64 dot products in a fixed
+//                  order), then E^{n+1}; the deposits are cleared for the next step.
+//
+// Particle store per species, ping-pong buffers b = step & 1:
+//   cell[b][i] int32 (cy*nx + cx, -1 = hole), pv[b][i] float4 {ox, oy, vx, vy},
+//   vz[b][i] float  -- 24 bytes per macroparticle.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "push_math.cuh"
+#include "slpic2d.h"
+
+namespace slpic {
+void set_create_error(const std::string &msg);  // api.cu
+}
+
+namespace slpic2d {
+
+using namespace slpic;
+
+constexpr int kMaxS = SLPIC_MAX_SPECIES;
+constexpr int kThreads = 256;
+constexpr int kItems = 4;                       // particles per thread per tile
+constexpr int kTile = kThreads * kItems;
+constexpr int kWarps = kThreads / 32;
+constexpr int kCompact2d = 16;                  // compacting step interval
+constexpr int kCgThreads = 256;
+constexpr long long kBarrierSpins = 1LL << 23;  // bounded grid-barrier wait (~1 s)
+
+struct Species2D {
+    int32_t *cell[2];
+    float4 *pv[2];
+    float *vz[2];
+    long long capacity;
+    float qm, v0, vth_src;
+    int kind;
+    double w, inv_w;
+    double rho_unit;  // q w / dx^2 * 2^-40
+};
+
+struct State2D {
+    long long step;
+    unsigned long long count[kMaxS][2];   // slots in use (live + holes) per buffer
+    unsigned long long holes[kMaxS][2];
+    unsigned long long absorbed_step[kMaxS][2];
+    long long absorbed_total[kMaxS][2];
+    long long injected_total[kMaxS];
+    double src_frac[kMaxS];
+    long long cg_total;
+    double cg_res;
+    int cg_iters;
+    int error;
+    unsigned bar_count, bar_gen;  // grid barrier of k_cg2d
+};
+
+struct Params2D {
+    int nx, ny, nn, ns;
+    float dt, dt_dx;
+    double dx, dt64, k2;          // k2 = dx^2 / eps0
+    double phi_lo, phi_hi, rtol2;  // rtol^2
+    int cg_maxit;
+    int src_mode, src_ref;
+    float src_lo, src_len;
+    double src_rate;
+    unsigned long long seed;
+    Species2D sp[kMaxS];
+    unsigned long long *acc;  // [ns][nn] int64 deposits (two's complement)
+    float2 *E;                // [nn] (Ex, Ey)
+    double *phi, *r, *pA, *pB, *q;  // [nn]; r, p, q are zero on the plate rows
+    double *part;             // [3][grid] per-CTA partial sums
+    State2D *st;
+};
+
+// ---------------------------------------------------------------------------------
+// Velocity push with a = (ax, ay, 0): the speed-limited solve of Appendix A,
+// Eq. slpicIntegrationV, depends only on the component w of v along a and on
+// |v_perp|, so the 1D solve (push_vx with a along +x) gives w at the end of the
+// step and v changes by (w_end - w) in the direction of a.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void push_v2(int kind, float ux, float uy, float uz, float ax, float ay,
+                                        float dt, float v0, float &vx, float &vy)
+{
+    if (kind == SLPIC_BETA_ONE) {
+        vx = __fadd_rn(ux, __fmul_rn(ax, dt));
+        vy = __fadd_rn(uy, __fmul_rn(ay, dt));
+        return;
+    }
+    const float A = __fsqrt_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)));
+    if (A == 0.0f) {
+        vx = ux;
+        vy = uy;
+        return;
+    }
+    const float hx = __fdiv_rn(ax, A), hy = __fdiv_rn(ay, A);
+    const float wa = __fadd_rn(__fmul_rn(ux, hx), __fmul_rn(uy, hy));
+    const float cr = __fsub_rn(__fmul_rn(ux, hy), __fmul_rn(uy, hx));
+    const float vp = __fsqrt_rn(__fadd_rn(__fmul_rn(cr, cr), __fmul_rn(uz, uz)));
+    const float we = push_vx(kind, wa, vp, 0.0f, A, dt, v0);
+    const float dw = __fsub_rn(we, wa);
+    vx = __fadd_rn(ux, __fmul_rn(dw, hx));
+    vy = __fadd_rn(uy, __fmul_rn(dw, hy));
+}
+
+// the 2D quantised deposit rule stated in slpic2d.h
+__device__ __forceinline__ void deposit2d(unsigned long long *acc, int k00, int k10, int k01,
+                                          int k11, float b, float ox, float oy)
+{
+    const float two40 = 1099511627776.0f;
+    const float bx = __fmul_rn(b, ox), by = __fmul_rn(b, oy), bxy = __fmul_rn(bx, oy);
+    const unsigned long long qT = rint_u64(__fmul_rn(b, two40));
+    const unsigned long long qX = rint_u64(__fmul_rn(bx, two40));
+    const unsigned long long qY = rint_u64(__fmul_rn(by, two40));
+    const unsigned long long qXY = rint_u64(__fmul_rn(bxy, two40));
+    atomicAdd(acc + k00, qT - qX - qY + qXY);
+    atomicAdd(acc + k10, qX - qXY);
+    atomicAdd(acc + k01, qY - qXY);
+    atomicAdd(acc + k11, qXY);
+}
+
+// ---------------------------------------------------------------------------------
+// Particle step.  COMPACT = false: slot i of the input goes to slot i of the
+// output (a hole where a particle is absorbed); true: the survivors are packed
+// (one global atomic per CTA tile).
+// ---------------------------------------------------------------------------------
+template <bool COMPACT>
+__global__ void __launch_bounds__(kThreads) k_particles2d(Params2D p)
+{
+    __shared__ int s_cnt[kItems * kWarps];
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned s_abs[2];
+    const int s = blockIdx.y;
+    const Species2D &sp = p.sp[s];
+    const long long step = *(volatile long long *)&p.st->step;
+    const int P = (int)(step & 1);
+    const long long n = (long long)p.st->count[s][P];
+    const int32_t *__restrict__ cin = sp.cell[P];
+    const float4 *__restrict__ vin = sp.pv[P];
+    const float *__restrict__ zin = sp.vz[P];
+    int32_t *__restrict__ cout = sp.cell[P ^ 1];
+    float4 *__restrict__ vout = sp.pv[P ^ 1];
+    float *__restrict__ zout = sp.vz[P ^ 1];
+    unsigned long long *acc = p.acc + (size_t)s * p.nn;
+    const int nx = p.nx, ny = p.ny;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 2)
+        s_abs[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned na0 = 0, na1 = 0;
+
+    const long long ntiles = (n + kTile - 1) / kTile;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long base = t * kTile;
+        int c[kItems];
+        float4 q[kItems];
+        float z[kItems];
+        bool live[kItems];
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const long long i = base + k * kThreads + threadIdx.x;
+            live[k] = i < n;
+            c[k] = -1;
+            if (live[k]) {
+                c[k] = __ldcs(cin + i);
+                q[k] = __ldcs(vin + i);
+                z[k] = __ldcs(zin + i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const bool was = live[k];
+            live[k] = live[k] && c[k] >= 0;
+            if (live[k]) {
+                const int cy = c[k] / nx, cx = c[k] - cy * nx;
+                const int cx1 = (cx + 1 == nx) ? 0 : cx + 1;
+                const int k00 = cy * nx + cx, k10 = cy * nx + cx1;
+                const float2 e00 = __ldg(p.E + k00), e10 = __ldg(p.E + k10);
+                const float2 e01 = __ldg(p.E + k00 + nx), e11 = __ldg(p.E + k10 + nx);
+                const float ox = q[k].x, oy = q[k].y;
+                const float wx0 = __fsub_rn(1.0f, ox), wy0 = __fsub_rn(1.0f, oy);
+                const float ex = __fadd_rn(
+                    __fmul_rn(wy0, __fadd_rn(__fmul_rn(wx0, e00.x), __fmul_rn(ox, e10.x))),
+                    __fmul_rn(oy, __fadd_rn(__fmul_rn(wx0, e01.x), __fmul_rn(ox, e11.x))));
+                const float ey = __fadd_rn(
+                    __fmul_rn(wy0, __fadd_rn(__fmul_rn(wx0, e00.y), __fmul_rn(ox, e10.y))),
+                    __fmul_rn(oy, __fadd_rn(__fmul_rn(wx0, e01.y), __fmul_rn(ox, e11.y))));
+                float vx, vy;
+                push_v2(sp.kind, q[k].z, q[k].w, z[k], __fmul_rn(sp.qm, ex), __fmul_rn(sp.qm, ey),
+                        p.dt, sp.v0, vx, vy);
+                // x^{n+1} = x^n + beta(|v^{n+1/2}|) v^{n+1/2} dt, in cell units
+                const float b = beta_q(sp.kind, vx, vy, z[k], sp.v0);
+                const float xn = __fadd_rn(ox, __fmul_rn(__fmul_rn(b, vx), p.dt_dx));
+                const float yn = __fadd_rn(oy, __fmul_rn(__fmul_rn(b, vy), p.dt_dx));
+                const float fx = floorf(xn), fy = floorf(yn);
+                int ncx = cx + (int)fx, ncy = cy + (int)fy;
+                float dxn = __fsub_rn(xn, fx), dyn = __fsub_rn(yn, fy);
+                if (dxn >= 1.0f) {
+                    dxn = 0.0f;
+                    ++ncx;
+                }
+                if (dyn >= 1.0f) {
+                    dyn = 0.0f;
+                    ++ncy;
+                }
+                ncx %= nx;
+                if (ncx < 0)
+                    ncx += nx;
+                if (ncy < 0) {
+                    ++na0;
+                    live[k] = false;
+                } else if (ncy >= ny) {
+                    ++na1;
+                    live[k] = false;
+                } else {
+                    const int ncx1 = (ncx + 1 == nx) ? 0 : ncx + 1;
+                    const int m00 = ncy * nx + ncx, m10 = ncy * nx + ncx1;
+                    deposit2d(acc, m00, m10, m00 + nx, m10 + nx, b, dxn, dyn);
+                    c[k] = m00;
+                    q[k] = make_float4(dxn, dyn, vx, vy);
+                }
+            }
+            if (!COMPACT && was) {
+                const long long i = base + k * kThreads + threadIdx.x;
+                if (live[k]) {
+                    __stcs(cout + i, c[k]);
+                    __stcs(vout + i, q[k]);
+                    __stcs(zout + i, z[k]);
+                } else {
+                    __stcs(cout + i, -1);
+                }
+            }
+        }
+        if (COMPACT) {
+            unsigned mask[kItems];
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                mask[k] = __ballot_sync(0xffffffffu, live[k]);
+                if (lane == 0)
+                    s_cnt[k * kWarps + warp] = __popc(mask[k]);
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const int v = s_cnt[lane];
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o)
+                        incl += y;
+                }
+                s_cnt[lane] = incl - v;
+                const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                if (lane == 0)
+                    s_base = tot ? atomicAdd(&p.st->count[s][P ^ 1], (unsigned long long)tot) : 0ULL;
+            }
+            __syncthreads();
+            const unsigned long long ob = s_base;
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                if (live[k]) {
+                    const unsigned long long o = ob + (unsigned long long)s_cnt[k * kWarps + warp] +
+                                                 __popc(mask[k] & ((1u << lane) - 1u));
+                    __stcs(cout + o, c[k]);
+                    __stcs(vout + o, q[k]);
+                    __stcs(zout + o, z[k]);
+                }
+            }
+            __syncthreads();  // s_cnt / s_base reused by the next tile
+        }
+    }
+    na0 = __reduce_add_sync(0xffffffffu, na0);
+    na1 = __reduce_add_sync(0xffffffffu, na1);
+    if (lane == 0) {
+        if (na0)
+            atomicAdd(&s_abs[0], na0);
+        if (na1)
+            atomicAdd(&s_abs[1], na1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 && s_abs[threadIdx.x])
+        atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
+}
+
+// rho^0 from the particles of the current buffer (after a load)
+__global__ void __launch_bounds__(kThreads) k_deposit2d(Params2D p)
+{
+    const int s = blockIdx.y;
+    const Species2D &sp = p.sp[s];
+    const int P = (int)(p.st->step & 1);
+    const long long n = (long long)p.st->count[s][P];
+    unsigned long long *acc = p.acc + (size_t)s * p.nn;
+    const int nx = p.nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = sp.cell[P][i];
+        if (c < 0)
+            continue;
+        const float4 q = sp.pv[P][i];
+        const int cy = c / nx, cx = c - cy * nx;
+        const int cx1 = (cx + 1 == nx) ? 0 : cx + 1;
+        const int k00 = cy * nx + cx, k10 = cy * nx + cx1;
+        deposit2d(acc, k00, k10, k00 + nx, k10 + nx, beta_q(sp.kind, q.z, q.w, sp.vz[P][i], sp.v0),
+                  q.x, q.y);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Source (the 1D volume source with its band across y, x uniform over the period)
+// and the step's bookkeeping; one CTA.  Particle i of species s draws
+// u_j = u24(SplitMix64(key(seed, step, s), 8i + j)): y = lo + u_0 len, x = u_5 nx (cells,
+// FP32), a physical Maxwellian velocity from u_1..u_4 (Box-Muller).
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_inject2d(Params2D p, int compact)
+{
+    __shared__ long long s_k[kMaxS], s_base[kMaxS];
+    __shared__ double s_frac[kMaxS];
+    __shared__ int s_cut[kMaxS];
+    State2D *st = p.st;
+    const long long step = st->step;
+    const int P = (int)(step & 1);
+    const int ns = p.ns;
+    if (threadIdx.x < ns) {
+        const int s = threadIdx.x;
+        double S = 0.0;
+        if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
+            const int r = p.src_ref;
+            S = (double)(st->absorbed_step[r][0] + st->absorbed_step[r][1]) * p.sp[r].w;
+        } else if (p.src_mode == SLPIC_SRC_RATE) {
+            S = p.src_rate * p.dt64;
+        }
+        long long k = 0;
+        double f = st->src_frac[s];
+        if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
+            f = fma(S, p.sp[s].inv_w, f);
+            k = (long long)floor(f);
+            f -= (double)k;
+        }
+        // in place: the output uses the input's slots; compacted: counted by atomics
+        const long long have = (long long)(compact ? st->count[s][P ^ 1] : st->count[s][P]);
+        const long long room = p.sp[s].capacity - have;
+        s_cut[s] = k > room;
+        s_k[s] = k > room ? room : k;
+        s_base[s] = have;
+        s_frac[s] = f;
+    }
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+        const Species2D &sp = p.sp[s];
+        const unsigned long long key = sm64_stream(p.seed, (unsigned long long)step, (unsigned)s);
+        unsigned long long *acc = p.acc + (size_t)s * p.nn;
+        for (long long i = threadIdx.x; i < s_k[s]; i += blockDim.x) {
+            const unsigned long long b8 = 8ULL * (unsigned long long)i;
+            const float u0 = u24(sm64_at(key, b8 + 0)), u1 = u24(sm64_at(key, b8 + 1));
+            const float u2 = u24(sm64_at(key, b8 + 2)), u3 = u24(sm64_at(key, b8 + 3));
+            const float u4 = u24(sm64_at(key, b8 + 4)), u5 = u24(sm64_at(key, b8 + 5));
+            const float yc = __fadd_rn(p.src_lo, __fmul_rn(u0, p.src_len));
+            float xc = __fmul_rn(u5, (float)p.nx);
+            if (xc >= (float)p.nx)
+                xc = 0.0f;
+            const float fx = floorf(xc), fy = floorf(yc);
+            const int cx = (int)fx, cy = min(max((int)fy, 0), p.ny - 1);
+            const float ox = __fsub_rn(xc, fx), oy = __fsub_rn(yc, fy);
+            const float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
+            float s2, c2;
+            sincospif(2.0f * u2, &s2, &c2);
+            const float vx = sp.vth_src * r1 * c2, vy = sp.vth_src * r1 * s2;
+            const float vz = sp.vth_src * r2 * cospif(2.0f * u4);
+            const long long o = s_base[s] + i;
+            const int c = cy * p.nx + cx;
+            sp.cell[P ^ 1][o] = c;
+            sp.pv[P ^ 1][o] = make_float4(ox, oy, vx, vy);
+            sp.vz[P ^ 1][o] = vz;
+            const int cx1 = (cx + 1 == p.nx) ? 0 : cx + 1;
+            deposit2d(acc, c, cy * p.nx + cx1, c + p.nx, cy * p.nx + cx1 + p.nx,
+                      beta_q(sp.kind, vx, vy, vz, sp.v0), ox, oy);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < ns) {
+        const int s = threadIdx.x;
+        if (s_cut[s])
+            atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
+        const unsigned long long a0 = st->absorbed_step[s][0], a1 = st->absorbed_step[s][1];
+        st->src_frac[s] = s_frac[s];
+        st->holes[s][P ^ 1] = compact ? 0ULL : st->holes[s][P] + a0 + a1;
+        st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + s_k[s]);
+        st->injected_total[s] += s_k[s];
+        st->absorbed_total[s][0] += (long long)a0;
+        st->absorbed_total[s][1] += (long long)a1;
+        st->absorbed_step[s][0] = 0ULL;
+        st->absorbed_step[s][1] = 0ULL;
+        st->count[s][P] = 0ULL;
+        st->holes[s][P] = 0ULL;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        st->step = step + 1;
+}
+
+// ---------------------------------------------------------------------------------
+// Field solve.  The unknowns are phi on rows j = 1..ny-1; with A the 5-point
+// stencil times dx^2 (diagonal 4) and the plates moved to the right-hand side,
+// A phi = b = (dx^2/eps0) rho + [j = 1] phi_lo + [j = ny-1] phi_hi.  Jacobi-
+// preconditioned CG (M = 4 I) from the previous phi:
+//   r = b - A phi, p = r/4, rz = r.r/4
+//   loop: q = A p; alpha = rz / p.q; phi += alpha p; r -= alpha q;
+//         stop if r.r <= rtol^2 b.b; p = r/4 + (r.r/4 / rz) p
+// Each iteration is two grid-wide phases: (p, q = A p, p.q) and (phi, r, r.r), the
+// new p formed on the fly from r and the previous p (two p buffers).  Dot products
+// are FP64 per-CTA partial sums, added in CTA order by every CTA: the same value
+// everywhere and in every run.
+// ---------------------------------------------------------------------------------
+
+// Grid barrier for a cooperative launch (all CTAs co-resident).  The wait is
+// bounded: past kBarrierSpins polls the kernel records SLPIC_ERR_TIMEOUT and
+// every CTA leaves at its next check.
+__device__ __forceinline__ bool grid_sync(State2D *st)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &st->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            st->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > kBarrierSpins) {
+                    atomicCAS(&st->error, 0, SLPIC_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)&st->error != SLPIC_ERR_TIMEOUT;
+}
+
+// block sum of v (FP64, fixed order), result valid in every thread
+__device__ __forceinline__ double block_sum(double v, double *s_red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0)
+        s_red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        t += s_red[w];
+    return t;
+}
+
+// sum of the CTAs' partials, in CTA order
+__device__ __forceinline__ double grid_total(const double *part, double *s_red)
+{
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        v += __ldcg(part + b);
+    // fixed assignment of CTAs to threads and a fixed tree: the same in every CTA
+    return block_sum(v, s_red);
+}
+
+// Arrays written by other CTAs of the cooperative grid are read with __ldcg
+// (L2, not the CTA's own L1).
+__device__ __forceinline__ double stencil(const double *u, int idx, int i, int nx)
+{
+    const int ip = (i + 1 == nx) ? idx + 1 - nx : idx + 1;
+    const int im = (i == 0) ? idx - 1 + nx : idx - 1;
+    return 4.0 * __ldcg(u + idx) -
+           (__ldcg(u + ip) + __ldcg(u + im) + __ldcg(u + idx - nx) + __ldcg(u + idx + nx));
+}
+
+// mode 0: the simulation's solve (b from the deposits, which are then cleared;
+// E written).  mode 1: b from p.r's initial content as rho (slpic2d_solve_poisson).
+__global__ void __launch_bounds__(kCgThreads) k_cg2d(Params2D p, int mode)
+{
+    __shared__ double s_red[kCgThreads / 32];
+    State2D *st = p.st;
+    const int nx = p.nx, ny = p.ny, nn = p.nn;
+    const int first = nx, last = ny * nx;  // interior nodes [first, last)
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    double *part0 = p.part, *part1 = p.part + gridDim.x, *part2 = p.part + 2 * gridDim.x;
+
+    // ---- b and r = b - A phi; ||b||^2, ||r||^2
+    double bb = 0.0, rr = 0.0;
+    for (long long t = gtid; t < nn; t += gstride) {
+        const int idx = (int)t;
+        const int j = idx / nx, i = idx - j * nx;
+        double rho = 0.0;
+        if (mode == 0) {
+            for (int s = 0; s < p.ns; ++s) {
+                unsigned long long *a = p.acc + (size_t)s * nn + idx;
+                rho = fma(p.sp[s].rho_unit, (double)(long long)*a, rho);
+                *a = 0ULL;
+            }
+        } else {
+            rho = p.r[idx];
+        }
+        if (idx < first || idx >= last)
+            continue;
+        double b = p.k2 * rho;
+        if (j == 1)
+            b += p.phi_lo;
+        if (j == ny - 1)
+            b += p.phi_hi;
+        // A phi (unknowns only) = stencil on the whole phi (plate rows included)
+        // + the plate terms, so r = b - A phi = k2 rho - stencil(phi)
+        const double r = p.k2 * rho - stencil(p.phi, idx, i, nx);
+        p.q[idx] = r;  // r is staged in q until every CTA has read rho (mode 1 reads p.r)
+        bb = fma(b, b, bb);
+        rr = fma(r, r, rr);
+    }
+    bb = block_sum(bb, s_red);
+    rr = block_sum(rr, s_red);
+    if (threadIdx.x == 0) {
+        part0[blockIdx.x] = bb;
+        part1[blockIdx.x] = rr;
+    }
+    if (!grid_sync(st))
+        return;
+    for (long long t = gtid; t < nn; t += gstride) {
+        const int idx = (int)t;
+        const bool in = idx >= first && idx < last;
+        p.r[idx] = in ? __ldcg(p.q + idx) : 0.0;
+        p.pA[idx] = 0.0;
+        p.pB[idx] = 0.0;
+    }
+    double BB = grid_total(part0, s_red);
+    double RR = grid_total(part1, s_red);
+    if (BB == 0.0)
+        BB = 1.0;
+    if (!grid_sync(st))
+        return;
+
+    int it = 0;
+    bool done = RR <= p.rtol2 * BB;
+    double rz = 0.25 * RR, beta = 0.0;
+    double *pold = p.pA, *pnew = p.pB;
+    while (!done && it < p.cg_maxit) {
+        // phase 1: p = r/4 + beta p_old, q = A p, partial p.q
+        double pq = 0.0;
+        for (long long t = gtid + first; t < last; t += gstride) {
+            const int idx = (int)t;
+            const int j = idx / nx, i = idx - j * nx;
+            const int ip = (i + 1 == nx) ? idx + 1 - nx : idx + 1;
+            const int im = (i == 0) ? idx - 1 + nx : idx - 1;
+            // p at the node and its 4 neighbours (zero on the plate rows)
+            const double pc = fma(beta, __ldcg(pold + idx), 0.25 * __ldcg(p.r + idx));
+            const double pe = fma(beta, __ldcg(pold + ip), 0.25 * __ldcg(p.r + ip));
+            const double pw = fma(beta, __ldcg(pold + im), 0.25 * __ldcg(p.r + im));
+            const double pn =
+                (j + 1 < ny) ? fma(beta, __ldcg(pold + idx + nx), 0.25 * __ldcg(p.r + idx + nx)) : 0.0;
+            const double ps =
+                (j > 1) ? fma(beta, __ldcg(pold + idx - nx), 0.25 * __ldcg(p.r + idx - nx)) : 0.0;
+            const double qv = 4.0 * pc - (pe + pw + pn + ps);
+            pnew[idx] = pc;
+            p.q[idx] = qv;
+            pq = fma(pc, qv, pq);
+        }
+        pq = block_sum(pq, s_red);
+        if (threadIdx.x == 0)
+            part2[blockIdx.x] = pq;
+        if (!grid_sync(st))
+            return;
+        const double alpha = rz / grid_total(part2, s_red);
+        // phase 2: phi += alpha p, r -= alpha q, partial r.r
+        double r2 = 0.0;
+        for (long long t = gtid + first; t < last; t += gstride) {
+            const int idx = (int)t;
+            p.phi[idx] = fma(alpha, pnew[idx], p.phi[idx]);
+            const double r = fma(-alpha, p.q[idx], p.r[idx]);
+            p.r[idx] = r;
+            r2 = fma(r, r, r2);
+        }
+        r2 = block_sum(r2, s_red);
+        if (threadIdx.x == 0)
+            part1[blockIdx.x] = r2;
+        if (!grid_sync(st))
+            return;
+        RR = grid_total(part1, s_red);
+        ++it;
+        done = RR <= p.rtol2 * BB;
+        const double rz1 = 0.25 * RR;
+        beta = rz1 / rz;
+        rz = rz1;
+        double *tmp = pold;
+        pold = pnew;
+        pnew = tmp;
+    }
+    // E on every node from the final phi (complete after the last barrier)
+    if (mode == 0) {
+        for (long long t = gtid; t < nn; t += gstride) {
+            const int idx = (int)t;
+            const int j = idx / nx, i = idx - j * nx;
+            const int ip = (i + 1 == nx) ? idx + 1 - nx : idx + 1;
+            const int im = (i == 0) ? idx - 1 + nx : idx - 1;
+            const double *f = p.phi;
+            const double ex = -(__ldcg(f + ip) - __ldcg(f + im)) * (0.5 / p.dx);
+            double ey;
+            if (j == 0)
+                ey = -(__ldcg(f + idx + nx) - __ldcg(f + idx)) / p.dx;
+            else if (j == ny)
+                ey = -(__ldcg(f + idx) - __ldcg(f + idx - nx)) / p.dx;
+            else
+                ey = -(__ldcg(f + idx + nx) - __ldcg(f + idx - nx)) * (0.5 / p.dx);
+            p.E[idx] = make_float2((float)ex, (float)ey);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->cg_iters = it;
+        st->cg_total += it;
+        st->cg_res = sqrt(RR / BB);
+        if (!done)
+            atomicCAS(&st->error, 0, SLPIC_ERR_NOCONVERGE);
+    }
+}
+
+}  // namespace slpic2d
+
+// =================================================================================
+// C ABI
+// =================================================================================
+using namespace slpic2d;
+
+struct slpic2d_sim {
+    slpic2d_config cfg{};
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    Params2D p{};
+    int ctas = 1;     // particle-kernel CTAs per species
+    int cg_ctas = 1;  // cooperative CG grid
+    bool prepared = false;
+    State2D *d_state = nullptr;
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+#define CK2(h, call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return SLPIC_ERR_CUDA;                                                         \
+        }                                                                                  \
+    } while (0)
+
+static int fail2(slpic2d_t *h, int code, const std::string &msg)
+{
+    h->err = msg;
+    return code;
+}
+
+static int device_status(slpic2d_t *h)
+{
+    CK2(h, cudaStreamSynchronize(h->stream));
+    int e = 0;
+    CK2(h, cudaMemcpy(&e, &h->d_state->error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        const char *m = e == SLPIC_ERR_CAPACITY ? "particle store full: injection truncated"
+                        : e == SLPIC_ERR_NOCONVERGE ? "CG did not reach cg_rtol within cg_maxit"
+                        : e == SLPIC_ERR_TIMEOUT ? "grid barrier of the CG kernel timed out"
+                                                 : "device error";
+        return fail2(h, e, m);
+    }
+    return SLPIC_OK;
+}
+
+static int launch_cg(slpic2d_t *h, int mode)
+{
+    Params2D p = h->p;
+    void *args[] = {&p, &mode};
+    CK2(h, cudaLaunchCooperativeKernel((const void *)k_cg2d, dim3(h->cg_ctas), dim3(kCgThreads),
+                                       args, 0, h->stream));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
+{
+    if (!c || !out) {
+        slpic::set_create_error("null argument");
+        return SLPIC_ERR_INVALID;
+    }
+    std::string why;
+    if (c->nx < 2 || c->ny < 2 || !(c->dx > 0) || !(c->dt > 0) || !(c->eps0 > 0))
+        why = "need nx >= 2, ny >= 2, dx > 0, dt > 0, eps0 > 0";
+    else if ((long long)c->nx * (c->ny + 1) > (1LL << 30))
+        why = "grid too large";
+    else if (c->n_species < 1 || c->n_species > SLPIC_MAX_SPECIES)
+        why = "n_species out of range";
+    else if (!(c->cg_rtol > 0 && c->cg_rtol < 1) || c->cg_maxit <= 0)
+        why = "need 0 < cg_rtol < 1 and cg_maxit > 0";
+    else if (c->src_mode < SLPIC_SRC_NONE || c->src_mode > SLPIC_SRC_RATE ||
+             (c->src_mode == SLPIC_SRC_LOSS_MATCHED &&
+              (c->src_ref_species < 0 || c->src_ref_species >= c->n_species)))
+        why = "bad source mode or reference species";
+    else if (c->src_mode != SLPIC_SRC_NONE &&
+             !(c->src_lo_cells >= 0 && c->src_len_cells >= 0 &&
+               c->src_lo_cells + c->src_len_cells <= c->ny))
+        why = "source band outside the grid";
+    for (int s = 0; why.empty() && s < c->n_species; ++s) {
+        const slpic_species &sp = c->species[s];
+        if (!(sp.m > 0) || !(sp.w > 0) || sp.capacity <= 0 || sp.capacity > (1LL << 31) - 1 ||
+            !std::isfinite(sp.q) || sp.beta_kind < 0 || sp.beta_kind > 2 || !(sp.T_src >= 0))
+            why = "species " + std::to_string(s) + ": bad parameters";
+        else if (sp.beta_kind != SLPIC_BETA_ONE && !(sp.v0 > 0))
+            why = "species " + std::to_string(s) + ": v0 must be > 0";
+        else if (sp.beta_kind != SLPIC_BETA_ONE && c->dt * sp.v0 > c->dx) {
+            slpic::set_create_error("species " + std::to_string(s) + ": dt * v0 > dx");
+            return SLPIC_ERR_CFL;
+        } else if (sp.beta_kind == SLPIC_BETA_ONE && c->max_speed > 0 &&
+                   c->dt * c->max_speed > c->dx) {
+            slpic::set_create_error("species " + std::to_string(s) + ": dt * max_speed > dx");
+            return SLPIC_ERR_CFL;
+        }
+    }
+    if (!why.empty()) {
+        slpic::set_create_error(why);
+        return SLPIC_ERR_INVALID;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        slpic::set_create_error("no CUDA device");
+        return SLPIC_ERR_CUDA;
+    }
+    slpic2d_t *h = new slpic2d_t();
+    h->cfg = *c;
+    auto bail = [&](int code, const std::string &m) {
+        slpic::set_create_error(m);
+        slpic2d_destroy(h);
+        return code;
+    };
+    auto alloc = [&](void **ptr, size_t bytes) -> bool {
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        h->allocs.push_back(*ptr);
+        return true;
+    };
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(SLPIC_ERR_CUDA, "stream creation failed");
+    h->stream = h->own_stream;
+    Params2D &p = h->p;
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.nn = c->nx * (c->ny + 1);
+    p.ns = c->n_species;
+    p.dt = (float)c->dt;
+    p.dt_dx = (float)(c->dt / c->dx);
+    p.dx = c->dx;
+    p.dt64 = c->dt;
+    p.k2 = c->dx * c->dx / c->eps0;
+    p.phi_lo = c->phi_lo;
+    p.phi_hi = c->phi_hi;
+    p.rtol2 = c->cg_rtol * c->cg_rtol;
+    p.cg_maxit = c->cg_maxit;
+    p.src_mode = c->src_mode;
+    p.src_ref = c->src_ref_species;
+    p.src_lo = (float)c->src_lo_cells;
+    p.src_len = (float)c->src_len_cells;
+    p.src_rate = c->src_rate;
+    p.seed = c->seed;
+    const size_t nn = (size_t)p.nn;
+    bool ok = alloc((void **)&h->d_state, sizeof(State2D)) &&
+              alloc((void **)&p.acc, sizeof(unsigned long long) * nn * p.ns) &&
+              alloc((void **)&p.E, sizeof(float2) * nn) && alloc((void **)&p.phi, sizeof(double) * nn) &&
+              alloc((void **)&p.r, sizeof(double) * nn) && alloc((void **)&p.pA, sizeof(double) * nn) &&
+              alloc((void **)&p.pB, sizeof(double) * nn) && alloc((void **)&p.q, sizeof(double) * nn);
+    for (int s = 0; ok && s < p.ns; ++s) {
+        const slpic_species &sp = c->species[s];
+        Species2D &d = p.sp[s];
+        for (int b = 0; ok && b < 2; ++b)
+            ok = alloc((void **)&d.cell[b], sizeof(int32_t) * sp.capacity) &&
+                 alloc((void **)&d.pv[b], sizeof(float4) * sp.capacity) &&
+                 alloc((void **)&d.vz[b], sizeof(float) * sp.capacity);
+        d.capacity = sp.capacity;
+        d.qm = (float)(sp.q / sp.m);
+        d.v0 = (float)sp.v0;
+        d.vth_src = (float)std::sqrt(sp.T_src / sp.m);
+        d.kind = sp.beta_kind;
+        d.w = sp.w;
+        d.inv_w = 1.0 / sp.w;
+        d.rho_unit = sp.q * sp.w / (c->dx * c->dx) * std::ldexp(1.0, -40);
+    }
+    if (!ok)
+        return bail(SLPIC_ERR_OOM, "device allocation failed");
+    p.st = h->d_state;
+    int dev = 0, sms = 1, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg2d, kCgThreads, 0) != cudaSuccess ||
+        occ < 1)
+        return bail(SLPIC_ERR_CUDA, "CG kernel occupancy query failed");
+    h->cg_ctas = sms * std::min(occ, 2);
+    h->ctas = sms * 4;
+    if (!alloc((void **)&p.part, sizeof(double) * 3 * h->cg_ctas))
+        return bail(SLPIC_ERR_OOM, "device allocation failed");
+    cudaError_t e = cudaMemset(h->d_state, 0, sizeof(State2D));
+    if (e == cudaSuccess)
+        e = cudaMemset(p.acc, 0, sizeof(unsigned long long) * nn * p.ns);
+    if (e == cudaSuccess)
+        e = cudaMemset(p.E, 0, sizeof(float2) * nn);
+    if (e == cudaSuccess)
+        e = cudaMemset(p.phi, 0, sizeof(double) * nn);
+    if (e != cudaSuccess)
+        return bail(SLPIC_ERR_CUDA, cudaGetErrorString(e));
+    // plate rows of phi
+    std::vector<double> row((size_t)p.nx, c->phi_lo);
+    cudaMemcpy(p.phi, row.data(), sizeof(double) * p.nx, cudaMemcpyHostToDevice);
+    std::fill(row.begin(), row.end(), c->phi_hi);
+    cudaMemcpy(p.phi + (size_t)p.ny * p.nx, row.data(), sizeof(double) * p.nx,
+               cudaMemcpyHostToDevice);
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return bail(SLPIC_ERR_CUDA, "initialisation failed");
+    *out = h;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_destroy(slpic2d_t *h)
+{
+    if (!h)
+        return SLPIC_OK;
+    if (h->own_stream)
+        cudaStreamSynchronize(h->own_stream);
+    for (void *a : h->allocs)
+        cudaFree(a);
+    if (h->own_stream)
+        cudaStreamDestroy(h->own_stream);
+    delete h;
+    return SLPIC_OK;
+}
+
+extern "C" const char *slpic2d_last_error(const slpic2d_t *h) { return h ? h->err.c_str() : ""; }
+
+extern "C" int slpic2d_set_stream(slpic2d_t *h, void *stream)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    h->stream = (cudaStream_t)stream;
+    return SLPIC_OK;
+}
+
+static int read_state(slpic2d_t *h, State2D &st)
+{
+    CK2(h, cudaStreamSynchronize(h->stream));
+    CK2(h, cudaMemcpy(&st, h->d_state, sizeof(State2D), cudaMemcpyDeviceToHost));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_load_particles(slpic2d_t *h, int s, int64_t n, const int32_t *cell,
+                                      const float *offset, const float *v)
+{
+    if (!h || s < 0 || s >= h->p.ns || n < 0 || (n > 0 && (!cell || !offset || !v)))
+        return h ? fail2(h, SLPIC_ERR_INVALID, "bad arguments") : SLPIC_ERR_INVALID;
+    if (n == 0)
+        return SLPIC_OK;
+    const int nx = h->p.nx, ny = h->p.ny;
+    for (int64_t i = 0; i < n; ++i) {
+        const float ox = offset[2 * i], oy = offset[2 * i + 1];
+        if (cell[i] < 0 || cell[i] >= nx * ny || !(ox >= 0.0f && ox < 1.0f) ||
+            !(oy >= 0.0f && oy < 1.0f) || !std::isfinite(v[3 * i]) ||
+            !std::isfinite(v[3 * i + 1]) || !std::isfinite(v[3 * i + 2]))
+            return fail2(h, SLPIC_ERR_INVALID,
+                         "particle " + std::to_string(i) + ": cell or offset out of range");
+    }
+    State2D st;
+    int rc = read_state(h, st);
+    if (rc)
+        return rc;
+    const int P = (int)(st.step & 1);
+    const long long have = (long long)st.count[s][P];
+    if (have + n > h->p.sp[s].capacity)
+        return fail2(h, SLPIC_ERR_CAPACITY, "load exceeds the species capacity");
+    std::vector<float4> pv((size_t)n);
+    std::vector<float> vz((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        pv[i] = make_float4(offset[2 * i], offset[2 * i + 1], v[3 * i], v[3 * i + 1]);
+        vz[i] = v[3 * i + 2];
+    }
+    const Species2D &d = h->p.sp[s];
+    CK2(h, cudaMemcpy(d.cell[P] + have, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    CK2(h, cudaMemcpy(d.pv[P] + have, pv.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
+    CK2(h, cudaMemcpy(d.vz[P] + have, vz.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+    const unsigned long long cnt = (unsigned long long)(have + n);
+    CK2(h, cudaMemcpy(&h->d_state->count[s][P], &cnt, sizeof(cnt), cudaMemcpyHostToDevice));
+    h->prepared = false;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_prepare(slpic2d_t *h)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    Params2D &p = h->p;
+    CK2(h, cudaMemsetAsync(p.acc, 0, sizeof(unsigned long long) * p.nn * p.ns, h->stream));
+    k_deposit2d<<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
+    CK2(h, cudaGetLastError());
+    int rc = launch_cg(h, 0);
+    if (rc)
+        return rc;
+    h->prepared = true;
+    return device_status(h);
+}
+
+extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
+{
+    if (!h || nsteps < 0)
+        return h ? fail2(h, SLPIC_ERR_INVALID, "nsteps < 0") : SLPIC_ERR_INVALID;
+    if (!h->prepared)
+        return fail2(h, SLPIC_ERR_INVALID, "slpic2d_prepare must follow a load");
+    State2D st;
+    int rc = read_state(h, st);
+    if (rc)
+        return rc;
+    if (st.error)
+        return device_status(h);
+    long long step = st.step;
+    Params2D &p = h->p;
+    for (int64_t k = 0; k < nsteps; ++k, ++step) {
+        const bool compact = (step % kCompact2d) == kCompact2d - 1;
+        if (compact)
+            k_particles2d<true><<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
+        else
+            k_particles2d<false><<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
+        k_inject2d<<<1, 1024, 0, h->stream>>>(p, compact ? 1 : 0);
+        CK2(h, cudaGetLastError());
+        rc = launch_cg(h, 0);
+        if (rc)
+            return rc;
+    }
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_synchronize(slpic2d_t *h)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    return device_status(h);
+}
+
+extern "C" int slpic2d_fields(slpic2d_t *h, double *rho, double *phi, float *Ex, float *Ey)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    int rc = device_status(h);
+    if (rc)
+        return rc;
+    const Params2D &p = h->p;
+    const size_t nn = (size_t)p.nn;
+    if (phi)
+        CK2(h, cudaMemcpy(phi, p.phi, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+    if (Ex || Ey) {
+        std::vector<float2> e(nn);
+        CK2(h, cudaMemcpy(e.data(), p.E, sizeof(float2) * nn, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < nn; ++k) {
+            if (Ex)
+                Ex[k] = e[k].x;
+            if (Ey)
+                Ey[k] = e[k].y;
+        }
+    }
+    if (rho) {
+        // rho of the current level from the deposits of the particles now stored
+        // (the consumed deposit was cleared by the solve): recomputed here
+        CK2(h, cudaMemsetAsync(p.acc, 0, sizeof(unsigned long long) * nn * p.ns, h->stream));
+        k_deposit2d<<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
+        CK2(h, cudaGetLastError());
+        CK2(h, cudaStreamSynchronize(h->stream));
+        std::vector<long long> a(nn * p.ns);
+        CK2(h, cudaMemcpy(a.data(), p.acc, sizeof(long long) * nn * p.ns, cudaMemcpyDeviceToHost));
+        CK2(h, cudaMemsetAsync(p.acc, 0, sizeof(unsigned long long) * nn * p.ns, h->stream));
+        for (size_t k = 0; k < nn; ++k) {
+            double v = 0.0;
+            for (int s = 0; s < p.ns; ++s)
+                v = std::fma(p.sp[s].rho_unit, (double)a[(size_t)s * nn + k], v);
+            rho[k] = v;
+        }
+    }
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_charge_raw(slpic2d_t *h, int s, int64_t *acc)
+{
+    if (!h || s < 0 || s >= h->p.ns || !acc)
+        return h ? fail2(h, SLPIC_ERR_INVALID, "bad arguments") : SLPIC_ERR_INVALID;
+    int rc = device_status(h);
+    if (rc)
+        return rc;
+    const Params2D &p = h->p;
+    const size_t nn = (size_t)p.nn;
+    CK2(h, cudaMemsetAsync(p.acc, 0, sizeof(unsigned long long) * nn * p.ns, h->stream));
+    k_deposit2d<<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
+    CK2(h, cudaGetLastError());
+    CK2(h, cudaStreamSynchronize(h->stream));
+    CK2(h, cudaMemcpy(acc, p.acc + (size_t)s * nn, sizeof(int64_t) * nn, cudaMemcpyDeviceToHost));
+    CK2(h, cudaMemsetAsync(p.acc, 0, sizeof(unsigned long long) * nn * p.ns, h->stream));
+    return device_status(h);
+}
+
+extern "C" int slpic2d_particle_count(slpic2d_t *h, int s, int64_t *n)
+{
+    if (!h || s < 0 || s >= h->p.ns || !n)
+        return h ? fail2(h, SLPIC_ERR_INVALID, "bad arguments") : SLPIC_ERR_INVALID;
+    State2D st;
+    int rc = read_state(h, st);
+    if (rc)
+        return rc;
+    const int P = (int)(st.step & 1);
+    *n = (int64_t)(st.count[s][P] - st.holes[s][P]);
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_get_particles(slpic2d_t *h, int s, int32_t *cell, float *offset, float *v,
+                                     int64_t *n)
+{
+    if (!h || s < 0 || s >= h->p.ns || !n || !cell || !offset || !v)
+        return h ? fail2(h, SLPIC_ERR_INVALID, "bad arguments") : SLPIC_ERR_INVALID;
+    State2D st;
+    int rc = read_state(h, st);
+    if (rc)
+        return rc;
+    const int P = (int)(st.step & 1);
+    const long long slots = (long long)st.count[s][P];
+    const long long live = slots - (long long)st.holes[s][P];
+    if (*n < live)
+        return fail2(h, SLPIC_ERR_CAPACITY, "output arrays too small");
+    std::vector<int32_t> c((size_t)slots);
+    std::vector<float4> pv((size_t)slots);
+    std::vector<float> vz((size_t)slots);
+    const Species2D &d = h->p.sp[s];
+    if (slots) {
+        CK2(h, cudaMemcpy(c.data(), d.cell[P], sizeof(int32_t) * slots, cudaMemcpyDeviceToHost));
+        CK2(h, cudaMemcpy(pv.data(), d.pv[P], sizeof(float4) * slots, cudaMemcpyDeviceToHost));
+        CK2(h, cudaMemcpy(vz.data(), d.vz[P], sizeof(float) * slots, cudaMemcpyDeviceToHost));
+    }
+    long long k = 0;
+    for (long long i = 0; i < slots; ++i) {
+        if (c[i] < 0)
+            continue;
+        cell[k] = c[i];
+        offset[2 * k] = pv[i].x;
+        offset[2 * k + 1] = pv[i].y;
+        v[3 * k] = pv[i].z;
+        v[3 * k + 1] = pv[i].w;
+        v[3 * k + 2] = vz[i];
+        ++k;
+    }
+    *n = k;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_diagnostics(slpic2d_t *h, slpic2d_diag *out)
+{
+    if (!h || !out)
+        return h ? fail2(h, SLPIC_ERR_INVALID, "bad arguments") : SLPIC_ERR_INVALID;
+    int rc = device_status(h);
+    if (rc)
+        return rc;
+    State2D st;
+    rc = read_state(h, st);
+    if (rc)
+        return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->step = st.step;
+    out->time = (double)st.step * h->cfg.dt;
+    const int P = (int)(st.step & 1);
+    for (int s = 0; s < h->p.ns; ++s) {
+        out->count[s] = (int64_t)(st.count[s][P] - st.holes[s][P]);
+        out->absorbed[s][0] = st.absorbed_total[s][0];
+        out->absorbed[s][1] = st.absorbed_total[s][1];
+        out->injected[s] = st.injected_total[s];
+    }
+    out->cg_iterations = st.cg_iters;
+    out->cg_iterations_total = st.cg_total;
+    out->cg_rel_residual = st.cg_res;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_solve_poisson(slpic2d_t *h, const double *rho, double *phi,
+                                     int32_t *iterations, double *rel_residual)
+{
+    if (!h || !rho || !phi)
+        return h ? fail2(h, SLPIC_ERR_INVALID, "bad arguments") : SLPIC_ERR_INVALID;
+    int rc = device_status(h);
+    if (rc)
+        return rc;
+    Params2D saved = h->p;
+    Params2D &p = h->p;
+    const size_t nn = (size_t)p.nn;
+    // private phi and rho buffers so the simulation's fields stay as they are
+    double *d_phi = nullptr;
+    CK2(h, cudaMalloc(&d_phi, sizeof(double) * nn));
+    std::vector<double> guess(phi, phi + nn);
+    for (int i = 0; i < p.nx; ++i) {
+        guess[i] = p.phi_lo;
+        guess[(size_t)p.ny * p.nx + i] = p.phi_hi;
+    }
+    cudaError_t e = cudaMemcpy(d_phi, guess.data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p.r, rho, sizeof(double) * nn, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_phi);
+        return fail2(h, SLPIC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    p.phi = d_phi;
+    rc = launch_cg(h, 1);
+    h->p = saved;
+    if (rc == SLPIC_OK)
+        rc = device_status(h);
+    if (rc == SLPIC_ERR_NOCONVERGE) {
+        // a standalone solve's non-convergence is reported, not kept as the
+        // simulation's error
+        const int zero = 0;
+        cudaMemcpy(&h->d_state->error, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+    State2D st;
+    if (rc == SLPIC_OK || rc == SLPIC_ERR_NOCONVERGE) {
+        if (read_state(h, st) == SLPIC_OK) {
+            if (iterations)
+                *iterations = st.cg_iters;
+            if (rel_residual)
+                *rel_residual = st.cg_res;
+        }
+        cudaMemcpy(phi, d_phi, sizeof(double) * nn, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(d_phi);
+    return rc;
+}

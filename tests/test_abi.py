@@ -95,3 +95,62 @@ def test_config_errors_need_no_device(lib):
     with pytest.raises(binding.SlpicError) as ei:
         binding.slpic_create(binding.config_from_problem(prob))
     assert ei.value.code == binding.SLPIC_ERR_INVALID
+
+
+# ------------------------------------------------------------------ 2D entry points
+HEADER2D = os.path.join(ROOT, "include", "slpic2d.h")
+
+
+def test_every_2d_function_is_exported(lib):
+    from paper_1511_08225_gb300 import binding2d
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER2D).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(slpic2d_[a-z0-9_]+)\s*\(", src)))
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding2d.EXPORTS2D) == names
+    assert binding2d.load_library().slpic2d_step.argtypes is not None
+
+
+def test_2d_struct_layout_matches_c(tmp_path):
+    from paper_1511_08225_gb300 import binding2d
+    prog = tmp_path / "layout2d.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slpic2d.h"', 'int main(void){']
+    for st in ("slpic2d_config", "slpic2d_diag"):
+        cls = getattr(binding2d, st)
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0;}")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout2d"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    for line in subprocess.check_output([str(exe)], text=True).split("\n"):
+        if not line.strip():
+            continue
+        parts = line.split()
+        cls = getattr(binding2d, parts[0])
+        if parts[1] == "size":
+            assert ctypes.sizeof(cls) == int(parts[2]), line
+        else:
+            assert getattr(cls, parts[1]).offset == int(parts[2]), line
+
+
+def test_2d_config_errors_need_no_device(lib):
+    from paper_1511_08225_gb300 import binding2d, inputs
+    prob = inputs.plasma2d_problem(nx=16, ny=16, ppc=1)
+    prob["dt"] = 2 * prob["dx"] / 0.1
+    with pytest.raises(binding.SlpicError) as ei:
+        binding2d.slpic2d_create(binding2d.config_from_problem(prob))
+    assert ei.value.code == binding.SLPIC_ERR_CFL
+    for key, val in (("cg_rtol", 0.0), ("cg_maxit", 0), ("nx", 1)):
+        prob = inputs.plasma2d_problem(nx=16, ny=16, ppc=1)
+        prob[key] = val
+        with pytest.raises(binding.SlpicError) as ei:
+            binding2d.slpic2d_create(binding2d.config_from_problem(prob))
+        assert ei.value.code == binding.SLPIC_ERR_INVALID
+    prob = inputs.plasma2d_problem(nx=16, ny=16, ppc=1)
+    prob["source"]["len_cells"] = 16.0
+    with pytest.raises(binding.SlpicError) as ei:
+        binding2d.slpic2d_create(binding2d.config_from_problem(prob))
+    assert ei.value.code == binding.SLPIC_ERR_INVALID

@@ -1,0 +1,260 @@
+"""Parity of the 2D CUDA path (include/slpic2d.h) with the FP64 oracle.
+
+Bars: deposits bit-exact (the 2D quantised rule); the CG potential within
+cond(A) * rtol of the oracle's direct solve, with the oracle's CG iteration
+count; one step's velocities within 1e-5 |v| of the oracle and positions
+within the move that error causes (1e-5 beta |v| dt) plus 8 ulp of the FP32
+offset, particles matched by vz (a has no z component, so vz is unchanged by
+the push and identifies a particle on both sides)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1511_08225_gb300 import binding2d, inputs
+
+pytestmark = pytest.mark.gpu
+
+TWO40 = 2.0 ** 40
+
+
+def _unique_vz(state):
+    """Make every vz bit pattern unique within a species (nudging repeats by one
+    ulp), so vz can key the particle matching."""
+    out = []
+    for c, o, v in state:
+        v = v.copy()
+        bits = v[:, 2].view(np.uint32)
+        _, first = np.unique(bits, return_index=True)
+        dup = np.setdiff1d(np.arange(bits.size), first)
+        for d in dup:
+            x = v[d, 2]
+            while True:
+                x = np.nextafter(x, np.float32(np.inf), dtype=np.float32)
+                if not np.any(v[:, 2].view(np.uint32) == np.float32(x).view(np.uint32)):
+                    break
+            v[d, 2] = x
+        out.append((c, o, v))
+    return out
+
+
+def _prob(nx=32, ny=24, ppc=12, kind=inputs.BETA_HEAVISIDE, v0=0.35, dx=0.5, dt=None,
+          source=inputs.SRC_NONE, rate=0.0, phi_hi=0.0, cg_rtol=1e-11):
+    p = inputs.plasma2d_problem(nx=nx, ny=ny, dx=dx, v0=v0, ppc=ppc, kind=kind, dt=dt,
+                                mass_ratio=25.0, T_i=0.5, source_mode=source, rate=rate,
+                                cg_rtol=cg_rtol)
+    p["phi_hi"] = phi_hi
+    return p
+
+
+def _nonneutral(state, frac=0.4, seed=1):
+    """Drop part of the electrons in one half of the box: strong, non-uniform E."""
+    rng = np.random.default_rng(seed)
+    c, o, v = state[0]
+    drop = (rng.random(c.size) < frac) & ((c % 1000) % 2 == 0)
+    return [(c[~drop], o[~drop], v[~drop])] + list(state[1:])
+
+
+def _sim(prob, st):
+    g = binding2d.Simulation2D(prob)
+    g.load_state(st)
+    g.prepare()
+    return g
+
+
+def _oracle(prob, st):
+    o = orc.OracleSim2D(prob)
+    for s, (c, off, v) in enumerate(st):
+        o.load_cells(s, c, off, v)
+    o.start()
+    return o
+
+
+def _cond(ny):
+    return 8.0 / (4.0 * math.sin(math.pi / (2 * ny)) ** 2)
+
+
+@pytest.mark.parametrize("kind", [inputs.BETA_ONE, inputs.BETA_HEAVISIDE,
+                                  inputs.BETA_RELATIVISTIC])
+def test_deposit2d_bit_exact(kind):
+    prob = _prob(nx=40, ny=30, ppc=20, kind=kind, v0=0.5, dt=0.5 if kind else 0.2)
+    st = inputs.load_state2d(prob, seed=3 + kind)
+    g = _sim(prob, st)
+    for s, (c, o, v) in enumerate(st):
+        ref = orc.deposit2d_q40(40, 30, c, o, v, kind, prob["species"][s]["v0"])
+        got = g.charge_raw(s)
+        assert np.array_equal(got, ref)
+    g.close()
+
+
+def test_cg_solve_matches_direct_solver():
+    """The cooperative CG kernel: the oracle's answer within cond(A) rtol and
+    the same iteration count as the oracle's CG (same algorithm, FP64) within
+    2; a solve warm-started from the answer takes 0 iterations."""
+    nx, ny, dx = 96, 72, 0.6
+    prob = _prob(nx=nx, ny=ny, ppc=1, dx=dx, cg_rtol=1e-9)
+    prob["phi_lo"], prob["phi_hi"] = 0.4, -0.2
+    g = binding2d.Simulation2D(prob)
+    rng = np.random.default_rng(5)
+    rho = rng.normal(size=(ny + 1, nx))
+    phi, it, res = g.solve_poisson(rho)
+    exact = orc.poisson2d_direct(rho, dx, 0.4, -0.2)
+    _, it_o, _ = orc.poisson2d_cg(rho, dx, None, 0.4, -0.2, rtol=1e-9)
+    assert res <= 1e-9
+    assert abs(it - it_o) <= 2, (it, it_o)
+    assert np.abs(phi - exact).max() <= _cond(ny) * 1e-9 * np.abs(exact).max()
+    assert np.all(phi[0] == 0.4) and np.all(phi[-1] == -0.2)
+    _, it0, _ = g.solve_poisson(rho, exact)
+    assert it0 == 0
+    g.close()
+
+
+def test_cg_reports_nonconvergence_and_stays_usable():
+    prob = _prob(nx=64, ny=64, ppc=1, cg_rtol=1e-12)
+    prob["cg_maxit"] = 3
+    g = binding2d.Simulation2D(prob)
+    rho = np.random.default_rng(1).normal(size=(65, 64))
+    with pytest.raises(binding2d.SlpicError) as ei:
+        g.solve_poisson(rho)
+    assert ei.value.code == binding2d.binding.SLPIC_ERR_NOCONVERGE
+    g.synchronize()  # the handle still works
+    g.close()
+
+
+def _compare_step2d(prob, st, g, o, rel=1e-5):
+    dx, nx, ny = prob["dx"], prob["nx"], prob["ny"]
+    Lx = nx * dx
+    stats = []
+    for s in range(len(st)):
+        c, off, v = g.particles(s)
+        kg = v[:, 2].astype(np.float32).view(np.uint32).astype(np.int64)
+        ko = o.v[s][:, 2].astype(np.float32).view(np.uint32).astype(np.int64)
+        og = np.argsort(kg)
+        pos = np.searchsorted(kg[og], ko)
+        pos = np.minimum(pos, kg.size - 1)
+        found = kg[og][pos] == ko
+        ia = np.nonzero(found)[0]
+        ib = og[pos[found]]
+        # survivors lost only within rounding of a plate
+        miss = np.nonzero(~found)[0]
+        if miss.size:
+            yo = o.y[s][miss]
+            assert (np.minimum(yo, ny * dx - yo) < 1e-4 * dx).all(), f"{miss.size} lost"
+        extra = np.setdiff1d(np.arange(kg.size), ib)
+        if extra.size:
+            yg = (c[extra] // nx + off[extra, 1].astype(np.float64)) * dx
+            assert (np.minimum(yg, ny * dx - yg) < 1e-4 * dx).all()
+        xg = (c[ib] % nx + off[ib, 0].astype(np.float64)) * dx
+        yg = (c[ib] // nx + off[ib, 1].astype(np.float64)) * dx
+        vg = v[ib].astype(np.float64)
+        vref = o.v[s][ia]
+        vn = np.linalg.norm(vref, axis=1)
+        dv = np.linalg.norm(vg - vref, axis=1)
+        # the input speed bounds |v| from the other side
+        cin, oin, vin = st[s]
+        kin = vin[:, 2].view(np.uint32).astype(np.int64)
+        oi = np.argsort(kin)
+        vin_m = vin[oi[np.searchsorted(kin[oi], ko[ia])]].astype(np.float64)
+        vnorm = np.maximum(vn, np.linalg.norm(vin_m, axis=1))
+        assert (dv <= rel * vnorm + 1e-30).all(), \
+            f"species {s}: worst dv/|v| {np.max(dv / np.maximum(vnorm, 1e-30)):.3e}"
+        sp = prob["species"][s]
+        b = orc._beta_vec(int(sp["kind"]), vn, float(sp["v0"]))
+        tol = rel * b * vnorm * prob["dt"] + 8 * 2.0 ** -24 * dx
+        ddx = (xg - o.x[s][ia] + 0.5 * Lx) % Lx - 0.5 * Lx
+        ddy = yg - o.y[s][ia]
+        assert (np.abs(ddx) <= tol).all(), f"species {s}: x error {np.max(np.abs(ddx) / tol):.2f} tol"
+        assert (np.abs(ddy) <= tol).all(), f"species {s}: y error {np.max(np.abs(ddy) / tol):.2f} tol"
+        stats.append((s, ia.size, float(np.max(dv / np.maximum(vnorm, 1e-30)))))
+    return stats
+
+
+@pytest.mark.parametrize("kind", [inputs.BETA_ONE, inputs.BETA_HEAVISIDE,
+                                  inputs.BETA_RELATIVISTIC])
+def test_single_step2d_matches_oracle(kind):
+    """Non-neutral load and a biased plate: strong fields in both directions,
+    particles in both beta regimes, some leaving through the plates."""
+    v0 = 0.35
+    prob = _prob(nx=48, ny=36, ppc=10, kind=kind, v0=v0, dx=0.5,
+                 dt=0.5 / (v0 if kind != inputs.BETA_ONE else 4.0), phi_hi=1.5)
+    st = _unique_vz(_nonneutral(inputs.load_state2d(prob, seed=11 + kind)))
+    g = _sim(prob, st)
+    o = _oracle(prob, st)
+    # the initial potentials agree within the CG tolerance
+    _, phi_g, _, _ = g.fields()
+    assert np.abs(phi_g - o.phi).max() <= _cond(36) * 1e-11 * max(1.0, np.abs(o.phi).max())
+    g.step(1)
+    g.synchronize()
+    o.step(1)
+    stats = _compare_step2d(prob, st, g, o)
+    print("parity2d", kind, stats)
+    d = g.diagnostics()
+    for s in range(2):
+        assert abs(d["count"][s] - o.x[s].size) <= 2
+        assert abs(d["absorbed"][s][0] + d["absorbed"][s][1] - o.flux[s].sum()) <= 2
+    g.close()
+
+
+def test_steps2d_deposit_totals_and_potential():
+    """Over several steps (with one compacting step): every deposit totals
+    sum_p rint(beta 2^40) over the GPU's own particles, and the GPU's potential
+    solves Poisson for the GPU's own rho (oracle direct solve) within the CG
+    bound."""
+    prob = _prob(nx=40, ny=32, ppc=8, v0=0.3, dt=1.5, cg_rtol=1e-10)
+    st = inputs.load_state2d(prob, seed=21)
+    g = _sim(prob, st)
+    for _ in range(3):
+        g.step(6)  # 18 steps: crosses the compacting step at 15
+        rho, phi, Ex, Ey = g.fields()
+        for s in range(2):
+            c, o, v = g.particles(s)
+            b = np.array([orc.beta_f32(1, *vv, np.float32(0.3)) for vv in v], np.float32)
+            qT = np.rint(b * np.float32(TWO40)).astype(np.int64)
+            assert int(g.charge_raw(s).sum()) == int(qT.sum())
+        ref = orc.poisson2d_direct(rho, prob["dx"])
+        assert np.abs(phi - ref).max() <= _cond(32) * 1e-10 * max(1e-6, np.abs(ref).max())
+        ex_o, ey_o = orc.efield2d(phi, prob["dx"])
+        assert np.abs(Ex - ex_o).max() <= 1e-6 * max(1e-6, np.abs(ex_o).max())
+        assert np.abs(Ey - ey_o).max() <= 1e-6 * max(1e-6, np.abs(ey_o).max())
+    d = g.diagnostics()
+    assert d["step"] == 18 and d["cg_iterations_total"] > 0
+    g.close()
+
+
+def test_source2d_matches_oracle_injection():
+    """RATE source: the same macroparticle count per step as the oracle, at the
+    same FP32 positions; velocities to FP32 libm accuracy."""
+    prob = _prob(nx=32, ny=40, ppc=2, v0=0.3, dt=1.0, source=inputs.SRC_RATE, rate=150.0)
+    st = inputs.load_state2d(prob, seed=4)
+    st = [(c[:0], o[:0], v[:0]) for c, o, v in st]  # empty box: only the source
+    g = _sim(prob, st)
+    o = _oracle(prob, st)
+    g.step(1)
+    o.step(1)
+    for s in range(2):
+        c, off, v = g.particles(s)
+        assert c.size == o.x[s].size > 0
+        # injected at step 0; the oracle keeps them in order, the GPU too (no compaction)
+        xg = (c % prob["nx"] + off[:, 0].astype(np.float64)) * prob["dx"]
+        yg = (c // prob["nx"] + off[:, 1].astype(np.float64)) * prob["dx"]
+        assert np.abs(xg - o.x[s]).max() <= 1e-6 and np.abs(yg - o.y[s]).max() <= 1e-6
+        assert np.abs(v - o.v[s]).max() <= 1e-5 * max(1.0, np.abs(o.v[s]).max())
+    g.close()
+
+
+def test_load2d_rejects_bad_particles_and_capacity():
+    prob = _prob(nx=16, ny=16, ppc=1)
+    g = binding2d.Simulation2D(prob)
+    with pytest.raises(binding2d.SlpicError):
+        g.load(0, np.array([16 * 16], np.int32), np.zeros((1, 2), np.float32),
+               np.zeros((1, 3), np.float32))
+    with pytest.raises(binding2d.SlpicError):
+        g.load(0, np.array([3], np.int32), np.array([[1.0, 0.0]], np.float32),
+               np.zeros((1, 3), np.float32))
+    cap = prob["species"][0]["capacity"]
+    with pytest.raises(binding2d.SlpicError) as ei:
+        g.load(0, np.zeros(cap + 1, np.int32), np.zeros((cap + 1, 2), np.float32),
+               np.zeros((cap + 1, 3), np.float32))
+    assert ei.value.code == binding2d.binding.SLPIC_ERR_CAPACITY
+    g.close()
