@@ -138,6 +138,18 @@ const char *slpic_last_error(const slpic_t *h);
 /* Message for the last slpic_create failure in this thread. */
 const char *slpic_create_error(void);
 
+/* A batch of m independent simulations (one per cfgs[i], each validated as by
+ * slpic_create, of any size, species and speed limit) advanced together: every
+ * slpic_step runs, for all instances at once, one particle launch (CTAs spread
+ * over the instances in proportion to their particles), one launch for the
+ * particles that need the iterative push, and one field launch (one thread-block
+ * cluster per instance), captured in a CUDA graph.  Per-instance calls (loads,
+ * fields, diagnostics, read-back) take the instance index.  slpic_save,
+ * slpic_restore and the kernel-timing calls are not available on a batch
+ * (SLPIC_ERR_INVALID).  On failure nothing is allocated and
+ * slpic_create_error() names the instance that failed. */
+int slpic_create_batch(const slpic_config *cfgs, int m, slpic_t **out);
+
 /* Run all further work on `stream` (a cudaStream_t; NULL = the legacy default
  * stream).  The handle starts on a private non-blocking stream. */
 int slpic_set_stream(slpic_t *h, void *stream);
@@ -151,7 +163,9 @@ int slpic_set_stream(slpic_t *h, void *stream);
  * v) gives SLPIC_ERR_INVALID and loads nothing; more than the free capacity
  * gives SLPIC_ERR_CAPACITY.  After the last load call slpic_prepare (or the
  * first slpic_step) deposits rho^0 with beta(|v^{-1/2}|) and solves E^0.
- * `instance` must be 0. */
+ * `instance` is 0 for a handle from slpic_create and 0..m-1 for a batch from
+ * slpic_create_batch (every per-instance entry point below takes it the same
+ * way; SLPIC_ERR_INVALID outside that range). */
 int slpic_load_particles(slpic_t *h, int instance, int species, int64_t n,
                          const int32_t *cell, const float *offset, const float *v);
 

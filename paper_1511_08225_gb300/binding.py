@@ -39,7 +39,7 @@ EXPORTS = (
     "slpic_fields", "slpic_density", "slpic_charge_raw", "slpic_particle_count",
     "slpic_get_particles", "slpic_diagnostics", "slpic_save", "slpic_restore",
     "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernels_per_step",
-    "slpic_particle_step_noalloc",
+    "slpic_particle_step_noalloc", "slpic_create_batch",
 )
 
 
@@ -96,6 +96,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     sig = {
         "slpic_create": (I, [ctypes.POINTER(slpic_config), ctypes.POINTER(P)]),
+        "slpic_create_batch": (I, [ctypes.POINTER(slpic_config), I, ctypes.POINTER(P)]),
         "slpic_destroy": (I, [P]),
         "slpic_last_error": (ctypes.c_char_p, [P]),
         "slpic_create_error": (ctypes.c_char_p, []),
@@ -403,3 +404,178 @@ class Simulation:
 
     def restore(self, blob):
         slpic_restore(self.h, blob)
+
+
+def slpic_create_batch(cfgs) -> ctypes.c_void_p:
+    arr = (slpic_config * len(cfgs))(*cfgs)
+    h = ctypes.c_void_p()
+    rc = load_library().slpic_create_batch(arr, len(cfgs), ctypes.byref(h))
+    _check(None, rc, "slpic_create_batch")
+    return h
+
+
+class Batch:
+    """A batch of independent simulations (slpic_create_batch) stepped together;
+    per-instance calls take the instance index."""
+
+    def __init__(self, probs):
+        self.probs = list(probs)
+        self.h = slpic_create_batch([config_from_problem(p) for p in self.probs])
+        self.nn = [int(p["n_cells"]) + (0 if p["periodic"] else 1) for p in self.probs]
+
+    def close(self):
+        if self.h:
+            slpic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, inst, species, cell, offset, v):
+        slpic_load_particles(self.h, inst, species, cell, offset, v)
+
+    def load_state(self, inst, state):
+        for s, (c, o, v) in enumerate(state):
+            self.load(inst, s, c, o, v)
+
+    def prepare(self):
+        slpic_prepare(self.h)
+
+    def step(self, n=1):
+        slpic_step(self.h, n)
+
+    def synchronize(self):
+        slpic_synchronize(self.h)
+
+    def fields(self, inst):
+        return slpic_fields(self.h, inst, self.nn[inst])
+
+    def charge_raw(self, inst, s):
+        return slpic_charge_raw(self.h, inst, s, self.nn[inst])
+
+    def count(self, inst, s):
+        return slpic_particle_count(self.h, inst, s)
+
+    def particles(self, inst, s):
+        return slpic_get_particles(self.h, inst, s)
+
+    def diagnostics(self, inst):
+        return slpic_diagnostics(self.h, inst)
+
+
+# ------------------------------------------------------------------ plain FP64 form
+#: every function declared in include/slpic_fp64.h
+EXPORTS_FP64 = (
+    "slpic_fp64_create", "slpic_fp64_destroy", "slpic_fp64_last_error", "slpic_fp64_set_stream",
+    "slpic_fp64_load_particles", "slpic_fp64_prepare", "slpic_fp64_step",
+    "slpic_fp64_synchronize", "slpic_fp64_fields", "slpic_fp64_particle_count",
+    "slpic_fp64_get_particles",
+)
+_fp64_ready = False
+
+
+def _fp64_lib():
+    global _fp64_ready
+    L = load_library()
+    if not _fp64_ready:
+        P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        sig = {
+            "slpic_fp64_create": (I, [ctypes.POINTER(slpic_config), ctypes.POINTER(P)]),
+            "slpic_fp64_destroy": (I, [P]),
+            "slpic_fp64_last_error": (ctypes.c_char_p, [P]),
+            "slpic_fp64_set_stream": (I, [P, P]),
+            "slpic_fp64_load_particles": (I, [P, I, I64, P, P]),
+            "slpic_fp64_prepare": (I, [P]),
+            "slpic_fp64_step": (I, [P, I64]),
+            "slpic_fp64_synchronize": (I, [P]),
+            "slpic_fp64_fields": (I, [P, P, P, P]),
+            "slpic_fp64_particle_count": (I, [P, I, ctypes.POINTER(I64)]),
+            "slpic_fp64_get_particles": (I, [P, I, I64, P, P, ctypes.POINTER(I64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _fp64_ready = True
+    return L
+
+
+def _check64(h, rc, where):
+    if rc != SLPIC_OK:
+        L = _fp64_lib()
+        msg = (L.slpic_fp64_last_error(h) if h else L.slpic_create_error()) or b""
+        raise SlpicError(rc, where, msg.decode())
+
+
+class SimulationFP64:
+    """The plain FP64 form (include/slpic_fp64.h) of the same problem."""
+
+    def __init__(self, prob: dict):
+        self.prob = prob
+        self.nn = int(prob["n_cells"]) + (0 if prob["periodic"] else 1)
+        self.ns = len(prob["species"])
+        cfg = config_from_problem(prob)
+        h = ctypes.c_void_p()
+        _check64(None, _fp64_lib().slpic_fp64_create(ctypes.byref(cfg), ctypes.byref(h)),
+                 "slpic_fp64_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _fp64_lib().slpic_fp64_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: int):
+        _check64(self.h, _fp64_lib().slpic_fp64_set_stream(self.h, ctypes.c_void_p(stream)),
+                 "slpic_fp64_set_stream")
+
+    def load(self, s, x, v):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        _check64(self.h, _fp64_lib().slpic_fp64_load_particles(self.h, s, x.size, _ptr(x), _ptr(v)),
+                 "slpic_fp64_load_particles")
+
+    def load_cells(self, s, cell, offset, v):
+        dx = float(self.prob["dx"])
+        x = (np.asarray(cell, np.float64) + np.asarray(offset, np.float32).astype(np.float64)) * dx
+        self.load(s, x, np.asarray(v, np.float32).astype(np.float64))
+
+    def prepare(self):
+        _check64(self.h, _fp64_lib().slpic_fp64_prepare(self.h), "slpic_fp64_prepare")
+
+    def step(self, n=1):
+        _check64(self.h, _fp64_lib().slpic_fp64_step(self.h, n), "slpic_fp64_step")
+
+    def synchronize(self):
+        _check64(self.h, _fp64_lib().slpic_fp64_synchronize(self.h), "slpic_fp64_synchronize")
+
+    def fields(self):
+        rho, phi, E = np.zeros(self.nn), np.zeros(self.nn), np.zeros(self.nn)
+        _check64(self.h, _fp64_lib().slpic_fp64_fields(self.h, _ptr(rho), _ptr(phi), _ptr(E)),
+                 "slpic_fp64_fields")
+        return rho, phi, E
+
+    def count(self, s):
+        n = ctypes.c_int64(0)
+        _check64(self.h, _fp64_lib().slpic_fp64_particle_count(self.h, s, ctypes.byref(n)),
+                 "slpic_fp64_particle_count")
+        return n.value
+
+    def particles(self, s):
+        n = self.count(s)
+        x = np.zeros(max(n, 1))
+        v = np.zeros((max(n, 1), 3))
+        got = ctypes.c_int64(0)
+        _check64(self.h, _fp64_lib().slpic_fp64_get_particles(self.h, s, max(n, 1), _ptr(x), _ptr(v),
+                                                              ctypes.byref(got)),
+                 "slpic_fp64_get_particles")
+        return x[:got.value], v[:got.value]

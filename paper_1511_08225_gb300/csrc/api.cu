@@ -53,6 +53,14 @@ struct slpic_sim {
     long long t_len = 0;             // steps per timed graph (0 = timing off)
     long long t_launched = 0;        // timed-graph launches since timing was enabled
 
+    // a batch of independent simulations (slpic_create_batch): each member does its
+    // own per-instance work (loads, read-back, diagnostics); the batch advances all
+    // of them together with the batched kernels, captured in g1 / gc / gK
+    std::vector<slpic_sim *> members;
+    StepParams *d_params = nullptr;  // [members] on the device
+    int4 *d_work = nullptr;          // particle-kernel work items
+    int n_work = 0, max_nn = 0, max_ns = 0, batch_hard_ctas = 4;
+
     std::string err;
 };
 
@@ -72,6 +80,22 @@ static int fail(slpic_t *h, int code, const std::string &msg)
     h->err = msg;
     return code;
 }
+
+// A batch handle forwards a per-instance call to its member (as instance 0).
+#define BATCH_FORWARD(h, instance, expr)                                                   \
+    do {                                                                                   \
+        if ((h) && !(h)->members.empty()) {                                                \
+            if ((instance) < 0 || (instance) >= (int)(h)->members.size())                  \
+                return fail((h), SLPIC_ERR_INVALID, "instance out of range");              \
+            slpic_t *m_ = (h)->members[(instance)];                                        \
+            const int rc_ = (expr);                                                        \
+            if (rc_)                                                                       \
+                (h)->err = m_->err;                                                        \
+            return rc_;                                                                    \
+        }                                                                                  \
+    } while (0)
+
+static bool is_batch(const slpic_t *h) { return h && !h->members.empty(); }
 
 static int check_handle(slpic_t *h, int instance)
 {
@@ -201,8 +225,10 @@ static void free_all(slpic_t *h)
 extern "C" const char *slpic_create_error(void) { return g_create_err.c_str(); }
 
 namespace slpic {
-// slpic2d_create reports its failures through slpic_create_error too
+// slpic2d_create and slpic_fp64_create report their failures through
+// slpic_create_error too, and the FP64 form validates its config as slpic_create does
 void set_create_error(const std::string &msg) { g_create_err = msg; }
+int check_config(const slpic_config *c, std::string &why) { return validate_config(c, why); }
 }  // namespace slpic
 
 extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
@@ -348,6 +374,10 @@ extern "C" int slpic_destroy(slpic_t *h)
         return SLPIC_OK;
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    for (slpic_t *m : h->members)
+        slpic_destroy(m);
+    cudaFree(h->d_params);
+    cudaFree(h->d_work);
     free_all(h);
     delete h;
     return SLPIC_OK;
@@ -362,6 +392,8 @@ extern "C" int slpic_set_stream(slpic_t *h, void *stream)
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
     h->stream = (cudaStream_t)stream;
+    for (slpic_t *m : h->members)
+        m->stream = h->stream;
     return SLPIC_OK;
 }
 
@@ -419,6 +451,9 @@ static int append_dev(slpic_t *h, int s, long long n, const int32_t *cell, const
 extern "C" int slpic_load_particles(slpic_t *h, int instance, int species, int64_t n,
                                     const int32_t *cell, const float *offset, const float *v)
 {
+    if (is_batch(h))
+        h->dirty = true;
+    BATCH_FORWARD(h, instance, slpic_load_particles(m_, 0, species, n, cell, offset, v));
     int rc = check_handle(h, instance);
     if (rc)
         return rc;
@@ -444,6 +479,9 @@ extern "C" int slpic_load_particles_dev(slpic_t *h, int instance, int species, i
                                         const int32_t *cell, const float *offset,
                                         const float *v)
 {
+    if (is_batch(h))
+        h->dirty = true;
+    BATCH_FORWARD(h, instance, slpic_load_particles_dev(m_, 0, species, n, cell, offset, v));
     int rc = check_handle(h, instance);
     if (rc)
         return rc;
@@ -457,6 +495,9 @@ extern "C" int slpic_load_particles_dev(slpic_t *h, int instance, int species, i
 extern "C" int slpic_load_particles_f64(slpic_t *h, int instance, int species, int64_t n,
                                         const double *x, const double *v)
 {
+    if (is_batch(h))
+        h->dirty = true;
+    BATCH_FORWARD(h, instance, slpic_load_particles_f64(m_, 0, species, n, x, v));
     int rc = check_handle(h, instance);
     if (rc)
         return rc;
@@ -488,11 +529,16 @@ extern "C" int slpic_load_particles_f64(slpic_t *h, int instance, int species, i
     return slpic_load_particles(h, instance, species, n, c.data(), o.data(), vf.data());
 }
 
+static int batch_prepare(slpic_t *h);
+static int batch_step(slpic_t *h, int64_t nsteps);
+
 extern "C" int slpic_prepare(slpic_t *h)
 {
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
+    if (is_batch(h))
+        return batch_prepare(h);
     const int P = (int)(h->step & 1);
     CK(h, cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * 2 * h->ns * h->nn, h->stream));
     for (int s = 0; s < h->ns; ++s) {
@@ -551,6 +597,8 @@ extern "C" int slpic_step(slpic_t *h, int64_t nsteps)
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
+    if (is_batch(h))
+        return batch_step(h, nsteps);
     if (nsteps < 0)
         return fail(h, SLPIC_ERR_INVALID, "nsteps < 0");
     if (h->dirty && (rc = slpic_prepare(h)))
@@ -592,6 +640,15 @@ extern "C" int slpic_synchronize(slpic_t *h)
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
+    if (is_batch(h)) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (slpic_t *m : h->members)
+            if ((rc = slpic_synchronize(m))) {
+                h->err = m->err;
+                return rc;
+            }
+        return SLPIC_OK;
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     int e = 0;
     CK(h, cudaMemcpy(&e, &h->d_state->error, sizeof(int), cudaMemcpyDeviceToHost));
@@ -616,6 +673,7 @@ static int sync_prepared(slpic_t *h, int instance)
 
 extern "C" int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, float *E)
 {
+    BATCH_FORWARD(h, instance, slpic_fields(m_, 0, rho, phi, E));
     int rc = sync_prepared(h, instance);
     if (rc)
         return rc;
@@ -636,6 +694,7 @@ extern "C" int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, 
 
 extern "C" int slpic_charge_raw(slpic_t *h, int instance, int species, int64_t *acc)
 {
+    BATCH_FORWARD(h, instance, slpic_charge_raw(m_, 0, species, acc));
     int rc = sync_prepared(h, instance);
     if (rc)
         return rc;
@@ -649,6 +708,7 @@ extern "C" int slpic_charge_raw(slpic_t *h, int instance, int species, int64_t *
 
 extern "C" int slpic_density(slpic_t *h, int instance, int species, double *n)
 {
+    BATCH_FORWARD(h, instance, slpic_density(m_, 0, species, n));
     if (!n)
         return h ? fail(h, SLPIC_ERR_INVALID, "n is NULL") : SLPIC_ERR_INVALID;
     std::vector<int64_t> acc(h ? h->nn : 0);
@@ -663,6 +723,7 @@ extern "C" int slpic_density(slpic_t *h, int instance, int species, double *n)
 
 extern "C" int slpic_particle_count(slpic_t *h, int instance, int species, int64_t *n)
 {
+    BATCH_FORWARD(h, instance, slpic_particle_count(m_, 0, species, n));
     int rc = sync_prepared(h, instance);
     if (rc)
         return rc;
@@ -679,6 +740,7 @@ extern "C" int slpic_particle_count(slpic_t *h, int instance, int species, int64
 extern "C" int slpic_get_particles(slpic_t *h, int instance, int species, int64_t cap,
                                    int32_t *cell, float *offset, float *v, int64_t *n_out)
 {
+    BATCH_FORWARD(h, instance, slpic_get_particles(m_, 0, species, cap, cell, offset, v, n_out));
     int64_t n_live = 0;
     int rc = slpic_particle_count(h, instance, species, &n_live);
     if (rc)
@@ -727,6 +789,7 @@ extern "C" int slpic_get_particles(slpic_t *h, int instance, int species, int64_
 
 extern "C" int slpic_diagnostics(slpic_t *h, int instance, slpic_diag *out)
 {
+    BATCH_FORWARD(h, instance, slpic_diagnostics(m_, 0, out));
     int rc = sync_prepared(h, instance);
     if (rc)
         return rc;
@@ -778,6 +841,8 @@ struct SaveHeader {
 
 extern "C" int slpic_save(slpic_t *h, void *buf, size_t *size)
 {
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
     int rc = sync_prepared(h, 0);
     if (rc)
         return rc;
@@ -832,6 +897,8 @@ extern "C" int slpic_save(slpic_t *h, void *buf, size_t *size)
 
 extern "C" int slpic_restore(slpic_t *h, const void *buf, size_t size)
 {
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
@@ -876,6 +943,8 @@ extern "C" int slpic_restore(slpic_t *h, const void *buf, size_t size)
 // ---- timing ----------------------------------------------------------------------
 extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
 {
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
@@ -901,6 +970,8 @@ extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
 extern "C" int slpic_kernel_times(slpic_t *h, double *particle_ms, double *hard_ms,
                                   double *field_ms, int64_t *steps)
 {
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
     int rc = check_handle(h, 0);
     if (rc)
         return rc;
@@ -932,5 +1003,183 @@ extern "C" int slpic_kernels_per_step(slpic_t *h, int *n)
     if (!h || !n)
         return SLPIC_ERR_INVALID;
     *n = 3;
+    return SLPIC_OK;
+}
+
+// =================================================================================
+// Batches of independent simulations (many sheaths of uneven size advanced together)
+// =================================================================================
+
+extern "C" int slpic_create_batch(const slpic_config *cfgs, int m, slpic_t **out)
+{
+    g_create_err.clear();
+    if (!cfgs || !out || m < 1) {
+        g_create_err = "need cfgs, out and m >= 1";
+        return SLPIC_ERR_INVALID;
+    }
+    std::vector<slpic_t *> members;
+    for (int i = 0; i < m; ++i) {
+        slpic_t *mh = nullptr;
+        const int rc = slpic_create(&cfgs[i], &mh);
+        if (rc) {
+            const std::string why = "instance " + std::to_string(i) + ": " + g_create_err;
+            for (slpic_t *x : members)
+                slpic_destroy(x);
+            g_create_err = why;
+            return rc;
+        }
+        members.push_back(mh);
+    }
+    slpic_t *h = new slpic_sim();
+    h->cfg = cfgs[0];
+    h->device = members[0]->device;
+    h->num_sms = members[0]->num_sms;
+    h->members = members;
+    for (slpic_t *x : members) {
+        h->max_nn = std::max(h->max_nn, x->nn);
+        h->max_ns = std::max(h->max_ns, x->ns);
+    }
+    auto bail = [&](int code, const std::string &msg) {
+        g_create_err = msg;
+        slpic_destroy(h);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(SLPIC_ERR_CUDA, "stream creation failed");
+    h->stream = h->own_stream;
+    for (slpic_t *x : members)
+        x->stream = h->stream;
+    if (cudaMalloc(&h->d_params, sizeof(StepParams) * m) != cudaSuccess)
+        return bail(SLPIC_ERR_OOM, "device allocation failed");
+    int occ = 0, occ_c = 0;
+    if (configure_batch_kernels(h->max_nn, &occ, &occ_c) != cudaSuccess || occ < 1 || occ_c < 1)
+        return bail(SLPIC_ERR_INVALID, "batched particle kernel cannot be resident");
+    h->ctas = occ;     // resident batched CTAs per SM (work-table sizing)
+    h->ctas_c = occ_c;
+    *out = h;
+    return SLPIC_OK;
+}
+
+// Work items of the batched particle kernels: every (instance, species) gets CTAs
+// in proportion to its particles (at least one), about `waves` full waves of the GPU.
+static int batch_tables(slpic_t *h)
+{
+    std::vector<long long> n;
+    long long total = 0;
+    for (slpic_t *m : h->members) {
+        DevState st;
+        int rc = read_state(m, &st);
+        if (rc) {
+            h->err = m->err;
+            return rc;
+        }
+        const int P = (int)(m->step & 1);
+        for (int s = 0; s < m->ns; ++s) {
+            n.push_back((long long)st.count[s][P]);
+            total += (long long)st.count[s][P];
+        }
+    }
+    const int waves = 2;
+    const long long budget = (long long)h->num_sms * std::min(h->ctas, h->ctas_c) * waves;
+    std::vector<int4> work;
+    size_t k = 0;
+    for (int i = 0; i < (int)h->members.size(); ++i) {
+        for (int s = 0; s < h->members[i]->ns; ++s, ++k) {
+            long long c = total > 0 ? (n[k] * budget + total - 1) / total : 1;
+            // a share large enough to amortise the per-CTA grid staging
+            const long long per = std::max(1LL, n[k] / 4096);
+            c = std::max(1LL, std::min(c, per));
+            for (int j = 0; j < (int)c; ++j)
+                work.push_back(make_int4(i, s, j, (int)c));
+        }
+    }
+    cudaFree(h->d_work);
+    h->d_work = nullptr;
+    CK(h, cudaMalloc(&h->d_work, sizeof(int4) * work.size()));
+    CK(h, cudaMemcpy(h->d_work, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice));
+    h->n_work = (int)work.size();
+    return SLPIC_OK;
+}
+
+static int batch_prepare(slpic_t *h)
+{
+    int rc;
+    for (slpic_t *m : h->members) {
+        if ((rc = slpic_prepare(m))) {
+            h->err = m->err;
+            return rc;
+        }
+    }
+    std::vector<StepParams> ps;
+    for (slpic_t *m : h->members)
+        ps.push_back(m->p);
+    CK(h, cudaMemcpyAsync(h->d_params, ps.data(), sizeof(StepParams) * ps.size(),
+                          cudaMemcpyHostToDevice, h->stream));
+    if ((rc = batch_tables(h)))
+        return rc;
+    // work items changed: the graphs are captured again on the next step
+    for (cudaGraphExec_t *g : {&h->g1, &h->gc, &h->gK})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    h->dirty = false;
+    return SLPIC_OK;
+}
+
+static int batch_capture(slpic_t *h, long long first_step, int nsteps, cudaGraphExec_t *out)
+{
+    const int m = (int)h->members.size();
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < nsteps; ++k) {
+        const bool compact = (first_step + k) % kCompactEvery == kCompactEvery - 1;
+        launch_particles_batch(h->d_params, h->d_work, h->n_work, h->max_nn, compact,
+                               h->cap_stream);
+        launch_hard_batch(h->d_params, m, h->batch_hard_ctas, compact, h->cap_stream);
+        launch_field_batch(h->d_params, m, h->max_nn, h->max_ns, compact ? 2 : 1, h->cap_stream);
+    }
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess) {
+        h->err = std::string("graph capture: ") + cudaGetErrorString(e);
+        return SLPIC_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e);
+    return SLPIC_OK;
+}
+
+static int batch_step(slpic_t *h, int64_t nsteps)
+{
+    int rc;
+    if (nsteps < 0)
+        return fail(h, SLPIC_ERR_INVALID, "nsteps < 0");
+    if (h->dirty && (rc = batch_prepare(h)))
+        return rc;
+    if (nsteps == 0)
+        return SLPIC_OK;
+    if (!h->g1 && (rc = batch_capture(h, 0, 1, &h->g1)))
+        return rc;
+    if (!h->gc && (rc = batch_capture(h, kCompactEvery - 1, 1, &h->gc)))
+        return rc;
+    int64_t left = nsteps;
+    while (left > 0) {
+        const long long phase = h->step % kCompactEvery;
+        int64_t adv = 1;
+        if (phase == 0 && left >= kCompactEvery) {
+            if (!h->gK && (rc = batch_capture(h, 0, kCompactEvery, &h->gK)))
+                return rc;
+            CK(h, cudaGraphLaunch(h->gK, h->stream));
+            adv = kCompactEvery;
+        } else {
+            CK(h, cudaGraphLaunch(phase == kCompactEvery - 1 ? h->gc : h->g1, h->stream));
+        }
+        h->step += adv;
+        for (slpic_t *m : h->members)
+            m->step += adv;
+        left -= adv;
+    }
     return SLPIC_OK;
 }

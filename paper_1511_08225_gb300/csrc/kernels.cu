@@ -10,6 +10,7 @@
 // Citations: Werner et al., arXiv 1511.08225, Appendix A, Eq. (slpicIntegration).
 #include <cooperative_groups.h>
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -110,7 +111,9 @@ __device__ __forceinline__ void list_hard(bool hard, long long i, const SpeciesD
         sp.hard[b + __popc(hm & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
-__global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
+// Bodies of the kernels take the parameters by reference (kernel parameter space
+// for one simulation, shared memory for a batch) and the CTA's share of the work.
+__device__ __forceinline__ void particles_compact(const StepParams &p, int s, int cta, int nctas)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned *s_lo = reinterpret_cast<unsigned *>(smem);  // [nn] deposit, low words
@@ -120,7 +123,6 @@ __global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
     __shared__ unsigned long long s_base;
     __shared__ unsigned int s_abs[2];
 
-    const int s = blockIdx.y;
     const SpeciesDev &sp = p.sp[s];
     const long long step = *(volatile long long *)&p.st->step;
     const int P = (int)(step & 1);
@@ -143,8 +145,8 @@ __global__ void __launch_bounds__(kPB, 3) k_particles_compact(StepParams p)
 
     DepositSplit32 dep{s_lo, s_hi};
     const long long ntiles = (n + kPT - 1) / kPT;
-    const long long t0 = ntiles * blockIdx.x / gridDim.x;
-    const long long t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    const long long t0 = ntiles * cta / nctas;
+    const long long t1 = ntiles * (cta + 1) / nctas;
 
     for (long long t = t0; t < t1; ++t) {
         const long long base = t * kPT;
@@ -196,7 +198,7 @@ constexpr int kWT = 32 * kWI;    // particles per warp-tile
 
 size_t particle_inplace_smem_bytes(int nn) { return (size_t)nn * 3 * sizeof(unsigned); }
 
-__global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
+__device__ __forceinline__ void particles_inplace(const StepParams &p, int s, int cta, int nctas)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned *s_lo = reinterpret_cast<unsigned *>(smem);  // [nn] deposit, low words
@@ -204,7 +206,6 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
     float *s_E = reinterpret_cast<float *>(s_hi + p.nn);  // [nn]
     __shared__ unsigned int s_abs[2];
 
-    const int s = blockIdx.y;
     const SpeciesDev &sp = p.sp[s];
     const long long step = *(volatile long long *)&p.st->step;
     const int P = (int)(step & 1);
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
     // warp-tiles of kWT consecutive particles: the CTA owns a contiguous range of
     // them and its warps take every kNW-th
     const long long nwt = (n + kWT - 1) / kWT;
-    const long long w0 = nwt * blockIdx.x / gridDim.x;
-    const long long w1 = nwt * (blockIdx.x + 1) / gridDim.x;
+    const long long w0 = nwt * cta / nctas;
+    const long long w1 = nwt * (cta + 1) / nctas;
     for (long long t = w0 + warp; t < w1; t += kNW) {
         const long long base = t * kWT;
         int c[kWI];
@@ -299,6 +300,46 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
         atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
 }
 
+// Copy one instance's parameters into shared memory (batched kernels).
+__device__ __forceinline__ void load_params(StepParams &dst, const StepParams *src)
+{
+    static_assert(sizeof(StepParams) % 8 == 0, "copied as 8-byte words");
+    const unsigned long long *a = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *b = reinterpret_cast<unsigned long long *>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepParams) / 8); k += blockDim.x)
+        b[k] = a[k];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPB, 3) k_particles_compact(const __grid_constant__ StepParams p)
+{
+    particles_compact(p, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kPB, 4) k_particles(const __grid_constant__ StepParams p)
+{
+    particles_inplace(p, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// Batched forms: CTA b works on (instance, species, share, shares) = work[b].
+__global__ void __launch_bounds__(kPB, 3)
+    k_particles_compact_batch(const StepParams *__restrict__ ps, const int4 *__restrict__ work)
+{
+    __shared__ StepParams s_p;
+    const int4 w = work[blockIdx.x];
+    load_params(s_p, ps + w.x);
+    particles_compact(s_p, w.y, w.z, w.w);
+}
+
+__global__ void __launch_bounds__(kPB, 4)
+    k_particles_batch(const StepParams *__restrict__ ps, const int4 *__restrict__ work)
+{
+    __shared__ StepParams s_p;
+    const int4 w = work[blockIdx.x];
+    load_params(s_p, ps + w.x);
+    particles_inplace(s_p, w.y, w.z, w.w);
+}
+
 // ---------------------------------------------------------------------------------
 // k_hard: the particles the particle kernel listed (those needing the piece walk and
 // Newton).  They cluster (strong fields, the source band), and each needs a long
@@ -308,7 +349,8 @@ __global__ void __launch_bounds__(kPB, 4) k_particles(StepParams p)
 // int64 accumulator.  After an in-place step a particle returns to its slot (a hole
 // if absorbed); after a compacting step survivors are appended to the output.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_hard(StepParams p, int compact)
+__device__ __forceinline__ void hard_body(const StepParams &p, int compact, long long gwarp,
+                                          long long nwarps)
 {
     __shared__ unsigned int s_abs[kMaxSpecies][2];
     if (threadIdx.x < 2 * kMaxSpecies)
@@ -317,8 +359,6 @@ __global__ void __launch_bounds__(256) k_hard(StepParams p, int compact)
     const long long step = *(volatile long long *)&p.st->step;
     const int P = (int)(step & 1);
     const int lane = threadIdx.x & 31;
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (int s = 0; s < p.ns; ++s) {
         const SpeciesDev &sp = p.sp[s];
         const long long nh = (long long)*(volatile unsigned long long *)&p.st->hard_n[s];
@@ -363,6 +403,21 @@ __global__ void __launch_bounds__(256) k_hard(StepParams p, int compact)
         if (s < p.ns && s_abs[s][w])
             atomicAdd(&p.st->absorbed_step[s][w], (unsigned long long)s_abs[s][w]);
     }
+}
+
+__global__ void __launch_bounds__(256) k_hard(const __grid_constant__ StepParams p, int compact)
+{
+    hard_body(p, compact, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+              (long long)gridDim.x * (blockDim.x >> 5));
+}
+
+// batched: grid (CTAs per instance, instances)
+__global__ void __launch_bounds__(256) k_hard_batch(const StepParams *__restrict__ ps, int compact)
+{
+    __shared__ StepParams s_p;
+    load_params(s_p, ps + blockIdx.y);
+    hard_body(s_p, compact, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+              (long long)gridDim.x * (blockDim.x >> 5));
 }
 
 // ---------------------------------------------------------------------------------
@@ -637,8 +692,7 @@ __device__ __forceinline__ double u128_to_double(u128 v)
     return d;
 }
 
-__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
-    k_field(StepParams p, int mode)
+__device__ __forceinline__ void field_body(const StepParams &p, int mode)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -873,6 +927,21 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
+    k_field(const __grid_constant__ StepParams p, int mode)
+{
+    field_body(p, mode);
+}
+
+// batched: one cluster per instance
+__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
+    k_field_batch(const StepParams *__restrict__ ps, int mode)
+{
+    __shared__ StepParams s_p;
+    load_params(s_p, ps + blockIdx.x / kFC);
+    field_body(s_p, mode);
+}
+
 // ---------------------------------------------------------------------------------
 // Diagnostics: per species sum(beta), sum(beta |v|^2) over the live particles.
 // out[2*s + 0/1], FP64, zeroed by the caller.
@@ -967,6 +1036,13 @@ int field_max_nodes() { return 1 << 16; }
 
 cudaError_t configure_kernels(int nn)
 {
+    // the attributes only ever grow: simulations of several sizes share the kernels
+    static std::mutex mu;
+    static int configured = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (nn <= configured)
+        return cudaSuccess;
+    configured = nn;
     cudaError_t e = cudaFuncSetAttribute(k_particles_compact,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)particle_kernel_smem_bytes(nn));
@@ -1010,6 +1086,48 @@ void launch_particles(const StepParams &p, int ctas_per_species, bool compact, c
 void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st)
 {
     k_hard<<<ctas, 256, 0, st>>>(p, compact ? 1 : 0);
+}
+
+void launch_particles_batch(const StepParams *d_params, const int4 *d_work, int n_work,
+                            int max_nn, bool compact, cudaStream_t st)
+{
+    if (compact)
+        k_particles_compact_batch<<<n_work, kPB, particle_kernel_smem_bytes(max_nn), st>>>(d_params,
+                                                                                          d_work);
+    else
+        k_particles_batch<<<n_work, kPB, particle_inplace_smem_bytes(max_nn), st>>>(d_params, d_work);
+}
+
+void launch_hard_batch(const StepParams *d_params, int m, int ctas_per_instance, bool compact,
+                       cudaStream_t st)
+{
+    k_hard_batch<<<dim3(ctas_per_instance, m), 256, 0, st>>>(d_params, compact ? 1 : 0);
+}
+
+void launch_field_batch(const StepParams *d_params, int m, int max_nn, int max_ns, int mode,
+                        cudaStream_t st)
+{
+    k_field_batch<<<m * kFC, kFCT, field_cluster_smem_bytes(max_nn, max_ns), st>>>(d_params, mode);
+}
+
+cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compact_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_particles_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)particle_inplace_smem_bytes(max_nn));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_particles_compact_batch,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)particle_kernel_smem_bytes(max_nn));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_field_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)field_cluster_smem_bytes(max_nn, kMaxSpecies));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(inplace_per_sm, k_particles_batch, kPB,
+                                                          particle_inplace_smem_bytes(max_nn));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(compact_per_sm, k_particles_compact_batch,
+                                                          kPB, particle_kernel_smem_bytes(max_nn));
+    return e;
 }
 
 size_t field_cluster_smem_bytes(int nn, int ns)

@@ -28,6 +28,15 @@ void launch_particles(const StepParams &p, int ctas_per_species, bool compact, c
 void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st);
 void launch_field(const StepParams &p, int mode, cudaStream_t st);
 void launch_potential(const StepParams &p, cudaStream_t st);
+// batched forms over many instances: d_params[m] on the device; the particle
+// kernels take one CTA per work item (instance, species, share, shares)
+cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compact_per_sm);
+void launch_particles_batch(const StepParams *d_params, const int4 *d_work, int n_work,
+                            int max_nn, bool compact, cudaStream_t st);
+void launch_hard_batch(const StepParams *d_params, int m, int ctas_per_instance, bool compact,
+                       cudaStream_t st);
+void launch_field_batch(const StepParams *d_params, int m, int max_nn, int max_ns, int mode,
+                        cudaStream_t st);
 void launch_deposit(const StepParams &p, int ctas_per_species, cudaStream_t st);
 void launch_diag(const StepParams &p, double *out, int ctas_per_species, cudaStream_t st);
 void launch_validate(const int32_t *cell, const float *off, const float *v, long long n,

@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(1024) k_inject2d(Params2D p, int compact)
 // every CTA leaves at its next check.
 __device__ __forceinline__ bool grid_sync(State2D *st)
 {
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *gen = &st->bar_gen;
@@ -452,9 +453,11 @@ __device__ __forceinline__ bool grid_sync(State2D *st)
             }
         }
         __threadfence();
+        // one decision per CTA, so that its threads leave or stay together
+        s_ok = *(volatile int *)&st->error != SLPIC_ERR_TIMEOUT;
     }
     __syncthreads();
-    return *(volatile int *)&st->error != SLPIC_ERR_TIMEOUT;
+    return s_ok != 0;
 }
 
 // block sum of v (FP64, fixed order), result valid in every thread

@@ -244,3 +244,22 @@ def load_state2d(prob: dict, seed: int | None = None):
         cell = (cy.astype(np.int64) * nx + cx).astype(np.int32)
         out.append((cell, np.stack([ox, oy], axis=1).astype(np.float32), v.astype(np.float32)))
     return out
+
+
+# ------------------------------------------------------------------ batches
+def batch_problems(m=256, seed=SEED, cells=(512, 8192), ppc=(100, 1000),
+                   mass_ratios=(1836.0, 73440.0), v0=(0.01, 0.5), dx=0.5, T_e=1.0, T_i=0.1):
+    """m independent sheaths of uneven size: cells ~ U{lo..hi}, ppc ~ U{lo..hi},
+    m_i/m_e drawn from mass_ratios with equal probability, v0 log-uniform in
+    [v0_lo, v0_hi] (in v_te), dt = dx / v0, T_e/T_i = 10 (instance i is seeded
+    seed + i)."""
+    rng = make_rng(seed)
+    out = []
+    for i in range(m):
+        n = int(rng.integers(cells[0], cells[1] + 1))
+        pc = int(rng.integers(ppc[0], ppc[1] + 1))
+        mr = float(mass_ratios[int(rng.integers(0, len(mass_ratios)))])
+        vv = float(math.exp(rng.uniform(math.log(v0[0]), math.log(v0[1]))))
+        out.append(sheath_problem(n_cells=n, dx=dx, v0=vv, ppc=pc, mass_ratio=mr, T_e=T_e,
+                                  T_i=T_i, seed=seed + i))
+    return out

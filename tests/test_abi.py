@@ -154,3 +154,13 @@ def test_2d_config_errors_need_no_device(lib):
     with pytest.raises(binding.SlpicError) as ei:
         binding2d.slpic2d_create(binding2d.config_from_problem(prob))
     assert ei.value.code == binding.SLPIC_ERR_INVALID
+
+
+def test_every_fp64_function_is_exported(lib):
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "slpic_fp64.h")).read(),
+                 flags=re.S)
+    names = sorted(set(re.findall(r"\b(slpic_fp64_[a-z0-9_]+)\s*\(", src)))
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.EXPORTS_FP64) == names
