@@ -112,6 +112,15 @@ int slpic2d_get_particles(slpic2d_t *h, int s, int32_t *cell, float *offset, flo
                           int64_t *n);
 int slpic2d_diagnostics(slpic2d_t *h, slpic2d_diag *out);
 
+/* Kernel timing: with on != 0, every following step (up to 4096) records CUDA
+ * events on the handle's stream around its three kernels; slpic2d_kernel_times
+ * synchronises and returns the mean per-step time (ms) of the particle kernel,
+ * the source kernel and the CG field kernel over the recorded steps (*steps of
+ * them), then starts a new recording. */
+int slpic2d_enable_kernel_timing(slpic2d_t *h, int on);
+int slpic2d_kernel_times(slpic2d_t *h, double *particle_ms, double *inject_ms, double *field_ms,
+                         int64_t *steps);
+
 /* The field solve alone, for a given charge density: rho and phi host arrays
  * of (ny+1)*nx entries (phi's rows 0 and ny are set to the plate potentials,
  * its other rows are the initial guess on entry and the solution on return).

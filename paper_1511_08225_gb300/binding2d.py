@@ -17,7 +17,8 @@ EXPORTS2D = (
     "slpic2d_create", "slpic2d_destroy", "slpic2d_last_error", "slpic2d_set_stream",
     "slpic2d_load_particles", "slpic2d_prepare", "slpic2d_step", "slpic2d_synchronize",
     "slpic2d_fields", "slpic2d_charge_raw", "slpic2d_particle_count", "slpic2d_get_particles",
-    "slpic2d_diagnostics", "slpic2d_solve_poisson",
+    "slpic2d_diagnostics", "slpic2d_solve_poisson", "slpic2d_enable_kernel_timing",
+    "slpic2d_kernel_times",
 )
 
 
@@ -66,6 +67,10 @@ def load_library() -> ctypes.CDLL:
         "slpic2d_get_particles": (I, [P, I, P, P, P, ctypes.POINTER(I64)]),
         "slpic2d_diagnostics": (I, [P, ctypes.POINTER(slpic2d_diag)]),
         "slpic2d_solve_poisson": (I, [P, P, P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]),
+        "slpic2d_enable_kernel_timing": (I, [P, I]),
+        "slpic2d_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -201,6 +206,21 @@ def slpic2d_solve_poisson(h, rho: np.ndarray, phi0: np.ndarray | None = None):
     _check(h, load_library().slpic2d_solve_poisson(h, _ptr(rho), _ptr(phi), ctypes.byref(it),
                                                    ctypes.byref(res)), "slpic2d_solve_poisson")
     return phi, it.value, res.value
+
+
+def slpic2d_enable_kernel_timing(h, on: bool = True):
+    _check(h, load_library().slpic2d_enable_kernel_timing(h, int(on)),
+           "slpic2d_enable_kernel_timing")
+
+
+def slpic2d_kernel_times(h):
+    """(particle_ms, inject_ms, field_ms, steps): mean per-step kernel times."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(h, load_library().slpic2d_kernel_times(h, ctypes.byref(a), ctypes.byref(b),
+                                                  ctypes.byref(c), ctypes.byref(n)),
+           "slpic2d_kernel_times")
+    return a.value, b.value, c.value, n.value
 
 
 class Simulation2D:

@@ -3,8 +3,8 @@
 // Per step (Appendix A, Eq. slpicIntegration):
 //   k_step64    gather E^n (FP64, grid in shared memory) -> velocity push in FP64
 //               -> x^{n+1} = x^n + beta v dt -> walls -> FP64 CIC deposit of
-//               rho^{n+1} (shared-memory double atomics, then global) -> survivors
-//               packed into the other buffer
+//               rho^{n+1} (global double atomics) -> survivors packed into the
+//               other buffer
 //   k_inject64  one CTA: source particles (FP64) appended and deposited; bookkeeping
 //   k_field64   one CTA: rho = sum_s q_s n_s, Poisson by FP64 prefix sums, E
 //
@@ -110,11 +110,13 @@ __device__ double push64(int kind, double ux, double uy, double uz, double ax, d
         return ux + ax * dt;  // beta == 1 (or no force): plain leapfrog
     const double A = fabs(ax), sg = ax > 0.0 ? 1.0 : -1.0;
     const double wa = sg * ux, D = uy * uy + uz * uz, budget = A * dt;
-    const double T = H64(kind, wa, D, v0) + budget;
+    const double Ha = H64(kind, wa, D, v0), T = Ha + budget;
+    // H is evaluated to a few ulp of its size: below that the residual is noise
+    const double gtol = 8.0 * 2.220446049250313e-16 * (fabs(Ha) + budget);
     double lo = wa, hi = wa + budget, w = hi;
-    for (int it = 0; it < 100; ++it) {
+    for (int it = 0; it < 60; ++it) {
         const double g = H64(kind, w, D, v0) - T;
-        if (g == 0.0)
+        if (fabs(g) <= gtol)
             break;
         if (g > 0.0)
             hi = w;
@@ -123,11 +125,10 @@ __device__ double push64(int kind, double ux, double uy, double uz, double ax, d
         double wn = w - g / inv_beta64(kind, w, D, v0);
         if (!(wn > lo && wn < hi))
             wn = 0.5 * (lo + hi);
-        if (fabs(wn - w) <= 1e-15 * fmax(1.0, fabs(w)) || hi - lo <= 1e-15 * fmax(1.0, fabs(w))) {
-            w = wn;
-            break;
-        }
+        const bool small = fabs(wn - w) <= 1e-14 * fmax(fabs(w), budget);
         w = wn;
+        if (small)
+            break;
     }
     return sg * w;
 }
@@ -151,7 +152,6 @@ __global__ void __launch_bounds__(kThreads) k_step64(P64 p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     double *s_E = reinterpret_cast<double *>(smem);  // [nn]
-    double *s_d = s_E + p.nn;                          // [nn] this CTA's deposit
     __shared__ int s_cnt[kItems * kWarps];
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_abs[2];
@@ -161,10 +161,8 @@ __global__ void __launch_bounds__(kThreads) k_step64(P64 p)
     const long long n = (long long)p.st->count[s][P];
     const int N = p.N, nn = p.nn;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = threadIdx.x; j < nn; j += blockDim.x) {
+    for (int j = threadIdx.x; j < nn; j += blockDim.x)
         s_E[j] = p.E[j];
-        s_d[j] = 0.0;
-    }
     if (threadIdx.x < 2)
         s_abs[threadIdx.x] = 0u;
     __syncthreads();
@@ -217,8 +215,8 @@ __global__ void __launch_bounds__(kThreads) k_step64(P64 p)
             int cn1 = cn + 1;
             if (p.periodic && cn1 == N)
                 cn1 = 0;
-            atomicAdd(s_d + cn, sp.w_dx * b * (1.0 - dn));
-            atomicAdd(s_d + cn1, sp.w_dx * b * dn);
+            atomicAdd(p.dens + (size_t)s * nn + cn, sp.w_dx * b * (1.0 - dn));
+            atomicAdd(p.dens + (size_t)s * nn + cn1, sp.w_dx * b * dn);
         }
         // pack the survivors (one global atomic per tile)
         unsigned mask[kItems];
@@ -258,9 +256,6 @@ __global__ void __launch_bounds__(kThreads) k_step64(P64 p)
         }
         __syncthreads();
     }
-    for (int j = threadIdx.x; j < nn; j += blockDim.x)
-        if (s_d[j] != 0.0)
-            atomicAdd(p.dens + (size_t)s * nn + j, s_d[j]);
     if (threadIdx.x < 2 && s_abs[threadIdx.x])
         atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
 }
@@ -532,7 +527,7 @@ extern "C" int slpic_fp64_create(const slpic_config *c, slpic_fp64_t **out)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int nn = c->bc == SLPIC_BC_PERIODIC ? c->n_cells : c->n_cells + 1;
-    const size_t smem = sizeof(double) * 2 * (size_t)nn;
+    const size_t smem = sizeof(double) * (size_t)nn;
     if (smem + 1024 > (size_t)max_smem || (nn + kFieldThreads - 1) / kFieldThreads > kMaxChunk) {
         slpic::set_create_error("grid too large for the FP64 kernels");
         return SLPIC_ERR_INVALID;
@@ -695,7 +690,7 @@ extern "C" int slpic_fp64_step(slpic_fp64_t *h, int64_t nsteps)
     if (!h || nsteps < 0)
         return h ? fail64(h, SLPIC_ERR_INVALID, "nsteps < 0") : SLPIC_ERR_INVALID;
     P64 &p = h->p;
-    const size_t smem = sizeof(double) * 2 * (size_t)p.nn;
+    const size_t smem = sizeof(double) * (size_t)p.nn;
     for (int64_t k = 0; k < nsteps; ++k) {
         k_step64<<<dim3(h->ctas, p.ns), kThreads, smem, h->stream>>>(p);
         k_inject64<<<1, 1024, 0, h->stream>>>(p);

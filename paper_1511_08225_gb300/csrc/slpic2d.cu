@@ -42,6 +42,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kCompact2d = 16;                  // compacting step interval
 constexpr int kCgThreads = 256;
 constexpr long long kBarrierSpins = 1LL << 23;  // bounded grid-barrier wait (~1 s)
+constexpr long long kMaxTimedSteps2d = 4096;    // steps recorded by the kernel timing
 
 struct Species2D {
     int32_t *cell[2];
@@ -657,6 +658,9 @@ struct slpic2d_sim {
     int ctas = 1;     // particle-kernel CTAs per species
     int cg_ctas = 1;  // cooperative CG grid
     bool prepared = false;
+    bool timing = false;               // record events around the kernels of each step
+    std::vector<cudaEvent_t> events;   // 4 per recorded step
+    long long t_steps = 0;             // steps recorded since the last read
     State2D *d_state = nullptr;
     std::vector<void *> allocs;
     std::string err;
@@ -850,6 +854,10 @@ extern "C" int slpic2d_destroy(slpic2d_t *h)
         return SLPIC_OK;
     if (h->own_stream)
         cudaStreamSynchronize(h->own_stream);
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->events)
+        cudaEventDestroy(e);
     for (void *a : h->allocs)
         cudaFree(a);
     if (h->own_stream)
@@ -946,16 +954,67 @@ extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
     Params2D &p = h->p;
     for (int64_t k = 0; k < nsteps; ++k, ++step) {
         const bool compact = (step % kCompact2d) == kCompact2d - 1;
+        cudaEvent_t *ev = nullptr;
+        if (h->timing && h->t_steps < kMaxTimedSteps2d) {
+            while ((long long)h->events.size() < 4 * (h->t_steps + 1)) {
+                cudaEvent_t e;
+                CK2(h, cudaEventCreate(&e));
+                h->events.push_back(e);
+            }
+            ev = &h->events[4 * h->t_steps++];
+        }
+        if (ev)
+            CK2(h, cudaEventRecord(ev[0], h->stream));
         if (compact)
             k_particles2d<true><<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
         else
             k_particles2d<false><<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
+        if (ev)
+            CK2(h, cudaEventRecord(ev[1], h->stream));
         k_inject2d<<<1, 1024, 0, h->stream>>>(p, compact ? 1 : 0);
         CK2(h, cudaGetLastError());
+        if (ev)
+            CK2(h, cudaEventRecord(ev[2], h->stream));
         rc = launch_cg(h, 0);
         if (rc)
             return rc;
+        if (ev)
+            CK2(h, cudaEventRecord(ev[3], h->stream));
     }
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_enable_kernel_timing(slpic2d_t *h, int on)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    h->timing = on != 0;
+    h->t_steps = 0;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_kernel_times(slpic2d_t *h, double *particle_ms, double *inject_ms,
+                                    double *field_ms, int64_t *steps)
+{
+    if (!h || !particle_ms || !inject_ms || !field_ms || !steps)
+        return h ? fail2(h, SLPIC_ERR_INVALID, "bad arguments") : SLPIC_ERR_INVALID;
+    CK2(h, cudaStreamSynchronize(h->stream));
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (long long t = 0; t < h->t_steps; ++t) {
+        float x = 0.f, y = 0.f, z = 0.f;
+        CK2(h, cudaEventElapsedTime(&x, h->events[4 * t], h->events[4 * t + 1]));
+        CK2(h, cudaEventElapsedTime(&y, h->events[4 * t + 1], h->events[4 * t + 2]));
+        CK2(h, cudaEventElapsedTime(&z, h->events[4 * t + 2], h->events[4 * t + 3]));
+        a += x;
+        b += y;
+        c += z;
+    }
+    *steps = h->t_steps;
+    const double n = h->t_steps ? (double)h->t_steps : 1.0;
+    *particle_ms = a / n;
+    *inject_ms = b / n;
+    *field_ms = c / n;
+    h->t_steps = 0;
     return SLPIC_OK;
 }
 
