@@ -1057,6 +1057,8 @@ extern "C" int slpic_create_batch(const slpic_config *cfgs, int m, slpic_t **out
         return bail(SLPIC_ERR_INVALID, "batched particle kernel cannot be resident");
     h->ctas = occ;     // resident batched CTAs per SM (work-table sizing)
     h->ctas_c = occ_c;
+    // the iterative-push kernel: the single simulation's whole-GPU grid, shared out
+    h->batch_hard_ctas = std::max(4, h->num_sms * 8 / m);
     *out = h;
     return SLPIC_OK;
 }

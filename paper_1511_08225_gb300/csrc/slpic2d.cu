@@ -40,7 +40,9 @@ constexpr int kItems = 4;                       // particles per thread per tile
 constexpr int kTile = kThreads * kItems;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCompact2d = 16;                  // compacting step interval
-constexpr int kCgThreads = 256;
+constexpr int kCgThreads = 512;
+constexpr int kBarGroup = 16;   // CTAs per first-level group of the grid barrier
+constexpr int kBarGroups = 64;  // first-level counters (CG grids up to 1,024 CTAs)
 constexpr long long kBarrierSpins = 1LL << 23;  // bounded grid-barrier wait (~1 s)
 constexpr long long kMaxTimedSteps2d = 4096;    // steps recorded by the kernel timing
 
@@ -67,7 +69,8 @@ struct State2D {
     double cg_res;
     int cg_iters;
     int error;
-    unsigned bar_count, bar_gen;  // grid barrier of k_cg2d
+    unsigned bar_count, bar_gen;  // grid barrier of k_cg2d: root counter, generation
+    unsigned bar_group[kBarGroups];  // first-level counters of the grid barrier
 };
 
 struct Params2D {
@@ -427,9 +430,12 @@ __global__ void __launch_bounds__(1024) k_inject2d(Params2D p, int compact)
 // everywhere and in every run.
 // ---------------------------------------------------------------------------------
 
-// Grid barrier for a cooperative launch (all CTAs co-resident).  The wait is
-// bounded: past kBarrierSpins polls the kernel records SLPIC_ERR_TIMEOUT and
-// every CTA leaves at its next check.
+// Grid barrier for a cooperative launch (all CTAs co-resident), two levels: CTAs
+// arrive on the counter of their group of kBarGroup, the last of each group on the
+// root counter, and the last of all advances the generation the others wait on
+// (each counter is reset by its last arriver before the generation moves).  The
+// wait is bounded: past kBarrierSpins polls the kernel records SLPIC_ERR_TIMEOUT
+// and every CTA leaves at its next check.
 __device__ __forceinline__ bool grid_sync(State2D *st)
 {
     __shared__ int s_ok;
@@ -438,12 +444,21 @@ __device__ __forceinline__ bool grid_sync(State2D *st)
         volatile unsigned *gen = &st->bar_gen;
         const unsigned g = *gen;
         __threadfence();
-        const unsigned arrived = atomicAdd(&st->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            st->bar_count = 0u;
+        const unsigned grp = blockIdx.x / kBarGroup;
+        const unsigned ngrp = (gridDim.x + kBarGroup - 1) / kBarGroup;
+        const unsigned in_grp = min((unsigned)kBarGroup, gridDim.x - grp * kBarGroup);
+        bool last = false;
+        if (atomicAdd(&st->bar_group[grp], 1u) == in_grp - 1) {
+            st->bar_group[grp] = 0u;
             __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
+            if (atomicAdd(&st->bar_count, 1u) == ngrp - 1) {
+                st->bar_count = 0u;
+                __threadfence();
+                atomicAdd(&st->bar_gen, 1u);
+                last = true;
+            }
+        }
+        if (!last) {
             long long spins = 0;
             while (*gen == g) {
                 if (++spins > kBarrierSpins) {
@@ -823,7 +838,7 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg2d, kCgThreads, 0) != cudaSuccess ||
         occ < 1)
         return bail(SLPIC_ERR_CUDA, "CG kernel occupancy query failed");
-    h->cg_ctas = sms * std::min(occ, 2);
+    h->cg_ctas = std::min(sms * std::min(occ, 1), kBarGroup * kBarGroups);
     h->ctas = sms * 4;
     if (!alloc((void **)&p.part, sizeof(double) * 3 * h->cg_ctas))
         return bail(SLPIC_ERR_OOM, "device allocation failed");
