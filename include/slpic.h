@@ -67,6 +67,14 @@ extern "C" {
 #define SLPIC_SRC_NONE 0
 #define SLPIC_SRC_LOSS_MATCHED 1 /* re-inject the physical count of ref-species losses */
 #define SLPIC_SRC_RATE 2         /* inject rate*dt physical pairs per step              */
+#define SLPIC_SRC_WALL 3         /* Sec. IV: every species with T_src > 0 enters through
+                                    the plate at x = L from a stationary Maxwellian plasma
+                                    of density src_rate: the one-sided flux
+                                    src_rate sqrt(T_src/m) / sqrt(2 pi) per unit area and
+                                    time, with the flux-weighted half-Maxwellian (|vx|
+                                    Rayleigh, towards -x; vy, vz Maxwellian), each particle
+                                    placed where it has moved since a uniformly random
+                                    entry time in the step.  Dirichlet boundaries only. */
 
 #define SLPIC_MAX_SPECIES 4
 
@@ -98,7 +106,8 @@ typedef struct {
     int32_t src_ref_species; /* LOSS_MATCHED: species whose losses are re-injected   */
     double src_lo_cells;   /* source band start, in cells                            */
     double src_len_cells;  /* source band length, in cells                           */
-    double src_rate;       /* RATE: physical pairs per unit time (per unit area)     */
+    double src_rate;       /* RATE: physical pairs per unit time (per unit area);
+                              WALL: density of the plasma behind the right plate     */
     slpic_species species[SLPIC_MAX_SPECIES];
 } slpic_config;
 

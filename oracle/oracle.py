@@ -33,7 +33,7 @@ _SRC = os.path.join(_HERE, "slpic_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 BETA_ONE, BETA_HEAVISIDE, BETA_RELATIVISTIC = 0, 1, 2
-SRC_NONE, SRC_LOSS_MATCHED, SRC_RATE = 0, 1, 2
+SRC_NONE, SRC_LOSS_MATCHED, SRC_RATE, SRC_WALL = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -111,6 +111,9 @@ def lib():
         L.orc_deposit2d_q40.argtypes = [_I, _I, _L, _P, _P, _P, _I, ctypes.c_float, _P]
         L.orc_push2d.restype = None
         L.orc_push2d.argtypes = [_I, _I, _D, _D, _P, _P, _L, _P, _P, _P, _P, _D, _I, _D, _P]
+        L.orc_inject_wall.restype = None
+        L.orc_inject_wall.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _L, _I,
+                                      _D, _D, _D, _I, _D, _P, _P]
         L.orc_inject2d.restype = None
         L.orc_inject2d.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _L,
                                    ctypes.c_float, ctypes.c_float, _I, _D, _D, _P, _P, _P]
@@ -365,6 +368,10 @@ class OracleSim:
             if float(sp.get("T", 0.0)) <= 0.0:
                 out.append(0)
                 continue
+            if mode == SRC_WALL:
+                # one-sided flux of a stationary Maxwellian of density `rate`
+                vth = np.sqrt(float(sp["T"]) / float(sp["m"]))
+                S = float(src["rate"]) * vth / np.sqrt(2.0 * np.pi) * self.dt
             self.frac[s] += S / float(sp["w"])
             k = int(np.floor(self.frac[s]))
             self.frac[s] -= k
@@ -383,9 +390,14 @@ class OracleSim:
             x = np.zeros(k)
             v = np.zeros((k, 3))
             vth = np.sqrt(float(sp["T"]) / float(sp["m"]))
-            L.orc_inject(int(self.prob["seed"]), self.step_index, s, k,
-                         np.float32(src["lo_cells"]), np.float32(src["len_cells"]),
-                         self.dx, vth, _ptr(x), _ptr(v))
+            if int(src.get("mode", SRC_NONE)) == SRC_WALL:
+                L.orc_inject_wall(int(self.prob["seed"]), self.step_index, s, k, self.N,
+                                  self.dx, self.dt, vth, int(sp["kind"]), float(sp["v0"]),
+                                  _ptr(x), _ptr(v))
+            else:
+                L.orc_inject(int(self.prob["seed"]), self.step_index, s, k,
+                             np.float32(src["lo_cells"]), np.float32(src["len_cells"]),
+                             self.dx, vth, _ptr(x), _ptr(v))
             self.load(s, x, v)
 
     def step(self, n: int = 1):

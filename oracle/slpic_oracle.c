@@ -951,3 +951,43 @@ void orc_inject2d(uint64_t seed, uint64_t step, uint32_t species, long n_new,
         v[3 * k + 2] = vth * r2 * cos(two_pi * u4);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Wall source (Sec. IV: electrons and ions enter from the right plate "as  */
+/* if from a stationary plasma").  A Maxwellian of density n and thermal    */
+/* speed vth sends n vth / sqrt(2 pi) particles per unit area and time      */
+/* through the plane x = L, with the flux-weighted half-Maxwellian:         */
+/* |vx| = vth sqrt(-2 ln u_1) towards -x, (vy, vz) Maxwellian from u_2, u_3. */
+/* Under Eq. (ConservSpeedLimApprox) a source of f enters g unchanged, and  */
+/* g-particles cross the plane at the rate int beta |vx| g = int |vx| f,    */
+/* so PIC and SLPIC inject the same count with the same distribution.  A    */
+/* particle entered at a uniformly random moment of the step and has moved  */
+/* since at its speed-limited velocity: x = L - u_0 beta(|v|) |vx| dt       */
+/* (a particle with vx = 0 is placed 2^-20 cells inside).  Macroparticle k  */
+/* of this step and species takes u_j = u24(SplitMix64(key, 8k + j)).       */
+/* ------------------------------------------------------------------------ */
+void orc_inject_wall(uint64_t seed, uint64_t step, uint32_t species, long n_new, int n_cells,
+                     double dx, double dt, double vth, int kind, double v0, double *x,
+                     double *v)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    const double L = dx * n_cells;
+    uint64_t key = orc_stream_key(seed, step, species);
+    for (long k = 0; k < n_new; ++k) {
+        double u0 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 0));
+        double u1 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 1));
+        double u2 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 2));
+        double u3 = orc_u24(orc_splitmix64_at(key, 8ULL * k + 3));
+        double vxm = vth * sqrt(-2.0 * log(u1));
+        double r2 = vth * sqrt(-2.0 * log(u2));
+        double vy = r2 * cos(two_pi * u3), vz = r2 * sin(two_pi * u3);
+        double b = orc_beta(kind, sqrt(vxm * vxm + vy * vy + vz * vz), v0);
+        double xk = L - u0 * b * vxm * dt;
+        if (!(xk < L))
+            xk = L - dx * (1.0 / 1048576.0);
+        x[k] = xk;
+        v[3 * k + 0] = -vxm;
+        v[3 * k + 1] = vy;
+        v[3 * k + 2] = vz;
+    }
+}

@@ -73,6 +73,9 @@ void orc_deposit2d_q40(int nx, int ny, long n, const int32_t *cell, const float 
 void orc_push2d(int nx, int ny, double dx, double dt, const double *Ex, const double *Ey,
                 long n, double *x, double *y, double *v, uint8_t *alive, double qm, int kind,
                 double v0, long *flux);
+void orc_inject_wall(uint64_t seed, uint64_t step, uint32_t species, long n_new, int n_cells,
+                     double dx, double dt, double vth, int kind, double v0, double *x,
+                     double *v);
 void orc_inject2d(uint64_t seed, uint64_t step, uint32_t species, long n_new,
                   float src_lo_cells, float src_len_cells, int nx, double dx, double vth,
                   double *x, double *y, double *v);

@@ -28,7 +28,7 @@ ERR_NAMES = {0: "OK", -1: "INVALID", -2: "CFL", -3: "OOM", -4: "CAPACITY",
 
 SLPIC_BETA_ONE, SLPIC_BETA_HEAVISIDE, SLPIC_BETA_RELATIVISTIC = 0, 1, 2
 SLPIC_BC_DIRICHLET_ABSORB, SLPIC_BC_PERIODIC = 0, 1
-SLPIC_SRC_NONE, SLPIC_SRC_LOSS_MATCHED, SLPIC_SRC_RATE = 0, 1, 2
+SLPIC_SRC_NONE, SLPIC_SRC_LOSS_MATCHED, SLPIC_SRC_RATE, SLPIC_SRC_WALL = 0, 1, 2, 3
 SLPIC_MAX_SPECIES = 4
 
 #: every function declared in include/slpic.h

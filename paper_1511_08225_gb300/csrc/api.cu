@@ -164,7 +164,16 @@ static int validate_config(const slpic_config *c, std::string &why)
             return SLPIC_ERR_INVALID;
         }
     }
-    if (c->src_mode != SLPIC_SRC_NONE) {
+    if (c->src_mode == SLPIC_SRC_WALL) {
+        if (c->bc != SLPIC_BC_DIRICHLET_ABSORB) {
+            why = "the wall source needs the absorbing plates";
+            return SLPIC_ERR_INVALID;
+        }
+        if (!(c->src_rate >= 0)) {
+            why = "src_rate (source density) < 0";
+            return SLPIC_ERR_INVALID;
+        }
+    } else if (c->src_mode != SLPIC_SRC_NONE) {
         if (c->src_mode != SLPIC_SRC_LOSS_MATCHED && c->src_mode != SLPIC_SRC_RATE) {
             why = "unknown src_mode";
             return SLPIC_ERR_INVALID;
@@ -356,6 +365,11 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
         d.rho_unit = d.qw_dx / 1099511627776.0;
         d.w = sp.w;
         d.inv_w = 1.0 / sp.w;
+        // wall source: macroparticles per step of the one-sided Maxwellian flux
+        d.wall_rate = cfg->src_mode == SLPIC_SRC_WALL && sp.T_src > 0
+                          ? cfg->src_rate * std::sqrt(sp.T_src / sp.m) /
+                                std::sqrt(2.0 * 3.14159265358979323846) * cfg->dt / sp.w
+                          : 0.0;
     }
     p.acc = h->d_acc;
     p.E = h->d_E;

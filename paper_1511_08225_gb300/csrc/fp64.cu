@@ -300,11 +300,14 @@ __global__ void __launch_bounds__(1024) k_inject64(P64 p)
             S = (double)(st->absorbed_step[r][0] + st->absorbed_step[r][1]) * p.sp[r].w;
         } else if (p.src_mode == SLPIC_SRC_RATE) {
             S = p.src_rate * p.dt;
+        } else if (p.src_mode == SLPIC_SRC_WALL) {
+            // one-sided flux of a stationary Maxwellian of density src_rate
+            S = p.src_rate * p.sp[s].vth / sqrt(2.0 * 3.14159265358979323846) * p.dt;
         }
         long long k = 0;
         double f = st->src_frac[s];
         if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth > 0.0) {
-            f += S * p.sp[s].inv_w;
+            f += S / p.sp[s].w;
             k = (long long)floor(f);
             f -= (double)k;
         }
@@ -323,12 +326,28 @@ __global__ void __launch_bounds__(1024) k_inject64(P64 p)
             mix64(p.seed ^ mix64((unsigned long long)step * 16ULL + (unsigned)s + 1ULL));
         for (long long i = threadIdx.x; i < s_k[s]; i += blockDim.x) {
             const unsigned long long b8 = 8ULL * (unsigned long long)i;
-            const double xc = p.src_lo + u53(key, b8) * p.src_len;
-            const double r1 = sqrt(-2.0 * log(u53(key, b8 + 1)));
-            const double r2 = sqrt(-2.0 * log(u53(key, b8 + 3)));
-            const double ph = two_pi * u53(key, b8 + 2), ph2 = two_pi * u53(key, b8 + 4);
-            const double vx = sp.vth * r1 * cos(ph), vy = sp.vth * r1 * sin(ph);
-            const double vz = sp.vth * r2 * cos(ph2);
+            double xc, vx, vy, vz;
+            if (p.src_mode == SLPIC_SRC_WALL) {
+                // through the plate at x = L (the library's wall source, in FP64)
+                const double vxm = sp.vth * sqrt(-2.0 * log(u53(key, b8 + 1)));
+                const double rw = sp.vth * sqrt(-2.0 * log(u53(key, b8 + 2)));
+                const double ph = two_pi * u53(key, b8 + 3);
+                vx = -vxm;
+                vy = rw * cos(ph);
+                vz = rw * sin(ph);
+                const double b = beta64(sp.kind, sqrt(vxm * vxm + vy * vy + vz * vz), sp.v0);
+                xc = p.N - u53(key, b8) * b * vxm * p.dt / p.dx;
+                if (!(xc < p.N))
+                    xc = p.N - 1.0 / 1048576.0;
+            } else {
+                xc = p.src_lo + u53(key, b8) * p.src_len;
+                const double r1 = sqrt(-2.0 * log(u53(key, b8 + 1)));
+                const double r2 = sqrt(-2.0 * log(u53(key, b8 + 3)));
+                const double ph = two_pi * u53(key, b8 + 2), ph2 = two_pi * u53(key, b8 + 4);
+                vx = sp.vth * r1 * cos(ph);
+                vy = sp.vth * r1 * sin(ph);
+                vz = sp.vth * r2 * cos(ph2);
+            }
             const long long o = s_base[s] + i;
             const double x = xc * p.dx;
             sp.x[P ^ 1][o] = x;

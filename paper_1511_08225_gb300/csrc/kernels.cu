@@ -533,16 +533,40 @@ __device__ void inject_species(const StepParams &p, int s, long long step, long 
         float u2 = u24(sm64_at(key, b8 + 2));
         float u3 = u24(sm64_at(key, b8 + 3));
         float u4 = u24(sm64_at(key, b8 + 4));
-        float xc = __fadd_rn(p.src_lo_cells, __fmul_rn(u0, p.src_len_cells));
-        float fc = floorf(xc);
-        int c = (int)fc;
-        float off = xc - fc;
-        // physical Maxwellian (Box-Muller); the g-source equals the f-source
-        float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
-        float s2, c2;
-        sincospif(2.0f * u2, &s2, &c2);
-        float4 q = make_float4(off, sp.vth_src * r1 * c2, sp.vth_src * r1 * s2,
-                               sp.vth_src * r2 * cospif(2.0f * u4));
+        int c;
+        float off;
+        float4 q;
+        if (p.src_mode == SLPIC_SRC_WALL) {
+            // through the plate at x = L: the flux-weighted half-Maxwellian (|vx|
+            // Rayleigh, towards -x), placed where it has moved since a uniformly
+            // random entry time in the step; a position that rounds to the plate is
+            // put at the largest cell coordinate below it
+            const float vxm = sp.vth_src * sqrtf(-2.0f * logf(u1));
+            const float rw = sp.vth_src * sqrtf(-2.0f * logf(u2));
+            float sw, cw;
+            sincospif(2.0f * u3, &sw, &cw);
+            const float vy = rw * cw, vz = rw * sw;
+            const float b = beta_q(sp.kind, -vxm, vy, vz, sp.v0);
+            float xc = __fsub_rn((float)N, __fmul_rn(u0, __fmul_rn(__fmul_rn(b, vxm), p.dt_dx)));
+            if (!(xc < (float)N))
+                xc = __int_as_float(__float_as_int((float)N) - 1);
+            xc = fmaxf(xc, 0.0f);
+            const float fc = floorf(xc);
+            c = (int)fc;
+            off = xc - fc;
+            q = make_float4(off, -vxm, vy, vz);
+        } else {
+            float xc = __fadd_rn(p.src_lo_cells, __fmul_rn(u0, p.src_len_cells));
+            float fc = floorf(xc);
+            c = (int)fc;
+            off = xc - fc;
+            // physical Maxwellian (Box-Muller); the g-source equals the f-source
+            float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
+            float s2, c2;
+            sincospif(2.0f * u2, &s2, &c2);
+            q = make_float4(off, sp.vth_src * r1 * c2, sp.vth_src * r1 * s2,
+                            sp.vth_src * r2 * cospif(2.0f * u4));
+        }
         sp.cell[Q][base + i] = c;
         sp.pv[Q][base + i] = q;
         int c1 = c + 1;
@@ -735,7 +759,13 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
             }
             long long k = 0;
             double f = st->src_frac[s];
-            if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
+            if (p.src_mode == SLPIC_SRC_WALL) {
+                if (p.sp[s].wall_rate > 0.0) {
+                    f += p.sp[s].wall_rate;
+                    k = (long long)floor(f);
+                    f -= (double)k;
+                }
+            } else if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
                 f = fma(S, p.sp[s].inv_w, f);
                 k = (long long)floor(f);
                 f -= (double)k;

@@ -40,7 +40,7 @@ constexpr int kItems = 4;                       // particles per thread per tile
 constexpr int kTile = kThreads * kItems;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCompact2d = 16;                  // compacting step interval
-constexpr int kCgThreads = 512;
+constexpr int kCgThreads = 256;
 constexpr int kBarGroup = 16;   // CTAs per first-level group of the grid barrier
 constexpr int kBarGroups = 64;  // first-level counters (CG grids up to 1,024 CTAs)
 constexpr long long kBarrierSpins = 1LL << 23;  // bounded grid-barrier wait (~1 s)
@@ -838,7 +838,7 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg2d, kCgThreads, 0) != cudaSuccess ||
         occ < 1)
         return bail(SLPIC_ERR_CUDA, "CG kernel occupancy query failed");
-    h->cg_ctas = std::min(sms * std::min(occ, 1), kBarGroup * kBarGroups);
+    h->cg_ctas = std::min(sms * std::min(occ, 2), kBarGroup * kBarGroups);
     h->ctas = sms * 4;
     if (!alloc((void **)&p.part, sizeof(double) * 3 * h->cg_ctas))
         return bail(SLPIC_ERR_OOM, "device allocation failed");

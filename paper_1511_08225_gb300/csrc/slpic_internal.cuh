@@ -52,6 +52,7 @@ struct SpeciesDev {
     double rho_unit; // q * w / dx * 2^-40: charge density of one fixed-point unit
     double w;        // g-weight
     double inv_w;    // 1 / w
+    double wall_rate;  // wall source: macroparticles entering per step (0 = none)
 };
 
 // Everything a kernel needs, passed by value (fixed at graph capture; the

@@ -28,7 +28,7 @@ import numpy as np
 from scipy import integrate
 
 BETA_ONE, BETA_HEAVISIDE, BETA_RELATIVISTIC = 0, 1, 2
-SRC_NONE, SRC_LOSS_MATCHED, SRC_RATE = 0, 1, 2
+SRC_NONE, SRC_LOSS_MATCHED, SRC_RATE, SRC_WALL = 0, 1, 2, 3
 
 SEED = 20151126
 
@@ -167,6 +167,40 @@ def sheath_problem(n_cells=4096, dx=0.5, v0=0.05, ppc=1000, mass_ratio=73440.0, 
             "phi_lo": 0.0, "phi_hi": 0.0, "eps0": 1.0, "seed": int(seed), "species": sp,
             "source": {"mode": int(source_mode), "lo_cells": 0.45 * n_cells,
                        "len_cells": 0.10 * n_cells, "rate": float(rate), "ref_species": 1}}
+
+
+ARGON_MASS_RATIO = 39.9 * 1836.0
+
+
+def paper_sheath_problem(kind=BETA_HEAVISIDE, n_cells=100, dx=0.25, v0=0.016, dt=None,
+                         delta_phi=12.5 / 2.2, T_i=0.5 / 2.2, ppc=1000, seed=SEED,
+                         capacity_factor=3.0):
+    """The collisionless argon sheath of Sec. IV in normalised units: T_e = 1 and
+    the density of the source plasma is 1, so lengths are in its Debye length
+    (0.16 cm in the paper).  100 cells of dx = 0.25 (L = 25, the paper's 4 cm),
+    plates at phi(0) = -12.5 V / 2.2 eV and phi(L) = 0, electrons and argon ions
+    (m_i/m_e = 39.9 x 1836, T_i = 0.5/2.2) entering through the right plate from a
+    stationary plasma (SRC_WALL), from an empty box.  kind BETA_ONE is plain PIC
+    with dt = dx / (5 v_te); the speed-limited run uses v0 = 0.016 v_te and
+    dt = dx / v0 (312.5 PIC steps).  The weights give ~ppc macroparticles per cell
+    at density 1 (w = dx <1/beta> / ppc, as for a load)."""
+    if dt is None:
+        dt = dx / 5.0 if kind == BETA_ONE else dx / v0
+    sp = [species("e", -1.0, 1.0, 1.0, v0, kind, ppc=ppc, dx=dx),
+          species("i", 1.0, ARGON_MASS_RATIO, T_i, v0, kind, ppc=ppc, dx=dx)]
+    for s in sp:
+        s["capacity"] = int(capacity_factor * ppc * n_cells) + 4096
+    return {"n_cells": int(n_cells), "dx": float(dx), "dt": float(dt), "periodic": False,
+            "phi_lo": -float(delta_phi), "phi_hi": 0.0, "eps0": 1.0, "seed": int(seed),
+            "species": sp,
+            "source": {"mode": SRC_WALL, "lo_cells": 0.0, "len_cells": 0.0, "rate": 1.0,
+                       "ref_species": 1}}
+
+
+def empty_state(prob: dict):
+    """No particles (the sheath fills from its source)."""
+    return [(np.zeros(0, np.int32), np.zeros(0, np.float32), np.zeros((0, 3), np.float32))
+            for _ in prob["species"]]
 
 
 def load_state(prob: dict, seed: int | None = None, quiet: bool = False):

@@ -262,6 +262,42 @@ def test_source_injection_matches_oracle():
     gpu.close()
 
 
+@pytest.mark.parametrize("kind", [ONE, HEAV])
+def test_wall_source_matches_oracle(kind):
+    """Sec. IV wall source into an empty box: per step the same macroparticle
+    counts as the oracle; the first step's particles at the oracle's positions
+    (FP32 arithmetic on one side, FP64 on the other: a few 1e-6 of the distance
+    moved, plus FP32 resolution of the position) and velocities to FP32 libm
+    accuracy; the counts stay equal over later steps."""
+    prob = inputs.paper_sheath_problem(kind=kind, ppc=200)
+    st = inputs.empty_state(prob)
+    gpu = _sim(prob, st)
+    o = _oracle(prob, st)
+    gpu.step(1)
+    o.step(1)
+    L = prob["n_cells"] * prob["dx"]
+    for s in range(2):
+        k = int(o.last_injected[s])
+        assert k > 0
+        c, off, v = gpu.particles(s)
+        assert c.size == o.x[s].size == k
+        xg = (c.astype(np.float64) + off.astype(np.float64)) * prob["dx"]
+        moved = L - o.x[s]
+        tol = 4e-6 * moved + 2.0 ** -24 * L * 2
+        assert (np.abs(xg - o.x[s]) <= tol).all(), np.max(np.abs(xg - o.x[s]) - tol)
+        np.testing.assert_allclose(v, o.v[s], rtol=4e-6, atol=4e-6 * np.abs(o.v[s]).max())
+    injected = np.array([int(o.last_injected[s]) for s in range(2)])
+    for _ in range(4):
+        gpu.step(1)
+        o.step(1)
+        injected += o.last_injected
+        d = gpu.diagnostics()
+        for s in range(2):
+            assert d["injected"][s] == injected[s]
+            assert abs(d["count"][s] - o.x[s].size) <= 2
+    gpu.close()
+
+
 # ------------------------------------------------------------------ API behaviour
 def test_checkpoint_restore_is_bitwise():
     prob = inputs.sheath_problem(n_cells=64, ppc=50, v0=0.1)

@@ -1,0 +1,58 @@
+"""The paper's collisionless argon sheath (Sec. IV), filled from its wall source,
+run to the paper's steady-state time (about 24 us, 3 ion crossing times) as plain
+PIC (beta = 1, dt = dx/(5 v_te), 190,600 steps) and as SLPIC (Heaviside beta,
+v0 = 0.016 v_te, dt = dx/v0, 610 steps).  Sec. IV states that the two reach the
+same steady state; the check is on the profiles averaged over the last third of
+each run: phi(x) within 3 % of the plate bias, and the physical electron and ion
+densities within 15 % of their peak where the density exceeds a fifth of it."""
+import numpy as np
+import pytest
+
+from paper_1511_08225_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+T_END = 9530.0  # 24 us in units of 1/omega_pe of the source plasma
+
+
+def _steady_profiles(kind, ppc=500):
+    prob = inputs.paper_sheath_problem(kind=kind, ppc=ppc)
+    sim = binding.Simulation(prob)
+    sim.load_state(inputs.empty_state(prob))
+    sim.prepare()
+    n = int(round(T_END / prob["dt"]))
+    start = 2 * n // 3
+    stride = max(1, (n - start) // 150)
+    sim.step(start)
+    acc = [0.0, 0.0, 0.0]
+    m, done = 0, start
+    while done < n:
+        k = min(stride, n - done)
+        sim.step(k)
+        done += k
+        _, phi, _ = sim.fields()
+        acc[0] = acc[0] + phi
+        acc[1] = acc[1] + sim.density(0)
+        acc[2] = acc[2] + sim.density(1)
+        m += 1
+    d = sim.diagnostics()
+    sim.close()
+    return [a / m for a in acc], d
+
+
+def test_slpic_and_pic_reach_the_same_sheath():
+    (phi_p, ne_p, ni_p), dp = _steady_profiles(inputs.BETA_ONE)
+    (phi_s, ne_s, ni_s), ds = _steady_profiles(inputs.BETA_HEAVISIDE)
+    dphi = 12.5 / 2.2
+    # the bias is held and the potential falls towards the left plate
+    assert phi_p[0] == pytest.approx(-dphi) and phi_s[0] == pytest.approx(-dphi)
+    assert np.abs(phi_s - phi_p).max() <= 0.03 * dphi
+    for a, b in ((ne_s, ne_p), (ni_s, ni_p)):
+        peak = max(a.max(), b.max())
+        bulk = (b > 0.2 * peak)
+        assert bulk.sum() > 20
+        assert np.abs(a - b)[bulk].max() <= 0.15 * peak
+    # ions leave through the left plate only; electrons mostly return to the right
+    for d in (dp, ds):
+        assert d["absorbed"][1][1] == 0 and d["absorbed"][1][0] > 0
+        assert d["absorbed"][0][1] > d["absorbed"][0][0]

@@ -380,3 +380,84 @@ def test_g_load_weight_counts_physical_density():
     assert dens == pytest.approx(1.0, rel=5e-3)
     # and the physical speed distribution is Maxwellian: <beta |v|^2> / <beta> = 3 T
     assert (b * r * r).sum() / b.sum() == pytest.approx(3.0, rel=1e-2)
+
+
+# ------------------------------------------------------------------ wall source (Sec. IV)
+def _wall_draw(kind, v0, n=200_000, vth=1.3, dt=0.7, dx=0.5, n_cells=40):
+    x, v = np.zeros(n), np.zeros((n, 3))
+    orc.lib().orc_inject_wall(7, 5, 1, n, n_cells, dx, dt, vth, kind, v0, orc._ptr(x),
+                              orc._ptr(v))
+    return x, v
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_wall_source_distribution(kind):
+    """Flux-weighted half-Maxwellian through x = L: vx < 0 with |vx| Rayleigh
+    (mean vth sqrt(pi/2), second moment 2 vth^2), vy and vz Maxwellian, and the
+    distance moved since entry, L - x = u beta |vx| dt, with u uniform."""
+    vth, dt, dx, N, v0 = 1.3, 0.7, 0.5, 40, 0.6
+    x, v = _wall_draw(kind, v0, vth=vth, dt=dt, dx=dx, n_cells=N)
+    L = N * dx
+    assert (v[:, 0] < 0).all() and (x < L).all() and (x > 0).all()
+    a = -v[:, 0]
+    assert abs(a.mean() / (vth * np.sqrt(np.pi / 2)) - 1) < 0.01
+    assert abs((a * a).mean() / (2 * vth * vth) - 1) < 0.01
+    for k in (1, 2):
+        assert abs(v[:, k].std() / vth - 1) < 0.01 and abs(v[:, k].mean()) < 0.01 * vth
+    b = orc._beta_vec(kind, np.linalg.norm(v, axis=1), v0)
+    u = (L - x) / (b * a * dt)
+    assert u.max() <= 1.0 + 1e-12 and abs(u.mean() - 0.5) < 0.005
+    assert abs(np.quantile(u, 0.25) - 0.25) < 0.005
+
+
+def test_wall_source_counts_follow_the_flux():
+    """Over K steps the macroparticles injected per species total
+    floor(K n vth / sqrt(2 pi) dt / w) (the fraction is carried)."""
+    prob = inputs.paper_sheath_problem(kind=inputs.BETA_ONE, ppc=20)
+    o = orc.OracleSim(prob)
+    o.start()
+    tot = np.zeros(2, np.int64)
+    K = 40
+    for _ in range(K):
+        o.push()
+        o.inject()
+        tot += o.last_injected
+        o.deposit()
+        o.solve()
+        o.step_index += 1
+    for s, sp in enumerate(prob["species"]):
+        rate = np.sqrt(sp["T"] / sp["m"]) / np.sqrt(2 * np.pi) * prob["dt"] / sp["w"]
+        assert abs(tot[s] - np.floor(K * rate)) <= 1
+
+
+@pytest.mark.parametrize("kind", [inputs.BETA_ONE, inputs.BETA_HEAVISIDE])
+def test_wall_source_fills_half_density(kind):
+    """Neutral test particles (q = 0) entering from a stationary plasma of
+    density 1 and leaving through the far plate stream across at the density of
+    the half-Maxwellian that moves inwards: 1/2 everywhere.  For the speed-limited
+    form this is the physical density sum w beta S / dx of the g-particles, so the
+    check pins the flux, the half-Maxwellian and the g = f/beta weighting of the
+    source (Sec. II) at once."""
+    N, dx = 20, 1.0
+    v0 = 0.5
+    dt = 1.0 if kind == inputs.BETA_ONE else dx / v0
+    sp = inputs.species("n", 0.0, 1.0, 1.0, v0, kind, ppc=100, dx=dx)
+    sp["w"] = 0.5 * dx / 100
+    sp["capacity"] = 100_000
+    prob = {"n_cells": N, "dx": dx, "dt": dt, "periodic": False, "phi_lo": 0.0, "phi_hi": 0.0,
+            "eps0": 1.0, "seed": 3, "species": [sp],
+            "source": {"mode": inputs.SRC_WALL, "lo_cells": 0.0, "len_cells": 0.0, "rate": 1.0,
+                       "ref_species": 0}}
+    o = orc.OracleSim(prob)
+    o.start()
+    t_end = 1000.0
+    n = int(t_end / dt)
+    o.step(int(0.8 * n))
+    acc, m = np.zeros(N + 1), 0
+    for _ in range(n - int(0.8 * n)):
+        o.step(1)
+        acc += o.dens[0]
+        m += 1
+    prof = acc[1:N] / m
+    assert abs(prof.mean() - 0.5) < 0.015, prof.mean()
+    assert np.abs(prof - 0.5).max() < 0.08, prof
