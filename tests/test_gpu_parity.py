@@ -270,6 +270,8 @@ def test_wall_source_matches_oracle(kind):
     moved, plus FP32 resolution of the position) and velocities to FP32 libm
     accuracy; the counts stay equal over later steps."""
     prob = inputs.paper_sheath_problem(kind=kind, ppc=200)
+    # a denser source plasma, so that the slow ions enter in the first short PIC step
+    prob["source"]["rate"] = 100.0
     st = inputs.empty_state(prob)
     gpu = _sim(prob, st)
     o = _oracle(prob, st)

@@ -3,8 +3,9 @@ run to the paper's steady-state time (about 24 us, 3 ion crossing times) as plai
 PIC (beta = 1, dt = dx/(5 v_te), 190,600 steps) and as SLPIC (Heaviside beta,
 v0 = 0.016 v_te, dt = dx/v0, 610 steps).  Sec. IV states that the two reach the
 same steady state; the check is on the profiles averaged over the last third of
-each run: phi(x) within 3 % of the plate bias, and the physical electron and ion
-densities within 15 % of their peak where the density exceeds a fifth of it."""
+each run: phi(x) within 3 % of the plate bias; the physical electron and ion
+densities within 10 % of their peak everywhere, and within 15 % of the PIC value
+(plus 1 % of the peak) over the middle 60 % of the gap."""
 import numpy as np
 import pytest
 
@@ -47,11 +48,11 @@ def test_slpic_and_pic_reach_the_same_sheath():
     # the bias is held and the potential falls towards the left plate
     assert phi_p[0] == pytest.approx(-dphi) and phi_s[0] == pytest.approx(-dphi)
     assert np.abs(phi_s - phi_p).max() <= 0.03 * dphi
+    mid = slice(20, 81)  # the middle 60 % of the gap
     for a, b in ((ne_s, ne_p), (ni_s, ni_p)):
         peak = max(a.max(), b.max())
-        bulk = (b > 0.2 * peak)
-        assert bulk.sum() > 20
-        assert np.abs(a - b)[bulk].max() <= 0.15 * peak
+        assert np.abs(a - b).max() <= 0.1 * peak
+        assert (np.abs(a - b)[mid] <= 0.15 * b[mid] + 0.01 * peak).all()
     # ions leave through the left plate only; electrons mostly return to the right
     for d in (dp, ds):
         assert d["absorbed"][1][1] == 0 and d["absorbed"][1][0] > 0
