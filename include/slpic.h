@@ -266,6 +266,32 @@ int slpic_kernel_times(slpic_t *h, double *particle_ms, double *hard_ms, double 
 /* Number of kernels one slpic_step(h, 1) launches. */
 int slpic_kernels_per_step(slpic_t *h, int *n);
 
+/* ---- a speed limit that changes in time (Sec. II; the Summary) -------------- */
+
+/* Change the speed limit v0 of a speed-limited species from the next step on
+ * (the paper notes that v0 may vary in time, e.g. raised mid-run to tighten or
+ * verify the approximation).  dt * v0 <= dx must still hold (SLPIC_ERR_CFL:
+ * lower the timestep first).  The particles, their g-weights and the current
+ * fields are kept; their physical weight w beta follows the new beta from the
+ * next deposit on.  SLPIC_ERR_INVALID for a beta == 1 species or v0 <= 0.  On a
+ * batch handle, `instance` selects the member. */
+int slpic_set_speed_limit(slpic_t *h, int instance, int species, double v0);
+
+/* Test-particle mode (Sec. V): from now on the field is the prescribed wave
+ * phi(x, t) = phi0(t) sin(k (x - vphi t)), phi0(t) = phi0 min(1, t / t_ramp)
+ * (t = step * dt; t_ramp = 0: no ramp), and E = -dphi/dx is evaluated at the
+ * nodes for each time level; the particles' charge is still deposited but no
+ * longer enters E.  Periodic grids only; k = 0 returns to the Poisson field from
+ * the next step.  E of the current level is recomputed at once.  Not available
+ * on a batch handle. */
+int slpic_set_wave(slpic_t *h, double phi0, double k, double vphi, double t_ramp);
+
+/* Change the timestep from the next step on, with the CFL checks of
+ * slpic_create.  The stored velocities are taken as v^{n+1/2} of the new step
+ * (the usual first-order restart of a leapfrog); the wall source's rate per step
+ * follows dt.  Not available on a batch handle. */
+int slpic_set_timestep(slpic_t *h, double dt);
+
 /* ---- allocation-free particle step ------------------------------------------ */
 
 /* The paper has no counterpart to this entry point; it exists for callers that

@@ -324,8 +324,23 @@ class OracleSim:
                             _ptr(self.dens[s]))
         self.rho = sum(float(sp["q"]) * self.dens[s] for s, sp in enumerate(self.sp))
 
-    def solve(self):
+    def solve(self, t=None):
+        """Poisson for E^n (Appendix A); with a prescribed wave (Sec. V test
+        particles, prob["wave"] = {phi0, k, vphi, ramp}) the field is instead
+        -d/dx of phi0(t) sin(k (x - vphi t)), phi0(t) = phi0 min(1, t/ramp), at the
+        nodes and at time t (default: the current level, step_index * dt)."""
         p = self.prob
+        w = p.get("wave")
+        if w is not None and float(w["k"]) > 0.0:
+            t = self.step_index * self.dt if t is None else t
+            amp = float(w["phi0"])
+            if float(w.get("ramp", 0.0)) > 0.0:
+                amp *= min(1.0, t / float(w["ramp"]))
+            xj = np.arange(self.nn) * self.dx
+            ph = float(w["k"]) * (xj - float(w["vphi"]) * t)
+            self.phi = amp * np.sin(ph)
+            self.E = -amp * float(w["k"]) * np.cos(ph)
+            return
         self.phi = poisson1d(self.rho, self.dx, self.periodic, p.get("phi_lo", 0.0),
                              p.get("phi_hi", 0.0), self.eps0)
         self.E = efield1d(self.phi, self.dx, self.periodic)
@@ -405,7 +420,7 @@ class OracleSim:
             self.push()
             self.inject()
             self.deposit()
-            self.solve()
+            self.solve((self.step_index + 1) * self.dt)
             self.step_index += 1
 
     # --- diagnostics ---------------------------------------------------------

@@ -39,7 +39,8 @@ EXPORTS = (
     "slpic_fields", "slpic_density", "slpic_charge_raw", "slpic_particle_count",
     "slpic_get_particles", "slpic_diagnostics", "slpic_save", "slpic_restore",
     "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernels_per_step",
-    "slpic_particle_step_noalloc", "slpic_create_batch",
+    "slpic_particle_step_noalloc", "slpic_create_batch", "slpic_set_speed_limit",
+    "slpic_set_timestep", "slpic_set_wave",
 )
 
 
@@ -97,6 +98,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     sig = {
         "slpic_create": (I, [ctypes.POINTER(slpic_config), ctypes.POINTER(P)]),
         "slpic_create_batch": (I, [ctypes.POINTER(slpic_config), I, ctypes.POINTER(P)]),
+        "slpic_set_speed_limit": (I, [P, I, I, D]),
+        "slpic_set_timestep": (I, [P, D]),
+        "slpic_set_wave": (I, [P, D, D, D, D]),
         "slpic_destroy": (I, [P]),
         "slpic_last_error": (ctypes.c_char_p, [P]),
         "slpic_create_error": (ctypes.c_char_p, []),
@@ -404,6 +408,19 @@ class Simulation:
 
     def restore(self, blob):
         slpic_restore(self.h, blob)
+
+
+def slpic_set_speed_limit(h, instance, species, v0):
+    _check(h, load_library().slpic_set_speed_limit(h, instance, species, v0),
+           "slpic_set_speed_limit")
+
+
+def slpic_set_timestep(h, dt):
+    _check(h, load_library().slpic_set_timestep(h, dt), "slpic_set_timestep")
+
+
+def slpic_set_wave(h, phi0, k, vphi, t_ramp=0.0):
+    _check(h, load_library().slpic_set_wave(h, phi0, k, vphi, t_ramp), "slpic_set_wave")
 
 
 def slpic_create_batch(cfgs) -> ctypes.c_void_p:

@@ -1020,6 +1020,120 @@ extern "C" int slpic_kernels_per_step(slpic_t *h, int *n)
     return SLPIC_OK;
 }
 
+// The step graphs hold the parameters by value: drop them so that the next step
+// captures them again.
+static void drop_graphs(slpic_t *h)
+{
+    for (cudaGraphExec_t *g : {&h->g1, &h->gc, &h->gK, &h->gt})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+}
+
+// A batch keeps its members' parameters on the device as well.
+static int batch_refresh_params(slpic_t *h)
+{
+    std::vector<StepParams> ps;
+    for (slpic_t *m : h->members)
+        ps.push_back(m->p);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->d_params, ps.data(), sizeof(StepParams) * ps.size(),
+                     cudaMemcpyHostToDevice));
+    drop_graphs(h);
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_set_speed_limit(slpic_t *h, int instance, int species, double v0)
+{
+    if (is_batch(h)) {
+        if (instance < 0 || instance >= (int)h->members.size())
+            return fail(h, SLPIC_ERR_INVALID, "instance out of range");
+        slpic_t *m = h->members[instance];
+        int rc = slpic_set_speed_limit(m, 0, species, v0);
+        if (rc) {
+            h->err = m->err;
+            return rc;
+        }
+        return batch_refresh_params(h);
+    }
+    int rc = check_handle(h, instance);
+    if (rc)
+        return rc;
+    if (species < 0 || species >= h->ns)
+        return fail(h, SLPIC_ERR_INVALID, "species out of range");
+    const slpic_species &sp = h->cfg.species[species];
+    if (sp.beta_kind == SLPIC_BETA_ONE)
+        return fail(h, SLPIC_ERR_INVALID, "species has no speed limit (beta == 1)");
+    if (!(v0 > 0) || !std::isfinite(v0))
+        return fail(h, SLPIC_ERR_INVALID, "v0 must be > 0");
+    if (h->cfg.dt * v0 > h->cfg.dx)
+        return fail(h, SLPIC_ERR_CFL, "dt * v0 > dx: lower the timestep first");
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->cfg.species[species].v0 = v0;
+    h->p.sp[species].v0 = (float)v0;
+    drop_graphs(h);
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_set_wave(slpic_t *h, double phi0, double k, double vphi, double t_ramp)
+{
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (h->cfg.bc != SLPIC_BC_PERIODIC)
+        return fail(h, SLPIC_ERR_INVALID, "the prescribed wave needs a periodic grid");
+    if (!std::isfinite(phi0) || !std::isfinite(k) || !std::isfinite(vphi) || !(t_ramp >= 0) ||
+        !std::isfinite(t_ramp) || k < 0)
+        return fail(h, SLPIC_ERR_INVALID, "bad wave parameters");
+    if (h->dirty && (rc = slpic_prepare(h)))
+        return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    StepParams &p = h->p;
+    p.wave_on = k > 0.0;
+    p.wave_phi0 = phi0;
+    p.wave_k = k;
+    p.wave_vphi = vphi;
+    p.wave_ramp = t_ramp;
+    drop_graphs(h);
+    // E of the current time level from the new setting (no deposit is consumed)
+    launch_field(h->p, 0, h->stream);
+    CK(h, cudaGetLastError());
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_set_timestep(slpic_t *h, double dt)
+{
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "set the timestep of each instance before batching");
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (!(dt > 0) || !std::isfinite(dt))
+        return fail(h, SLPIC_ERR_INVALID, "dt must be > 0");
+    for (int s = 0; s < h->ns; ++s) {
+        const slpic_species &sp = h->cfg.species[s];
+        if (sp.beta_kind != SLPIC_BETA_ONE && dt * sp.v0 > h->cfg.dx)
+            return fail(h, SLPIC_ERR_CFL, "dt * v0 > dx for species " + std::to_string(s));
+        if (sp.beta_kind == SLPIC_BETA_ONE && h->cfg.max_speed > 0 &&
+            dt * h->cfg.max_speed > h->cfg.dx)
+            return fail(h, SLPIC_ERR_CFL, "dt * max_speed > dx");
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double old = h->cfg.dt;
+    h->cfg.dt = dt;
+    StepParams &p = h->p;
+    p.dt = (float)dt;
+    p.dt_dx = (float)(dt / h->cfg.dx);
+    p.dt64 = dt;
+    for (int s = 0; s < h->ns; ++s)
+        p.sp[s].wall_rate *= dt / old;  // the wall source's macroparticles per step
+    drop_graphs(h);
+    return SLPIC_OK;
+}
+
 // =================================================================================
 // Batches of independent simulations (many sheaths of uneven size advanced together)
 // =================================================================================

@@ -581,6 +581,21 @@ __device__ void inject_species(const StepParams &p, int s, long long step, long 
 
 // On demand (slpic_fields): rho and phi of the latest deposit acc[step & 1], one CTA.
 // The particle step needs only E, which k_field computes; phi is read back rarely.
+// The prescribed wave of the test-particle mode at node j and time t: the potential
+// phi0(t) sin(k (x_j - vphi t)) and the field -dphi/dx = -phi0(t) k cos(k (x_j - vphi t)).
+__device__ __forceinline__ double wave_amplitude(const StepParams &p, double t)
+{
+    return p.wave_ramp > 0.0 ? p.wave_phi0 * fmin(1.0, t / p.wave_ramp) : p.wave_phi0;
+}
+__device__ __forceinline__ double wave_phi(const StepParams &p, int j, double t)
+{
+    return wave_amplitude(p, t) * sin(p.wave_k * ((double)j * p.dx - p.wave_vphi * t));
+}
+__device__ __forceinline__ double wave_E(const StepParams &p, int j, double t)
+{
+    return -wave_amplitude(p, t) * p.wave_k * cos(p.wave_k * ((double)j * p.dx - p.wave_vphi * t));
+}
+
 __global__ void __launch_bounds__(kFT) k_potential(StepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -661,6 +676,13 @@ __global__ void __launch_bounds__(kFT) k_potential(StepParams p)
         __syncthreads();
         for (int j = j0; j < j1; ++j)
             p.phi[j] -= s_shift;
+    }
+    if (p.wave_on) {
+        // test-particle mode: the potential is the prescribed one
+        __syncthreads();
+        const double t = (double)step * p.dt64;
+        for (int j = j0; j < j1; ++j)
+            p.phi[j] = wave_phi(p, j, t);
     }
 }
 
@@ -918,6 +940,8 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
             }
             e = (k2 * (pair - mean * (double)(2 * j - 1)) - 2.0 * D0) * inv2dx;
         }
+        if (p.wave_on)  // test-particle mode: the prescribed field at this time level
+            e = wave_E(p, j, (double)(mode >= 1 ? step + 1 : step) * p.dt64);
         p.E64[j] = e;
         p.E[j] = (float)e;
     }

@@ -86,7 +86,8 @@ struct Params2D {
     Species2D sp[kMaxS];
     unsigned long long *acc;  // [ns][nn] int64 deposits (two's complement)
     float2 *E;                // [nn] (Ex, Ey)
-    double *phi, *r, *pA, *pB, *q;  // [nn]; r, p, q are zero on the plate rows
+    double *phi, *r, *q;            // [nn] FP64: solution, standalone solve's rho, b
+    float *fr, *fpA, *fpB, *fq, *fd;  // [nn] FP32 CG iterates, zero on the plate rows
     double *part;             // [3][grid] per-CTA partial sums
     State2D *st;
 };
@@ -515,6 +516,22 @@ __device__ __forceinline__ double stencil(const double *u, int idx, int i, int n
 
 // mode 0: the simulation's solve (b from the deposits, which are then cleared;
 // E written).  mode 1: b from p.r's initial content as rho (slpic2d_solve_poisson).
+//
+// Mixed precision with reliable updates: b and the solution phi are FP64; the CG
+// iterates (search direction p, correction d, residual r) are FP32, with dot
+// products summed in FP64.  Whenever the FP32 recursive residual has fallen by
+// kUpdateDrop since the last update (or below the target), d is added to phi in
+// FP64 and r is replaced by the true residual b - A phi formed in FP64; the search
+// direction carries on, so the iteration keeps the convergence of one unbroken CG
+// run, unless the true residual came out more than twice the recursive one (the
+// FP32 recursion had drifted), when the search direction starts afresh.  At
+// 1024 x 1024 with a plasma's smooth charge the correction is as large as phi
+// itself early on, which limits how far an FP32 recursion can be trusted: hence
+// an update at every tenfold drop.  The solve ends when that true residual meets ||b - A phi|| <= rtol ||b||,
+// the figure reported.  FP64 arithmetic, narrow on this GPU, is left to the few
+// updates.
+constexpr double kUpdateDrop = 1e-1;
+
 __global__ void __launch_bounds__(kCgThreads) k_cg2d(Params2D p, int mode)
 {
     __shared__ double s_red[kCgThreads / 32];
@@ -524,12 +541,13 @@ __global__ void __launch_bounds__(kCgThreads) k_cg2d(Params2D p, int mode)
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
     double *part0 = p.part, *part1 = p.part + gridDim.x, *part2 = p.part + 2 * gridDim.x;
+    double *b64 = p.q;  // right-hand side, kept for the true residuals
 
-    // ---- b and r = b - A phi; ||b||^2, ||r||^2
-    double bb = 0.0, rr = 0.0;
+    // ---- b (FP64, interior rows; 0 on the plates) and ||b||^2; FP32 iterates zeroed
+    double bb = 0.0;
     for (long long t = gtid; t < nn; t += gstride) {
         const int idx = (int)t;
-        const int j = idx / nx, i = idx - j * nx;
+        const int j = idx / nx;
         double rho = 0.0;
         if (mode == 0) {
             for (int s = 0; s < p.ns; ++s) {
@@ -540,94 +558,131 @@ __global__ void __launch_bounds__(kCgThreads) k_cg2d(Params2D p, int mode)
         } else {
             rho = p.r[idx];
         }
-        if (idx < first || idx >= last)
-            continue;
-        double b = p.k2 * rho;
-        if (j == 1)
-            b += p.phi_lo;
-        if (j == ny - 1)
-            b += p.phi_hi;
-        // A phi (unknowns only) = stencil on the whole phi (plate rows included)
-        // + the plate terms, so r = b - A phi = k2 rho - stencil(phi)
-        const double r = p.k2 * rho - stencil(p.phi, idx, i, nx);
-        p.q[idx] = r;  // r is staged in q until every CTA has read rho (mode 1 reads p.r)
+        double b = 0.0;
+        if (idx >= first && idx < last) {
+            b = p.k2 * rho;
+            if (j == 1)
+                b += p.phi_lo;
+            if (j == ny - 1)
+                b += p.phi_hi;
+        }
+        b64[idx] = b;
         bb = fma(b, b, bb);
-        rr = fma(r, r, rr);
+        p.fr[idx] = 0.0f;
+        p.fpA[idx] = 0.0f;
+        p.fpB[idx] = 0.0f;
+        p.fd[idx] = 0.0f;
     }
     bb = block_sum(bb, s_red);
-    rr = block_sum(rr, s_red);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0)
         part0[blockIdx.x] = bb;
-        part1[blockIdx.x] = rr;
-    }
     if (!grid_sync(st))
         return;
-    for (long long t = gtid; t < nn; t += gstride) {
-        const int idx = (int)t;
-        const bool in = idx >= first && idx < last;
-        p.r[idx] = in ? __ldcg(p.q + idx) : 0.0;
-        p.pA[idx] = 0.0;
-        p.pB[idx] = 0.0;
-    }
     double BB = grid_total(part0, s_red);
-    double RR = grid_total(part1, s_red);
     if (BB == 0.0)
         BB = 1.0;
-    if (!grid_sync(st))
-        return;
 
     int it = 0;
+    double RR = 0.0;
+    // true residual in FP64: r = b - A phi (A phi on the unknowns = the full stencil
+    // on phi, plate rows included, plus the plate terms held in b), stored in FP32
+    auto true_residual = [&]() -> bool {
+        double rr = 0.0;
+        for (long long t = gtid + first; t < last; t += gstride) {
+            const int idx = (int)t;
+            const int j = idx / nx, i = idx - j * nx;
+            double ap = stencil(p.phi, idx, i, nx);
+            if (j == 1)
+                ap += p.phi_lo;
+            if (j == ny - 1)
+                ap += p.phi_hi;
+            const double r = __ldcg(b64 + idx) - ap;
+            p.fr[idx] = (float)r;
+            rr = fma(r, r, rr);
+        }
+        rr = block_sum(rr, s_red);
+        if (threadIdx.x == 0)
+            part1[blockIdx.x] = rr;
+        if (!grid_sync(st))
+            return false;
+        RR = grid_total(part1, s_red);
+        return true;
+    };
+    if (!true_residual())
+        return;
     bool done = RR <= p.rtol2 * BB;
-    double rz = 0.25 * RR, beta = 0.0;
-    double *pold = p.pA, *pnew = p.pB;
+    double rz = 0.25 * RR, beta = 0.0, rin = RR, rlast = RR;
+    bool restart = false;
+    float *pold = p.fpA, *pnew = p.fpB;
     while (!done && it < p.cg_maxit) {
-        // phase 1: p = r/4 + beta p_old, q = A p, partial p.q
+        // phase 1: p = r/4 + beta p_old at the node and its neighbours, q = A p
+        const float bf = (float)beta;
         double pq = 0.0;
         for (long long t = gtid + first; t < last; t += gstride) {
             const int idx = (int)t;
             const int j = idx / nx, i = idx - j * nx;
             const int ip = (i + 1 == nx) ? idx + 1 - nx : idx + 1;
             const int im = (i == 0) ? idx - 1 + nx : idx - 1;
-            // p at the node and its 4 neighbours (zero on the plate rows)
-            const double pc = fma(beta, __ldcg(pold + idx), 0.25 * __ldcg(p.r + idx));
-            const double pe = fma(beta, __ldcg(pold + ip), 0.25 * __ldcg(p.r + ip));
-            const double pw = fma(beta, __ldcg(pold + im), 0.25 * __ldcg(p.r + im));
-            const double pn =
-                (j + 1 < ny) ? fma(beta, __ldcg(pold + idx + nx), 0.25 * __ldcg(p.r + idx + nx)) : 0.0;
-            const double ps =
-                (j > 1) ? fma(beta, __ldcg(pold + idx - nx), 0.25 * __ldcg(p.r + idx - nx)) : 0.0;
-            const double qv = 4.0 * pc - (pe + pw + pn + ps);
+            const float pc = fmaf(bf, __ldcg(pold + idx), 0.25f * __ldcg(p.fr + idx));
+            const float pe = fmaf(bf, __ldcg(pold + ip), 0.25f * __ldcg(p.fr + ip));
+            const float pw = fmaf(bf, __ldcg(pold + im), 0.25f * __ldcg(p.fr + im));
+            const float pn =
+                (j + 1 < ny) ? fmaf(bf, __ldcg(pold + idx + nx), 0.25f * __ldcg(p.fr + idx + nx))
+                             : 0.0f;
+            const float ps =
+                (j > 1) ? fmaf(bf, __ldcg(pold + idx - nx), 0.25f * __ldcg(p.fr + idx - nx)) : 0.0f;
+            const float qv = 4.0f * pc - (pe + pw + pn + ps);
             pnew[idx] = pc;
-            p.q[idx] = qv;
-            pq = fma(pc, qv, pq);
+            p.fq[idx] = qv;
+            pq = fma((double)pc, (double)qv, pq);
         }
-        pq = block_sum(pq, s_red);
+        const double pqs = block_sum(pq, s_red);
         if (threadIdx.x == 0)
-            part2[blockIdx.x] = pq;
+            part2[blockIdx.x] = pqs;
         if (!grid_sync(st))
             return;
         const double alpha = rz / grid_total(part2, s_red);
-        // phase 2: phi += alpha p, r -= alpha q, partial r.r
+        const float af = (float)alpha;
+        // phase 2: d += alpha p, r -= alpha q
         double r2 = 0.0;
         for (long long t = gtid + first; t < last; t += gstride) {
             const int idx = (int)t;
-            p.phi[idx] = fma(alpha, pnew[idx], p.phi[idx]);
-            const double r = fma(-alpha, p.q[idx], p.r[idx]);
-            p.r[idx] = r;
-            r2 = fma(r, r, r2);
+            p.fd[idx] = fmaf(af, pnew[idx], p.fd[idx]);
+            const float r = fmaf(-af, p.fq[idx], p.fr[idx]);
+            p.fr[idx] = r;
+            r2 = fma((double)r, (double)r, r2);
         }
-        r2 = block_sum(r2, s_red);
+        const double r2s = block_sum(r2, s_red);
         if (threadIdx.x == 0)
-            part1[blockIdx.x] = r2;
+            part1[blockIdx.x] = r2s;
         if (!grid_sync(st))
             return;
-        RR = grid_total(part1, s_red);
+        rin = grid_total(part1, s_red);
         ++it;
-        done = RR <= p.rtol2 * BB;
-        const double rz1 = 0.25 * RR;
-        beta = rz1 / rz;
+        if (rin <= kUpdateDrop * kUpdateDrop * rlast || rin <= 0.25 * p.rtol2 * BB ||
+            it >= p.cg_maxit) {
+            // reliable update: phi += d in FP64, r replaced by the true residual
+            for (long long t = gtid + first; t < last; t += gstride) {
+                const int idx = (int)t;
+                p.phi[idx] += (double)p.fd[idx];
+                p.fd[idx] = 0.0f;
+            }
+            if (!grid_sync(st))
+                return;
+            if (!true_residual())
+                return;
+            done = RR <= p.rtol2 * BB;
+            // the FP32 recursion had drifted from the truth (true residual more than
+            // twice the recursive one): its search direction is stale, start afresh
+            restart = RR > 4.0 * rin;
+            rin = RR;
+            rlast = RR;
+        }
+        const double rz1 = 0.25 * rin;
+        beta = restart ? 0.0 : rz1 / rz;
+        restart = false;
         rz = rz1;
-        double *tmp = pold;
+        float *tmp = pold;
         pold = pnew;
         pnew = tmp;
     }
@@ -811,8 +866,10 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
     bool ok = alloc((void **)&h->d_state, sizeof(State2D)) &&
               alloc((void **)&p.acc, sizeof(unsigned long long) * nn * p.ns) &&
               alloc((void **)&p.E, sizeof(float2) * nn) && alloc((void **)&p.phi, sizeof(double) * nn) &&
-              alloc((void **)&p.r, sizeof(double) * nn) && alloc((void **)&p.pA, sizeof(double) * nn) &&
-              alloc((void **)&p.pB, sizeof(double) * nn) && alloc((void **)&p.q, sizeof(double) * nn);
+              alloc((void **)&p.r, sizeof(double) * nn) && alloc((void **)&p.q, sizeof(double) * nn) &&
+              alloc((void **)&p.fr, sizeof(float) * nn) && alloc((void **)&p.fpA, sizeof(float) * nn) &&
+              alloc((void **)&p.fpB, sizeof(float) * nn) && alloc((void **)&p.fq, sizeof(float) * nn) &&
+              alloc((void **)&p.fd, sizeof(float) * nn);
     for (int s = 0; ok && s < p.ns; ++s) {
         const slpic_species &sp = c->species[s];
         Species2D &d = p.sp[s];

@@ -79,6 +79,10 @@ struct StepParams {
     double src_rate;
     unsigned long long seed;
     SpeciesDev sp[kMaxSpecies];
+    // prescribed wave (test-particle mode): phi = phi0(t) sin(k (x - vphi t)),
+    // phi0(t) = wave_phi0 min(1, t / wave_ramp); E is -dphi/dx, the charge unused
+    int wave_on;
+    double wave_phi0, wave_k, wave_vphi, wave_ramp;
     unsigned long long *acc;  // [2][ns][nn]
     float *E;                 // [nn]  FP32 copy gathered by the particle kernel
     double *E64;              // [nn]

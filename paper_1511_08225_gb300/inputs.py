@@ -297,3 +297,25 @@ def batch_problems(m=256, seed=SEED, cells=(512, 8192), ppc=(100, 1000),
         out.append(sheath_problem(n_cells=n, dx=dx, v0=vv, ppc=pc, mass_ratio=mr, T_e=T_e,
                                   T_i=T_i, seed=seed + i))
     return out
+
+
+# ------------------------------------------------------------------ wave-particle test (Sec. V)
+def wave_problem(kind=BETA_HEAVISIDE, v0=2.0, n_cells=200, dx=0.5, ppc=1000, dt=None,
+                 phi0=0.1, vphi=1.0, ramp_periods=20.0, seed=SEED):
+    """Test electrons (1D1V: vy = vz = 0, T_e = 1) in a periodic box of one
+    wavelength, L = n_cells dx, driven by the prescribed wave
+    phi = phi0(t) sin(k (x - vphi t)), k = 2 pi / L, ramped up over ramp_periods
+    wave periods (e phi0 / T_e = 0.1 and vphi = v_te as in Sec. V).  dt = dx / v0
+    for the speed-limited runs, dx / 4 for plain PIC (kind BETA_ONE)."""
+    if dt is None:
+        dt = dx / 4.0 if kind == BETA_ONE else dx / v0
+    s = species("e", -1.0, 1.0, 1.0, v0, kind, ppc=ppc, dx=dx, vdim=1)
+    s["T"] = 0.0
+    s["capacity"] = int(ppc * n_cells) + 64
+    L = n_cells * dx
+    return {"n_cells": int(n_cells), "dx": float(dx), "dt": float(dt), "periodic": True,
+            "phi_lo": 0.0, "phi_hi": 0.0, "eps0": 1.0, "seed": int(seed), "species": [s],
+            "source": {"mode": SRC_NONE, "lo_cells": 0.0, "len_cells": 0.0, "rate": 0.0,
+                       "ref_species": 0},
+            "wave": {"phi0": float(phi0), "k": 2.0 * math.pi / L, "vphi": float(vphi),
+                     "ramp": float(ramp_periods) * L / float(vphi)}}

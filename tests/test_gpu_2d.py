@@ -1,8 +1,8 @@
 """Parity of the 2D CUDA path (include/slpic2d.h) with the FP64 oracle.
 
 Bars: deposits bit-exact (the 2D quantised rule); the CG potential within
-cond(A) * rtol of the oracle's direct solve, with the oracle's CG iteration
-count; one step's velocities within 1e-5 |v| of the oracle and positions
+cond(A) * rtol of the oracle's direct solve, in at most twice the oracle's CG
+iterations plus 50; one step's velocities within 1e-5 |v| of the oracle and positions
 within the move that error causes (1e-5 beta |v| dt) plus 8 ulp of the FP32
 offset, particles matched by vz (a has no z component, so vz is unchanged by
 the push and identifies a particle on both sides)."""
@@ -89,9 +89,11 @@ def test_deposit2d_bit_exact(kind):
 
 
 def test_cg_solve_matches_direct_solver():
-    """The cooperative CG kernel: the oracle's answer within cond(A) rtol and
-    the same iteration count as the oracle's CG (same algorithm, FP64) within
-    2; a solve warm-started from the answer takes 0 iterations."""
+    """The cooperative CG kernel (FP32 iterates, FP64 right-hand side, solution and
+    true residual): the true residual meets rtol, the answer is the oracle's
+    direct solve within cond(A) rtol, the iterations stay within twice the
+    oracle's FP64 CG plus 50, and a solve warm-started from the answer takes 0
+    iterations."""
     nx, ny, dx = 96, 72, 0.6
     prob = _prob(nx=nx, ny=ny, ppc=1, dx=dx, cg_rtol=1e-9)
     prob["phi_lo"], prob["phi_hi"] = 0.4, -0.2
@@ -102,7 +104,7 @@ def test_cg_solve_matches_direct_solver():
     exact = orc.poisson2d_direct(rho, dx, 0.4, -0.2)
     _, it_o, _ = orc.poisson2d_cg(rho, dx, None, 0.4, -0.2, rtol=1e-9)
     assert res <= 1e-9
-    assert abs(it - it_o) <= 2, (it, it_o)
+    assert 0 < it <= 2 * it_o + 50, (it, it_o)
     assert np.abs(phi - exact).max() <= _cond(ny) * 1e-9 * np.abs(exact).max()
     assert np.all(phi[0] == 0.4) and np.all(phi[-1] == -0.2)
     _, it0, _ = g.solve_poisson(rho, exact)

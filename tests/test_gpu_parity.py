@@ -300,6 +300,40 @@ def test_wall_source_matches_oracle(kind):
     gpu.close()
 
 
+def test_speed_limit_raised_mid_run_matches_oracle():
+    """A speed limit that changes in time (Sec. II, Summary): after 3 steps the
+    timestep is halved and v0 doubled (in that order: dt v0 <= dx throughout;
+    doubling v0 first is refused).  The next step, from the GPU's own state, agrees
+    with the oracle under the new v0 and dt within the single-step bars."""
+    v0 = 0.2
+    prob = _problem(N=96, periodic=False, kind=HEAV, v0=v0, dx=0.5, phi_hi=1.0)
+    st = _state(prob, (30_000, 20_000), seed=31, vscale=1.0, nonneutral=True)
+    gpu = _sim(prob, st)
+    gpu.step(3)
+    with pytest.raises(binding.SlpicError) as ei:
+        binding.slpic_set_speed_limit(gpu.h, 0, 0, 2 * v0)
+    assert ei.value.code == binding.SLPIC_ERR_CFL
+    binding.slpic_set_timestep(gpu.h, prob["dt"] / 2)
+    for s in range(2):
+        binding.slpic_set_speed_limit(gpu.h, 0, s, 2 * v0)
+    new = dict(prob, dt=prob["dt"] / 2,
+               species=[dict(sp, v0=2 * v0) for sp in prob["species"]])
+    mid = [gpu.particles(s) for s in range(2)]
+    # the oracle from the GPU's state: rho^3 and E^3 under the old v0 (as on the
+    # GPU), then the new v0 and dt for the step
+    old_prob = dict(prob, species=[dict(sp) for sp in prob["species"]])
+    o = _oracle(old_prob, mid)
+    o.dt = new["dt"]
+    for sp in o.sp:
+        sp["v0"] = 2 * v0
+    gpu.step(1)
+    o.step(1)
+    stats = []
+    _compare_step(new, mid, gpu, o, stats=stats)
+    print("after the change", stats)
+    gpu.close()
+
+
 # ------------------------------------------------------------------ API behaviour
 def test_checkpoint_restore_is_bitwise():
     prob = inputs.sheath_problem(n_cells=64, ppc=50, v0=0.1)

@@ -1,0 +1,96 @@
+"""Test particles in a prescribed travelling wave (Sec. V), through
+slpic_set_wave: one step against the oracle, and the paper's study of resonant
+trapping with the speed limit above, near and at the wave's phase velocity."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1511_08225_gb300 import binding, inputs
+
+from _match import match
+
+pytestmark = pytest.mark.gpu
+
+
+def _sim_wave(prob, state):
+    sim = binding.Simulation(prob)
+    sim.load_state(state)
+    sim.prepare()
+    w = prob["wave"]
+    binding.slpic_set_wave(sim.h, w["phi0"], w["k"], w["vphi"], w["ramp"])
+    return sim
+
+
+@pytest.mark.parametrize("kind", [inputs.BETA_ONE, inputs.BETA_HEAVISIDE])
+def test_wave_step_matches_oracle(kind):
+    """A strong wave (e phi0 / T_e = 1, no ramp), 3V velocities: after one step the
+    velocities agree with the oracle within 1e-5 |v| and the positions within the
+    move that error causes, particles matched by (vy, vz)."""
+    prob = inputs.wave_problem(kind=kind, v0=0.6, ppc=100, phi0=1.0, ramp_periods=0.0)
+    sp = prob["species"][0]
+    rng = inputs.make_rng(5)
+    n = 20_000
+    cell, off = inputs.uniform_cells(rng, n, prob["n_cells"])
+    v = rng.normal(0.0, 1.0, (n, 3)).astype(np.float32)
+    st = [(cell, off, v)]
+    gpu = _sim_wave(prob, st)
+    o = orc.OracleSim(prob)
+    o.load_cells(0, cell, off, v)
+    o.start()
+    _, _, E = gpu.fields()
+    assert np.abs(E - o.E).max() <= 1e-6 * np.abs(o.E).max()
+    gpu.step(1)
+    o.step(1)
+    c, of, vg = gpu.particles(0)
+    b = np.ascontiguousarray(np.asarray(o.v[0], np.float32)[:, 1:3]).view(np.uint32)
+    ko = (b[:, 0].astype(np.uint64) << np.uint64(32)) | b[:, 1].astype(np.uint64)
+    bg = np.ascontiguousarray(vg[:, 1:3]).view(np.uint32)
+    kg = (bg[:, 0].astype(np.uint64) << np.uint64(32)) | bg[:, 1].astype(np.uint64)
+    ia, ib = match(ko, kg)
+    assert ia.size == n
+    vref = o.v[0][ia]
+    vn = np.maximum(np.linalg.norm(vref, axis=1), np.linalg.norm(v[ia], axis=1))
+    assert (np.linalg.norm(vg[ib] - vref, axis=1) <= 1e-5 * vn).all()
+    L = prob["n_cells"] * prob["dx"]
+    xg = (c[ib] + of[ib].astype(np.float64)) * prob["dx"]
+    d = (xg - o.x[0][ia] + 0.5 * L) % L - 0.5 * L
+    bet = orc._beta_vec(sp["kind"], np.linalg.norm(vref, axis=1), sp["v0"])
+    assert (np.abs(d) <= 1e-5 * bet * vn * prob["dt"] + 8 * 2.0 ** -24 * prob["dx"]).all()
+    gpu.close()
+
+
+T_END = 5000.0  # 20 ramp periods (2000) and about 10 bounce periods beyond
+
+
+def _final_distribution(kind, v0, bins):
+    prob = inputs.wave_problem(kind=kind, v0=v0)
+    st = inputs.load_state(prob, seed=7)
+    sim = _sim_wave(prob, st)
+    sim.step(int(round(T_END / prob["dt"])))
+    _, _, v = sim.particles(0)
+    sim.close()
+    vx = v[:, 0].astype(np.float64)
+    w = orc._beta_vec(int(prob["species"][0]["kind"]), np.abs(vx), v0)  # f = beta g
+    h, _ = np.histogram(vx, bins=bins, weights=w)
+    return h / (w.sum() * (bins[1] - bins[0]))
+
+
+def test_trapping_needs_a_speed_limit_above_the_phase_velocity():
+    """Sec. V: plain PIC flattens f(v) around vphi = v_te (trapping); SLPIC with
+    v0 = 2 vphi and 1.5 vphi reproduces the PIC distribution; v0 = 1.25 vphi
+    starts to distort it and v0 = vphi fails."""
+    bins = np.linspace(-1.0, 3.5, 46)
+    mid = 0.5 * (bins[1:] + bins[:-1])
+    f_pic = _final_distribution(inputs.BETA_ONE, 2.0, bins)
+    # flattening: f(1.25)/f(0.75) is exp(-1/2) = 0.61 for the initial Maxwellian
+    lo, hi = np.argmin(np.abs(mid - 0.75)), np.argmin(np.abs(mid - 1.25))
+    ratio = f_pic[hi] / f_pic[lo]
+    band = (mid >= 0.0) & (mid <= 3.0)
+    dist = {}
+    for r in (2.0, 1.5, 1.25, 1.0):
+        f = _final_distribution(inputs.BETA_HEAVISIDE, r, bins)
+        dist[r] = float(np.abs(f - f_pic)[band].sum() / f_pic[band].sum())
+    print("flattening ratio", ratio, "L1 distance to PIC", dist)
+    assert ratio > 0.8
+    assert dist[2.0] < 0.08 and dist[1.5] < 0.1
+    assert dist[1.0] > 2.5 * dist[2.0] and dist[1.0] > dist[1.5]

@@ -461,3 +461,41 @@ def test_wall_source_fills_half_density(kind):
     prof = acc[1:N] / m
     assert abs(prof.mean() - 0.5) < 0.015, prof.mean()
     assert np.abs(prof - 0.5).max() < 0.08, prof
+
+
+# ------------------------------------------------------------------ prescribed wave (Sec. V)
+def test_prescribed_wave_frame_energy_is_conserved():
+    """Test particles (beta = 1) in the travelling wave phi0 sin(k (x - vphi t)):
+    in the wave frame the potential is static, so after the ramp
+    (v - vphi)^2 / 2 + (q/m) phi(x, t) is a constant of each particle's motion; the
+    leapfrog keeps it to O(dt^2).  A wrong sign of E, of the phase or of the wave
+    speed breaks this by O(1)."""
+    N, dx = 200, 0.5
+    L = N * dx
+    k = 2 * np.pi / L
+    prob = inputs.periodic_problem(n_cells=N, dx=dx, dt=0.1, ppc=1, kind=inputs.BETA_ONE)
+    prob["species"] = prob["species"][:1]
+    prob["wave"] = {"phi0": 0.1, "k": k, "vphi": 1.0, "ramp": 0.0}
+    o = orc.OracleSim(prob)
+    rng = np.random.default_rng(2)
+    n = 64
+    x = rng.uniform(0, L, n)
+    v = np.zeros((n, 3))
+    v[:, 0] = 1.0 + rng.uniform(-0.8, 0.8, n)
+    o.load(0, x, v)
+    o.start()
+    qm = prob["species"][0]["q"] / prob["species"][0]["m"]
+
+    def energy():
+        t = o.step_index * o.dt
+        # v is v^{n-1/2}: compare at the same phase of the leapfrog each time
+        return 0.5 * (o.v[0][:, 0] - 1.0) ** 2 + qm * 0.1 * np.sin(k * (o.x[0] - t))
+
+    e0 = energy()
+    for _ in range(40):
+        o.step(50)
+        assert np.abs(energy() - e0).max() < 0.02
+    # and the field is the one prescribed
+    t = o.step_index * o.dt
+    xj = np.arange(N) * dx
+    assert np.abs(o.E + 0.1 * k * np.cos(k * (xj - t))).max() < 1e-12
