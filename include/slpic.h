@@ -242,7 +242,9 @@ int slpic_diagnostics(slpic_t *h, int instance, slpic_diag *out);
 /* Serialise the complete state (particles, deposit, fields, counters, source
  * remainders, step index) into a host buffer.  With buf == NULL, *size
  * receives the bytes needed.  Restoring into a handle created from the same
- * config continues bit for bit. */
+ * config continues bit for bit.  Settings changed after creation
+ * (slpic_set_speed_limit, slpic_set_timestep, slpic_set_wave) are not part of
+ * the checkpoint: set them again on the restored handle. */
 int slpic_save(slpic_t *h, void *buf, size_t *size);
 int slpic_restore(slpic_t *h, const void *buf, size_t size);
 
