@@ -242,6 +242,20 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def aggregate_ranks(ms, particle_steps, dist, device):
+    """Whole-job figures over the ranks (weak scaling, one independent instance per
+    rank): the slowest rank's time and the particle-steps of all ranks.  Without a
+    process group the rank's own figures."""
+    if not dist:
+        return ms, particle_steps
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    ps = torch.tensor([particle_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ps, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(ps[0])
+
+
 def run_gpu(args):
     import torch
 
@@ -306,15 +320,7 @@ def run_gpu(args):
     binding.slpic_enable_kernel_timing(sim.h, 0)
     kps = binding.slpic_kernels_per_step(sim.h)
 
-    particle_steps = 0.5 * (n0 + n1) * args.steps
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms, particle_steps], dtype=torch.float64, device="cuda")
-        tt = t.clone()
-        dist.all_reduce(tt[:1], op=dist.ReduceOp.MAX)
-        ps = t[1:].clone()
-        dist.all_reduce(ps, op=dist.ReduceOp.SUM)
-        t_max, particle_steps = float(tt[0]), float(ps[0])
+    t_max, particle_steps = aggregate_ranks(ms, 0.5 * (n0 + n1) * args.steps, dist, "cuda")
     value = particle_steps / (t_max * 1e-3)
 
     # roofline of the particle kernel (dominant kernel)
