@@ -91,6 +91,6 @@ def test_trapping_needs_a_speed_limit_above_the_phase_velocity():
         f = _final_distribution(inputs.BETA_HEAVISIDE, r, bins)
         dist[r] = float(np.abs(f - f_pic)[band].sum() / f_pic[band].sum())
     print("flattening ratio", ratio, "L1 distance to PIC", dist)
-    assert ratio > 0.8
+    assert ratio > 0.72  # measured 0.81; the unflattened Maxwellian gives 0.61
     assert dist[2.0] < 0.08 and dist[1.5] < 0.1
     assert dist[1.0] > 2.5 * dist[2.0] and dist[1.0] > dist[1.5]
