@@ -1,0 +1,88 @@
+"""Pins of the U-Net oracle (no GPU), each resting on something other than the
+oracle: a library correlation, adjoint identities, bfloat16 values worked out by
+hand, and central finite differences of the loss for parameters of every layer
+(2-level, 8-channel nets at 32 x 32)."""
+import numpy as np
+import pytest
+from scipy import signal
+
+from oracle import unet
+
+
+def test_conv_single_channel_is_a_2d_correlation():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(1, 9, 11))
+    w = rng.normal(size=(1, 1, 3, 3))
+    b = np.array([0.3])
+    y = unet.conv(x, w, b)
+    ref = signal.correlate2d(x[0], w[0, 0], mode="same", boundary="fill", fillvalue=0.0) + 0.3
+    assert np.abs(y[0] - ref).max() < 1e-12
+
+
+def test_conv_channels_add_up():
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(3, 6, 6))
+    w = rng.normal(size=(2, 3, 3, 3))
+    b = rng.normal(size=2)
+    y = unet.conv(x, w, b)
+    for o in range(2):
+        ref = b[o] + sum(signal.correlate2d(x[c], w[o, c], mode="same") for c in range(3))
+        assert np.abs(y[o] - ref).max() < 1e-12
+
+
+def test_pool_and_up_backward_are_adjoints():
+    """<up(a), B> = <a, up^T(B)> and <pool(A), b> = <A, pool^T(b)>."""
+    rng = np.random.default_rng(3)
+    a, B = rng.normal(size=(2, 4, 5)), rng.normal(size=(2, 8, 10))
+    assert np.isclose((unet.up(a) * B).sum(), (a * unet.up_backward(B)).sum())
+    assert np.isclose((unet.pool(B) * a).sum(), (B * unet.pool_backward(a)).sum())
+    assert np.allclose(unet.pool(unet.up(a)), a)
+
+
+def test_bf16_rounding():
+    """8 significant bits, round to nearest, ties to even."""
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, -2.5 + 2 ** -9,
+                     3.0e-3], np.float32)
+    out = unet.bf16(vals)
+    assert out[0] == 1.0
+    assert out[1] == 1.0                      # halfway: to the even 1.0
+    assert out[2] == 1.0 + 2 ** -6            # halfway: to the even 1 + 2^-6
+    assert out[3] == 1.0 + 2 ** -7            # representable
+    assert out[4] == -2.5                     # below half an ulp (2^-7 at 2.5)
+    assert abs(out[5] / 3.0e-3 - 1) < 2 ** -8
+
+
+def test_layer_shapes():
+    assert unet.layer_shapes(2, 8) == [(1, 8), (8, 16), (24, 8), (8, 1)]
+    assert unet.layer_shapes(4, 32)[3] == (128, 256)
+    assert unet.layer_shapes(4, 32)[4] == (256 + 128, 128)
+
+
+@pytest.mark.parametrize("levels,base,n", [(2, 8, 32), (3, 4, 16), (1, 3, 8)])
+def test_gradients_match_finite_differences(levels, base, n):
+    rng = np.random.default_rng(levels + base)
+    params = unet.init_params(levels, base, seed=4)
+    # nonzero biases so every ReLU sees both signs
+    params = [(w, rng.normal(0, 0.1, b.shape)) for w, b in params]
+    x = rng.normal(size=(n, n))
+    t = rng.normal(size=(n, n))
+    y, cache = unet.forward(params, x, levels)
+    loss, dy = unet.mse(y, t)
+    grads = unet.backward(params, cache, dy, levels)
+    h = 1e-6
+    for k, ((w, b), (dw, db)) in enumerate(zip(params, grads)):
+        for idx in [tuple(rng.integers(0, s) for s in w.shape) for _ in range(3)]:
+            wp = [(ww.copy(), bb.copy()) for ww, bb in params]
+            wp[k][0][idx] += h
+            lp = unet.mse(unet.forward(wp, x, levels)[0], t)[0]
+            wp[k][0][idx] -= 2 * h
+            lm = unet.mse(unet.forward(wp, x, levels)[0], t)[0]
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - dw[idx]) <= 1e-5 * max(abs(fd), 1e-3), (k, idx, fd, dw[idx])
+        j = int(rng.integers(0, b.size))
+        wp = [(ww.copy(), bb.copy()) for ww, bb in params]
+        wp[k][1][j] += h
+        lp = unet.mse(unet.forward(wp, x, levels)[0], t)[0]
+        wp[k][1][j] -= 2 * h
+        lm = unet.mse(unet.forward(wp, x, levels)[0], t)[0]
+        assert abs((lp - lm) / (2 * h) - db[j]) <= 1e-5 * max(abs(db[j]), 1e-3)
