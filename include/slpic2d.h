@@ -34,6 +34,7 @@
 #define SLPIC2D_H
 
 #include "slpic.h"
+#include "slpic_unet.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -128,6 +129,23 @@ int slpic2d_kernel_times(slpic2d_t *h, double *particle_ms, double *inject_ms, d
  * (may be NULL) report the solve.  Leaves the simulation's own fields alone. */
 int slpic2d_solve_poisson(slpic2d_t *h, const double *rho, double *phi, int32_t *iterations,
                           double *rel_residual);
+
+/* Initial guess of the CG in each following slpic2d_step (the answer is the same
+ * to cg_rtol whatever the guess; the iterations it takes are not):
+ *   SLPIC2D_WARM_PREV  the potential of the previous step (the default);
+ *   SLPIC2D_WARM_ZERO  the straight line between the plate potentials;
+ *   SLPIC2D_WARM_UNET  that line plus net(rho), rho the step's charge density on
+ *                      rows 0..ny-1 (row 0 set to 0) as an (H, W) = (ny, nx)
+ *                      FP32 image (slpic_unet.h), net's output taken on the
+ *                      interior rows 1..ny-1.
+ * net: required for SLPIC2D_WARM_UNET (grid (ny, nx), max_batch >= 1), ignored
+ * otherwise.  It is borrowed: it must outlive its use, and is run on this
+ * handle's stream, so it must not be used on another stream meanwhile.  The
+ * network's time counts in the field time of slpic2d_kernel_times. */
+#define SLPIC2D_WARM_PREV 0
+#define SLPIC2D_WARM_ZERO 1
+#define SLPIC2D_WARM_UNET 2
+int slpic2d_set_warm_start(slpic2d_t *h, int32_t mode, slpic_unet_t *net);
 
 #ifdef __cplusplus
 }

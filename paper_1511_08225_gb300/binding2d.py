@@ -18,8 +18,10 @@ EXPORTS2D = (
     "slpic2d_load_particles", "slpic2d_prepare", "slpic2d_step", "slpic2d_synchronize",
     "slpic2d_fields", "slpic2d_charge_raw", "slpic2d_particle_count", "slpic2d_get_particles",
     "slpic2d_diagnostics", "slpic2d_solve_poisson", "slpic2d_enable_kernel_timing",
-    "slpic2d_kernel_times",
+    "slpic2d_kernel_times", "slpic2d_set_warm_start",
 )
+
+SLPIC2D_WARM_PREV, SLPIC2D_WARM_ZERO, SLPIC2D_WARM_UNET = 0, 1, 2
 
 
 class slpic2d_config(ctypes.Structure):
@@ -68,6 +70,7 @@ def load_library() -> ctypes.CDLL:
         "slpic2d_diagnostics": (I, [P, ctypes.POINTER(slpic2d_diag)]),
         "slpic2d_solve_poisson": (I, [P, P, P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]),
         "slpic2d_enable_kernel_timing": (I, [P, I]),
+        "slpic2d_set_warm_start": (I, [P, I32, P]),
         "slpic2d_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]),
@@ -208,6 +211,12 @@ def slpic2d_solve_poisson(h, rho: np.ndarray, phi0: np.ndarray | None = None):
     return phi, it.value, res.value
 
 
+def slpic2d_set_warm_start(h, mode: int, net=None):
+    """net: a binding_unet.UNet (or its raw handle) for SLPIC2D_WARM_UNET."""
+    nh = getattr(net, "h", net)
+    _check(h, load_library().slpic2d_set_warm_start(h, mode, nh), "slpic2d_set_warm_start")
+
+
 def slpic2d_enable_kernel_timing(h, on: bool = True):
     _check(h, load_library().slpic2d_enable_kernel_timing(h, int(on)),
            "slpic2d_enable_kernel_timing")
@@ -258,6 +267,9 @@ class Simulation2D:
 
     def synchronize(self):
         slpic2d_synchronize(self.h)
+
+    def set_warm_start(self, mode: int, net=None):
+        slpic2d_set_warm_start(self.h, mode, net)
 
     def fields(self):
         return slpic2d_fields(self.h, self.nx, self.ny)

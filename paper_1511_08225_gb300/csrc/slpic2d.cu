@@ -25,6 +25,7 @@
 
 #include "push_math.cuh"
 #include "slpic2d.h"
+#include "unet_internal.h"
 
 namespace slpic {
 void set_create_error(const std::string &msg);  // api.cu
@@ -714,6 +715,39 @@ __global__ void __launch_bounds__(kCgThreads) k_cg2d(Params2D p, int mode)
     }
 }
 
+// ---- initial guess of the CG (slpic2d_set_warm_start) ------------------------------
+// rho of rows 0..ny-1 as FP32 from the deposits (left in place for the CG kernel);
+// row 0, a plate, is zero.  The layout is the nodal one, so the array is the
+// U-Net's (H, W) = (ny, nx) input.
+__global__ void __launch_bounds__(kThreads) k_rho32(Params2D p, float *__restrict__ out)
+{
+    const long long n = (long long)p.ny * p.nx;
+    for (long long t = (long long)blockIdx.x * kThreads + threadIdx.x; t < n;
+         t += (long long)gridDim.x * kThreads) {
+        double rho = 0.0;
+        if (t >= p.nx)
+            for (int s = 0; s < p.ns; ++s)
+                rho = fma(p.sp[s].rho_unit, (double)(long long)p.acc[(size_t)s * p.nn + t], rho);
+        out[t] = (float)rho;
+    }
+}
+
+// phi on the interior rows = the straight line between the plate potentials plus
+// y (the network's guess for the zero-plate problem), or the line alone when y is
+// null (the zero guess).
+__global__ void __launch_bounds__(kThreads) k_guess(Params2D p, const float *__restrict__ y)
+{
+    const long long first = p.nx, last = (long long)p.ny * p.nx;
+    for (long long t = first + (long long)blockIdx.x * kThreads + threadIdx.x; t < last;
+         t += (long long)gridDim.x * kThreads) {
+        const int j = (int)(t / p.nx);
+        double v = p.phi_lo + (p.phi_hi - p.phi_lo) * ((double)j / p.ny);
+        if (y)
+            v += (double)y[t];
+        p.phi[t] = v;
+    }
+}
+
 }  // namespace slpic2d
 
 // =================================================================================
@@ -732,6 +766,9 @@ struct slpic2d_sim {
     std::vector<cudaEvent_t> events;   // 4 per recorded step
     long long t_steps = 0;             // steps recorded since the last read
     State2D *d_state = nullptr;
+    int warm_mode = SLPIC2D_WARM_PREV;  // initial guess of each step's CG
+    slpic_unet_t *net = nullptr;        // SLPIC2D_WARM_UNET: borrowed network
+    float *rho32 = nullptr, *guess32 = nullptr;  // its input and output (ny * nx)
     std::vector<void *> allocs;
     std::string err;
 };
@@ -772,6 +809,52 @@ static int launch_cg(slpic2d_t *h, int mode)
     void *args[] = {&p, &mode};
     CK2(h, cudaLaunchCooperativeKernel((const void *)k_cg2d, dim3(h->cg_ctas), dim3(kCgThreads),
                                        args, 0, h->stream));
+    return SLPIC_OK;
+}
+
+// The initial guess of the step's CG, on the handle's stream (SLPIC2D_WARM_PREV:
+// phi as the previous step left it).
+static int warm_start(slpic2d_t *h)
+{
+    const unsigned grid = (unsigned)std::min<long long>(
+        ((long long)h->p.ny * h->p.nx + kThreads - 1) / kThreads, 152LL * 8);
+    if (h->warm_mode == SLPIC2D_WARM_ZERO) {
+        k_guess<<<grid, kThreads, 0, h->stream>>>(h->p, nullptr);
+    } else if (h->warm_mode == SLPIC2D_WARM_UNET) {
+        k_rho32<<<grid, kThreads, 0, h->stream>>>(h->p, h->rho32);
+        CK2(h, cudaGetLastError());
+        const int rc = slpic_unet_forward_on(h->net, 1, h->rho32, h->guess32, h->stream);
+        if (rc)
+            return fail2(h, rc, std::string("U-Net forward: ") + slpic_unet_last_error(h->net));
+        k_guess<<<grid, kThreads, 0, h->stream>>>(h->p, h->guess32);
+    }
+    CK2(h, cudaGetLastError());
+    return SLPIC_OK;
+}
+
+extern "C" int slpic2d_set_warm_start(slpic2d_t *h, int32_t mode, slpic_unet_t *net)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    if (mode != SLPIC2D_WARM_PREV && mode != SLPIC2D_WARM_ZERO && mode != SLPIC2D_WARM_UNET)
+        return fail2(h, SLPIC_ERR_INVALID, "unknown warm-start mode");
+    if (mode == SLPIC2D_WARM_UNET) {
+        if (!net)
+            return fail2(h, SLPIC_ERR_INVALID, "SLPIC2D_WARM_UNET needs a network");
+        int H, W, nb;
+        slpic_unet_shape(net, &H, &W, &nb);
+        if (H != h->p.ny || W != h->p.nx)
+            return fail2(h, SLPIC_ERR_INVALID, "the network's grid must be (ny, nx)");
+        if (!h->rho32) {
+            const size_t n = (size_t)h->p.ny * h->p.nx;
+            CK2(h, cudaMalloc(&h->rho32, sizeof(float) * n));
+            h->allocs.push_back(h->rho32);
+            CK2(h, cudaMalloc(&h->guess32, sizeof(float) * n));
+            h->allocs.push_back(h->guess32);
+        }
+    }
+    h->warm_mode = mode;
+    h->net = mode == SLPIC2D_WARM_UNET ? net : nullptr;
     return SLPIC_OK;
 }
 
@@ -1047,6 +1130,8 @@ extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
         CK2(h, cudaGetLastError());
         if (ev)
             CK2(h, cudaEventRecord(ev[2], h->stream));
+        if ((rc = warm_start(h)))
+            return rc;
         rc = launch_cg(h, 0);
         if (rc)
             return rc;

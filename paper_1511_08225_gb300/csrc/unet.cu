@@ -1,0 +1,852 @@
+// unet.cu -- the small convolutional U-Net that warm-starts the 2D CG
+// (include/slpic_unet.h): forward, backward and Adam, hand-written.
+//
+// The paper has no learned part; the network is the plain U-Net pattern at the
+// size the 2D solve needs.  Level l = 0..L-1 has C_l = C 2^l channels:
+//   encoder  e_0 = relu(conv(x)),  e_l = relu(conv(pool(e_{l-1})))
+//   decoder  d_{L-1} = e_{L-1},    d_l = relu(conv(concat(up(d_{l+1}), e_l)))
+//   output   y = conv(d_0)
+// conv: 3x3, zero padding, bias; pool: 2x2 mean; up: nearest x2; concat: the
+// upsampled channels first.  Activations and gradients are FP32 (N, C, H, W);
+// the convolutions use BF16 copies of the FP32 master weights (biases stay FP32)
+// and accumulate in FP32; weight-gradient sums are FP64 across threads.  The loss
+// is the mean squared error; training is Adam.
+//
+// Tensors are addressed through views (base, channels of the underlying buffer,
+// channel offset), so e_l is written straight into the second half of level l's
+// concat buffer and its gradient is read from the second half of the concat
+// gradient: the concatenation costs no copy.  The ReLU mask is taken from the
+// stored activation (a > 0 exactly when z > 0).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "slpic_unet.h"
+#include "unet_internal.h"
+
+namespace {
+
+constexpr int kT = 256;   // threads per CTA
+constexpr int kOCB = 8;   // output channels per thread in the convolutions
+
+struct TV {               // (n, c, pix) at p[(n*ctot + coff + c)*HW + pix]
+    float *p;
+    int ctot, coff;
+};
+
+__device__ __forceinline__ float *at(TV v, int n, int c, size_t HW)
+{
+    return v.p + ((size_t)n * v.ctot + v.coff + c) * HW;
+}
+
+// ---- convolution forward: a = conv(x) (relu'd when relu != 0) -------------------
+// One thread per output pixel and kOCB output channels; blockIdx = (pixel tile,
+// channel group, sample).
+__global__ void __launch_bounds__(kT) k_conv_fwd(TV x, int cin, const __nv_bfloat16 *__restrict__ w,
+                                               const float *__restrict__ b, int cout, TV a,
+                                               int relu, int H, int W)
+{
+    const int pix = blockIdx.x * kT + threadIdx.x;
+    if (pix >= H * W)
+        return;
+    const int i = pix / W, j = pix - i * W;
+    const int n = blockIdx.z, o0 = blockIdx.y * kOCB;
+    const size_t HW = (size_t)H * W;
+    float acc[kOCB];
+#pragma unroll
+    for (int k = 0; k < kOCB; ++k)
+        acc[k] = (o0 + k < cout) ? b[o0 + k] : 0.0f;
+    for (int c = 0; c < cin; ++c) {
+        const float *xc = at(x, n, c, HW);
+        float v[9];
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+            const int ii = i + di - 1;
+#pragma unroll
+            for (int dj = 0; dj < 3; ++dj) {
+                const int jj = j + dj - 1;
+                v[di * 3 + dj] = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? xc[ii * W + jj] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kOCB; ++k) {
+            if (o0 + k < cout) {
+                const __nv_bfloat16 *wk = w + ((size_t)(o0 + k) * cin + c) * 9;
+#pragma unroll
+                for (int t = 0; t < 9; ++t)
+                    acc[k] = __fmaf_rn(__bfloat162float(wk[t]), v[t], acc[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kOCB; ++k) {
+        if (o0 + k >= cout)
+            break;
+        at(a, n, o0 + k, HW)[pix] = relu ? fmaxf(acc[k], 0.0f) : acc[k];
+    }
+}
+
+// ---- gradient of the convolution's input: dx = conv^T(dz) ------------------------
+// dx[c,i,j] = sum_{o,di,dj} w[o,c,di,dj] dz[o, i-di+1, j-dj+1]
+__global__ void __launch_bounds__(kT) k_conv_bwd_x(TV dz, int cout, const __nv_bfloat16 *__restrict__ w,
+                                                 int cin, TV dx, int H, int W)
+{
+    const int pix = blockIdx.x * kT + threadIdx.x;
+    if (pix >= H * W)
+        return;
+    const int i = pix / W, j = pix - i * W;
+    const int n = blockIdx.z, c0 = blockIdx.y * kOCB;
+    const size_t HW = (size_t)H * W;
+    float acc[kOCB];
+#pragma unroll
+    for (int k = 0; k < kOCB; ++k)
+        acc[k] = 0.0f;
+    for (int o = 0; o < cout; ++o) {
+        const float *dc = at(dz, n, o, HW);
+        float g[9];
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+            const int ii = i - di + 1;
+#pragma unroll
+            for (int dj = 0; dj < 3; ++dj) {
+                const int jj = j - dj + 1;
+                g[di * 3 + dj] = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? dc[ii * W + jj] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kOCB; ++k) {
+            if (c0 + k < cin) {
+                const __nv_bfloat16 *wk = w + ((size_t)o * cin + c0 + k) * 9;
+#pragma unroll
+                for (int t = 0; t < 9; ++t)
+                    acc[k] = __fmaf_rn(__bfloat162float(wk[t]), g[t], acc[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kOCB; ++k) {
+        if (c0 + k >= cin)
+            break;
+        at(dx, n, c0 + k, HW)[pix] = acc[k];
+    }
+}
+
+// ---- gradient of the weights and bias: one CTA per (c, o) ----------------------
+// dw[o,c,di,dj] = sum_{n,i,j} dz[n,o,i,j] x[n,c,i+di-1,j+dj-1];  db[o] = sum dz[n,o]
+// (written by the c = 0 CTA).  FP32 per thread, FP64 across threads.
+__global__ void __launch_bounds__(kT) k_conv_bwd_w(TV x, int cin, TV dz, int cout,
+                                                 float *__restrict__ dw, float *__restrict__ db,
+                                                 int H, int W, int nb)
+{
+    __shared__ double s_red[kT / 32][10];
+    const int c = blockIdx.x, o = blockIdx.y;
+    const size_t HW = (size_t)H * W;
+    float acc[10];
+#pragma unroll
+    for (int t = 0; t < 10; ++t)
+        acc[t] = 0.0f;
+    for (int n = 0; n < nb; ++n) {
+        const float *xc = at(x, n, c, HW);
+        const float *gc = at(dz, n, o, HW);
+        for (int pix = threadIdx.x; pix < H * W; pix += kT) {
+            const int i = pix / W, j = pix - i * W;
+            const float g = gc[pix];
+#pragma unroll
+            for (int di = 0; di < 3; ++di) {
+                const int ii = i + di - 1;
+#pragma unroll
+                for (int dj = 0; dj < 3; ++dj) {
+                    const int jj = j + dj - 1;
+                    const float v = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? xc[ii * W + jj] : 0.0f;
+                    acc[di * 3 + dj] = __fmaf_rn(g, v, acc[di * 3 + dj]);
+                }
+            }
+            acc[9] += g;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 10; ++t) {
+        double v = acc[t];
+        for (int off = 16; off; off >>= 1)
+            v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0)
+            s_red[warp][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double v = 0.0;
+        for (int k = 0; k < kT / 32; ++k)
+            v += s_red[k][threadIdx.x];
+        if (threadIdx.x < 9)
+            dw[((size_t)o * cin + c) * 9 + threadIdx.x] = (float)v;
+        else if (c == 0)
+            db[o] = (float)v;
+    }
+}
+
+// ---- elementwise layers (grid-stride over n, c, pixel) ----------------------------
+__device__ __forceinline__ void split(size_t t, int C, size_t HW, int &n, int &c, size_t &pix)
+{
+    pix = t % HW;
+    const size_t nc = t / HW;
+    c = (int)(nc % C);
+    n = (int)(nc / C);
+}
+
+// g = a > 0 ? g : 0, in place (the ReLU's backward pass, mask from its output)
+__global__ void k_relu_bwd(TV a, TV g, int C, size_t HW, int nb)
+{
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW;
+         t += (size_t)gridDim.x * kT) {
+        int n, c;
+        size_t pix;
+        split(t, C, HW, n, c, pix);
+        float *gp = at(g, n, c, HW) + pix;
+        if (!(at(a, n, c, HW)[pix] > 0.0f))
+            *gp = 0.0f;
+    }
+}
+
+// out (H/2, W/2) = 2x2 mean of in (H, W)
+__global__ void k_pool_fwd(TV in, TV out, int C, int H, int W, int nb)
+{
+    const int h = H / 2, w = W / 2;
+    const size_t HW = (size_t)H * W, hw = (size_t)h * w;
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * hw;
+         t += (size_t)gridDim.x * kT) {
+        int n, c;
+        size_t pix;
+        split(t, C, hw, n, c, pix);
+        const int i = (int)(pix / w), j = (int)(pix - (size_t)i * w);
+        const float *s = at(in, n, c, HW) + (size_t)(2 * i) * W + 2 * j;
+        at(out, n, c, hw)[pix] = 0.25f * ((s[0] + s[1]) + (s[W] + s[W + 1]));
+    }
+}
+
+// din (H, W) += pool^T(dout): a quarter of the coarse gradient to each of the four
+__global__ void k_pool_bwd_add(TV dout, TV din, int C, int H, int W, int nb)
+{
+    const size_t HW = (size_t)H * W, hw = (size_t)(H / 2) * (W / 2);
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW;
+         t += (size_t)gridDim.x * kT) {
+        int n, c;
+        size_t pix;
+        split(t, C, HW, n, c, pix);
+        const int i = (int)(pix / W), j = (int)(pix - (size_t)i * W);
+        at(din, n, c, HW)[pix] += 0.25f * at(dout, n, c, hw)[(size_t)(i / 2) * (W / 2) + j / 2];
+    }
+}
+
+// out (2H, 2W) = nearest-neighbour upsampling of in (H, W)
+__global__ void k_up_fwd(TV in, TV out, int C, int H, int W, int nb)
+{
+    const int W2 = 2 * W;
+    const size_t HW = (size_t)H * W, HW4 = 4 * HW;
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW4;
+         t += (size_t)gridDim.x * kT) {
+        int n, c;
+        size_t pix;
+        split(t, C, HW4, n, c, pix);
+        const int i = (int)(pix / W2), j = (int)(pix - (size_t)i * W2);
+        at(out, n, c, HW4)[pix] = at(in, n, c, HW)[(size_t)(i / 2) * W + j / 2];
+    }
+}
+
+// din (H, W) = up^T(dout): the sum of the four fine gradients
+__global__ void k_up_bwd(TV dout, TV din, int C, int H, int W, int nb)
+{
+    const int W2 = 2 * W;
+    const size_t HW = (size_t)H * W, HW4 = 4 * HW;
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW;
+         t += (size_t)gridDim.x * kT) {
+        int n, c;
+        size_t pix;
+        split(t, C, HW, n, c, pix);
+        const int i = (int)(pix / W), j = (int)(pix - (size_t)i * W);
+        const float *s = at(dout, n, c, HW4) + (size_t)(2 * i) * W2 + 2 * j;
+        at(din, n, c, HW)[pix] = (s[0] + s[1]) + (s[W2] + s[W2 + 1]);
+    }
+}
+
+// ---- input normalisation: s_n = rms(x_n) (1 for an all-zero sample), xs = x / s_n
+// One CTA per sample; FP64 sum.  With normalise == 0, s_n = 1.
+__global__ void __launch_bounds__(kT) k_norm_in(const float *__restrict__ x, float *__restrict__ xs,
+                                              float *__restrict__ s, size_t HW, int normalise)
+{
+    __shared__ double s_red[kT / 32];
+    __shared__ float s_scale;
+    const int n = blockIdx.x;
+    const float *xn = x + (size_t)n * HW;
+    double acc = 0.0;
+    if (normalise)
+        for (size_t q = threadIdx.x; q < HW; q += kT)
+            acc += (double)xn[q] * xn[q];
+    for (int off = 16; off; off >>= 1)
+        acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kT / 32; ++k)
+            v += s_red[k];
+        float sc = normalise ? (float)sqrt(v / (double)HW) : 1.0f;
+        if (!(sc > 0.0f))
+            sc = 1.0f;
+        s_scale = sc;
+        s[n] = sc;
+    }
+    __syncthreads();
+    const float inv = 1.0f / s_scale;
+    for (size_t q = threadIdx.x; q < HW; q += kT)
+        xs[(size_t)n * HW + q] = xn[q] * inv;
+}
+
+// y = y_net * s_n * out_scale
+__global__ void k_scale_out(const float *__restrict__ ynet, float *__restrict__ y,
+                            const float *__restrict__ s, float out_scale, size_t HW, int nb)
+{
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * HW;
+         t += (size_t)gridDim.x * kT)
+        y[t] = ynet[t] * (s[t / HW] * out_scale);
+}
+
+// mean squared error against the target in network units, t / (s_n out_scale):
+// dy = 2 r / count; per-CTA FP64 partial sums of r^2
+__global__ void __launch_bounds__(kT) k_mse(const float *__restrict__ ynet,
+                                          const float *__restrict__ t, const float *__restrict__ s,
+                                          float out_scale, float *__restrict__ dy, size_t HW,
+                                          int nb, double *__restrict__ part)
+{
+    __shared__ double s_red[kT / 32];
+    const size_t count = (size_t)nb * HW;
+    double acc = 0.0;
+    for (size_t q = blockIdx.x * (size_t)kT + threadIdx.x; q < count; q += (size_t)gridDim.x * kT) {
+        const float r = ynet[q] - t[q] / (s[q / HW] * out_scale);
+        dy[q] = 2.0f * r / (float)count;
+        acc += (double)r * r;
+    }
+    for (int off = 16; off; off >>= 1)
+        acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kT / 32; ++k)
+            v += s_red[k];
+        part[blockIdx.x] = v;
+    }
+}
+
+// loss = sum(part[0..np)) / count, in CTA order (one CTA)
+__global__ void k_loss(const double *__restrict__ part, int np, double count, double *loss)
+{
+    __shared__ double s_red[kT / 32];
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < np; q += kT)
+        acc += part[q];
+    for (int off = 16; off; off >>= 1)
+        acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kT / 32; ++k)
+            v += s_red[k];
+        *loss = v / count;
+    }
+}
+
+// Adam (Kingma & Ba, 2015) on the FP32 master parameters; the BF16 copy follows.
+// c1 = 1 - b1^t and c2 = 1 - b2^t are the bias corrections of step t.
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, __nv_bfloat16 *__restrict__ pb, size_t n, float lr,
+                       float b1, float b2, float eps, float c1, float c2)
+{
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < n; t += (size_t)gridDim.x * kT) {
+        const float gt = g[t];
+        const float mt = b1 * m[t] + (1.0f - b1) * gt;
+        const float vt = b2 * v[t] + (1.0f - b2) * gt * gt;
+        m[t] = mt;
+        v[t] = vt;
+        const float w = p[t] - lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+        p[t] = w;
+        pb[t] = __float2bfloat16_rn(w);
+    }
+}
+
+__global__ void k_to_bf16(const float *__restrict__ p, __nv_bfloat16 *__restrict__ pb, size_t n)
+{
+    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < n; t += (size_t)gridDim.x * kT)
+        pb[t] = __float2bfloat16_rn(p[t]);
+}
+
+}  // namespace
+
+// =====================================================================================
+// Host side: buffers, the layer schedule, the C ABI.
+// =====================================================================================
+struct ConvSpec {
+    int cin, cout, level;   // level: the grid the conv runs on
+    size_t w_off, b_off;    // into the flat parameter array
+};
+
+struct slpic_unet {
+    slpic_unet_config cfg{};
+    int L = 0, C = 0, H = 0, W = 0, nbmax = 0;
+    std::vector<ConvSpec> conv;   // 2L convs in parameter order
+    size_t nparam = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16 *pb = nullptr;
+    // forward activations (per level; see the schedule below)
+    float *xin = nullptr, *s = nullptr, *ynet = nullptr;
+    std::vector<float *> cat, d, pin;  // cat, d: levels 0..L-2; pin: levels 1..L-1
+    float *etop = nullptr;             // e_{L-1}
+    // gradients (allocated on first use)
+    bool have_grads = false;
+    float *dy = nullptr;
+    std::vector<float *> dcat, gd, dpool;  // dcat: 0..L-2; gd: 0..L-1; dpool: 1..L-1
+    double *part = nullptr, *loss = nullptr;
+    long long adam_t = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<void *> allocs;
+    std::string err;
+};
+
+namespace {
+
+constexpr int kMseCtas = 608;  // 4 per SM
+
+#define CKU(h, call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+            return e_ == cudaErrorMemoryAllocation ? SLPIC_ERR_OOM : SLPIC_ERR_CUDA;       \
+        }                                                                                  \
+    } while (0)
+
+int failu(slpic_unet_t *h, int code, const std::string &msg)
+{
+    h->err = msg;
+    return code;
+}
+
+int ch(const slpic_unet_t *h, int l) { return h->C << l; }
+int hl(const slpic_unet_t *h, int l) { return h->H >> l; }
+int wl(const slpic_unet_t *h, int l) { return h->W >> l; }
+size_t hwl(const slpic_unet_t *h, int l) { return (size_t)hl(h, l) * wl(h, l); }
+
+int alloc(slpic_unet_t *h, void **ptr, size_t bytes)
+{
+    CKU(h, cudaMalloc(ptr, bytes));
+    h->allocs.push_back(*ptr);
+    return SLPIC_OK;
+}
+
+int alloc_f(slpic_unet_t *h, float **ptr, size_t count)
+{
+    return alloc(h, (void **)ptr, sizeof(float) * count);
+}
+
+// views: e_l (inside cat[l] for l <= L-2), d_l, the conv input of level l
+TV view_e(slpic_unet_t *h, int l)
+{
+    if (l == h->L - 1)
+        return TV{h->etop, ch(h, l), 0};
+    return TV{h->cat[l], ch(h, l + 1) + ch(h, l), ch(h, l + 1)};
+}
+TV view_d(slpic_unet_t *h, int l) { return l == h->L - 1 ? view_e(h, l) : TV{h->d[l], ch(h, l), 0}; }
+TV view_enc_in(slpic_unet_t *h, int l)
+{
+    return l == 0 ? TV{h->xin, 1, 0} : TV{h->pin[l], ch(h, l - 1), 0};
+}
+// gradient at e_l: inside dcat[l] for l <= L-2, else gd[L-1]
+TV view_de(slpic_unet_t *h, int l)
+{
+    if (l == h->L - 1)
+        return TV{h->gd[l], ch(h, l), 0};
+    return TV{h->dcat[l], ch(h, l + 1) + ch(h, l), ch(h, l + 1)};
+}
+
+unsigned grid_for(size_t n)
+{
+    size_t b = (n + kT - 1) / kT;
+    if (b > 152 * 16)
+        b = 152 * 16;
+    return (unsigned)(b ? b : 1);
+}
+
+void conv_fwd(slpic_unet_t *h, int k, TV x, TV a, int relu, int nb, cudaStream_t st)
+{
+    const ConvSpec &c = h->conv[k];
+    const int H = hl(h, c.level), W = wl(h, c.level);
+    dim3 grid((unsigned)((H * W + kT - 1) / kT), (unsigned)((c.cout + kOCB - 1) / kOCB), (unsigned)nb);
+    k_conv_fwd<<<grid, kT, 0, st>>>(x, c.cin, h->pb + c.w_off, h->p + c.b_off, c.cout, a, relu, H, W);
+}
+
+void conv_bwd(slpic_unet_t *h, int k, TV x, TV dz, TV *dx, int nb, cudaStream_t st)
+{
+    const ConvSpec &c = h->conv[k];
+    const int H = hl(h, c.level), W = wl(h, c.level);
+    k_conv_bwd_w<<<dim3((unsigned)c.cin, (unsigned)c.cout), kT, 0, st>>>(
+        x, c.cin, dz, c.cout, h->g + c.w_off, h->g + c.b_off, H, W, nb);
+    if (dx) {
+        dim3 grid((unsigned)((H * W + kT - 1) / kT), (unsigned)((c.cin + kOCB - 1) / kOCB),
+                  (unsigned)nb);
+        k_conv_bwd_x<<<grid, kT, 0, st>>>(dz, c.cout, h->pb + c.w_off, c.cin, *dx, H, W);
+    }
+}
+
+void relu_bwd(slpic_unet_t *h, TV a, TV gv, int C, int level, int nb, cudaStream_t st)
+{
+    const size_t HW = hwl(h, level);
+    k_relu_bwd<<<grid_for((size_t)nb * C * HW), kT, 0, st>>>(a, gv, C, HW, nb);
+}
+
+// The forward pass on the normalised input h->xin: fills every activation and
+// h->ynet (network units).
+void forward_net(slpic_unet_t *h, int nb, cudaStream_t st)
+{
+    const int L = h->L;
+    for (int l = 0; l < L; ++l) {
+        if (l > 0) {
+            const size_t n = (size_t)nb * ch(h, l - 1) * hwl(h, l);
+            k_pool_fwd<<<grid_for(n), kT, 0, st>>>(view_e(h, l - 1), view_enc_in(h, l), ch(h, l - 1),
+                                                   hl(h, l - 1), wl(h, l - 1), nb);
+        }
+        conv_fwd(h, l, view_enc_in(h, l), view_e(h, l), 1, nb, st);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const size_t n = (size_t)nb * ch(h, l + 1) * hwl(h, l);
+        TV up_dst{h->cat[l], ch(h, l + 1) + ch(h, l), 0};
+        k_up_fwd<<<grid_for(n), kT, 0, st>>>(view_d(h, l + 1), up_dst, ch(h, l + 1), hl(h, l + 1),
+                                             wl(h, l + 1), nb);
+        conv_fwd(h, L + (L - 2 - l), TV{h->cat[l], ch(h, l + 1) + ch(h, l), 0}, view_d(h, l), 1, nb,
+                 st);
+    }
+    conv_fwd(h, 2 * L - 1, view_d(h, 0), TV{h->ynet, 1, 0}, 0, nb, st);
+}
+
+// The backward pass from h->dy (network units); parameter gradients into h->g.
+void backward_net(slpic_unet_t *h, int nb, cudaStream_t st)
+{
+    const int L = h->L;
+    TV gd0{h->gd[0], ch(h, 0), 0};
+    conv_bwd(h, 2 * L - 1, view_d(h, 0), TV{h->dy, 1, 0}, &gd0, nb, st);
+    for (int l = 0; l <= L - 2; ++l) {
+        const int k = L + (L - 2 - l);
+        TV gdl{h->gd[l], ch(h, l), 0};
+        relu_bwd(h, view_d(h, l), gdl, ch(h, l), l, nb, st);
+        TV catv{h->cat[l], ch(h, l + 1) + ch(h, l), 0};
+        TV dcatv{h->dcat[l], ch(h, l + 1) + ch(h, l), 0};
+        conv_bwd(h, k, catv, gdl, &dcatv, nb, st);
+        const size_t n = (size_t)nb * ch(h, l + 1) * hwl(h, l + 1);
+        k_up_bwd<<<grid_for(n), kT, 0, st>>>(dcatv, TV{h->gd[l + 1], ch(h, l + 1), 0}, ch(h, l + 1),
+                                             hl(h, l + 1), wl(h, l + 1), nb);
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        TV de = view_de(h, l);
+        relu_bwd(h, view_e(h, l), de, ch(h, l), l, nb, st);
+        if (l > 0) {
+            TV dp{h->dpool[l], ch(h, l - 1), 0};
+            conv_bwd(h, l, view_enc_in(h, l), de, &dp, nb, st);
+            const size_t n = (size_t)nb * ch(h, l - 1) * hwl(h, l - 1);
+            k_pool_bwd_add<<<grid_for(n), kT, 0, st>>>(dp, view_de(h, l - 1), ch(h, l - 1),
+                                                       hl(h, l - 1), wl(h, l - 1), nb);
+        } else {
+            conv_bwd(h, l, view_enc_in(h, l), de, nullptr, nb, st);
+        }
+    }
+}
+
+int ensure_grads(slpic_unet_t *h)
+{
+    if (h->have_grads)
+        return SLPIC_OK;
+    const int L = h->L, nb = h->nbmax;
+    int rc;
+    if ((rc = alloc_f(h, &h->g, h->nparam)) || (rc = alloc_f(h, &h->m, h->nparam)) ||
+        (rc = alloc_f(h, &h->v, h->nparam)) || (rc = alloc_f(h, &h->dy, (size_t)nb * hwl(h, 0))))
+        return rc;
+    if ((rc = alloc(h, (void **)&h->part, sizeof(double) * kMseCtas)) ||
+        (rc = alloc(h, (void **)&h->loss, sizeof(double))))
+        return rc;
+    h->dcat.assign(L, nullptr);
+    h->gd.assign(L, nullptr);
+    h->dpool.assign(L, nullptr);
+    for (int l = 0; l < L; ++l) {
+        if ((rc = alloc_f(h, &h->gd[l], (size_t)nb * ch(h, l) * hwl(h, l))))
+            return rc;
+        if (l <= L - 2 &&
+            (rc = alloc_f(h, &h->dcat[l], (size_t)nb * (ch(h, l + 1) + ch(h, l)) * hwl(h, l))))
+            return rc;
+        if (l >= 1 && (rc = alloc_f(h, &h->dpool[l], (size_t)nb * ch(h, l - 1) * hwl(h, l))))
+            return rc;
+    }
+    CKU(h, cudaMemsetAsync(h->m, 0, sizeof(float) * h->nparam, h->stream));
+    CKU(h, cudaMemsetAsync(h->v, 0, sizeof(float) * h->nparam, h->stream));
+    h->adam_t = 0;
+    h->have_grads = true;
+    return SLPIC_OK;
+}
+
+// SplitMix64 (Steele, Lea & Flood, 2014) and Box-Muller for the initial weights
+uint64_t splitmix64(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+double uniform01(uint64_t &x) { return ((splitmix64(x) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+int check_batch(slpic_unet_t *h, int nb, const void *a, const void *b)
+{
+    if (nb < 1 || nb > h->nbmax)
+        return failu(h, SLPIC_ERR_INVALID, "nb outside 1..max_batch");
+    if (!a || !b)
+        return failu(h, SLPIC_ERR_INVALID, "null array");
+    return SLPIC_OK;
+}
+
+int run_gradients(slpic_unet_t *h, int nb, const float *x, const float *t, cudaStream_t st)
+{
+    int rc = ensure_grads(h);
+    if (rc)
+        return rc;
+    const size_t HW = hwl(h, 0);
+    k_norm_in<<<nb, kT, 0, st>>>(x, h->xin, h->s, HW, h->cfg.normalise);
+    forward_net(h, nb, st);
+    k_mse<<<kMseCtas, kT, 0, st>>>(h->ynet, t, h->s, (float)h->cfg.out_scale, h->dy, HW, nb, h->part);
+    k_loss<<<1, kT, 0, st>>>(h->part, kMseCtas, (double)nb * HW, h->loss);
+    backward_net(h, nb, st);
+    CKU(h, cudaGetLastError());
+    return SLPIC_OK;
+}
+
+}  // namespace
+
+extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **out)
+{
+    if (!cfg || !out)
+        return SLPIC_ERR_INVALID;
+    *out = nullptr;
+    const slpic_unet_config &c = *cfg;
+    if (c.levels < 1 || c.levels > 12 || c.base < 1 || c.max_batch < 1 || c.height < 1 ||
+        c.width < 1 || !(c.out_scale > 0))
+        return SLPIC_ERR_INVALID;
+    const int f = 1 << (c.levels - 1);
+    if (c.height % f || c.width % f || (long long)c.height * c.width > (1LL << 28) ||
+        ((long long)c.base << (c.levels - 1)) > 4096)
+        return SLPIC_ERR_INVALID;
+    slpic_unet_t *h = new slpic_unet_t;
+    h->cfg = c;
+    if (!(h->cfg.adam_beta1 > 0))
+        h->cfg.adam_beta1 = 0.9;
+    if (!(h->cfg.adam_beta2 > 0))
+        h->cfg.adam_beta2 = 0.999;
+    if (!(h->cfg.adam_eps > 0))
+        h->cfg.adam_eps = 1e-8;
+    h->L = c.levels;
+    h->C = c.base;
+    h->H = c.height;
+    h->W = c.width;
+    h->nbmax = c.max_batch;
+    const int L = h->L;
+    // parameter layout: encoder 0..L-1, decoder L-2..0, output
+    auto add = [&](int cin, int cout, int level) {
+        ConvSpec s{cin, cout, level, h->nparam, h->nparam + (size_t)cout * cin * 9};
+        h->nparam = s.b_off + cout;
+        h->conv.push_back(s);
+    };
+    add(1, ch(h, 0), 0);
+    for (int l = 1; l < L; ++l)
+        add(ch(h, l - 1), ch(h, l), l);
+    for (int l = L - 2; l >= 0; --l)
+        add(ch(h, l + 1) + ch(h, l), ch(h, l), l);
+    add(ch(h, 0), 1, 0);
+
+    const int nb = h->nbmax;
+    int rc = SLPIC_OK;
+    h->cat.assign(L, nullptr);
+    h->d.assign(L, nullptr);
+    h->pin.assign(L, nullptr);
+    if (!rc) rc = alloc_f(h, &h->p, h->nparam);
+    if (!rc) rc = alloc(h, (void **)&h->pb, sizeof(__nv_bfloat16) * h->nparam);
+    if (!rc) rc = alloc_f(h, &h->xin, (size_t)nb * hwl(h, 0));
+    if (!rc) rc = alloc_f(h, &h->s, (size_t)nb);
+    if (!rc) rc = alloc_f(h, &h->ynet, (size_t)nb * hwl(h, 0));
+    if (!rc) rc = alloc_f(h, &h->etop, (size_t)nb * ch(h, L - 1) * hwl(h, L - 1));
+    for (int l = 0; l < L && !rc; ++l) {
+        if (l <= L - 2) {
+            rc = alloc_f(h, &h->cat[l], (size_t)nb * (ch(h, l + 1) + ch(h, l)) * hwl(h, l));
+            if (!rc)
+                rc = alloc_f(h, &h->d[l], (size_t)nb * ch(h, l) * hwl(h, l));
+        }
+        if (!rc && l >= 1)
+            rc = alloc_f(h, &h->pin[l], (size_t)nb * ch(h, l - 1) * hwl(h, l));
+    }
+    if (!rc) {
+        // He-normal weights, zero biases
+        std::vector<float> init(h->nparam, 0.0f);
+        uint64_t st = c.seed;
+        for (const ConvSpec &s : h->conv) {
+            const double sd = std::sqrt(2.0 / (9.0 * s.cin));
+            for (size_t q = 0; q < (size_t)s.cout * s.cin * 9; q += 2) {
+                const double u1 = uniform01(st), u2 = uniform01(st);
+                const double r = std::sqrt(-2.0 * std::log(u1));
+                init[s.w_off + q] = (float)(sd * r * std::cos(6.283185307179586 * u2));
+                if (q + 1 < (size_t)s.cout * s.cin * 9)
+                    init[s.w_off + q + 1] = (float)(sd * r * std::sin(6.283185307179586 * u2));
+            }
+        }
+        rc = slpic_unet_set_params(h, init.data());
+    }
+    if (rc) {
+        slpic_unet_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_unet_destroy(slpic_unet_t *h)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    cudaStreamSynchronize(h->stream);
+    for (void *a : h->allocs)
+        cudaFree(a);
+    delete h;
+    return SLPIC_OK;
+}
+
+extern "C" const char *slpic_unet_last_error(slpic_unet_t *h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" int slpic_unet_set_stream(slpic_unet_t *h, void *stream)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    h->stream = (cudaStream_t)stream;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_unet_param_count(slpic_unet_t *h, int64_t *n)
+{
+    if (!h || !n)
+        return SLPIC_ERR_INVALID;
+    *n = (int64_t)h->nparam;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_unet_set_params(slpic_unet_t *h, const float *params)
+{
+    if (!h || !params)
+        return h ? failu(h, SLPIC_ERR_INVALID, "null array") : SLPIC_ERR_INVALID;
+    CKU(h, cudaMemcpyAsync(h->p, params, sizeof(float) * h->nparam, cudaMemcpyHostToDevice, h->stream));
+    k_to_bf16<<<grid_for(h->nparam), kT, 0, h->stream>>>(h->p, h->pb, h->nparam);
+    CKU(h, cudaGetLastError());
+    CKU(h, cudaStreamSynchronize(h->stream));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_unet_get_params(slpic_unet_t *h, float *params)
+{
+    if (!h || !params)
+        return h ? failu(h, SLPIC_ERR_INVALID, "null array") : SLPIC_ERR_INVALID;
+    CKU(h, cudaMemcpyAsync(params, h->p, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
+    CKU(h, cudaStreamSynchronize(h->stream));
+    return SLPIC_OK;
+}
+
+int slpic_unet_forward_on(slpic_unet_t *h, int nb, const float *x, float *y, cudaStream_t st)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    int rc = check_batch(h, nb, x, y);
+    if (rc)
+        return rc;
+    const size_t HW = hwl(h, 0);
+    k_norm_in<<<nb, kT, 0, st>>>(x, h->xin, h->s, HW, h->cfg.normalise);
+    forward_net(h, nb, st);
+    k_scale_out<<<grid_for((size_t)nb * HW), kT, 0, st>>>(h->ynet, y, h->s, (float)h->cfg.out_scale,
+                                                          HW, nb);
+    CKU(h, cudaGetLastError());
+    return SLPIC_OK;
+}
+
+void slpic_unet_shape(const slpic_unet_t *h, int *height, int *width, int *max_batch)
+{
+    *height = h->H;
+    *width = h->W;
+    *max_batch = h->nbmax;
+}
+
+extern "C" int slpic_unet_forward(slpic_unet_t *h, int32_t nb, const float *x, float *y)
+{
+    return h ? slpic_unet_forward_on(h, nb, x, y, h->stream) : SLPIC_ERR_INVALID;
+}
+
+extern "C" int slpic_unet_gradients(slpic_unet_t *h, int32_t nb, const float *x, const float *t,
+                                    double *loss, float *grads)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    int rc = check_batch(h, nb, x, t);
+    if (rc || (rc = run_gradients(h, nb, x, t, h->stream)))
+        return rc;
+    if (grads)
+        CKU(h, cudaMemcpyAsync(grads, h->g, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost,
+                               h->stream));
+    if (loss)
+        CKU(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (grads || loss)
+        CKU(h, cudaStreamSynchronize(h->stream));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_unet_train_step(slpic_unet_t *h, int32_t nb, const float *x, const float *t,
+                                     double lr, double *loss)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    if (!(lr > 0))
+        return failu(h, SLPIC_ERR_INVALID, "lr must be > 0");
+    int rc = check_batch(h, nb, x, t);
+    if (rc || (rc = run_gradients(h, nb, x, t, h->stream)))
+        return rc;
+    ++h->adam_t;
+    const double b1 = h->cfg.adam_beta1, b2 = h->cfg.adam_beta2;
+    const double c1 = 1.0 - std::pow(b1, (double)h->adam_t);
+    const double c2 = 1.0 - std::pow(b2, (double)h->adam_t);
+    k_adam<<<grid_for(h->nparam), kT, 0, h->stream>>>(h->p, h->g, h->m, h->v, h->pb, h->nparam,
+                                                     (float)lr, (float)b1, (float)b2,
+                                                     (float)h->cfg.adam_eps, (float)c1, (float)c2);
+    CKU(h, cudaGetLastError());
+    if (loss) {
+        CKU(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CKU(h, cudaStreamSynchronize(h->stream));
+    }
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_unet_reset_optimizer(slpic_unet_t *h)
+{
+    if (!h)
+        return SLPIC_ERR_INVALID;
+    if (h->have_grads) {
+        CKU(h, cudaMemsetAsync(h->m, 0, sizeof(float) * h->nparam, h->stream));
+        CKU(h, cudaMemsetAsync(h->v, 0, sizeof(float) * h->nparam, h->stream));
+    }
+    h->adam_t = 0;
+    return SLPIC_OK;
+}

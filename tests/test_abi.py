@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1511_08225_gb300 import binding
@@ -164,3 +165,60 @@ def test_every_fp64_function_is_exported(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(binding.EXPORTS_FP64) == names
+
+
+# ------------------------------------------------------------------ U-Net entry points
+def test_every_unet_function_is_exported(lib):
+    from paper_1511_08225_gb300 import binding_unet
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "slpic_unet.h")).read(),
+                 flags=re.S)
+    names = sorted(set(re.findall(r"\b(slpic_unet_[a-z0-9_]+)\s*\(", src)))
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding_unet.EXPORTS_UNET) == names
+    assert binding_unet.load_library().slpic_unet_forward.argtypes is not None
+
+
+def test_unet_config_layout_matches_c(tmp_path):
+    from paper_1511_08225_gb300 import binding_unet
+    cls = binding_unet.slpic_unet_config
+    prog = tmp_path / "layout_unet.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slpic_unet.h"', 'int main(void){',
+             'printf("size %zu\\n", sizeof(slpic_unet_config));']
+    for f, _ in cls._fields_:
+        lines.append(f'printf("{f} %zu\\n", offsetof(slpic_unet_config, {f}));')
+    lines.append("return 0;}")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout_unet"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    for line in subprocess.check_output([str(exe)], text=True).split("\n"):
+        if line.strip():
+            name, val = line.split()
+            want = ctypes.sizeof(cls) if name == "size" else getattr(cls, name).offset
+            assert want == int(val), line
+
+
+@pytest.mark.parametrize("bad", [dict(levels=0), dict(base=0), dict(height=30),
+                                 dict(width=12, levels=4), dict(max_batch=0),
+                                 dict(out_scale=0.0), dict(levels=13)])
+def test_unet_config_errors_need_no_device(lib, bad):
+    from paper_1511_08225_gb300 import binding_unet
+    c = binding_unet.slpic_unet_config()
+    c.levels, c.base, c.height, c.width, c.max_batch, c.out_scale = 3, 4, 32, 32, 1, 1.0
+    for k, v in bad.items():
+        setattr(c, k, v)
+    with pytest.raises(binding.SlpicError) as ei:
+        binding_unet.slpic_unet_create(c)
+    assert ei.value.code == binding.SLPIC_ERR_INVALID
+
+
+def test_unet_parameter_layout_round_trips():
+    from oracle import unet as ounet
+    from paper_1511_08225_gb300 import binding_unet
+    assert binding_unet.layer_shapes(3, 4) == ounet.layer_shapes(3, 4)
+    params = ounet.init_params(3, 4, seed=1)
+    flat = binding_unet.join_params(params)
+    back = binding_unet.split_params(flat, 3, 4)
+    for (w, b), (w2, b2) in zip(params, back):
+        assert np.array_equal(np.float32(w), w2) and np.array_equal(np.float32(b), b2)
