@@ -137,14 +137,21 @@ int slpic2d_solve_poisson(slpic2d_t *h, const double *rho, double *phi, int32_t 
  *   SLPIC2D_WARM_UNET  that line plus net(rho), rho the step's charge density on
  *                      rows 0..ny-1 (row 0 set to 0) as an (H, W) = (ny, nx)
  *                      FP32 image (slpic_unet.h), net's output taken on the
- *                      interior rows 1..ny-1.
- * net: required for SLPIC2D_WARM_UNET (grid (ny, nx), max_batch >= 1), ignored
- * otherwise.  It is borrowed: it must outlive its use, and is run on this
+ *                      interior rows 1..ny-1;
+ *   SLPIC2D_WARM_UNET_DELTA  the previous step's potential plus
+ *                      net(rho - rho_prev), rho_prev the image of the step
+ *                      before, for a network trained on the changes between
+ *                      consecutive steps (the first step after this call or
+ *                      slpic2d_prepare has no rho_prev and takes the previous
+ *                      potential alone).
+ * net: required for the two network modes (grid (ny, nx), max_batch >= 1),
+ * ignored otherwise.  It is borrowed: it must outlive its use, and is run on this
  * handle's stream, so it must not be used on another stream meanwhile.  The
  * network's time counts in the field time of slpic2d_kernel_times. */
 #define SLPIC2D_WARM_PREV 0
 #define SLPIC2D_WARM_ZERO 1
 #define SLPIC2D_WARM_UNET 2
+#define SLPIC2D_WARM_UNET_DELTA 3
 int slpic2d_set_warm_start(slpic2d_t *h, int32_t mode, slpic_unet_t *net);
 
 #ifdef __cplusplus

@@ -32,7 +32,14 @@
  * Initialisation: He-normal weights, N(0, 2 / (9 c_in)), from a SplitMix64
  * stream seeded with `seed` and Box-Muller; zero biases.
  *
- * Training: mean squared error, L = mean over n, pixels of (y_net - t_net)^2;
+ * Training loss, with e = y_net - t_net and count = nb * H * W:
+ *   SLPIC_UNET_LOSS_MSE     L = sum e^2 / count;
+ *   SLPIC_UNET_LOSS_ENERGY  L = sum_n (e_n . A e_n) / count, the energy norm of
+ *       the error under the 2D field solve's 5-point operator A (slpic2d.h) on
+ *       the image read as that solver's grid: row 0 a plate, the other plate
+ *       just past row H-1, both at zero; columns periodic; e zeroed on row 0;
+ *       A e = 4 e - e(x+-1) - e(y+-1).  The conjugate-gradient solve's error
+ *       falls in this norm, so it is the measure of a guess.
  * Adam (Kingma & Ba, 2015) with bias correction on the FP32 master weights.
  *
  * Arrays: x, y, t are DEVICE pointers to nb * H * W FP32 values (sample-major,
@@ -55,12 +62,17 @@ extern "C" {
 
 typedef struct slpic_unet slpic_unet_t;
 
+#define SLPIC_UNET_LOSS_MSE 0
+#define SLPIC_UNET_LOSS_ENERGY 1
+
 typedef struct {
     int32_t levels;        /* L >= 1                                                 */
     int32_t base;          /* C >= 1: channels of level 0                             */
     int32_t height, width; /* H, W >= 1, both divisible by 2^(L-1); H*W <= 2^28       */
     int32_t max_batch;     /* samples per call, >= 1 (activation buffers sized for it)*/
     int32_t normalise;     /* per-sample RMS scaling of input and output (see above)  */
+    int32_t loss;          /* SLPIC_UNET_LOSS_MSE or SLPIC_UNET_LOSS_ENERGY           */
+    int32_t reserved;      /* 0                                                       */
     double out_scale;      /* output factor (> 0)                                     */
     double adam_beta1;     /* 0 -> 0.9                                                */
     double adam_beta2;     /* 0 -> 0.999                                              */

@@ -160,3 +160,21 @@ def mse(y, t):
     """Mean squared error and its gradient."""
     r = y - t
     return float((r * r).mean()), 2.0 * r / r.size
+
+
+def energy(y, t):
+    """Energy-norm loss of the error e = y - t on the 2D solver's grid, for one
+    (H, W) image: rows are y (row 0 a plate, the other plate just past row H-1,
+    both held at zero), columns x (periodic).  e is zeroed on row 0 (the plate's
+    value is not the network's), and
+        L = (e . A e) / (H W),  A e = 4 e - e(x+1) - e(x-1) - e(y+1) - e(y-1)
+    (the 5-point operator of the field solve, zero outside rows 0..H-1); the
+    gradient is 2 A e / (H W), zero on row 0.  Returns (L, dL/dy)."""
+    e = np.array(y - t, dtype=np.float64)
+    e[0] = 0.0
+    ep = np.zeros((e.shape[0] + 1, e.shape[1]))
+    ep[:-1] = e
+    ae = 4 * e - np.roll(e, 1, axis=1) - np.roll(e, -1, axis=1) - ep[1:] - np.roll(ep, 1, axis=0)[:-1]
+    ae[0] = 0.0
+    n = e.size
+    return float((e * ae).sum() / n), 2.0 * ae / n

@@ -21,7 +21,7 @@ EXPORTS2D = (
     "slpic2d_kernel_times", "slpic2d_set_warm_start",
 )
 
-SLPIC2D_WARM_PREV, SLPIC2D_WARM_ZERO, SLPIC2D_WARM_UNET = 0, 1, 2
+SLPIC2D_WARM_PREV, SLPIC2D_WARM_ZERO, SLPIC2D_WARM_UNET, SLPIC2D_WARM_UNET_DELTA = 0, 1, 2, 3
 
 
 class slpic2d_config(ctypes.Structure):

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -732,6 +733,25 @@ __global__ void __launch_bounds__(kThreads) k_rho32(Params2D p, float *__restric
     }
 }
 
+// x = a - b (the change of the charge image since the previous step)
+__global__ void __launch_bounds__(kThreads) k_sub32(const float *__restrict__ a,
+                                                  const float *__restrict__ b,
+                                                  float *__restrict__ x, long long n)
+{
+    for (long long t = (long long)blockIdx.x * kThreads + threadIdx.x; t < n;
+         t += (long long)gridDim.x * kThreads)
+        x[t] = a[t] - b[t];
+}
+
+// phi += y on the interior rows (the previous potential plus the predicted change)
+__global__ void __launch_bounds__(kThreads) k_guess_add(Params2D p, const float *__restrict__ y)
+{
+    const long long first = p.nx, last = (long long)p.ny * p.nx;
+    for (long long t = first + (long long)blockIdx.x * kThreads + threadIdx.x; t < last;
+         t += (long long)gridDim.x * kThreads)
+        p.phi[t] += (double)y[t];
+}
+
 // phi on the interior rows = the straight line between the plate potentials plus
 // y (the network's guess for the zero-plate problem), or the line alone when y is
 // null (the zero guess).
@@ -769,6 +789,8 @@ struct slpic2d_sim {
     int warm_mode = SLPIC2D_WARM_PREV;  // initial guess of each step's CG
     slpic_unet_t *net = nullptr;        // SLPIC2D_WARM_UNET: borrowed network
     float *rho32 = nullptr, *guess32 = nullptr;  // its input and output (ny * nx)
+    float *rho32_prev = nullptr, *drho32 = nullptr;  // SLPIC2D_WARM_UNET_DELTA
+    bool have_prev_rho = false;
     std::vector<void *> allocs;
     std::string err;
 };
@@ -827,6 +849,21 @@ static int warm_start(slpic2d_t *h)
         if (rc)
             return fail2(h, rc, std::string("U-Net forward: ") + slpic_unet_last_error(h->net));
         k_guess<<<grid, kThreads, 0, h->stream>>>(h->p, h->guess32);
+    } else if (h->warm_mode == SLPIC2D_WARM_UNET_DELTA) {
+        // phi (still the previous step's) + net(rho - rho_prev); the first step
+        // after a reset has no rho_prev and starts from the previous phi alone
+        k_rho32<<<grid, kThreads, 0, h->stream>>>(h->p, h->rho32);
+        CK2(h, cudaGetLastError());
+        if (h->have_prev_rho) {
+            const long long n = (long long)h->p.ny * h->p.nx;
+            k_sub32<<<grid, kThreads, 0, h->stream>>>(h->rho32, h->rho32_prev, h->drho32, n);
+            const int rc = slpic_unet_forward_on(h->net, 1, h->drho32, h->guess32, h->stream);
+            if (rc)
+                return fail2(h, rc, std::string("U-Net forward: ") + slpic_unet_last_error(h->net));
+            k_guess_add<<<grid, kThreads, 0, h->stream>>>(h->p, h->guess32);
+        }
+        std::swap(h->rho32, h->rho32_prev);
+        h->have_prev_rho = true;
     }
     CK2(h, cudaGetLastError());
     return SLPIC_OK;
@@ -836,11 +873,13 @@ extern "C" int slpic2d_set_warm_start(slpic2d_t *h, int32_t mode, slpic_unet_t *
 {
     if (!h)
         return SLPIC_ERR_INVALID;
-    if (mode != SLPIC2D_WARM_PREV && mode != SLPIC2D_WARM_ZERO && mode != SLPIC2D_WARM_UNET)
+    if (mode != SLPIC2D_WARM_PREV && mode != SLPIC2D_WARM_ZERO && mode != SLPIC2D_WARM_UNET &&
+        mode != SLPIC2D_WARM_UNET_DELTA)
         return fail2(h, SLPIC_ERR_INVALID, "unknown warm-start mode");
-    if (mode == SLPIC2D_WARM_UNET) {
+    const bool uses_net = mode == SLPIC2D_WARM_UNET || mode == SLPIC2D_WARM_UNET_DELTA;
+    if (uses_net) {
         if (!net)
-            return fail2(h, SLPIC_ERR_INVALID, "SLPIC2D_WARM_UNET needs a network");
+            return fail2(h, SLPIC_ERR_INVALID, "this warm-start mode needs a network");
         int H, W, nb;
         slpic_unet_shape(net, &H, &W, &nb);
         if (H != h->p.ny || W != h->p.nx)
@@ -851,10 +890,15 @@ extern "C" int slpic2d_set_warm_start(slpic2d_t *h, int32_t mode, slpic_unet_t *
             h->allocs.push_back(h->rho32);
             CK2(h, cudaMalloc(&h->guess32, sizeof(float) * n));
             h->allocs.push_back(h->guess32);
+            CK2(h, cudaMalloc(&h->rho32_prev, sizeof(float) * n));
+            h->allocs.push_back(h->rho32_prev);
+            CK2(h, cudaMalloc(&h->drho32, sizeof(float) * n));
+            h->allocs.push_back(h->drho32);
         }
     }
     h->warm_mode = mode;
-    h->net = mode == SLPIC2D_WARM_UNET ? net : nullptr;
+    h->net = uses_net ? net : nullptr;
+    h->have_prev_rho = false;
     return SLPIC_OK;
 }
 
@@ -1090,6 +1134,7 @@ extern "C" int slpic2d_prepare(slpic2d_t *h)
     if (rc)
         return rc;
     h->prepared = true;
+    h->have_prev_rho = false;
     return device_status(h);
 }
 

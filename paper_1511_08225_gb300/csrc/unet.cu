@@ -344,6 +344,58 @@ __global__ void __launch_bounds__(kT) k_mse(const float *__restrict__ ynet,
     }
 }
 
+// energy-norm loss, pass 1: e = y_net - t / (s_n out_scale), zero on row 0
+__global__ void k_energy_err(const float *__restrict__ ynet, const float *__restrict__ t,
+                             const float *__restrict__ s, float out_scale, float *__restrict__ e,
+                             int H, int W, int nb)
+{
+    const size_t HW = (size_t)H * W;
+    for (size_t q = blockIdx.x * (size_t)kT + threadIdx.x; q < (size_t)nb * HW;
+         q += (size_t)gridDim.x * kT) {
+        const size_t pix = q % HW;
+        e[q] = pix < (size_t)W ? 0.0f : ynet[q] - t[q] / (s[q / HW] * out_scale);
+    }
+}
+
+// pass 2: dy = 2 A e / count (zero on row 0), per-CTA FP64 partial sums of e . A e;
+// A e = 4 e - e(x+-1) (periodic) - e(y+-1) (zero outside rows 0..H-1)
+__global__ void __launch_bounds__(kT) k_energy_grad(const float *__restrict__ e,
+                                                  float *__restrict__ dy, int H, int W, int nb,
+                                                  double *__restrict__ part)
+{
+    __shared__ double s_red[kT / 32];
+    const size_t HW = (size_t)H * W, count = (size_t)nb * HW;
+    double acc = 0.0;
+    for (size_t q = blockIdx.x * (size_t)kT + threadIdx.x; q < count; q += (size_t)gridDim.x * kT) {
+        const size_t pix = q % HW;
+        const int i = (int)(pix / W), j = (int)(pix - (size_t)i * W);
+        float g = 0.0f;
+        if (i > 0) {
+            const float *en = e + (q - pix);
+            const float c = en[pix];
+            const float xl = en[(size_t)i * W + (j == 0 ? W - 1 : j - 1)];
+            const float xr = en[(size_t)i * W + (j == W - 1 ? 0 : j + 1)];
+            const float yd = en[pix - W];
+            const float yu = i + 1 < H ? en[pix + W] : 0.0f;
+            const float ae = 4.0f * c - ((xl + xr) + (yd + yu));
+            g = 2.0f * ae / (float)count;
+            acc += (double)c * ae;
+        }
+        dy[q] = g;
+    }
+    for (int off = 16; off; off >>= 1)
+        acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kT / 32; ++k)
+            v += s_red[k];
+        part[blockIdx.x] = v;
+    }
+}
+
 // loss = sum(part[0..np)) / count, in CTA order (one CTA)
 __global__ void k_loss(const double *__restrict__ part, int np, double count, double *loss)
 {
@@ -411,7 +463,7 @@ struct slpic_unet {
     float *etop = nullptr;             // e_{L-1}
     // gradients (allocated on first use)
     bool have_grads = false;
-    float *dy = nullptr;
+    float *dy = nullptr, *eb = nullptr;  // eb: the error image of the energy loss
     std::vector<float *> dcat, gd, dpool;  // dcat: 0..L-2; gd: 0..L-1; dpool: 1..L-1
     double *part = nullptr, *loss = nullptr;
     long long adam_t = 0;
@@ -576,6 +628,8 @@ int ensure_grads(slpic_unet_t *h)
     if ((rc = alloc_f(h, &h->g, h->nparam)) || (rc = alloc_f(h, &h->m, h->nparam)) ||
         (rc = alloc_f(h, &h->v, h->nparam)) || (rc = alloc_f(h, &h->dy, (size_t)nb * hwl(h, 0))))
         return rc;
+    if (h->cfg.loss == SLPIC_UNET_LOSS_ENERGY && (rc = alloc_f(h, &h->eb, (size_t)nb * hwl(h, 0))))
+        return rc;
     if ((rc = alloc(h, (void **)&h->part, sizeof(double) * kMseCtas)) ||
         (rc = alloc(h, (void **)&h->loss, sizeof(double))))
         return rc;
@@ -626,7 +680,14 @@ int run_gradients(slpic_unet_t *h, int nb, const float *x, const float *t, cudaS
     const size_t HW = hwl(h, 0);
     k_norm_in<<<nb, kT, 0, st>>>(x, h->xin, h->s, HW, h->cfg.normalise);
     forward_net(h, nb, st);
-    k_mse<<<kMseCtas, kT, 0, st>>>(h->ynet, t, h->s, (float)h->cfg.out_scale, h->dy, HW, nb, h->part);
+    if (h->cfg.loss == SLPIC_UNET_LOSS_ENERGY) {
+        k_energy_err<<<grid_for((size_t)nb * HW), kT, 0, st>>>(h->ynet, t, h->s, (float)h->cfg.out_scale,
+                                                               h->eb, h->H, h->W, nb);
+        k_energy_grad<<<kMseCtas, kT, 0, st>>>(h->eb, h->dy, h->H, h->W, nb, h->part);
+    } else {
+        k_mse<<<kMseCtas, kT, 0, st>>>(h->ynet, t, h->s, (float)h->cfg.out_scale, h->dy, HW, nb,
+                                       h->part);
+    }
     k_loss<<<1, kT, 0, st>>>(h->part, kMseCtas, (double)nb * HW, h->loss);
     backward_net(h, nb, st);
     CKU(h, cudaGetLastError());
@@ -642,7 +703,8 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
     *out = nullptr;
     const slpic_unet_config &c = *cfg;
     if (c.levels < 1 || c.levels > 12 || c.base < 1 || c.max_batch < 1 || c.height < 1 ||
-        c.width < 1 || !(c.out_scale > 0))
+        c.width < 1 || !(c.out_scale > 0) ||
+        (c.loss != SLPIC_UNET_LOSS_MSE && c.loss != SLPIC_UNET_LOSS_ENERGY))
         return SLPIC_ERR_INVALID;
     const int f = 1 << (c.levels - 1);
     if (c.height % f || c.width % f || (long long)c.height * c.width > (1LL << 28) ||

@@ -45,9 +45,9 @@ def collect_pairs(prob: dict, seeds, pairs_per_seed: int, every: int, skip: int,
                   keep_prev: bool = False):
     """Run the 2D problem from each seed's load, skip `skip` steps, then take a
     (rho, phi) pair every `every` steps.  Returns a dict of numpy arrays:
-    rho, phi (N, ny+1, nx) FP64 and, with keep_prev, phi_prev, the potential of the
-    step before each pair (the previous-step guess)."""
-    rho, phi, prev = [], [], []
+    rho, phi (N, ny+1, nx) FP64 and, with keep_prev, rho_prev and phi_prev, those
+    of the step before each pair (phi_prev is the previous-step guess)."""
+    rho, phi, prev, rprev = [], [], [], []
     for seed in seeds:
         p = dict(prob, seed=int(seed))
         sim = binding2d.Simulation2D(p)
@@ -58,7 +58,9 @@ def collect_pairs(prob: dict, seeds, pairs_per_seed: int, every: int, skip: int,
             if every > 1:
                 sim.step(every - 1)
             if keep_prev:
-                prev.append(sim.fields()[1])
+                r0, f0, _, _ = sim.fields()
+                rprev.append(r0)
+                prev.append(f0)
             sim.step(1)
             r, f, _, _ = sim.fields()
             rho.append(r)
@@ -67,6 +69,7 @@ def collect_pairs(prob: dict, seeds, pairs_per_seed: int, every: int, skip: int,
     out = {"rho": np.stack(rho), "phi": np.stack(phi)}
     if keep_prev:
         out["phi_prev"] = np.stack(prev)
+        out["rho_prev"] = np.stack(rprev)
     return out
 
 
@@ -74,6 +77,15 @@ def images(pairs: dict, phi_lo: float = 0.0, phi_hi: float = 0.0):
     """(x, t): the network's input and target images, (N, ny, nx) FP32."""
     x = np.stack([rho_image(r) for r in pairs["rho"]])
     t = np.stack([phi_image(f, phi_lo, phi_hi) for f in pairs["phi"]])
+    return x, t
+
+
+def delta_images(pairs: dict):
+    """(x, t) for the change between consecutive steps (pairs collected with
+    keep_prev): x = image(rho - rho_prev), t = image(phi - phi_prev) (the plate
+    potentials cancel)."""
+    x = np.stack([rho_image(a - b) for a, b in zip(pairs["rho"], pairs["rho_prev"])])
+    t = np.stack([phi_image(a - b) for a, b in zip(pairs["phi"], pairs["phi_prev"])])
     return x, t
 
 

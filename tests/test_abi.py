@@ -201,7 +201,7 @@ def test_unet_config_layout_matches_c(tmp_path):
 
 @pytest.mark.parametrize("bad", [dict(levels=0), dict(base=0), dict(height=30),
                                  dict(width=12, levels=4), dict(max_batch=0),
-                                 dict(out_scale=0.0), dict(levels=13)])
+                                 dict(out_scale=0.0), dict(levels=13), dict(loss=2)])
 def test_unet_config_errors_need_no_device(lib, bad):
     from paper_1511_08225_gb300 import binding_unet
     c = binding_unet.slpic_unet_config()

@@ -31,7 +31,7 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
 
 
-def _oracle_grads(params, xs, ts, levels):
+def _oracle_grads(params, xs, ts, levels, energy=False):
     """Summed over the samples, for the mean over all samples and pixels."""
     pb = _bf(params)
     count = xs.size
@@ -39,9 +39,15 @@ def _oracle_grads(params, xs, ts, levels):
     loss = 0.0
     for x, t in zip(xs, ts):
         y, cache = ounet.forward(pb, x.astype(np.float64), levels)
-        r = y - t
-        loss += float((r * r).sum())
-        g = ounet.backward(pb, cache, 2.0 * r / count, levels)
+        if energy:
+            lk, dy = ounet.energy(y, t)
+            loss += lk * y.size
+            dy = dy * (y.size / count)
+        else:
+            r = y - t
+            loss += float((r * r).sum())
+            dy = 2.0 * r / count
+        g = ounet.backward(pb, cache, dy, levels)
         grads = g if grads is None else [(a + c, b + d) for (a, b), (c, d) in zip(grads, g)]
     return loss / count, grads
 
@@ -100,6 +106,23 @@ def test_gradients_match_oracle(levels, base, n, nb):
     # the parameters are left alone
     for (w, b), (w2, b2) in zip(params, net.params()):
         assert np.array_equal(w, w2) and np.array_equal(b, b2)
+    net.close()
+
+
+@pytest.mark.parametrize("levels,base,n,nb", [(2, 8, 32, 2), (3, 4, 16, 1)])
+def test_energy_loss_gradients_match_oracle(levels, base, n, nb):
+    params = _params(levels, base, seed=5 + levels)
+    rng = np.random.default_rng(20 + levels)
+    xs, ts = rng.normal(size=(nb, n, n)), rng.normal(size=(nb, n, n))
+    net = binding_unet.UNet(levels, base, n, n, max_batch=nb, normalise=False,
+                            loss=binding_unet.SLPIC_UNET_LOSS_ENERGY)
+    net.set_params(params)
+    loss, grads = net.gradients(_dev(xs), _dev(ts))
+    ref_loss, ref = _oracle_grads(params, xs, ts, levels, energy=True)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    for k, ((dw, db), (rw, rb)) in enumerate(zip(grads, ref)):
+        assert np.abs(dw - rw).max() <= TOL * np.abs(rw).max(), ("W", k)
+        assert np.abs(db - rb).max() <= TOL * max(np.abs(rb).max(), 1e-12), ("b", k)
     net.close()
 
 

@@ -86,3 +86,35 @@ def test_gradients_match_finite_differences(levels, base, n):
         wp[k][1][j] -= 2 * h
         lm = unet.mse(unet.forward(wp, x, levels)[0], t)[0]
         assert abs((lp - lm) / (2 * h) - db[j]) <= 1e-5 * max(abs(db[j]), 1e-3)
+
+
+def test_energy_loss_is_the_sum_over_grid_edges():
+    """Discrete Green identity: e . A e is the sum over all grid edges of the
+    squared difference across the edge, the edges to the plates (held at zero)
+    included, and the periodic edge in x too."""
+    rng = np.random.default_rng(9)
+    y, t = rng.normal(size=(6, 5)), rng.normal(size=(6, 5))
+    loss, _ = unet.energy(y, t)
+    e = y - t
+    e[0] = 0.0
+    full = np.zeros((8, 5))          # plate row, rows 0..5 (row 0 zeroed), plate row
+    full[1:7] = e
+    s = ((full[1:] - full[:-1]) ** 2).sum()          # vertical edges, both plates
+    s += ((e - np.roll(e, -1, axis=1)) ** 2)[1:].sum()   # horizontal, periodic, interior rows
+    # row 0 is a plate: its vertical edge to row 1 counts once, as above
+    assert loss * e.size == pytest.approx(s, rel=1e-12)
+    assert loss > 0
+
+
+def test_energy_gradient_matches_finite_differences():
+    rng = np.random.default_rng(10)
+    y, t = rng.normal(size=(5, 4)), rng.normal(size=(5, 4))
+    _, g = unet.energy(y, t)
+    h = 1e-6
+    for idx in [(0, 1), (1, 0), (4, 3), (2, 2)]:
+        yp, ym = y.copy(), y.copy()
+        yp[idx] += h
+        ym[idx] -= h
+        fd = (unet.energy(yp, t)[0] - unet.energy(ym, t)[0]) / (2 * h)
+        assert fd == pytest.approx(g[idx], abs=1e-8)
+    assert np.all(g[0] == 0.0)
