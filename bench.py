@@ -625,6 +625,149 @@ def run_2d(args):
     return 0
 
 
+def fp32_fma_peak_tflops():
+    """FP32 FMA peak from unit counts: SMs x 128 FP32 lanes x 2 flops x the maximum
+    SM clock (GB300: 152 x 128 x 2 x 2.07 GHz = 80.5 TFLOP/s)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", "0"], capture_output=True, text=True, timeout=20).stdout.split()
+        mhz = float(out[0]) if out else mhz
+    except Exception:
+        pass
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def unet_macs(levels, base, H, W):
+    """Multiply-adds of one forward pass (3x3 convs)."""
+    from paper_1511_08225_gb300 import binding_unet
+    tot = 0
+    for k, (ci, co) in enumerate(binding_unet.layer_shapes(levels, base)):
+        lvl = k if k < levels else (0 if k == 2 * levels - 1 else 2 * levels - 2 - k)
+        tot += 9 * ci * co * (H >> lvl) * (W >> lvl)
+    return tot
+
+
+def run_unet2d(args):
+    """The 2D workload with the learned warm start of the CG: (rho, phi) pairs from a
+    run of one seed, two U-Nets trained on them by the library (phi from rho, and the
+    change of phi from the change of rho), then four identical copies of a run of
+    another seed, timed with the CG started from the previous phi, the zero guess,
+    the network's phi and the previous phi plus the network's change."""
+    import torch
+    from paper_1511_08225_gb300 import binding2d, binding_unet, inputs, warmstart
+    from paper_1511_08225_gb300 import build as pkg_build
+    pkg_build.build()
+    torch.cuda.set_device(0)
+    nx, ny = args.nx, args.ny
+    prob = inputs.plasma2d_problem(nx=nx, ny=ny, ppc=args.ppc2d, v0=0.1, capacity_factor=2.0)
+    t0 = time.perf_counter()
+    pairs = warmstart.collect_pairs(prob, seeds=(inputs.SEED + 1,), pairs_per_seed=args.unet_pairs,
+                                    every=2, skip=10, keep_prev=True)
+    collect_s = time.perf_counter() - t0
+    L, C = 4, args.unet_base
+    nets, train_info = {}, {}
+    for name, (x, t) in (("direct", warmstart.images(pairs)), ("delta", warmstart.delta_images(pairs))):
+        net = binding_unet.UNet(L, C, ny, nx, max_batch=args.unet_batch, normalise=True,
+                                out_scale=warmstart.output_scale(x, t), seed=1)
+        xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        losses = warmstart.fit(net, xd, td, steps=args.unet_train_steps, batch=args.unet_batch,
+                               lr=2e-3, log_every=max(args.unet_train_steps // 4, 1))
+        torch.cuda.synchronize()
+        train_info[name] = {"seconds": time.perf_counter() - t1, "loss_first": losses[0][1],
+                            "loss_last": losses[-1][1]}
+        nets[name] = net
+        del xd, td
+    del pairs
+    # the network's forward pass alone, CUDA events on its stream
+    xin = torch.randn(1, ny, nx, device="cuda")
+    yout = torch.zeros_like(xin)
+    for _ in range(3):
+        nets["direct"].forward(xin, yout)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        nets["direct"].forward(xin, yout)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 10
+    fwd_tflops = 2 * unet_macs(L, C, ny, nx) / (fwd_ms * 1e-3) / 1e12
+    peak = fp32_fma_peak_tflops()
+
+    state = inputs.load_state2d(prob)
+    modes = (("prev", binding2d.SLPIC2D_WARM_PREV, None), ("zero", binding2d.SLPIC2D_WARM_ZERO, None),
+             ("unet", binding2d.SLPIC2D_WARM_UNET, nets["direct"]),
+             ("unet_delta", binding2d.SLPIC2D_WARM_UNET_DELTA, nets["delta"]))
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = {}
+    for name, mode, net in modes:
+        stream = torch.cuda.Stream()
+        sim = binding2d.Simulation2D(prob)
+        binding2d.slpic2d_set_stream(sim.h, stream.cuda_stream)
+        sim.load_state(state)
+        sim.prepare()
+        sim.step(args.warmup)
+        sim.set_warm_start(mode, net)
+        sim.step(1)  # the change mode's first step has no previous charge
+        sim.synchronize()
+        d0 = sim.diagnostics()
+        n0 = sum(binding2d.slpic2d_particle_count(sim.h, s) for s in range(2))
+        torch.cuda.synchronize()
+        clocks.mark(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(args.steps)
+        b.record(stream)
+        b.synchronize()
+        clocks.mark(False)
+        ms = a.elapsed_time(b)
+        d1 = sim.diagnostics()
+        n1 = sum(binding2d.slpic2d_particle_count(sim.h, s) for s in range(2))
+        res[name] = {"ms_per_step": ms / args.steps,
+                     "cg_iterations_per_step": (d1["cg_iterations_total"] - d0["cg_iterations_total"])
+                     / args.steps,
+                     "particle_steps_per_s": 0.5 * (n0 + n1) * args.steps / (ms * 1e-3),
+                     "cg_rel_residual_last": d1["cg_rel_residual"]}
+        sim.close()
+    clocks.stop()
+    for net in nets.values():
+        net.close()
+    best = res["unet_delta"]
+    line = {
+        "metric": METRIC, "value": best["particle_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "impl": "gb300",
+        "config": {"workload": f"2D3V electrostatic SLPIC with a learned CG warm start: {nx}x{ny} "
+                               f"cells, {args.ppc2d} ppc/species (the plasma2d workload); U-Net "
+                               f"{L} levels, {C}..{C << (L - 1)} channels, BF16 weights, FP32 "
+                               f"accumulation, trained on {args.unet_pairs} (rho, phi) pairs of "
+                               f"one seed (every 2nd step after 10), {args.unet_train_steps} Adam "
+                               f"steps of {args.unet_batch}; timed on another seed; value is the "
+                               f"previous-phi-plus-network-change mode",
+                   "l2": "state larger than L2"},
+        "warm_start": res,
+        "cg_iterations_saved_vs_zero": 1 - best["cg_iterations_per_step"] / res["zero"]["cg_iterations_per_step"],
+        "cg_iterations_saved_vs_prev": 1 - best["cg_iterations_per_step"] / res["prev"]["cg_iterations_per_step"],
+        "unet": {"forward_ms": fwd_ms, "forward_tflops": fwd_tflops, "training": train_info,
+                 "pair_collection_s": collect_s},
+        "roofline": {"bound": "alu", "achieved": fwd_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fwd_tflops / peak, "traffic": None, "kernel": "U-Net forward (k_conv_fwd)",
+                     "peak_source": "FP32 FMA from unit counts: SMs x 128 lanes x 2 x max SM clock"},
+        "cpu_baseline": None, "clocks": clocks.summary(),
+        # per step in the change mode: particle, source, rho image, difference, the
+        # network's forward (4L launches), guess, CG
+        "gpu_launches": args.steps * (6 + 4 * L),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_paper_sheath(args):
     """The paper's own benchmark (Sec. IV): the argon sheath filled from its wall
     source, run to steady state (24 us of plasma time) as plain PIC (beta = 1,
@@ -720,15 +863,19 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="sheath1d",
-                    choices=["sheath1d", "plasma2d", "batch", "paper_sheath"],
+                    choices=["sheath1d", "plasma2d", "batch", "paper_sheath", "unet2d"],
                     help="sheath1d (the headline), plasma2d (2D3V + CG), batch (many "
                          "independent sheaths) or paper_sheath (the paper's SLPIC-vs-PIC "
-                         "sheath speedup)")
+                         "sheath speedup) or unet2d (plasma2d with the learned CG warm start)")
     ap.add_argument("--ppc-sheath", type=int, default=500)
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--ppc2d", type=int, default=64)
     ap.add_argument("--batch-m", type=int, default=256)
+    ap.add_argument("--unet-pairs", type=int, default=96)
+    ap.add_argument("--unet-train-steps", type=int, default=1500)
+    ap.add_argument("--unet-batch", type=int, default=4)
+    ap.add_argument("--unet-base", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -740,6 +887,8 @@ def main():
         return run_batch(args)
     if args.workload == "paper_sheath":
         return run_paper_sheath(args)
+    if args.workload == "unet2d":
+        return run_unet2d(args)
     return run_gpu(args)
 
 
