@@ -29,6 +29,7 @@ struct slpic_sim {
     int ctas = 1;        // in-place particle-kernel CTAs per species
     int ctas_c = 1;      // compacting particle-kernel CTAs per species
     int hard_ctas = 1;   // k_hard CTAs
+    int tma_stages = 0;  // k_particles_tma ring stages for in-place steps (0: k_particles)
     int small_ctas = 1;  // CTAs per species for deposit / diag
     long long step = 0;  // host mirror of DevState::step
     bool dirty = true;   // particles loaded since the last deposit/solve
@@ -326,6 +327,7 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     h->ctas_c = std::max(1, sms * occ_c / ns);
     h->small_ctas = std::max(1, sms * 2 / ns);
     h->hard_ctas = sms * 8;
+    CKC(configure_particles_tma(nn, &h->tma_stages));
 
     StepParams &p = h->p;
     p.n_cells = cfg->n_cells;
@@ -585,7 +587,10 @@ static int capture(slpic_t *h, long long first_step, int nsteps, bool timed,
         // record inside a capture only orders streams)
         if (timed)
             cudaEventRecordWithFlags(h->events[4 * k], h->cap_stream, cudaEventRecordExternal);
-        launch_particles(h->p, compact ? h->ctas_c : h->ctas, compact, h->cap_stream);
+        if (!compact && h->tma_stages)
+            launch_particles_tma(h->p, h->num_sms, h->tma_stages, h->cap_stream);
+        else
+            launch_particles(h->p, compact ? h->ctas_c : h->ctas, compact, h->cap_stream);
         if (timed)
             cudaEventRecordWithFlags(h->events[4 * k + 1], h->cap_stream, cudaEventRecordExternal);
         launch_hard(h->p, h->hard_ctas, compact, h->cap_stream);

@@ -300,6 +300,260 @@ __device__ __forceinline__ void particles_inplace(const StepParams &p, int s, in
         atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
 }
 
+// ---------------------------------------------------------------------------------
+// The in-place step with the particle stream staged by TMA bulk copies: one CTA of
+// kTmaThreads per SM; warp kTmaConsumers/32 is the producer, whose lane 0 keeps a
+// ring of kTmaTile-particle tiles (float4 and cell) in flight with
+// cp.async.bulk, each stage guarded by a "full" mbarrier (transaction bytes) and an
+// "empty" one (one arrival per consumer warp).  Consumer warps read a tile from
+// shared memory into registers, free the stage, and then do exactly what
+// particles_inplace does per particle.  Loads thus stay in flight while the warps
+// compute, independent of how many warps the registers and the deposit histogram
+// leave resident.  Each CTA walks every species in turn (the histogram is flushed
+// and cleared between species), taking an equal share of each species' tiles.
+// Every wait is bounded (about a second of clock64) and stops early once any wait
+// in the CTA has failed; the failure is recorded as SLPIC_ERR_TIMEOUT and the warps
+// still pass every barrier, so the kernel always returns.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr)
+{
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// true once the phase of `parity` has completed; false after ~1 s or once another
+// wait of the CTA has failed (*fail set), recording SLPIC_ERR_TIMEOUT
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, volatile int *fail,
+                                          int *error)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity)) {
+        if (*fail)
+            return false;
+        if (clock64() - t0 > 2000000000LL) {
+            *fail = 1;
+            atomicCAS(error, 0, SLPIC_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// named barrier of the consumer warps only
+__device__ __forceinline__ void consumers_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kTmaConsumers) : "memory");
+}
+
+size_t particle_tma_smem_bytes(int nn, int stages)
+{
+    return (size_t)16 * stages + (size_t)stages * kTmaTile * 20 + (size_t)nn * 3 * sizeof(unsigned);
+}
+
+// tiles [t0, t1) of species s for CTA `cta` of `nctas`
+__device__ __forceinline__ void tma_share(long long n, int cta, int nctas, long long &t0, long long &t1)
+{
+    const long long nt = (n + kTmaTile - 1) / kTmaTile;
+    t0 = nt * cta / nctas;
+    t1 = nt * (cta + 1) / nctas;
+}
+
+__global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_constant__ StepParams p,
+                                                                 int stages)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *empty = full + stages;
+    float4 *s_v = reinterpret_cast<float4 *>(smem + 16 * stages);
+    int32_t *s_c = reinterpret_cast<int32_t *>(s_v + (size_t)stages * kTmaTile);
+    unsigned *s_lo = reinterpret_cast<unsigned *>(s_c + (size_t)stages * kTmaTile);
+    unsigned *s_hi = s_lo + p.nn;
+    float *s_E = reinterpret_cast<float *>(s_hi + p.nn);
+    __shared__ unsigned s_abs[2];
+    __shared__ int s_fail;
+
+    const long long step = *(volatile long long *)&p.st->step;
+    const int P = (int)(step & 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < p.nn; j += kTmaThreads) {
+        s_lo[j] = 0u;
+        s_hi[j] = 0u;
+        s_E[j] = p.E[j];
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < stages; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kTmaConsumers / 32);
+        }
+        s_abs[0] = s_abs[1] = 0u;
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    volatile int *fail = &s_fail;
+
+    if (warp == kTmaConsumers / 32) {
+        // ---- producer: lane 0 issues every tile of this CTA, species by species
+        if (lane == 0) {
+            long long k = 0;
+            for (int s = 0; s < p.ns && !*fail; ++s) {
+                const SpeciesDev &sp = p.sp[s];
+                const long long n = (long long)*(volatile unsigned long long *)&p.st->count[s][P];
+                long long t0, t1;
+                tma_share(n, blockIdx.x, gridDim.x, t0, t1);
+                for (long long t = t0; t < t1; ++t, ++k) {
+                    const int st = (int)(k % stages);
+                    const unsigned ph = (unsigned)((k / stages) & 1);
+                    if (k >= stages && !mbar_wait(&empty[st], ph ^ 1u, fail, &p.st->error))
+                        break;
+                    const long long i0 = t * kTmaTile;
+                    const int cnt = (int)min((long long)kTmaTile, n - i0);
+                    const int cb = cnt & ~3;  // cells by bulk copy (16-byte multiple)
+                    mbar_expect_tx(&full[st], (unsigned)(cnt * 16 + cb * 4));
+                    bulk_load(s_v + (size_t)st * kTmaTile, sp.pv[P] + i0, (unsigned)cnt * 16, &full[st]);
+                    if (cb)
+                        bulk_load(s_c + (size_t)st * kTmaTile, sp.cell[P] + i0, (unsigned)cb * 4,
+                                  &full[st]);
+                }
+            }
+            // every copy issued has landed before the CTA may exit
+            for (long long j = (k > stages ? k - stages : 0); j < k; ++j)
+                if (!mbar_wait(&full[j % stages], (unsigned)((j / stages) & 1), fail, &p.st->error))
+                    break;
+        }
+    } else {
+        // ---- consumers
+        long long k = 0;
+        for (int s = 0; s < p.ns; ++s) {
+            const SpeciesDev &sp = p.sp[s];
+            const long long n = (long long)*(volatile unsigned long long *)&p.st->count[s][P];
+            const int32_t *__restrict__ cin = sp.cell[P];
+            int32_t *__restrict__ cout = sp.cell[P ^ 1];
+            float4 *__restrict__ vout = sp.pv[P ^ 1];
+            DepositSplit32 dep{s_lo, s_hi};
+            unsigned nabs0 = 0u, nabs1 = 0u;
+            long long t0, t1;
+            tma_share(n, blockIdx.x, gridDim.x, t0, t1);
+            for (long long t = t0; t < t1; ++t, ++k) {
+                const int st = (int)(k % stages);
+                const unsigned ph = (unsigned)((k / stages) & 1);
+                const bool ok = !*fail && mbar_wait(&full[st], ph, fail, &p.st->error);
+                const long long i0 = t * kTmaTile;
+                const int cnt = (int)min((long long)kTmaTile, n - i0);
+                const int cb = cnt & ~3;
+                int c[kTmaPer];
+                float4 q[kTmaPer];
+                bool act[kTmaPer];
+#pragma unroll
+                for (int m = 0; m < kTmaPer; ++m) {
+                    const int j = m * kTmaConsumers + threadIdx.x;
+                    act[m] = ok && j < cnt;
+                    c[m] = -1;
+                    if (act[m]) {
+                        q[m] = s_v[(size_t)st * kTmaTile + j];
+                        c[m] = j < cb ? s_c[(size_t)st * kTmaTile + j] : __ldcs(cin + i0 + j);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0 && ok)
+                    mbar_arrive(&empty[st]);  // the stage is in registers: free it
+#pragma unroll
+                for (int m = 0; m < kTmaPer; ++m) {
+                    const long long i = i0 + m * kTmaConsumers + threadIdx.x;
+                    bool hard = false;
+                    if (act[m]) {
+                        if (c[m] < 0) {
+                            __stcs(cout + i, -1);  // a hole stays a hole
+                        } else {
+                            float ax = gather_ax(p, sp, s_E, c[m], q[m].x);
+                            float vx;
+                            if (push_vx_easy(sp.kind, q[m].y, q[m].z, q[m].w, ax, p.dt, sp.v0, vx)) {
+                                int wall = 0;
+                                if (move_and_deposit(p, sp, dep, c[m], q[m], vx, wall)) {
+                                    __stcs(cout + i, c[m]);
+                                    __stcs(vout + i, q[m]);
+                                } else {
+                                    __stcs(cout + i, -1);
+                                    if (wall)
+                                        ++nabs1;
+                                    else
+                                        ++nabs0;
+                                }
+                            } else {
+                                hard = true;  // k_hard pushes it and writes its slot
+                            }
+                        }
+                    }
+                    list_hard(hard, i, sp, &p.st->hard_n[s]);
+                }
+            }
+            // species done: absorbed counts, histogram flush and clear
+            const unsigned a0 = __reduce_add_sync(0xffffffffu, nabs0);
+            const unsigned a1 = __reduce_add_sync(0xffffffffu, nabs1);
+            if (lane == 0) {
+                if (a0)
+                    atomicAdd(&s_abs[0], a0);
+                if (a1)
+                    atomicAdd(&s_abs[1], a1);
+            }
+            consumers_sync();
+            unsigned long long *acc = p.acc + ((size_t)(P ^ 1) * p.ns + s) * p.nn;
+            for (int j = threadIdx.x; j < p.nn; j += kTmaConsumers) {
+                const unsigned long long v = ((unsigned long long)s_hi[j] << 32) + s_lo[j];
+                if (v)
+                    atomicAdd(acc + j, v);
+                s_lo[j] = 0u;
+                s_hi[j] = 0u;
+            }
+            if (threadIdx.x < 2) {
+                if (s_abs[threadIdx.x])
+                    atomicAdd(&p.st->absorbed_step[s][threadIdx.x],
+                              (unsigned long long)s_abs[threadIdx.x]);
+                s_abs[threadIdx.x] = 0u;
+            }
+            consumers_sync();
+        }
+    }
+    __syncthreads();
+}
+
 // Copy one instance's parameters into shared memory (batched kernels).
 __device__ __forceinline__ void load_params(StepParams &dst, const StepParams *src)
 {
@@ -1135,6 +1389,32 @@ void launch_particles(const StepParams &p, int ctas_per_species, bool compact, c
         k_particles_compact<<<grid, kPB, particle_kernel_smem_bytes(p.nn), st>>>(p);
     else
         k_particles<<<grid, kPB, particle_inplace_smem_bytes(p.nn), st>>>(p);
+}
+
+cudaError_t configure_particles_tma(int nn, int *stages)
+{
+    *stages = 0;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess)
+        return e;
+    const long long room = (long long)optin - 1024;  // static shared memory and margin
+    int k = 4;
+    while (k >= 2 && (long long)particle_tma_smem_bytes(nn, k) > room)
+        --k;
+    if (k < 2)
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(k_particles_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
+    if (e == cudaSuccess)
+        *stages = k;
+    return e;
+}
+
+void launch_particles_tma(const StepParams &p, int ctas, int stages, cudaStream_t st)
+{
+    k_particles_tma<<<ctas, kTmaThreads, particle_tma_smem_bytes(p.nn, stages), st>>>(p, stages);
 }
 
 void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st)

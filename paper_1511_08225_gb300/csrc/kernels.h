@@ -25,6 +25,17 @@ cudaError_t configure_kernels(int nn);
 cudaError_t particle_ctas_per_sm(int nn, int *inplace, int *compacting);
 
 void launch_particles(const StepParams &p, int ctas_per_species, bool compact, cudaStream_t st);
+// k_particles_tma: the in-place step with the particle stream staged by TMA bulk
+// copies, one CTA of kTmaThreads per SM (kTmaConsumers consumer threads, one
+// producer warp), tiles of kTmaTile particles in a ring of `stages` stages.
+constexpr int kTmaThreads = 1024;
+constexpr int kTmaConsumers = 992;
+constexpr int kTmaPer = 2;                         // particles per consumer thread per tile
+constexpr int kTmaTile = kTmaConsumers * kTmaPer;  // 1,984 particles: 7,936 B of cells
+size_t particle_tma_smem_bytes(int nn, int stages);
+// ring stages that fit beside an nn-node grid (at most 4); 0 if fewer than 2 fit
+cudaError_t configure_particles_tma(int nn, int *stages);
+void launch_particles_tma(const StepParams &p, int ctas, int stages, cudaStream_t st);
 void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st);
 void launch_field(const StepParams &p, int mode, cudaStream_t st);
 void launch_potential(const StepParams &p, cudaStream_t st);
