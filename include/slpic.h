@@ -124,6 +124,8 @@ typedef struct {
     int64_t absorbed[SLPIC_MAX_SPECIES][2]; /* macroparticles absorbed at x=0 / x=L,
                                                cumulative                         */
     int64_t injected[SLPIC_MAX_SPECIES];    /* macroparticles injected, cumulative */
+    int64_t iterative[SLPIC_MAX_SPECIES];   /* pushes that took the iterative path
+                                               (piece walk and Newton), cumulative  */
 } slpic_diag;
 
 typedef struct slpic_sim slpic_t;

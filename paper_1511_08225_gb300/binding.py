@@ -71,7 +71,8 @@ class slpic_diag(ctypes.Structure):
                 ("kinetic", ctypes.c_double * SLPIC_MAX_SPECIES),
                 ("field_energy", ctypes.c_double),
                 ("absorbed", (ctypes.c_int64 * 2) * SLPIC_MAX_SPECIES),
-                ("injected", ctypes.c_int64 * SLPIC_MAX_SPECIES)]
+                ("injected", ctypes.c_int64 * SLPIC_MAX_SPECIES),
+                ("iterative", ctypes.c_int64 * SLPIC_MAX_SPECIES)]
 
 
 class SlpicError(RuntimeError):
@@ -286,7 +287,7 @@ def slpic_diagnostics(h, instance=0) -> dict:
             "sum_wbeta": list(d.sum_wbeta), "kinetic": list(d.kinetic),
             "field_energy": d.field_energy,
             "absorbed": [[d.absorbed[s][0], d.absorbed[s][1]] for s in range(SLPIC_MAX_SPECIES)],
-            "injected": list(d.injected)}
+            "injected": list(d.injected), "iterative": list(d.iterative)}
 
 
 def slpic_save(h) -> bytes:

@@ -838,6 +838,7 @@ extern "C" int slpic_diagnostics(slpic_t *h, int instance, slpic_diag *out)
         out->absorbed[s][0] = st.absorbed_total[s][0];
         out->absorbed[s][1] = st.absorbed_total[s][1];
         out->injected[s] = st.injected_total[s];
+        out->iterative[s] = st.iterative_total[s];
     }
     double fe = 0.0;
     for (int j = 0; j < h->nn; ++j) {

@@ -613,42 +613,62 @@ __device__ __forceinline__ void hard_body(const StepParams &p, int compact, long
     const long long step = *(volatile long long *)&p.st->step;
     const int P = (int)(step & 1);
     const int lane = threadIdx.x & 31;
-    for (int s = 0; s < p.ns; ++s) {
-        const SpeciesDev &sp = p.sp[s];
-        const long long nh = (long long)*(volatile unsigned long long *)&p.st->hard_n[s];
-        DepositU64 dep{p.acc + ((size_t)(P ^ 1) * p.ns + s) * p.nn};
-        for (long long b = gwarp * 32; b < nh; b += nwarps * 32) {
-            const long long t = b + lane;
-            bool live = false;
-            int c = 0, slot = 0;
-            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (t < nh) {
-                slot = sp.hard[t];
-                c = sp.cell[P][slot];
-                q = sp.pv[P][slot];
-                float ax = gather_ax(p, sp, p.E, c, q.x);
-                float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
-                int wall = 0;
-                live = move_and_deposit(p, sp, dep, c, q, vx, wall);
-                if (!live)
-                    atomicAdd(&s_abs[s][wall], 1u);
-            }
-            if (compact) {
-                const unsigned m = __ballot_sync(0xffffffffu, live);
-                unsigned long long o = 0;
-                if (lane == 0 && m)
-                    o = atomicAdd(&p.st->count[s][P ^ 1], (unsigned long long)__popc(m));
-                o = __shfl_sync(0xffffffffu, o, 0);
-                if (live) {
-                    o += __popc(m & ((1u << lane) - 1u));
-                    sp.cell[P ^ 1][o] = c;
-                    sp.pv[P ^ 1][o] = q;
+    // the species' lists as one index space, so that the serial pushes of different
+    // species run side by side rather than one after the other
+    long long pre[kMaxSpecies + 1];  // kept in registers: constant indices only
+    pre[0] = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s)
+        pre[s + 1] = pre[s] + (s < p.ns ? (long long)*(volatile unsigned long long *)&p.st->hard_n[s] : 0);
+    const long long total = pre[kMaxSpecies];
+    for (long long b = gwarp * 32; b < total; b += nwarps * 32) {
+        const long long t = b + lane;
+        bool live = false;
+        int s = -1, c = 0, slot = 0;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < total) {
+            long long base = 0;
+            s = 0;
+#pragma unroll
+            for (int k = 1; k < kMaxSpecies; ++k)
+                if (t >= pre[k]) {
+                    s = k;
+                    base = pre[k];
                 }
-            } else if (t < nh) {
-                sp.cell[P ^ 1][slot] = live ? c : -1;
-                if (live)
-                    sp.pv[P ^ 1][slot] = q;
+            const SpeciesDev &sp = p.sp[s];
+            DepositU64 dep{p.acc + ((size_t)(P ^ 1) * p.ns + s) * p.nn};
+            slot = sp.hard[t - base];
+            c = sp.cell[P][slot];
+            q = sp.pv[P][slot];
+            float ax = gather_ax(p, sp, p.E, c, q.x);
+            float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
+            int wall = 0;
+            live = move_and_deposit(p, sp, dep, c, q, vx, wall);
+            if (!live)
+                atomicAdd(&s_abs[s][wall], 1u);
+        }
+        if (compact) {
+            // survivors appended to their species' output, one atomic per species present
+            for (int s2 = 0; s2 < p.ns; ++s2) {
+                const bool mine = live && s == s2;
+                const unsigned m = __ballot_sync(0xffffffffu, mine);
+                if (!m)
+                    continue;
+                unsigned long long o = 0;
+                if (lane == __ffs(m) - 1)
+                    o = atomicAdd(&p.st->count[s2][P ^ 1], (unsigned long long)__popc(m));
+                o = __shfl_sync(0xffffffffu, o, __ffs(m) - 1);
+                if (mine) {
+                    o += __popc(m & ((1u << lane) - 1u));
+                    p.sp[s2].cell[P ^ 1][o] = c;
+                    p.sp[s2].pv[P ^ 1][o] = q;
+                }
             }
+        } else if (t < total) {
+            const SpeciesDev &sp = p.sp[s];
+            sp.cell[P ^ 1][slot] = live ? c : -1;
+            if (live)
+                sp.pv[P ^ 1][slot] = q;
         }
     }
     __syncthreads();
@@ -1225,6 +1245,7 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
             st->absorbed_step[s][1] = 0ULL;
             st->count[s][P] = 0ULL;
             st->holes[s][P] = 0ULL;
+            st->iterative_total[s] += (long long)st->hard_n[s];
             st->hard_n[s] = 0ULL;
         }
         // the step index is read at the start of every CTA: advance it last

@@ -32,6 +32,7 @@ struct DevState {
     unsigned long long absorbed_step[kMaxSpecies][2];  // absorbed this step, per wall
     long long absorbed_total[kMaxSpecies][2];
     long long injected_total[kMaxSpecies];
+    long long iterative_total[kMaxSpecies];        // pushed by k_hard (walk + Newton), cumulative
     double src_frac[kMaxSpecies];                  // fractional macroparticles carried over
     unsigned long long holes[kMaxSpecies][2];      // absorbed slots (cell < 0) per buffer
     unsigned long long hard_n[kMaxSpecies];        // particles listed for k_hard this step
