@@ -630,6 +630,20 @@ def run_2d(args):
     return 0
 
 
+def bf16_peak_tflops():
+    """Dense BF16 tensor peak for a kernel timed alone: MEASURED_PEAKS.json's burst
+    cuBLAS figure, else the fallback of 1,900 TFLOP/s."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            if d.get("bf16_tflops"):
+                return float(d["bf16_tflops"]), "measured"
+        except (ValueError, OSError):
+            pass
+    return 1900.0, "fallback"
+
+
 def fp32_fma_peak_tflops():
     """FP32 FMA peak from unit counts: SMs x 128 FP32 lanes x 2 flops x the maximum
     SM clock (GB300: 152 x 128 x 2 x 2.07 GHz = 80.5 TFLOP/s)."""
@@ -676,7 +690,8 @@ def run_unet2d(args):
     nets, train_info = {}, {}
     for name, (x, t) in (("direct", warmstart.images(pairs)), ("delta", warmstart.delta_images(pairs))):
         net = binding_unet.UNet(L, C, ny, nx, max_batch=args.unet_batch, normalise=True,
-                                out_scale=warmstart.output_scale(x, t), seed=1)
+                                out_scale=warmstart.output_scale(x, t), seed=1,
+                                tensor_cores=not args.unet_cuda_cores)
         xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -701,7 +716,13 @@ def run_unet2d(args):
     e1.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 10
     fwd_tflops = 2 * unet_macs(L, C, ny, nx) / (fwd_ms * 1e-3) / 1e12
-    peak = fp32_fma_peak_tflops()
+    if args.unet_cuda_cores:
+        peak, peak_src = fp32_fma_peak_tflops(), "FP32 FMA from unit counts: SMs x 128 lanes x 2 x max SM clock"
+        bound, kern = "alu", "U-Net forward (k_conv_fwd, CUDA cores)"
+    else:
+        peak, kind = bf16_peak_tflops()
+        peak_src = f"{kind} dense BF16 (cuBLAS burst)"
+        bound, kern = "tensor", "U-Net forward (k_conv_fwd_tc, tcgen05)"
 
     state = inputs.load_state2d(prob)
     modes = (("prev", binding2d.SLPIC2D_WARM_PREV, None), ("zero", binding2d.SLPIC2D_WARM_ZERO, None),
@@ -751,7 +772,8 @@ def run_unet2d(args):
         "config": {"workload": f"2D3V electrostatic SLPIC with a learned CG warm start: {nx}x{ny} "
                                f"cells, {args.ppc2d} ppc/species (the plasma2d workload); U-Net "
                                f"{L} levels, {C}..{C << (L - 1)} channels, BF16 weights, FP32 "
-                               f"accumulation, trained on {args.unet_pairs} (rho, phi) pairs of "
+                               f"accumulation, convolutions forward on "
+                               f"{'CUDA cores' if args.unet_cuda_cores else 'tensor cores (BF16 operands)'}, trained on {args.unet_pairs} (rho, phi) pairs of "
                                f"one seed (every 2nd step after 10), {args.unet_train_steps} Adam "
                                f"steps of {args.unet_batch}; timed on another seed; value is the "
                                f"previous-phi-plus-network-change mode",
@@ -761,9 +783,9 @@ def run_unet2d(args):
         "cg_iterations_saved_vs_prev": 1 - best["cg_iterations_per_step"] / res["prev"]["cg_iterations_per_step"],
         "unet": {"forward_ms": fwd_ms, "forward_tflops": fwd_tflops, "training": train_info,
                  "pair_collection_s": collect_s},
-        "roofline": {"bound": "alu", "achieved": fwd_tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": fwd_tflops / peak, "traffic": None, "kernel": "U-Net forward (k_conv_fwd)",
-                     "peak_source": "FP32 FMA from unit counts: SMs x 128 lanes x 2 x max SM clock"},
+        "roofline": {"bound": bound, "achieved": fwd_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fwd_tflops / peak, "traffic": None, "kernel": kern,
+                     "peak_source": peak_src},
         "cpu_baseline": None, "clocks": clocks.summary(),
         # per step in the change mode: particle, source, rho image, difference, the
         # network's forward (4L launches), guess, CG
@@ -881,6 +903,8 @@ def main():
     ap.add_argument("--unet-train-steps", type=int, default=1500)
     ap.add_argument("--unet-batch", type=int, default=4)
     ap.add_argument("--unet-base", type=int, default=32)
+    ap.add_argument("--unet-cuda-cores", action="store_true",
+                    help="U-Net forward convolutions on the CUDA cores (FP32 activations)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

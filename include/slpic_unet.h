@@ -25,6 +25,11 @@
  * Precision: activations and gradients FP32; the convolutions multiply by a
  * BF16 copy (round to nearest even) of the FP32 master weights and accumulate in
  * FP32; biases FP32; weight-gradient sums FP64 across threads; loss sums FP64.
+ * With tensor_cores = 1 the forward convolutions (output channels up to 256) run
+ * as implicit GEMMs on the tensor cores (tcgen05, BF16 x BF16, FP32 accumulate in
+ * tensor memory): each conv's input is also rounded to BF16 (nearest even), and
+ * the weight gradient multiplies by that rounded input; the input gradient passes
+ * the rounding through unchanged.
  *
  * Parameters: one flat FP32 array, conv by conv in the order encoder
  * l = 0..L-1, decoder l = L-2..0, output; each conv its weights
@@ -72,7 +77,7 @@ typedef struct {
     int32_t max_batch;     /* samples per call, >= 1 (activation buffers sized for it)*/
     int32_t normalise;     /* per-sample RMS scaling of input and output (see above)  */
     int32_t loss;          /* SLPIC_UNET_LOSS_MSE or SLPIC_UNET_LOSS_ENERGY           */
-    int32_t reserved;      /* 0                                                       */
+    int32_t tensor_cores;  /* 1: convolutions forward on the tensor cores (below)     */
     double out_scale;      /* output factor (> 0)                                     */
     double adam_beta1;     /* 0 -> 0.9                                                */
     double adam_beta2;     /* 0 -> 0.999                                              */

@@ -99,9 +99,13 @@ def up_backward(dy):
 
 
 # ------------------------------------------------------------------ network
-def forward(params, x, levels: int):
+def forward(params, x, levels: int, act_bf16: bool = False):
     """y and the cache the backward pass needs.  x: (H, W), H and W divisible by
-    2^(levels-1)."""
+    2^(levels-1).  With act_bf16 every conv's input is rounded to bfloat16 first
+    (the precision of tensor-core operands); the cache keeps the rounded inputs,
+    so the weight gradients multiply by them, and the input gradients pass the
+    rounding through unchanged."""
+    rnd = (lambda a: bf16(a)) if act_bf16 else (lambda a: a)
     cache = {"in": [], "pre": []}
     k = 0
     h = x[None].astype(np.float64)
@@ -109,6 +113,7 @@ def forward(params, x, levels: int):
     for l in range(levels):
         if l > 0:
             h = pool(h)
+        h = rnd(h)
         cache["in"].append(h)
         z = conv(h, *params[k])
         cache["pre"].append(z)
@@ -117,12 +122,13 @@ def forward(params, x, levels: int):
         k += 1
     d = enc[-1]
     for l in range(levels - 2, -1, -1):
-        cat = np.concatenate([up(d), enc[l]], axis=0)
+        cat = rnd(np.concatenate([up(d), enc[l]], axis=0))
         cache["in"].append(cat)
         z = conv(cat, *params[k])
         cache["pre"].append(z)
         d = np.maximum(z, 0.0)
         k += 1
+    d = rnd(d)
     cache["in"].append(d)
     y = conv(d, *params[k])
     return y[0], cache

@@ -29,7 +29,7 @@ class slpic_unet_config(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("base", ctypes.c_int32),
                 ("height", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("normalise", ctypes.c_int32),
-                ("loss", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("loss", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
                 ("out_scale", ctypes.c_double), ("adam_beta1", ctypes.c_double),
                 ("adam_beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
                 ("seed", ctypes.c_uint64)]
@@ -171,11 +171,12 @@ class UNet:
 
     def __init__(self, levels: int, base: int, height: int, width: int, max_batch: int = 1,
                  normalise: bool = True, out_scale: float = 1.0, seed: int = 0,
-                 loss: int = SLPIC_UNET_LOSS_MSE):
+                 loss: int = SLPIC_UNET_LOSS_MSE, tensor_cores: bool = False):
         c = slpic_unet_config()
         c.levels, c.base, c.height, c.width = levels, base, height, width
         c.max_batch, c.normalise, c.out_scale, c.seed = max_batch, int(normalise), out_scale, seed
         c.loss = loss
+        c.tensor_cores = int(tensor_cores)
         self.cfg = c
         self.levels, self.base = levels, base
         self.h = slpic_unet_create(c)

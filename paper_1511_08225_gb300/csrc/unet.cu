@@ -90,6 +90,218 @@ __global__ void __launch_bounds__(kT) k_conv_fwd(TV x, int cin, const __nv_bfloa
     }
 }
 
+// ---- convolution forward on the tensor cores (tcgen05) -----------------------------
+// Implicit GEMM: D[m][o] = sum_k A[m][k] B[o][k] with m the tile's 128 pixels, o
+// the output channels (N = cout padded to a multiple of 16), k = c*9 + di*3 + dj
+// (K = cin*9 padded to a multiple of 64).  A is the im2col gather of the FP32
+// activations, rounded to BF16 by the threads that build it; B is the BF16 weight
+// copy, packed once per parameter change (k_pack_tc) into the exact shared-memory
+// image of each 64-wide K chunk.  Both operands are K-major without swizzle: core
+// matrices of 8 rows x 16 B, 128 B each, core (row group g, K group j) at g*1024 +
+// j*128 within a chunk.  The accumulator lives in TMEM (128 lanes = pixels, N
+// columns, FP32); one thread issues the MMAs (4 per chunk, K = 16 each) and
+// commits them to the chunk buffer's mbarrier, so the threads build chunk k+1
+// while the tensor cores work on chunk k.  The epilogue reads TMEM (tcgen05.ld,
+// warp w owns lanes 32w..32w+31), adds the bias, applies the ReLU and stores.
+constexpr int kTcM = 128;                 // pixels per CTA tile
+constexpr int kTcKC = 64;                 // K per chunk
+constexpr int kTcChunkA = kTcM * kTcKC * 2;  // bytes of one A chunk (16 KB)
+
+__device__ __forceinline__ uint32_t tc_smem(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (row group) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major
+__device__ __forceinline__ uint32_t tc_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity, int *flag)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+            "selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(tc_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+        if (clock64() - t0 > 2000000000LL) {  // ~1 s: record and give up
+            atomicExch(flag, 1);
+            return false;
+        }
+    }
+}
+
+// packed[conv chunk kc][o/8][j][o%8][k%8] = w[o][64 kc + 8 j + k%8] (0 outside)
+__global__ void k_pack_tc(const __nv_bfloat16 *__restrict__ w, int cout, int K, int Np, int nkc,
+                          __nv_bfloat16 *__restrict__ packed)
+{
+    const size_t total = (size_t)nkc * Np * kTcKC;
+    for (size_t e = blockIdx.x * (size_t)kT + threadIdx.x; e < total; e += (size_t)gridDim.x * kT) {
+        const int kc = (int)(e / ((size_t)Np * kTcKC));
+        const int r = (int)(e - (size_t)kc * Np * kTcKC);
+        const int g = r / (8 * kTcKC);  // row group (8 rows x 64 k)
+        const int rem = r - g * 8 * kTcKC;
+        const int j = rem / 64, rr = (rem / 8) % 8, kk = rem % 8;
+        const int o = g * 8 + rr, k = kc * kTcKC + j * 8 + kk;
+        packed[e] = (o < cout && k < K) ? w[(size_t)o * K + k] : __float2bfloat16_rn(0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(kTcM) k_conv_fwd_tc(TV x, int cin, const __nv_bfloat16 *__restrict__ wp,
+                                                    const float *__restrict__ b, int cout, int Np,
+                                                    TV a, int relu, int H, int W, int *flag)
+{
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const int chunkB = Np * kTcKC * 2;
+
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n = blockIdx.y;
+    const size_t HW = (size_t)H * W;
+    const int pix = blockIdx.x * kTcM + tid;
+    const bool in = pix < (int)HW;
+    const int i = in ? pix / W : 0, j = in ? pix - (pix / W) * W : 0;
+    const int K = cin * 9, nkc = (K + kTcKC - 1) / kTcKC;
+    const uint32_t ncols = Np <= 32 ? 32u : Np <= 64 ? 64u : Np <= 128 ? 128u : 256u;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc_smem(&s_tmem)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&s_bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&s_bar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    // this thread's A row: (row group, row in group) of pixel `tid`
+    const int arow = (tid >> 3) * 1024 + (tid & 7) * 16;
+    int c = 0, t = 0;  // (channel, tap) of the chunk's first k
+    for (int kc = 0; kc < nkc; ++kc) {
+        const int buf = kc & 1;
+        unsigned char *bufA = tsm + buf * kTcChunkA;
+        unsigned char *bufB = tsm + 2 * kTcChunkA + buf * chunkB;
+        if (kc >= 2 && !s_fail) {
+            // the MMAs of chunk kc-2 have read this buffer
+            if (!tc_wait(&s_bar[buf], (unsigned)(((kc - 2) >> 1) & 1), flag))
+                s_fail = 1;
+        }
+        __syncthreads();
+        if (s_fail)
+            break;
+        // A: 8 groups of 8 consecutive k for this pixel, one 16-byte store each
+        const float *xn = at(x, n, 0, HW);
+#pragma unroll 1
+        for (int g = 0; g < kTcKC / 8; ++g) {
+            uint32_t packed[4];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                float v2[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    float v = 0.0f;
+                    if (in && c < cin) {
+                        const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
+                        if (ii >= 0 && ii < H && jj >= 0 && jj < W)
+                            v = xn[(size_t)c * HW + (size_t)ii * W + jj];
+                    }
+                    v2[u] = v;
+                    if (++t == 9) {
+                        t = 0;
+                        ++c;
+                    }
+                }
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v2[0], v2[1]);
+                packed[q >> 1] = *reinterpret_cast<const uint32_t *>(&h2);
+            }
+            *reinterpret_cast<uint4 *>(bufA + arow + g * 128) =
+                make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+        // B: the packed chunk image, 16 bytes per thread and step
+        const uint4 *src = reinterpret_cast<const uint4 *>(wp + (size_t)kc * Np * kTcKC);
+        uint4 *dst = reinterpret_cast<uint4 *>(bufB);
+        for (int e = tid; e < chunkB / 16; e += kTcM)
+            dst[e] = src[e];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = tc_idesc(Np);
+#pragma unroll
+            for (int kk = 0; kk < kTcKC / 16; ++kk) {
+                const uint64_t da = tc_desc(tc_smem(bufA) + kk * 256);
+                const uint64_t db = tc_desc(tc_smem(bufB) + kk * 256);
+                const uint32_t accum = (kc > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_smem(&s_bar[buf]))
+                : "memory");
+        }
+    }
+    // all MMAs done (a commit tracks every earlier MMA of its thread)
+    bool ok = !s_fail;
+    if (ok)
+        ok = tc_wait(&s_bar[(nkc - 1) & 1], (unsigned)(((nkc - 1) >> 1) & 1), flag);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncwarp();
+    if (__all_sync(0xffffffffu, ok)) {
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int o0 = 0; o0 < Np; o0 += 8) {
+            uint32_t v[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7])
+                : "r"(lane_base + (uint32_t)o0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (in) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int o = o0 + q;
+                    if (o < cout) {
+                        const float z = __uint_as_float(v[q]) + b[o];
+                        at(a, n, o, HW)[pix] = relu ? fmaxf(z, 0.0f) : z;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
 // ---- gradient of the convolution's input: dx = conv^T(dz) ------------------------
 // dx[c,i,j] = sum_{o,di,dj} w[o,c,di,dj] dz[o, i-di+1, j-dj+1]
 __global__ void __launch_bounds__(kT) k_conv_bwd_x(TV dz, int cout, const __nv_bfloat16 *__restrict__ w,
@@ -140,7 +352,7 @@ __global__ void __launch_bounds__(kT) k_conv_bwd_x(TV dz, int cout, const __nv_b
 // (written by the c = 0 CTA).  FP32 per thread, FP64 across threads.
 __global__ void __launch_bounds__(kT) k_conv_bwd_w(TV x, int cin, TV dz, int cout,
                                                  float *__restrict__ dw, float *__restrict__ db,
-                                                 int H, int W, int nb)
+                                                 int H, int W, int nb, int xbf16)
 {
     __shared__ double s_red[kT / 32][10];
     const int c = blockIdx.x, o = blockIdx.y;
@@ -161,7 +373,9 @@ __global__ void __launch_bounds__(kT) k_conv_bwd_w(TV x, int cin, TV dz, int cou
 #pragma unroll
                 for (int dj = 0; dj < 3; ++dj) {
                     const int jj = j + dj - 1;
-                    const float v = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? xc[ii * W + jj] : 0.0f;
+                    float v = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? xc[ii * W + jj] : 0.0f;
+                    if (xbf16)  // the forward pass multiplied the BF16-rounded input
+                        v = __bfloat162float(__float2bfloat16_rn(v));
                     acc[di * 3 + dj] = __fmaf_rn(g, v, acc[di * 3 + dj]);
                 }
             }
@@ -448,6 +662,8 @@ __global__ void k_to_bf16(const float *__restrict__ p, __nv_bfloat16 *__restrict
 struct ConvSpec {
     int cin, cout, level;   // level: the grid the conv runs on
     size_t w_off, b_off;    // into the flat parameter array
+    int Np = 0, nkc = 0;    // tensor-core form: padded N, K chunks
+    size_t tc_off = 0;      // its packed weights in wtc
 };
 
 struct slpic_unet {
@@ -467,6 +683,11 @@ struct slpic_unet {
     std::vector<float *> dcat, gd, dpool;  // dcat: 0..L-2; gd: 0..L-1; dpool: 1..L-1
     double *part = nullptr, *loss = nullptr;
     long long adam_t = 0;
+    // tensor-core forward (cfg.tensor_cores): packed BF16 weights, stale after a
+    // parameter change until the next forward repacks them
+    __nv_bfloat16 *wtc = nullptr;
+    bool tc_dirty = true;
+    int *d_flag = nullptr;  // a bounded wait of a tensor-core kernel ran out
     cudaStream_t stream = nullptr;
     std::vector<void *> allocs;
     std::string err;
@@ -489,6 +710,16 @@ int failu(slpic_unet_t *h, int code, const std::string &msg)
 {
     h->err = msg;
     return code;
+}
+
+// after a synchronisation: a bounded wait of a tensor-core kernel that ran out
+int check_flag(slpic_unet_t *h)
+{
+    if (!h->d_flag)
+        return SLPIC_OK;
+    int f = 0;
+    CKU(h, cudaMemcpy(&f, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    return f ? failu(h, SLPIC_ERR_TIMEOUT, "a tensor-core convolution timed out") : SLPIC_OK;
 }
 
 int ch(const slpic_unet_t *h, int l) { return h->C << l; }
@@ -536,10 +767,21 @@ unsigned grid_for(size_t n)
     return (unsigned)(b ? b : 1);
 }
 
+constexpr int kTcMaxN = 256;
+
+size_t tc_smem_bytes(int Np) { return 2 * (size_t)kTcChunkA + 2 * (size_t)Np * kTcKC * 2; }
+
 void conv_fwd(slpic_unet_t *h, int k, TV x, TV a, int relu, int nb, cudaStream_t st)
 {
     const ConvSpec &c = h->conv[k];
     const int H = hl(h, c.level), W = wl(h, c.level);
+    if (h->cfg.tensor_cores && c.Np <= kTcMaxN) {
+        dim3 g((unsigned)((H * W + kTcM - 1) / kTcM), (unsigned)nb);
+        k_conv_fwd_tc<<<g, kTcM, tc_smem_bytes(c.Np), st>>>(x, c.cin, h->wtc + c.tc_off,
+                                                             h->p + c.b_off, c.cout, c.Np, a, relu,
+                                                             H, W, h->d_flag);
+        return;
+    }
     dim3 grid((unsigned)((H * W + kT - 1) / kT), (unsigned)((c.cout + kOCB - 1) / kOCB), (unsigned)nb);
     k_conv_fwd<<<grid, kT, 0, st>>>(x, c.cin, h->pb + c.w_off, h->p + c.b_off, c.cout, a, relu, H, W);
 }
@@ -549,7 +791,8 @@ void conv_bwd(slpic_unet_t *h, int k, TV x, TV dz, TV *dx, int nb, cudaStream_t 
     const ConvSpec &c = h->conv[k];
     const int H = hl(h, c.level), W = wl(h, c.level);
     k_conv_bwd_w<<<dim3((unsigned)c.cin, (unsigned)c.cout), kT, 0, st>>>(
-        x, c.cin, dz, c.cout, h->g + c.w_off, h->g + c.b_off, H, W, nb);
+        x, c.cin, dz, c.cout, h->g + c.w_off, h->g + c.b_off, H, W, nb,
+        (h->cfg.tensor_cores && c.Np <= kTcMaxN) ? 1 : 0);
     if (dx) {
         dim3 grid((unsigned)((H * W + kT - 1) / kT), (unsigned)((c.cin + kOCB - 1) / kOCB),
                   (unsigned)nb);
@@ -568,6 +811,13 @@ void relu_bwd(slpic_unet_t *h, TV a, TV gv, int C, int level, int nb, cudaStream
 void forward_net(slpic_unet_t *h, int nb, cudaStream_t st)
 {
     const int L = h->L;
+    if (h->cfg.tensor_cores && h->tc_dirty) {
+        for (const ConvSpec &c : h->conv)
+            if (c.Np <= kTcMaxN)
+                k_pack_tc<<<grid_for((size_t)c.nkc * c.Np * kTcKC), kT, 0, st>>>(
+                    h->pb + c.w_off, c.cout, c.cin * 9, c.Np, c.nkc, h->wtc + c.tc_off);
+        h->tc_dirty = false;
+    }
     for (int l = 0; l < L; ++l) {
         if (l > 0) {
             const size_t n = (size_t)nb * ch(h, l - 1) * hwl(h, l);
@@ -704,7 +954,8 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
     const slpic_unet_config &c = *cfg;
     if (c.levels < 1 || c.levels > 12 || c.base < 1 || c.max_batch < 1 || c.height < 1 ||
         c.width < 1 || !(c.out_scale > 0) ||
-        (c.loss != SLPIC_UNET_LOSS_MSE && c.loss != SLPIC_UNET_LOSS_ENERGY))
+        (c.loss != SLPIC_UNET_LOSS_MSE && c.loss != SLPIC_UNET_LOSS_ENERGY) ||
+        (c.tensor_cores != 0 && c.tensor_cores != 1))
         return SLPIC_ERR_INVALID;
     const int f = 1 << (c.levels - 1);
     if (c.height % f || c.width % f || (long long)c.height * c.width > (1LL << 28) ||
@@ -736,6 +987,14 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
     for (int l = L - 2; l >= 0; --l)
         add(ch(h, l + 1) + ch(h, l), ch(h, l), l);
     add(ch(h, 0), 1, 0);
+    size_t ntc = 0;  // packed tensor-core weights
+    for (ConvSpec &s : h->conv) {
+        s.Np = (s.cout + 15) / 16 * 16;
+        s.nkc = (s.cin * 9 + kTcKC - 1) / kTcKC;
+        s.tc_off = ntc;
+        if (s.Np <= kTcMaxN)
+            ntc += (size_t)s.nkc * s.Np * kTcKC;
+    }
 
     const int nb = h->nbmax;
     int rc = SLPIC_OK;
@@ -744,6 +1003,19 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
     h->pin.assign(L, nullptr);
     if (!rc) rc = alloc_f(h, &h->p, h->nparam);
     if (!rc) rc = alloc(h, (void **)&h->pb, sizeof(__nv_bfloat16) * h->nparam);
+    if (!rc && c.tensor_cores) {
+        rc = alloc(h, (void **)&h->wtc, sizeof(__nv_bfloat16) * (ntc ? ntc : 1));
+        if (!rc)
+            rc = alloc(h, (void **)&h->d_flag, sizeof(int));
+        if (!rc) {
+            cudaError_t e = cudaMemset(h->d_flag, 0, sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes(kTcMaxN));
+            if (e != cudaSuccess)
+                rc = failu(h, SLPIC_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
     if (!rc) rc = alloc_f(h, &h->xin, (size_t)nb * hwl(h, 0));
     if (!rc) rc = alloc_f(h, &h->s, (size_t)nb);
     if (!rc) rc = alloc_f(h, &h->ynet, (size_t)nb * hwl(h, 0));
@@ -816,6 +1088,7 @@ extern "C" int slpic_unet_set_params(slpic_unet_t *h, const float *params)
         return h ? failu(h, SLPIC_ERR_INVALID, "null array") : SLPIC_ERR_INVALID;
     CKU(h, cudaMemcpyAsync(h->p, params, sizeof(float) * h->nparam, cudaMemcpyHostToDevice, h->stream));
     k_to_bf16<<<grid_for(h->nparam), kT, 0, h->stream>>>(h->p, h->pb, h->nparam);
+    h->tc_dirty = true;
     CKU(h, cudaGetLastError());
     CKU(h, cudaStreamSynchronize(h->stream));
     return SLPIC_OK;
@@ -827,7 +1100,7 @@ extern "C" int slpic_unet_get_params(slpic_unet_t *h, float *params)
         return h ? failu(h, SLPIC_ERR_INVALID, "null array") : SLPIC_ERR_INVALID;
     CKU(h, cudaMemcpyAsync(params, h->p, sizeof(float) * h->nparam, cudaMemcpyDeviceToHost, h->stream));
     CKU(h, cudaStreamSynchronize(h->stream));
-    return SLPIC_OK;
+    return check_flag(h);
 }
 
 int slpic_unet_forward_on(slpic_unet_t *h, int nb, const float *x, float *y, cudaStream_t st)
@@ -871,8 +1144,10 @@ extern "C" int slpic_unet_gradients(slpic_unet_t *h, int32_t nb, const float *x,
                                h->stream));
     if (loss)
         CKU(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    if (grads || loss)
+    if (grads || loss) {
         CKU(h, cudaStreamSynchronize(h->stream));
+        return check_flag(h);
+    }
     return SLPIC_OK;
 }
 
@@ -890,6 +1165,7 @@ extern "C" int slpic_unet_train_step(slpic_unet_t *h, int32_t nb, const float *x
     const double b1 = h->cfg.adam_beta1, b2 = h->cfg.adam_beta2;
     const double c1 = 1.0 - std::pow(b1, (double)h->adam_t);
     const double c2 = 1.0 - std::pow(b2, (double)h->adam_t);
+    h->tc_dirty = true;
     k_adam<<<grid_for(h->nparam), kT, 0, h->stream>>>(h->p, h->g, h->m, h->v, h->pb, h->nparam,
                                                      (float)lr, (float)b1, (float)b2,
                                                      (float)h->cfg.adam_eps, (float)c1, (float)c2);
@@ -897,6 +1173,7 @@ extern "C" int slpic_unet_train_step(slpic_unet_t *h, int32_t nb, const float *x
     if (loss) {
         CKU(h, cudaMemcpyAsync(loss, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CKU(h, cudaStreamSynchronize(h->stream));
+        return check_flag(h);
     }
     return SLPIC_OK;
 }

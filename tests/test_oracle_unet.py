@@ -118,3 +118,25 @@ def test_energy_gradient_matches_finite_differences():
         fd = (unet.energy(yp, t)[0] - unet.energy(ym, t)[0]) / (2 * h)
         assert fd == pytest.approx(g[idx], abs=1e-8)
     assert np.all(g[0] == 0.0)
+
+
+def test_bf16_activation_mode_rounds_every_conv_input():
+    """The tensor-core precision: every conv input the cache keeps is a bfloat16
+    value, the output stays within the rounding's bound of the FP64 forward, and
+    the rounding is really applied (the two differ)."""
+    levels, base, n = 3, 4, 16
+    rng = np.random.default_rng(11)
+    params = [(unet.bf16(w), rng.normal(0, 0.1, b.shape)) for w, b in unet.init_params(levels, base, 5)]
+    x = rng.normal(size=(n, n))
+    y64, _ = unet.forward(params, x, levels)
+    y16, cache = unet.forward(params, x, levels, act_bf16=True)
+    for a in cache["in"]:
+        assert np.array_equal(unet.bf16(a), a)
+    rel = np.abs(y16 - y64).max() / np.abs(y64).max()
+    assert 1e-6 < rel < 3e-2, rel
+    # the backward pass takes the rounded inputs: its weight gradient of the
+    # output conv is the correlation of the rounded d_0 with dy
+    dy = rng.normal(size=(n, n))
+    g = unet.backward(params, cache, dy, levels)
+    dw_ref = np.einsum("hw,chw->c", dy, cache["in"][-1])  # centre tap, no shift
+    assert np.allclose(g[-1][0][0, :, 1, 1], dw_ref, rtol=1e-12, atol=1e-12)
