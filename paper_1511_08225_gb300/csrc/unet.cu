@@ -17,6 +17,7 @@
 // concat buffer and its gradient is read from the second half of the concat
 // gradient: the concatenation costs no copy.  The ReLU mask is taken from the
 // stored activation (a > 0 exactly when z > 0).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kT) k_conv_fwd(TV x, int cin, const __nv_bfloa
 // while the tensor cores work on chunk k.  The epilogue reads TMEM (tcgen05.ld,
 // warp w owns lanes 32w..32w+31), adds the bias, applies the ReLU and stores.
 constexpr int kTcM = 128;                 // pixels per CTA tile
+constexpr int kTcThreads = 256;           // two threads per pixel build the A chunk
 constexpr int kTcKC = 64;                 // K per chunk
 constexpr int kTcChunkA = kTcM * kTcKC * 2;  // bytes of one A chunk (16 KB)
 
@@ -147,10 +149,15 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity, int *fla
     }
 }
 
-// packed[conv chunk kc][o/8][j][o%8][k%8] = w[o][64 kc + 8 j + k%8] (0 outside)
-__global__ void k_pack_tc(const __nv_bfloat16 *__restrict__ w, int cout, int K, int Np, int nkc,
+// The GEMM's K runs over (tap t, channel c) with the channel fastest and each
+// tap's channels padded to cp = cin rounded up to 16: k = t cp + c.  Every 8-k core
+// row then lies within one tap.
+// packed[conv chunk kc][o/8][j][o%8][kk] = w[o][c][t] for k = 64 kc + 8 j + kk
+// (0 for padding)
+__global__ void k_pack_tc(const __nv_bfloat16 *__restrict__ w, int cout, int cin, int Np, int nkc,
                           __nv_bfloat16 *__restrict__ packed)
 {
+    const int cp = (cin + 15) / 16 * 16;
     const size_t total = (size_t)nkc * Np * kTcKC;
     for (size_t e = blockIdx.x * (size_t)kT + threadIdx.x; e < total; e += (size_t)gridDim.x * kT) {
         const int kc = (int)(e / ((size_t)Np * kTcKC));
@@ -159,11 +166,13 @@ __global__ void k_pack_tc(const __nv_bfloat16 *__restrict__ w, int cout, int K, 
         const int rem = r - g * 8 * kTcKC;
         const int j = rem / 64, rr = (rem / 8) % 8, kk = rem % 8;
         const int o = g * 8 + rr, k = kc * kTcKC + j * 8 + kk;
-        packed[e] = (o < cout && k < K) ? w[(size_t)o * K + k] : __float2bfloat16_rn(0.0f);
+        const int t = k / cp, c = k - t * cp;
+        packed[e] = (o < cout && t < 9 && c < cin) ? w[((size_t)o * cin + c) * 9 + t]
+                                                   : __float2bfloat16_rn(0.0f);
     }
 }
 
-__global__ void __launch_bounds__(kTcM) k_conv_fwd_tc(TV x, int cin, const __nv_bfloat16 *__restrict__ wp,
+__global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(TV x, int cin, const __nv_bfloat16 *__restrict__ wp,
                                                     const float *__restrict__ b, int cout, int Np,
                                                     TV a, int relu, int H, int W, int *flag)
 {
@@ -174,12 +183,13 @@ __global__ void __launch_bounds__(kTcM) k_conv_fwd_tc(TV x, int cin, const __nv_
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int m = tid & (kTcM - 1), half = tid >> 7;  // pixel row; which 4 K groups
     const int n = blockIdx.y;
     const size_t HW = (size_t)H * W;
-    const int pix = blockIdx.x * kTcM + tid;
+    const int pix = blockIdx.x * kTcM + m;
     const bool in = pix < (int)HW;
     const int i = in ? pix / W : 0, j = in ? pix - (pix / W) * W : 0;
-    const int K = cin * 9, nkc = (K + kTcKC - 1) / kTcKC;
+    const int cp = (cin + 15) / 16 * 16, nkc = (9 * cp + kTcKC - 1) / kTcKC;
     const uint32_t ncols = Np <= 32 ? 32u : Np <= 64 ? 64u : Np <= 128 ? 128u : 256u;
 
     if (warp == 0) {
@@ -199,9 +209,17 @@ __global__ void __launch_bounds__(kTcM) k_conv_fwd_tc(TV x, int cin, const __nv_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    // this thread's A row: (row group, row in group) of pixel `tid`
-    const int arow = (tid >> 3) * 1024 + (tid & 7) * 16;
-    int c = 0, t = 0;  // (channel, tap) of the chunk's first k
+    // this thread's A row: (row group, row in group) of pixel m
+    const int arow = (m >> 3) * 1024 + (m & 7) * 16;
+    const float *xn = at(x, n, 0, HW) + (in ? pix : 0);
+    // the pixel's 9 taps: offset from the pixel, and whether it lies in the image
+    unsigned tapok = 0u;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
+        if (in && ii >= 0 && ii < H && jj >= 0 && jj < W)
+            tapok |= 1u << t;
+    }
     for (int kc = 0; kc < nkc; ++kc) {
         const int buf = kc & 1;
         unsigned char *bufA = tsm + buf * kTcChunkA;
@@ -214,39 +232,37 @@ __global__ void __launch_bounds__(kTcM) k_conv_fwd_tc(TV x, int cin, const __nv_
         __syncthreads();
         if (s_fail)
             break;
-        // A: 8 groups of 8 consecutive k for this pixel, one 16-byte store each
-        const float *xn = at(x, n, 0, HW);
-#pragma unroll 1
-        for (int g = 0; g < kTcKC / 8; ++g) {
-            uint32_t packed[4];
+        // A: this thread's 4 groups of 8 consecutive k for its pixel (32 loads in
+        // flight), one 16-byte store per group
+        {
+            float v[kTcKC / 2];
 #pragma unroll
-            for (int q = 0; q < 8; q += 2) {
-                float v2[2];
+            for (int g = 0; g < 4; ++g) {
+                const int k0 = kc * kTcKC + (half * 4 + g) * 8;  // 8 k, one tap
+                const int t = k0 / cp, c0 = k0 - t * cp;
+                const bool ok = t < 9 && ((tapok >> t) & 1u);
+                const float *src = xn + ((t / 3 - 1) * W + (t % 3 - 1)) + (size_t)c0 * HW;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    float v = 0.0f;
-                    if (in && c < cin) {
-                        const int ii = i + t / 3 - 1, jj = j + t % 3 - 1;
-                        if (ii >= 0 && ii < H && jj >= 0 && jj < W)
-                            v = xn[(size_t)c * HW + (size_t)ii * W + jj];
-                    }
-                    v2[u] = v;
-                    if (++t == 9) {
-                        t = 0;
-                        ++c;
-                    }
-                }
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(v2[0], v2[1]);
-                packed[q >> 1] = *reinterpret_cast<const uint32_t *>(&h2);
+                for (int e = 0; e < 8; ++e)
+                    v[8 * g + e] = (ok && c0 + e < cin) ? __ldg(src + (size_t)e * HW) : 0.0f;
             }
-            *reinterpret_cast<uint4 *>(bufA + arow + g * 128) =
-                make_uint4(packed[0], packed[1], packed[2], packed[3]);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                uint32_t w4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * g + 2 * q], v[8 * g + 2 * q + 1]);
+                    w4[q] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                *reinterpret_cast<uint4 *>(bufA + arow + (half * 4 + g) * 128) =
+                    make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            }
         }
         // B: the packed chunk image, 16 bytes per thread and step
         const uint4 *src = reinterpret_cast<const uint4 *>(wp + (size_t)kc * Np * kTcKC);
         uint4 *dst = reinterpret_cast<uint4 *>(bufB);
-        for (int e = tid; e < chunkB / 16; e += kTcM)
-            dst[e] = src[e];
+        for (int e = tid; e < chunkB / 16; e += kTcThreads)
+            dst[e] = __ldg(src + e);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -275,8 +291,9 @@ __global__ void __launch_bounds__(kTcM) k_conv_fwd_tc(TV x, int cin, const __nv_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncwarp();
     if (__all_sync(0xffffffffu, ok)) {
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int o0 = 0; o0 < Np; o0 += 8) {
+        // warp w reads TMEM lanes 32 (w mod 4) .. +31; the two warpgroups split the columns
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        for (int o0 = half * (Np / 2); o0 < (half + 1) * (Np / 2); o0 += 8) {
             uint32_t v[8];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -403,87 +420,81 @@ __global__ void __launch_bounds__(kT) k_conv_bwd_w(TV x, int cin, TV dz, int cou
     }
 }
 
-// ---- elementwise layers (grid-stride over n, c, pixel) ----------------------------
-__device__ __forceinline__ void split(size_t t, int C, size_t HW, int &n, int &c, size_t &pix)
+// ---- elementwise layers: blockIdx.y walks the planes (n, c), x the pixels ----------
+// plane q = n*C + c of a view
+__device__ __forceinline__ float *plane(TV v, int q, int C, size_t HW)
 {
-    pix = t % HW;
-    const size_t nc = t / HW;
-    c = (int)(nc % C);
-    n = (int)(nc / C);
+    const int n = q / C, c = q - n * C;
+    return at(v, n, c, HW);
 }
 
 // g = a > 0 ? g : 0, in place (the ReLU's backward pass, mask from its output)
-__global__ void k_relu_bwd(TV a, TV g, int C, size_t HW, int nb)
+__global__ void k_relu_bwd(TV a, TV g, int C, int HW, int nplanes)
 {
-    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW;
-         t += (size_t)gridDim.x * kT) {
-        int n, c;
-        size_t pix;
-        split(t, C, HW, n, c, pix);
-        float *gp = at(g, n, c, HW) + pix;
-        if (!(at(a, n, c, HW)[pix] > 0.0f))
-            *gp = 0.0f;
+    for (int q = blockIdx.y; q < nplanes; q += gridDim.y) {
+        const float *ap = plane(a, q, C, HW);
+        float *gp = plane(g, q, C, HW);
+        for (int p = blockIdx.x * kT + threadIdx.x; p < HW; p += gridDim.x * kT)
+            if (!(ap[p] > 0.0f))
+                gp[p] = 0.0f;
     }
 }
 
 // out (H/2, W/2) = 2x2 mean of in (H, W)
-__global__ void k_pool_fwd(TV in, TV out, int C, int H, int W, int nb)
+__global__ void k_pool_fwd(TV in, TV out, int C, int H, int W, int nplanes)
 {
     const int h = H / 2, w = W / 2;
-    const size_t HW = (size_t)H * W, hw = (size_t)h * w;
-    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * hw;
-         t += (size_t)gridDim.x * kT) {
-        int n, c;
-        size_t pix;
-        split(t, C, hw, n, c, pix);
-        const int i = (int)(pix / w), j = (int)(pix - (size_t)i * w);
-        const float *s = at(in, n, c, HW) + (size_t)(2 * i) * W + 2 * j;
-        at(out, n, c, hw)[pix] = 0.25f * ((s[0] + s[1]) + (s[W] + s[W + 1]));
+    for (int q = blockIdx.y; q < nplanes; q += gridDim.y) {
+        const float *ip = plane(in, q, C, (size_t)H * W);
+        float *op = plane(out, q, C, (size_t)h * w);
+        for (int p = blockIdx.x * kT + threadIdx.x; p < h * w; p += gridDim.x * kT) {
+            const int i = p / w, j = p - i * w;
+            const float *s = ip + (size_t)(2 * i) * W + 2 * j;
+            op[p] = 0.25f * ((s[0] + s[1]) + (s[W] + s[W + 1]));
+        }
     }
 }
 
 // din (H, W) += pool^T(dout): a quarter of the coarse gradient to each of the four
-__global__ void k_pool_bwd_add(TV dout, TV din, int C, int H, int W, int nb)
+__global__ void k_pool_bwd_add(TV dout, TV din, int C, int H, int W, int nplanes)
 {
-    const size_t HW = (size_t)H * W, hw = (size_t)(H / 2) * (W / 2);
-    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW;
-         t += (size_t)gridDim.x * kT) {
-        int n, c;
-        size_t pix;
-        split(t, C, HW, n, c, pix);
-        const int i = (int)(pix / W), j = (int)(pix - (size_t)i * W);
-        at(din, n, c, HW)[pix] += 0.25f * at(dout, n, c, hw)[(size_t)(i / 2) * (W / 2) + j / 2];
+    const int w = W / 2;
+    for (int q = blockIdx.y; q < nplanes; q += gridDim.y) {
+        const float *op = plane(dout, q, C, (size_t)(H / 2) * w);
+        float *ip = plane(din, q, C, (size_t)H * W);
+        for (int p = blockIdx.x * kT + threadIdx.x; p < H * W; p += gridDim.x * kT) {
+            const int i = p / W, j = p - i * W;
+            ip[p] += 0.25f * op[(size_t)(i / 2) * w + j / 2];
+        }
     }
 }
 
 // out (2H, 2W) = nearest-neighbour upsampling of in (H, W)
-__global__ void k_up_fwd(TV in, TV out, int C, int H, int W, int nb)
+__global__ void k_up_fwd(TV in, TV out, int C, int H, int W, int nplanes)
 {
     const int W2 = 2 * W;
-    const size_t HW = (size_t)H * W, HW4 = 4 * HW;
-    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW4;
-         t += (size_t)gridDim.x * kT) {
-        int n, c;
-        size_t pix;
-        split(t, C, HW4, n, c, pix);
-        const int i = (int)(pix / W2), j = (int)(pix - (size_t)i * W2);
-        at(out, n, c, HW4)[pix] = at(in, n, c, HW)[(size_t)(i / 2) * W + j / 2];
+    for (int q = blockIdx.y; q < nplanes; q += gridDim.y) {
+        const float *ip = plane(in, q, C, (size_t)H * W);
+        float *op = plane(out, q, C, (size_t)4 * H * W);
+        for (int p = blockIdx.x * kT + threadIdx.x; p < 4 * H * W; p += gridDim.x * kT) {
+            const int i = p / W2, j = p - i * W2;
+            op[p] = ip[(size_t)(i / 2) * W + j / 2];
+        }
     }
 }
 
 // din (H, W) = up^T(dout): the sum of the four fine gradients
-__global__ void k_up_bwd(TV dout, TV din, int C, int H, int W, int nb)
+__global__ void k_up_bwd(TV dout, TV din, int C, int H, int W, int nplanes)
 {
     const int W2 = 2 * W;
-    const size_t HW = (size_t)H * W, HW4 = 4 * HW;
-    for (size_t t = blockIdx.x * (size_t)kT + threadIdx.x; t < (size_t)nb * C * HW;
-         t += (size_t)gridDim.x * kT) {
-        int n, c;
-        size_t pix;
-        split(t, C, HW, n, c, pix);
-        const int i = (int)(pix / W), j = (int)(pix - (size_t)i * W);
-        const float *s = at(dout, n, c, HW4) + (size_t)(2 * i) * W2 + 2 * j;
-        at(din, n, c, HW)[pix] = (s[0] + s[1]) + (s[W2] + s[W2 + 1]);
+    for (int q = blockIdx.y; q < nplanes; q += gridDim.y) {
+        const float *op = plane(dout, q, C, (size_t)4 * H * W);
+        float *ip = plane(din, q, C, (size_t)H * W);
+        for (int p = blockIdx.x * kT + threadIdx.x; p < H * W; p += gridDim.x * kT) {
+            const int i = p / W, j = p - i * W;
+            const float *s = op + (size_t)(2 * i) * W2 + 2 * j;
+            ip[p] = (s[0] + s[1]) + (s[W2] + s[W2 + 1]);
+        }
     }
 }
 
@@ -777,7 +788,7 @@ void conv_fwd(slpic_unet_t *h, int k, TV x, TV a, int relu, int nb, cudaStream_t
     const int H = hl(h, c.level), W = wl(h, c.level);
     if (h->cfg.tensor_cores && c.Np <= kTcMaxN) {
         dim3 g((unsigned)((H * W + kTcM - 1) / kTcM), (unsigned)nb);
-        k_conv_fwd_tc<<<g, kTcM, tc_smem_bytes(c.Np), st>>>(x, c.cin, h->wtc + c.tc_off,
+        k_conv_fwd_tc<<<g, kTcThreads, tc_smem_bytes(c.Np), st>>>(x, c.cin, h->wtc + c.tc_off,
                                                              h->p + c.b_off, c.cout, c.Np, a, relu,
                                                              H, W, h->d_flag);
         return;
@@ -800,10 +811,17 @@ void conv_bwd(slpic_unet_t *h, int k, TV x, TV dz, TV *dx, int nb, cudaStream_t 
     }
 }
 
+// (pixel blocks, planes) for an elementwise kernel over `pixels` per plane
+dim3 plane_grid(size_t pixels, int nplanes)
+{
+    const size_t bx = std::min<size_t>((pixels + kT - 1) / kT, 1024);
+    return dim3((unsigned)std::max<size_t>(bx, 1), (unsigned)std::min(nplanes, 65535));
+}
+
 void relu_bwd(slpic_unet_t *h, TV a, TV gv, int C, int level, int nb, cudaStream_t st)
 {
     const size_t HW = hwl(h, level);
-    k_relu_bwd<<<grid_for((size_t)nb * C * HW), kT, 0, st>>>(a, gv, C, HW, nb);
+    k_relu_bwd<<<plane_grid(HW, nb * C), kT, 0, st>>>(a, gv, C, (int)HW, nb * C);
 }
 
 // The forward pass on the normalised input h->xin: fills every activation and
@@ -815,22 +833,20 @@ void forward_net(slpic_unet_t *h, int nb, cudaStream_t st)
         for (const ConvSpec &c : h->conv)
             if (c.Np <= kTcMaxN)
                 k_pack_tc<<<grid_for((size_t)c.nkc * c.Np * kTcKC), kT, 0, st>>>(
-                    h->pb + c.w_off, c.cout, c.cin * 9, c.Np, c.nkc, h->wtc + c.tc_off);
+                    h->pb + c.w_off, c.cout, c.cin, c.Np, c.nkc, h->wtc + c.tc_off);
         h->tc_dirty = false;
     }
     for (int l = 0; l < L; ++l) {
-        if (l > 0) {
-            const size_t n = (size_t)nb * ch(h, l - 1) * hwl(h, l);
-            k_pool_fwd<<<grid_for(n), kT, 0, st>>>(view_e(h, l - 1), view_enc_in(h, l), ch(h, l - 1),
-                                                   hl(h, l - 1), wl(h, l - 1), nb);
-        }
+        if (l > 0)
+            k_pool_fwd<<<plane_grid(hwl(h, l), nb * ch(h, l - 1)), kT, 0, st>>>(
+                view_e(h, l - 1), view_enc_in(h, l), ch(h, l - 1), hl(h, l - 1), wl(h, l - 1),
+                nb * ch(h, l - 1));
         conv_fwd(h, l, view_enc_in(h, l), view_e(h, l), 1, nb, st);
     }
     for (int l = L - 2; l >= 0; --l) {
-        const size_t n = (size_t)nb * ch(h, l + 1) * hwl(h, l);
         TV up_dst{h->cat[l], ch(h, l + 1) + ch(h, l), 0};
-        k_up_fwd<<<grid_for(n), kT, 0, st>>>(view_d(h, l + 1), up_dst, ch(h, l + 1), hl(h, l + 1),
-                                             wl(h, l + 1), nb);
+        k_up_fwd<<<plane_grid(hwl(h, l), nb * ch(h, l + 1)), kT, 0, st>>>(
+            view_d(h, l + 1), up_dst, ch(h, l + 1), hl(h, l + 1), wl(h, l + 1), nb * ch(h, l + 1));
         conv_fwd(h, L + (L - 2 - l), TV{h->cat[l], ch(h, l + 1) + ch(h, l), 0}, view_d(h, l), 1, nb,
                  st);
     }
@@ -850,9 +866,9 @@ void backward_net(slpic_unet_t *h, int nb, cudaStream_t st)
         TV catv{h->cat[l], ch(h, l + 1) + ch(h, l), 0};
         TV dcatv{h->dcat[l], ch(h, l + 1) + ch(h, l), 0};
         conv_bwd(h, k, catv, gdl, &dcatv, nb, st);
-        const size_t n = (size_t)nb * ch(h, l + 1) * hwl(h, l + 1);
-        k_up_bwd<<<grid_for(n), kT, 0, st>>>(dcatv, TV{h->gd[l + 1], ch(h, l + 1), 0}, ch(h, l + 1),
-                                             hl(h, l + 1), wl(h, l + 1), nb);
+        k_up_bwd<<<plane_grid(hwl(h, l + 1), nb * ch(h, l + 1)), kT, 0, st>>>(
+            dcatv, TV{h->gd[l + 1], ch(h, l + 1), 0}, ch(h, l + 1), hl(h, l + 1), wl(h, l + 1),
+            nb * ch(h, l + 1));
     }
     for (int l = L - 1; l >= 0; --l) {
         TV de = view_de(h, l);
@@ -860,9 +876,8 @@ void backward_net(slpic_unet_t *h, int nb, cudaStream_t st)
         if (l > 0) {
             TV dp{h->dpool[l], ch(h, l - 1), 0};
             conv_bwd(h, l, view_enc_in(h, l), de, &dp, nb, st);
-            const size_t n = (size_t)nb * ch(h, l - 1) * hwl(h, l - 1);
-            k_pool_bwd_add<<<grid_for(n), kT, 0, st>>>(dp, view_de(h, l - 1), ch(h, l - 1),
-                                                       hl(h, l - 1), wl(h, l - 1), nb);
+            k_pool_bwd_add<<<plane_grid(hwl(h, l - 1), nb * ch(h, l - 1)), kT, 0, st>>>(
+                dp, view_de(h, l - 1), ch(h, l - 1), hl(h, l - 1), wl(h, l - 1), nb * ch(h, l - 1));
         } else {
             conv_bwd(h, l, view_enc_in(h, l), de, nullptr, nb, st);
         }
@@ -990,7 +1005,7 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
     size_t ntc = 0;  // packed tensor-core weights
     for (ConvSpec &s : h->conv) {
         s.Np = (s.cout + 15) / 16 * 16;
-        s.nkc = (s.cin * 9 + kTcKC - 1) / kTcKC;
+        s.nkc = (9 * ((s.cin + 15) / 16 * 16) + kTcKC - 1) / kTcKC;
         s.tc_off = ntc;
         if (s.Np <= kTcMaxN)
             ntc += (size_t)s.nkc * s.Np * kTcKC;
