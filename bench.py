@@ -296,6 +296,9 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     sim.step(args.warmup)
+    tuning = binding.slpic_get_tuning(sim.h)
+    if args.autotune:  # outside the timed region; the trials advance the run
+        tuning, _ = binding.slpic_autotune(sim.h, steps_per_trial=256)
     sim.synchronize()
     n0 = live()
     barrier()
@@ -335,11 +338,13 @@ def run_gpu(args):
     achieved = BYTES_PER_PARTICLE_STEP * n_mean / (push_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": profiled_traffic(n_mean),
-            "kernel": "k_particles_tma (in-place steps; k_particles_compact every 16th)",
+            "kernel": (f"{'k_particles_tma' if tuning['particle_kernel'] == 0 else 'k_particles'} "
+                       f"(in-place steps; k_particles_compact every {tuning['compact_every']})"),
             "kernel_ms": push_ms, "hard_kernel_ms": hard_ms,
             "field_kernel_ms": field_ms, "iterative_pushes_per_step": iterative_per_step,
             "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
-            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+            "peak_source": f"{peak_kind} HBM copy bandwidth", "tuning": tuning,
+            "autotuned": bool(args.autotune)}
 
     # end to end through the C ABI with pinned host buffers: load, steps with
     # a read-back of the fields after every step
@@ -486,6 +491,9 @@ def run_batch(args):
     clocks = ClockSampler(0)
     clocks.start()
     b.step(args.warmup)
+    tuning = binding.slpic_get_tuning(b.h)
+    if args.autotune:  # outside the timed region; the trials advance the run
+        tuning, _ = binding.slpic_autotune(b.h, steps_per_trial=16)
     b.synchronize()
     n0 = live()
     torch.cuda.synchronize()
@@ -522,7 +530,8 @@ def run_batch(args):
                      "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
                      "peak_source": f"{peak_kind} HBM copy bandwidth",
                      "note": "whole-step time (particles, iterative push, field) against "
-                             "the particle kernel's algorithmic bytes: a lower bound"},
+                             "the particle kernel's algorithmic bytes: a lower bound",
+                     "tuning": tuning, "autotuned": bool(args.autotune)},
         "gpu_launches": 3 * args.steps, "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -899,6 +908,9 @@ def main():
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--ppc2d", type=int, default=64)
     ap.add_argument("--batch-m", type=int, default=256)
+    ap.add_argument("--autotune", action="store_true",
+                    help="sheath1d / batch: pick the compaction interval, particle kernel and "
+                         "batch work split with slpic_autotune after the warm-up")
     ap.add_argument("--unet-pairs", type=int, default=96)
     ap.add_argument("--unet-train-steps", type=int, default=1500)
     ap.add_argument("--unet-batch", type=int, default=4)

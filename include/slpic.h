@@ -270,6 +270,42 @@ int slpic_kernel_times(slpic_t *h, double *particle_ms, double *hard_ms, double 
 /* Number of kernels one slpic_step(h, 1) launches. */
 int slpic_kernels_per_step(slpic_t *h, int *n);
 
+/* ---- performance settings and the autotuner ----------------------------------
+ * None of these changes a result.  The source draws its random numbers by (seed,
+ * step, species, particle index), the deposit is an integer sum and the field
+ * follows from it, so the same steps give the same particles (as a set: their
+ * slots may differ), fields and diagnostics whatever the settings.
+ *   compact_every    a compacting particle step (survivors packed, holes
+ *                    dropped) every this many steps, 2..1024 (default 16); holes
+ *                    of absorbed particles occupy slots until then
+ *   particle_kernel  in-place steps: 0 = the TMA-staged kernel when the grid
+ *                    leaves room for its ring (default), 1 = the per-warp kernel;
+ *                    single simulations only
+ *   batch_waves      batches: particle-kernel work items ~ waves x resident CTAs
+ *                    of the GPU, 1..16 (default 2)
+ *   batch_min_share  batches: fewest particles per work item, 256..2^20
+ *                    (default 4096)
+ * slpic_set_tuning takes effect from the next step (the step graphs are captured
+ * again).  slpic_autotune runs a coordinate search over candidate values (intervals
+ * 8/16/32/64; the two kernels; waves 1/2/4/8; shares 1k/4k/16k/64k), each trial a
+ * few steps to capture the graphs and then steps_per_trial steps (rounded up to
+ * whole intervals) timed with CUDA events on the handle's stream, and keeps the
+ * fastest.  The trials are real steps: the simulation advances by all of them.
+ * An interval is tried only if the free capacity exceeds twice the holes and
+ * source particles it may gather, so a trial never truncates the source.
+ * *chosen (may be NULL) receives the settings kept, *ms_per_step (may be NULL)
+ * their time per step.  Synchronises. */
+typedef struct {
+    int32_t compact_every;
+    int32_t particle_kernel;
+    int32_t batch_waves;
+    int32_t batch_min_share;
+} slpic_tuning;
+
+int slpic_get_tuning(slpic_t *h, slpic_tuning *out);
+int slpic_set_tuning(slpic_t *h, const slpic_tuning *t);
+int slpic_autotune(slpic_t *h, int32_t steps_per_trial, slpic_tuning *chosen, double *ms_per_step);
+
 /* ---- a speed limit that changes in time (Sec. II; the Summary) -------------- */
 
 /* Change the speed limit v0 of a speed-limited species from the next step on

@@ -40,7 +40,8 @@ EXPORTS = (
     "slpic_get_particles", "slpic_diagnostics", "slpic_save", "slpic_restore",
     "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernels_per_step",
     "slpic_particle_step_noalloc", "slpic_create_batch", "slpic_set_speed_limit",
-    "slpic_set_timestep", "slpic_set_wave",
+    "slpic_set_timestep", "slpic_set_wave", "slpic_get_tuning", "slpic_set_tuning",
+    "slpic_autotune",
 )
 
 
@@ -75,6 +76,11 @@ class slpic_diag(ctypes.Structure):
                 ("iterative", ctypes.c_int64 * SLPIC_MAX_SPECIES)]
 
 
+class slpic_tuning(ctypes.Structure):
+    _fields_ = [("compact_every", ctypes.c_int32), ("particle_kernel", ctypes.c_int32),
+                ("batch_waves", ctypes.c_int32), ("batch_min_share", ctypes.c_int32)]
+
+
 class SlpicError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where}: SLPIC_ERR_{ERR_NAMES.get(code, code)} ({code}): {msg}")
@@ -102,6 +108,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "slpic_set_speed_limit": (I, [P, I, I, D]),
         "slpic_set_timestep": (I, [P, D]),
         "slpic_set_wave": (I, [P, D, D, D, D]),
+        "slpic_get_tuning": (I, [P, ctypes.POINTER(slpic_tuning)]),
+        "slpic_set_tuning": (I, [P, ctypes.POINTER(slpic_tuning)]),
+        "slpic_autotune": (I, [P, ctypes.c_int32, ctypes.POINTER(slpic_tuning),
+                               ctypes.POINTER(D)]),
         "slpic_destroy": (I, [P]),
         "slpic_last_error": (ctypes.c_char_p, [P]),
         "slpic_create_error": (ctypes.c_char_p, []),
@@ -422,6 +432,33 @@ def slpic_set_timestep(h, dt):
 
 def slpic_set_wave(h, phi0, k, vphi, t_ramp=0.0):
     _check(h, load_library().slpic_set_wave(h, phi0, k, vphi, t_ramp), "slpic_set_wave")
+
+
+def _tuning_dict(t: slpic_tuning) -> dict:
+    return {f: getattr(t, f) for f, _ in slpic_tuning._fields_}
+
+
+def slpic_get_tuning(h) -> dict:
+    t = slpic_tuning()
+    _check(h, load_library().slpic_get_tuning(h, ctypes.byref(t)), "slpic_get_tuning")
+    return _tuning_dict(t)
+
+
+def slpic_set_tuning(h, **settings):
+    """Change some of compact_every, particle_kernel, batch_waves, batch_min_share."""
+    t = slpic_tuning(**slpic_get_tuning(h))
+    for k, v in settings.items():
+        setattr(t, k, int(v))
+    _check(h, load_library().slpic_set_tuning(h, ctypes.byref(t)), "slpic_set_tuning")
+
+
+def slpic_autotune(h, steps_per_trial: int = 64):
+    """(chosen settings, ms per step); the simulation advances by the trials."""
+    t = slpic_tuning()
+    ms = ctypes.c_double()
+    _check(h, load_library().slpic_autotune(h, steps_per_trial, ctypes.byref(t), ctypes.byref(ms)),
+           "slpic_autotune")
+    return _tuning_dict(t), ms.value
 
 
 def slpic_create_batch(cfgs) -> ctypes.c_void_p:

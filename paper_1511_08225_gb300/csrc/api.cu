@@ -5,6 +5,7 @@
 // the time level from device memory, so one graph serves every step.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -30,6 +31,12 @@ struct slpic_sim {
     int ctas_c = 1;      // compacting particle-kernel CTAs per species
     int hard_ctas = 1;   // k_hard CTAs
     int tma_stages = 0;  // k_particles_tma ring stages for in-place steps (0: k_particles)
+    // performance settings (slpic_set_tuning / slpic_autotune); results do not depend
+    // on them
+    int compact_every = kCompactEvery;  // a compacting particle step every this many
+    int particle_kernel = 0;            // in-place steps: 0 TMA-staged if it fits, 1 per-warp
+    int batch_waves = 2;                // batches: work items ~ waves x resident CTAs
+    int batch_min_share = 4096;         // batches: fewest particles per work item
     int small_ctas = 1;  // CTAs per species for deposit / diag
     long long step = 0;  // host mirror of DevState::step
     bool dirty = true;   // particles loaded since the last deposit/solve
@@ -48,7 +55,7 @@ struct slpic_sim {
 
     cudaGraphExec_t g1 = nullptr;   // one in-place step
     cudaGraphExec_t gc = nullptr;   // one compacting step
-    cudaGraphExec_t gK = nullptr;   // one cycle: kCompactEvery - 1 in-place steps, 1 compacting
+    cudaGraphExec_t gK = nullptr;   // one cycle: compact_every - 1 in-place steps, 1 compacting
     cudaGraphExec_t gt = nullptr;   // timed graph: t_len steps (whole cycles) with their own events
     std::vector<cudaEvent_t> events; // 3 per step of the timed graph
     long long t_len = 0;             // steps per timed graph (0 = timing off)
@@ -572,7 +579,7 @@ extern "C" int slpic_prepare(slpic_t *h)
 }
 
 // Capture the timesteps first_step .. first_step + nsteps - 1 into a graph: an
-// in-place particle step, or a compacting one on every kCompactEvery-th step, each
+// in-place particle step, or a compacting one on every compact_every-th step, each
 // followed by k_hard and the field kernel.  With `timed`, event-record nodes (4 per
 // step, from h->events) bracket the three kernels; every replay re-records them, so
 // the events describe the most recent replay.
@@ -582,12 +589,12 @@ static int capture(slpic_t *h, long long first_step, int nsteps, bool timed,
     cudaGraph_t g = nullptr;
     CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < nsteps; ++k) {
-        const bool compact = (first_step + k) % kCompactEvery == kCompactEvery - 1;
+        const bool compact = (first_step + k) % h->compact_every == h->compact_every - 1;
         // "external" records become event-record nodes of the graph (a plain
         // record inside a capture only orders streams)
         if (timed)
             cudaEventRecordWithFlags(h->events[4 * k], h->cap_stream, cudaEventRecordExternal);
-        if (!compact && h->tma_stages)
+        if (!compact && h->tma_stages && h->particle_kernel == 0)
             launch_particles_tma(h->p, h->num_sms, h->tma_stages, h->cap_stream);
         else
             launch_particles(h->p, compact ? h->ctas_c : h->ctas, compact, h->cap_stream);
@@ -624,14 +631,14 @@ extern "C" int slpic_step(slpic_t *h, int64_t nsteps)
         return rc;
     if (nsteps == 0)
         return SLPIC_OK;
-    // graphs: steps whose index is 0 mod kCompactEvery start a cycle
+    // graphs: steps whose index is 0 mod compact_every start a cycle
     if (!h->g1 && (rc = capture(h, 0, 1, false, &h->g1)))
         return rc;
-    if (!h->gc && (rc = capture(h, kCompactEvery - 1, 1, false, &h->gc)))
+    if (!h->gc && (rc = capture(h, h->compact_every - 1, 1, false, &h->gc)))
         return rc;
     int64_t left = nsteps;
     while (left > 0) {
-        const long long phase = h->step % kCompactEvery;
+        const long long phase = h->step % h->compact_every;
         if (phase == 0 && h->t_len > 0 && left >= h->t_len) {
             if (!h->gt && (rc = capture(h, 0, (int)h->t_len, true, &h->gt)))
                 return rc;
@@ -639,14 +646,14 @@ extern "C" int slpic_step(slpic_t *h, int64_t nsteps)
             h->t_launched++;
             h->step += h->t_len;
             left -= h->t_len;
-        } else if (phase == 0 && left >= kCompactEvery) {
-            if (!h->gK && (rc = capture(h, 0, kCompactEvery, false, &h->gK)))
+        } else if (phase == 0 && left >= h->compact_every) {
+            if (!h->gK && (rc = capture(h, 0, h->compact_every, false, &h->gK)))
                 return rc;
             CK(h, cudaGraphLaunch(h->gK, h->stream));
-            h->step += kCompactEvery;
-            left -= kCompactEvery;
+            h->step += h->compact_every;
+            left -= h->compact_every;
         } else {
-            CK(h, cudaGraphLaunch(phase == kCompactEvery - 1 ? h->gc : h->g1, h->stream));
+            CK(h, cudaGraphLaunch(phase == h->compact_every - 1 ? h->gc : h->g1, h->stream));
             h->step += 1;
             left -= 1;
         }
@@ -674,8 +681,9 @@ extern "C" int slpic_synchronize(slpic_t *h)
     if (e) {
         int zero = 0;
         CK(h, cudaMemcpy(&h->d_state->error, &zero, sizeof(int), cudaMemcpyHostToDevice));
-        return fail(h, e, e == SLPIC_ERR_CAPACITY ? "particle store full: injection truncated"
-                                                  : "device error");
+        return fail(h, e, e == SLPIC_ERR_CAPACITY  ? "particle store full: injection truncated"
+                          : e == SLPIC_ERR_TIMEOUT ? "a bounded wait of the particle kernel ran out"
+                                                   : "device error");
     }
     return SLPIC_OK;
 }
@@ -970,7 +978,7 @@ extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
         return rc;
     if (steps_per_graph < 0 || steps_per_graph > 4096)
         return fail(h, SLPIC_ERR_INVALID, "steps_per_graph must be in 0..4096");
-    steps_per_graph = (steps_per_graph + kCompactEvery - 1) / kCompactEvery * kCompactEvery;
+    steps_per_graph = (steps_per_graph + h->compact_every - 1) / h->compact_every * h->compact_every;
     CK(h, cudaStreamSynchronize(h->stream));
     if (h->gt) {
         cudaGraphExecDestroy(h->gt);
@@ -1216,7 +1224,7 @@ static int batch_tables(slpic_t *h)
             total += (long long)st.count[s][P];
         }
     }
-    const int waves = 2;
+    const int waves = h->batch_waves;
     const long long budget = (long long)h->num_sms * std::min(h->ctas, h->ctas_c) * waves;
     std::vector<int4> work;
     size_t k = 0;
@@ -1224,7 +1232,7 @@ static int batch_tables(slpic_t *h)
         for (int s = 0; s < h->members[i]->ns; ++s, ++k) {
             long long c = total > 0 ? (n[k] * budget + total - 1) / total : 1;
             // a share large enough to amortise the per-CTA grid staging
-            const long long per = std::max(1LL, n[k] / 4096);
+            const long long per = std::max(1LL, n[k] / h->batch_min_share);
             c = std::max(1LL, std::min(c, per));
             for (int j = 0; j < (int)c; ++j)
                 work.push_back(make_int4(i, s, j, (int)c));
@@ -1270,7 +1278,7 @@ static int batch_capture(slpic_t *h, long long first_step, int nsteps, cudaGraph
     cudaGraph_t g = nullptr;
     CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < nsteps; ++k) {
-        const bool compact = (first_step + k) % kCompactEvery == kCompactEvery - 1;
+        const bool compact = (first_step + k) % h->compact_every == h->compact_every - 1;
         launch_particles_batch(h->d_params, h->d_work, h->n_work, h->max_nn, compact,
                                h->cap_stream);
         launch_hard_batch(h->d_params, m, h->batch_hard_ctas, compact, h->cap_stream);
@@ -1298,24 +1306,189 @@ static int batch_step(slpic_t *h, int64_t nsteps)
         return SLPIC_OK;
     if (!h->g1 && (rc = batch_capture(h, 0, 1, &h->g1)))
         return rc;
-    if (!h->gc && (rc = batch_capture(h, kCompactEvery - 1, 1, &h->gc)))
+    if (!h->gc && (rc = batch_capture(h, h->compact_every - 1, 1, &h->gc)))
         return rc;
     int64_t left = nsteps;
     while (left > 0) {
-        const long long phase = h->step % kCompactEvery;
+        const long long phase = h->step % h->compact_every;
         int64_t adv = 1;
-        if (phase == 0 && left >= kCompactEvery) {
-            if (!h->gK && (rc = batch_capture(h, 0, kCompactEvery, &h->gK)))
+        if (phase == 0 && left >= h->compact_every) {
+            if (!h->gK && (rc = batch_capture(h, 0, h->compact_every, &h->gK)))
                 return rc;
             CK(h, cudaGraphLaunch(h->gK, h->stream));
-            adv = kCompactEvery;
+            adv = h->compact_every;
         } else {
-            CK(h, cudaGraphLaunch(phase == kCompactEvery - 1 ? h->gc : h->g1, h->stream));
+            CK(h, cudaGraphLaunch(phase == h->compact_every - 1 ? h->gc : h->g1, h->stream));
         }
         h->step += adv;
         for (slpic_t *m : h->members)
             m->step += adv;
         left -= adv;
     }
+    return SLPIC_OK;
+}
+
+// ---- performance settings and the autotuner -----------------------------------------
+// Neither the compaction interval, the particle kernel nor a batch's work split
+// changes a result: the source draws its random numbers by (seed, step, species,
+// particle index), the deposit is an integer sum, and the field solve follows from
+// the deposit, so only the slots the particles occupy differ.
+static int tuning_valid(const slpic_tuning *t)
+{
+    return t && t->compact_every >= 2 && t->compact_every <= 1024 &&
+           (t->particle_kernel == 0 || t->particle_kernel == 1) && t->batch_waves >= 1 &&
+           t->batch_waves <= 16 && t->batch_min_share >= 256 && t->batch_min_share <= (1 << 20);
+}
+
+extern "C" int slpic_get_tuning(slpic_t *h, slpic_tuning *out)
+{
+    if (!h || !out)
+        return SLPIC_ERR_INVALID;
+    out->compact_every = h->compact_every;
+    out->particle_kernel = h->particle_kernel;
+    out->batch_waves = h->batch_waves;
+    out->batch_min_share = h->batch_min_share;
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_set_tuning(slpic_t *h, const slpic_tuning *t)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (!tuning_valid(t))
+        return fail(h, SLPIC_ERR_INVALID, "tuning out of range");
+    CK(h, cudaStreamSynchronize(h->stream));
+    const bool split = is_batch(h) && (t->batch_waves != h->batch_waves ||
+                                       t->batch_min_share != h->batch_min_share);
+    h->compact_every = t->compact_every;
+    h->particle_kernel = t->particle_kernel;
+    h->batch_waves = t->batch_waves;
+    h->batch_min_share = t->batch_min_share;
+    drop_graphs(h);
+    if (split && !h->dirty && (rc = batch_tables(h)))
+        return rc;
+    return SLPIC_OK;
+}
+
+// The smallest (free slots) / (slots one step may add) over instances and species:
+// a step adds the source's particles (twice the mean rate so far, plus a margin),
+// and holes stay until the next compacting step, so an interval of `every` steps
+// is safe while this is well above `every`.
+static int slots_headroom(slpic_t *h, long long *ratio)
+{
+    std::vector<slpic_t *> sims = is_batch(h) ? h->members : std::vector<slpic_t *>{h};
+    long long best = 1LL << 40;
+    for (slpic_t *m : sims) {
+        DevState a;
+        int rc = read_state(m, &a);
+        if (rc)
+            return rc;
+        const int P = (int)(m->step & 1);
+        for (int s = 0; s < m->ns; ++s) {
+            const long long used = (long long)a.count[s][P];
+            const long long cap = m->cfg.species[s].capacity;
+            const long long inj = m->step > 0 ? a.injected_total[s] / std::max(1LL, m->step) : 0;
+            best = std::min(best, (cap - used) / (2 * inj + 64));
+        }
+    }
+    *ratio = best;
+    return SLPIC_OK;
+}
+
+static int time_steps(slpic_t *h, long long n, double *ms_per_step)
+{
+    cudaEvent_t a, b;
+    CK(h, cudaEventCreate(&a));
+    CK(h, cudaEventCreate(&b));
+    cudaEventRecord(a, h->stream);
+    int rc = slpic_step(h, n);
+    cudaEventRecord(b, h->stream);
+    if (rc == SLPIC_OK) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess)
+            rc = fail(h, SLPIC_ERR_CUDA, cudaGetErrorString(e));
+        *ms_per_step = ms / (double)n;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc == SLPIC_OK ? slpic_synchronize(h) : rc;
+}
+
+extern "C" int slpic_autotune(slpic_t *h, int32_t steps_per_trial, slpic_tuning *chosen,
+                              double *ms_per_step)
+{
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (steps_per_trial < 1 || steps_per_trial > 100000)
+        return fail(h, SLPIC_ERR_INVALID, "steps_per_trial must be in 1..100000");
+    if ((rc = slpic_step(h, 0)) || (rc = slpic_synchronize(h)))
+        return rc;
+    // one trial: the settings, steps up to a cycle boundary plus one cycle (the
+    // graphs are captured there), then whole cycles timed with events
+    auto trial = [&](const slpic_tuning &t, double *ms) -> int {
+        int r = slpic_set_tuning(h, &t);
+        if (r)
+            return r;
+        const long long cyc = t.compact_every;
+        if ((r = slpic_step(h, cyc + (cyc - h->step % cyc) % cyc)))
+            return r;
+        return time_steps(h, (steps_per_trial + cyc - 1) / cyc * cyc, ms);
+    };
+    slpic_tuning best{};
+    slpic_get_tuning(h, &best);
+    double best_ms = 0.0;
+    if ((rc = trial(best, &best_ms)))
+        return rc;
+    // coordinate search: each setting in turn over its candidates, the others held
+    // at their best so far
+    enum { kEvery, kKernel, kWaves, kShare };
+    std::vector<int> order = {kEvery};
+    if (is_batch(h)) {
+        order.push_back(kWaves);
+        order.push_back(kShare);
+    } else if (h->tma_stages) {
+        order.push_back(kKernel);
+    }
+    for (int which : order) {
+        const slpic_tuning base = best;
+        std::vector<slpic_tuning> cands;
+        const std::vector<int> vals =
+            which == kEvery ? std::vector<int>{8, 16, 32, 64}
+            : which == kKernel ? std::vector<int>{0, 1}
+            : which == kWaves  ? std::vector<int>{1, 2, 4, 8}
+                               : std::vector<int>{1024, 4096, 16384, 65536};
+        for (int v : vals) {
+            slpic_tuning t = base;
+            (which == kEvery ? t.compact_every : which == kKernel ? t.particle_kernel
+                             : which == kWaves ? t.batch_waves : t.batch_min_share) = v;
+            if (memcmp(&t, &base, sizeof t) == 0)
+                continue;  // measured already
+            if (which == kEvery) {
+                long long ratio = 0;
+                if ((rc = slots_headroom(h, &ratio)))
+                    return rc;
+                if (ratio < 2LL * v)
+                    continue;  // its holes might not fit: never risk a truncated source
+            }
+            double ms = 0.0;
+            if ((rc = trial(t, &ms)))
+                return rc;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+    }
+    if ((rc = slpic_set_tuning(h, &best)))
+        return rc;
+    if (chosen)
+        *chosen = best;
+    if (ms_per_step)
+        *ms_per_step = best_ms;
     return SLPIC_OK;
 }

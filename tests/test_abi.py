@@ -47,9 +47,10 @@ def test_struct_layout_matches_c(tmp_path):
     fields_cfg = [f for f, _ in binding.slpic_config._fields_]
     fields_sp = [f for f, _ in binding.slpic_species._fields_]
     fields_dg = [f for f, _ in binding.slpic_diag._fields_]
+    fields_tu = [f for f, _ in binding.slpic_tuning._fields_]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "slpic.h"', 'int main(void){']
     for st, fl in (("slpic_config", fields_cfg), ("slpic_species", fields_sp),
-                   ("slpic_diag", fields_dg)):
+                   ("slpic_diag", fields_dg), ("slpic_tuning", fields_tu)):
         lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
         for f in fl:
             lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
