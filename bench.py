@@ -545,7 +545,8 @@ def run_2d(args):
     import torch
     from paper_1511_08225_gb300 import binding2d, inputs
     from paper_1511_08225_gb300 import build as pkg_build
-    prob = inputs.plasma2d_problem(nx=args.nx, ny=args.ny, ppc=args.ppc2d, v0=0.1)
+    prob = inputs.plasma2d_problem(nx=args.nx, ny=args.ny, ppc=args.ppc2d, v0=0.1,
+                                   solver=args.solver)
     state = inputs.load_state2d(prob)
     pkg_build.build()
     torch.cuda.set_device(0)
@@ -619,8 +620,11 @@ def run_2d(args):
         "config": {"workload": f"2D3V electrostatic SLPIC: {args.nx}x{args.ny} cells, dx=1 "
                                f"lambda_De, {args.ppc2d} ppc/species, periodic x, absorbing "
                                f"phi=0 plates in y, m_i/m_e=1836, Heaviside beta v0=0.1 v_te, "
-                               f"dt=dx/v0, central LOSS_MATCHED source band; Jacobi-PCG to "
-                               f"1e-8 relative residual, warm-started",
+                               f"dt=dx/v0, central LOSS_MATCHED source band; "
+                               + ("Jacobi-PCG to 1e-8 relative residual, warm-started"
+                                  if args.solver == "cg" else
+                                  "direct FP64 solve: FFT along x, Thomas per mode along y"),
+                   "solver": args.solver,
                    "l2": "state larger than L2"},
         "particles_at_load": int(n_load), "particles_timed_mean": n_mean,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -907,6 +911,8 @@ def main():
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--ppc2d", type=int, default=64)
+    ap.add_argument("--solver", default="cg", choices=["cg", "fft"],
+                    help="plasma2d: the 2D field solver")
     ap.add_argument("--batch-m", type=int, default=256)
     ap.add_argument("--autotune", action="store_true",
                     help="sheath1d / batch: pick the compaction interval, particle kernel and "

@@ -57,7 +57,25 @@ typedef struct {
     double src_rate;         /* RATE: physical pairs per unit time                    */
     double cg_rtol;          /* relative residual target of each solve (e.g. 1e-8)    */
     slpic_species species[SLPIC_MAX_SPECIES];
+    int32_t solver;          /* SLPIC2D_SOLVER_CG (default) or SLPIC2D_SOLVER_FFT      */
+    int32_t reserved;        /* 0                                                     */
 } slpic2d_config;
+
+/* Field solvers.  Both solve the same 5-point system exactly as stated above.
+ *   SLPIC2D_SOLVER_CG   Jacobi-preconditioned CG to ||b - A phi|| <= cg_rtol ||b||
+ *                       (FP32 iterates, FP64 reliable updates), warm-started
+ *                       (slpic2d_set_warm_start).
+ *   SLPIC2D_SOLVER_FFT  direct: the system is separable (periodic x, Dirichlet y),
+ *                       so a discrete Fourier transform along x (radix-2, FP64;
+ *                       nx a power of two, 2..8192) turns it into one tridiagonal
+ *                       system along y per mode, (4 - 2 cos(2 pi k/nx)) u_j -
+ *                       u_{j-1} - u_{j+1} = b^_j, solved by the Thomas algorithm
+ *                       (its multipliers depend on the grid only and are tabulated
+ *                       at creation), then transformed back.  No iterations; the
+ *                       true relative residual (~1e-15) is still formed, reported
+ *                       and held to cg_rtol. */
+#define SLPIC2D_SOLVER_CG 0
+#define SLPIC2D_SOLVER_FFT 1
 
 typedef struct {
     int64_t step;

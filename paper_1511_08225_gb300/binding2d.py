@@ -33,7 +33,11 @@ class slpic2d_config(ctypes.Structure):
                 ("src_ref_species", ctypes.c_int32), ("cg_maxit", ctypes.c_int32),
                 ("src_lo_cells", ctypes.c_double), ("src_len_cells", ctypes.c_double),
                 ("src_rate", ctypes.c_double), ("cg_rtol", ctypes.c_double),
-                ("species", slpic_species * SLPIC_MAX_SPECIES)]
+                ("species", slpic_species * SLPIC_MAX_SPECIES),
+                ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+SLPIC2D_SOLVER_CG, SLPIC2D_SOLVER_FFT = 0, 1
 
 
 class slpic2d_diag(ctypes.Structure):
@@ -112,6 +116,7 @@ def config_from_problem(prob: dict) -> slpic2d_config:
     c.src_rate = float(src.get("rate", 0.0))
     c.cg_rtol = float(prob.get("cg_rtol", 1e-8))
     c.cg_maxit = int(prob.get("cg_maxit", 20000))
+    c.solver = {"cg": SLPIC2D_SOLVER_CG, "fft": SLPIC2D_SOLVER_FFT}[prob.get("solver", "cg")]
     for s, sp in enumerate(prob["species"]):
         d = c.species[s]
         d.q, d.m, d.w, d.v0 = float(sp["q"]), float(sp["m"]), float(sp["w"]), float(sp["v0"])

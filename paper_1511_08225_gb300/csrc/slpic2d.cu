@@ -92,6 +92,12 @@ struct Params2D {
     float *fr, *fpA, *fpB, *fq, *fd;  // [nn] FP32 CG iterates, zero on the plate rows
     double *part;             // [3][grid] per-CTA partial sums
     State2D *st;
+    // direct solver (SLPIC2D_SOLVER_FFT)
+    int solver, log2nx;
+    double2 *tw;              // [nx/2] (cos, sin)(2 pi m / nx)
+    double2 *spec;            // [nn] Fourier coefficients along x, row by row
+    double *inv_m;            // [nn] Thomas multipliers 1/m_j per (row j, mode k)
+    double *rpart;            // [2 (ny+1)] per-row sums of r^2 and b^2
 };
 
 // ---------------------------------------------------------------------------------
@@ -516,6 +522,26 @@ __device__ __forceinline__ double stencil(const double *u, int idx, int i, int n
            (__ldcg(u + ip) + __ldcg(u + im) + __ldcg(u + idx - nx) + __ldcg(u + idx + nx));
 }
 
+// E = -grad phi at node idx: centred differences, one-sided on the plates, periodic
+// in x.  phi is read through L2 (written by other CTAs of the same grid).
+__device__ __forceinline__ void store_E(const Params2D &p, int idx)
+{
+    const int nx = p.nx, ny = p.ny;
+    const int j = idx / nx, i = idx - j * nx;
+    const int ip = (i + 1 == nx) ? idx + 1 - nx : idx + 1;
+    const int im = (i == 0) ? idx - 1 + nx : idx - 1;
+    const double *f = p.phi;
+    const double ex = -(__ldcg(f + ip) - __ldcg(f + im)) * (0.5 / p.dx);
+    double ey;
+    if (j == 0)
+        ey = -(__ldcg(f + idx + nx) - __ldcg(f + idx)) / p.dx;
+    else if (j == ny)
+        ey = -(__ldcg(f + idx) - __ldcg(f + idx - nx)) / p.dx;
+    else
+        ey = -(__ldcg(f + idx + nx) - __ldcg(f + idx - nx)) * (0.5 / p.dx);
+    p.E[idx] = make_float2((float)ex, (float)ey);
+}
+
 // mode 0: the simulation's solve (b from the deposits, which are then cleared;
 // E written).  mode 1: b from p.r's initial content as rho (slpic2d_solve_poisson).
 //
@@ -689,24 +715,9 @@ __global__ void __launch_bounds__(kCgThreads) k_cg2d(Params2D p, int mode)
         pnew = tmp;
     }
     // E on every node from the final phi (complete after the last barrier)
-    if (mode == 0) {
-        for (long long t = gtid; t < nn; t += gstride) {
-            const int idx = (int)t;
-            const int j = idx / nx, i = idx - j * nx;
-            const int ip = (i + 1 == nx) ? idx + 1 - nx : idx + 1;
-            const int im = (i == 0) ? idx - 1 + nx : idx - 1;
-            const double *f = p.phi;
-            const double ex = -(__ldcg(f + ip) - __ldcg(f + im)) * (0.5 / p.dx);
-            double ey;
-            if (j == 0)
-                ey = -(__ldcg(f + idx + nx) - __ldcg(f + idx)) / p.dx;
-            else if (j == ny)
-                ey = -(__ldcg(f + idx) - __ldcg(f + idx - nx)) / p.dx;
-            else
-                ey = -(__ldcg(f + idx + nx) - __ldcg(f + idx - nx)) * (0.5 / p.dx);
-            p.E[idx] = make_float2((float)ex, (float)ey);
-        }
-    }
+    if (mode == 0)
+        for (long long t = gtid; t < nn; t += gstride)
+            store_E(p, (int)t);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->cg_iters = it;
         st->cg_total += it;
@@ -714,6 +725,229 @@ __global__ void __launch_bounds__(kCgThreads) k_cg2d(Params2D p, int mode)
         if (!done)
             atomicCAS(&st->error, 0, SLPIC_ERR_NOCONVERGE);
     }
+}
+
+// ---- the direct solver (SLPIC2D_SOLVER_FFT) -----------------------------------------
+// The 5-point system A phi = b on the interior rows j = 1..ny-1 is periodic in x,
+// so the discrete Fourier transform along x diagonalises its x part: mode k of row
+// j obeys (4 - 2 cos(2 pi k/nx)) u_j - u_{j-1} - u_{j+1} = b^_j with u_0 = u_ny = 0
+// (the plate potentials are in b).  Three passes: a forward radix-2 FFT per row
+// (one CTA per row, the row in shared memory, FP64), the Thomas algorithm per mode
+// (one thread per k, the multipliers tabulated at creation), the inverse FFT per
+// row.  Then E and the true residual as for the CG.
+constexpr int kFftThreads = 256;
+
+// in-place radix-2 FFT of x[0..n) held in bit-reversed order; sign -1 forward,
+// +1 inverse (unnormalised)
+__device__ void fft_smem(double2 *x, const double2 *__restrict__ tw, int n, double sign)
+{
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1, step = n / len;
+        __syncthreads();
+        for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+            const int g = b / half, pos = b - g * half;
+            const int i0 = g * len + pos, i1 = i0 + half;
+            const double2 w = tw[pos * step];
+            const double wr = w.x, wi = sign * w.y;
+            const double2 v = x[i1];
+            const double tr = wr * v.x - wi * v.y, ti = wr * v.y + wi * v.x;
+            const double2 u = x[i0];
+            x[i0] = make_double2(u.x + tr, u.y + ti);
+            x[i1] = make_double2(u.x - tr, u.y - ti);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_sum_fft(double v, double *s_red)
+{
+    for (int off = 16; off; off >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kFftThreads / 32; ++w)
+            t += s_red[w];
+    __syncthreads();
+    return t;
+}
+
+// forward: b of row j (from the deposits, then cleared, in mode 0; from rho in p.r
+// in mode 1) into p.q, its transform into p.spec; ||b_j||^2 into rpart
+__global__ void __launch_bounds__(kFftThreads) k_fft_rows(Params2D p, int mode)
+{
+    extern __shared__ double2 sx[];
+    __shared__ double s_red[kFftThreads / 32];
+    const int nx = p.nx, ny = p.ny, j = blockIdx.x + 1;
+    const int shift = 32 - p.log2nx;
+    double bb = 0.0;
+    for (int i = threadIdx.x; i < nx; i += kFftThreads) {
+        const int idx = j * nx + i;
+        double rho = 0.0;
+        if (mode == 0) {
+            for (int s = 0; s < p.ns; ++s) {
+                unsigned long long *a = p.acc + (size_t)s * p.nn + idx;
+                rho = fma(p.sp[s].rho_unit, (double)(long long)*a, rho);
+                *a = 0ULL;
+            }
+            // the plate rows' deposits are consumed here too
+            if (j == 1)
+                for (int s = 0; s < p.ns; ++s)
+                    p.acc[(size_t)s * p.nn + i] = 0ULL;
+            if (j == ny - 1)
+                for (int s = 0; s < p.ns; ++s)
+                    p.acc[(size_t)s * p.nn + (size_t)ny * nx + i] = 0ULL;
+        } else {
+            rho = p.r[idx];
+        }
+        double b = p.k2 * rho;
+        if (j == 1)
+            b += p.phi_lo;
+        if (j == ny - 1)
+            b += p.phi_hi;
+        p.q[idx] = b;
+        bb = fma(b, b, bb);
+        sx[__brev((unsigned)i) >> shift] = make_double2(b, 0.0);
+    }
+    const double bbs = block_sum_fft(bb, s_red);
+    if (threadIdx.x == 0)
+        p.rpart[2 * j + 1] = bbs;
+    fft_smem(sx, p.tw, nx, -1.0);
+    for (int k = threadIdx.x; k < nx; k += kFftThreads)
+        p.spec[(size_t)j * nx + k] = sx[k];
+}
+
+// Thomas per mode k: forward u'_j = (b^_j + u'_{j-1}) / m_j, back u_j = u'_j + u_{j+1} / m_j.
+// One thread per mode; rows are taken kTriRows at a time, their loads issued together
+// before the dependent chain runs through them, so a block costs one memory latency.
+// Launched as one warp per CTA, so that the nx chains spread over as many SMs as
+// they can fill.
+constexpr int kTriRows = 16;
+constexpr int kTriThreads = 32;
+
+__global__ void __launch_bounds__(kTriThreads) k_tridiag_modes(Params2D p)
+{
+    const int nx = p.nx, ny = p.ny;
+    const int k = blockIdx.x * kTriThreads + threadIdx.x;
+    if (k >= nx)
+        return;
+    double2 *__restrict__ spec = p.spec;
+    const double *__restrict__ invm = p.inv_m;
+    double2 d = make_double2(0.0, 0.0);
+    for (int j0 = 1; j0 < ny; j0 += kTriRows) {
+        double2 v[kTriRows];
+        double m[kTriRows];
+#pragma unroll
+        for (int r = 0; r < kTriRows; ++r)
+            if (j0 + r < ny) {
+                const size_t o = (size_t)(j0 + r) * nx + k;
+                v[r] = spec[o];
+                m[r] = __ldg(invm + o);
+            }
+#pragma unroll
+        for (int r = 0; r < kTriRows; ++r)
+            if (j0 + r < ny) {
+                d = make_double2((v[r].x + d.x) * m[r], (v[r].y + d.y) * m[r]);
+                v[r] = d;
+            }
+#pragma unroll
+        for (int r = 0; r < kTriRows; ++r)
+            if (j0 + r < ny)
+                spec[(size_t)(j0 + r) * nx + k] = v[r];
+    }
+    double2 u = make_double2(0.0, 0.0);
+    const int nb = (ny - 1 + kTriRows - 1) / kTriRows;  // blocks of rows 1..ny-1
+    for (int b = nb - 1; b >= 0; --b) {
+        const int j0 = 1 + b * kTriRows;
+        double2 v[kTriRows];
+        double m[kTriRows];
+#pragma unroll
+        for (int r = 0; r < kTriRows; ++r)
+            if (j0 + r < ny) {
+                const size_t o = (size_t)(j0 + r) * nx + k;
+                v[r] = spec[o];
+                m[r] = __ldg(invm + o);
+            }
+#pragma unroll
+        for (int r = kTriRows - 1; r >= 0; --r)
+            if (j0 + r < ny) {
+                u = make_double2(fma(u.x, m[r], v[r].x), fma(u.y, m[r], v[r].y));
+                v[r] = u;
+            }
+#pragma unroll
+        for (int r = 0; r < kTriRows; ++r)
+            if (j0 + r < ny)
+                spec[(size_t)(j0 + r) * nx + k] = v[r];
+    }
+}
+
+// inverse: phi of row j from its coefficients
+__global__ void __launch_bounds__(kFftThreads) k_ifft_rows(Params2D p)
+{
+    extern __shared__ double2 sx[];
+    const int nx = p.nx, j = blockIdx.x + 1;
+    const int shift = 32 - p.log2nx;
+    for (int k = threadIdx.x; k < nx; k += kFftThreads)
+        sx[__brev((unsigned)k) >> shift] = p.spec[(size_t)j * nx + k];
+    fft_smem(sx, p.tw, nx, 1.0);
+    const double inv = 1.0 / nx;
+    for (int i = threadIdx.x; i < nx; i += kFftThreads)
+        p.phi[(size_t)j * nx + i] = sx[i].x * inv;
+}
+
+// E on every node (mode 0) and the true residual r = b - A phi per row
+__global__ void __launch_bounds__(kFftThreads) k_fft_finish(Params2D p, int mode)
+{
+    __shared__ double s_red[kFftThreads / 32];
+    const int nx = p.nx, ny = p.ny, j = blockIdx.x;  // rows 0..ny
+    double rr = 0.0;
+    for (int i = threadIdx.x; i < nx; i += kFftThreads) {
+        const int idx = j * nx + i;
+        if (mode == 0)
+            store_E(p, idx);
+        if (j >= 1 && j < ny) {
+            const int ip = (i + 1 == nx) ? idx + 1 - nx : idx + 1;
+            const int im = (i == 0) ? idx - 1 + nx : idx - 1;
+            const double *f = p.phi;
+            double ap = 4.0 * f[idx] - (f[ip] + f[im]);
+            if (j > 1)
+                ap -= f[idx - nx];
+            if (j < ny - 1)
+                ap -= f[idx + nx];
+            const double r = p.q[idx] - ap;
+            rr = fma(r, r, rr);
+        }
+    }
+    const double rrs = block_sum_fft(rr, s_red);
+    if (threadIdx.x == 0)
+        p.rpart[2 * j] = (j >= 1 && j < ny) ? rrs : 0.0;
+}
+
+// the per-row sums added in a fixed order (contiguous runs of rows per thread, then
+// a fixed tree: the same result every run) and the bookkeeping of a solve
+__global__ void __launch_bounds__(kFftThreads) k_fft_report(Params2D p)
+{
+    __shared__ double s_red[kFftThreads / 32];
+    const int rows = p.ny - 1, per = (rows + kFftThreads - 1) / kFftThreads;
+    double r = 0.0, b = 0.0;
+    for (int q = 0; q < per; ++q) {
+        const int j = 1 + threadIdx.x * per + q;
+        if (j < p.ny) {
+            r += p.rpart[2 * j];
+            b += p.rpart[2 * j + 1];
+        }
+    }
+    const double R = block_sum_fft(r, s_red);
+    const double B = block_sum_fft(b, s_red);
+    if (threadIdx.x != 0)
+        return;
+    State2D *st = p.st;
+    st->cg_iters = 0;
+    st->cg_res = B > 0.0 ? sqrt(R / B) : 0.0;
+    if (B > 0.0 && R > p.rtol2 * B)
+        atomicCAS(&st->error, 0, SLPIC_ERR_NOCONVERGE);
 }
 
 // ---- initial guess of the CG (slpic2d_set_warm_start) ------------------------------
@@ -902,6 +1136,22 @@ extern "C" int slpic2d_set_warm_start(slpic2d_t *h, int32_t mode, slpic_unet_t *
     return SLPIC_OK;
 }
 
+// The field solve of the configured solver (mode as for k_cg2d).
+static int launch_solve(slpic2d_t *h, int mode)
+{
+    if (h->p.solver != SLPIC2D_SOLVER_FFT)
+        return launch_cg(h, mode);
+    const Params2D &p = h->p;
+    const size_t smem = (size_t)16 * p.nx;
+    k_fft_rows<<<p.ny - 1, kFftThreads, smem, h->stream>>>(p, mode);
+    k_tridiag_modes<<<(p.nx + kTriThreads - 1) / kTriThreads, kTriThreads, 0, h->stream>>>(p);
+    k_ifft_rows<<<p.ny - 1, kFftThreads, smem, h->stream>>>(p);
+    k_fft_finish<<<p.ny + 1, kFftThreads, 0, h->stream>>>(p, mode);
+    k_fft_report<<<1, kFftThreads, 0, h->stream>>>(p);
+    CK2(h, cudaGetLastError());
+    return SLPIC_OK;
+}
+
 extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
 {
     if (!c || !out) {
@@ -917,6 +1167,10 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
         why = "n_species out of range";
     else if (!(c->cg_rtol > 0 && c->cg_rtol < 1) || c->cg_maxit <= 0)
         why = "need 0 < cg_rtol < 1 and cg_maxit > 0";
+    else if (c->solver != SLPIC2D_SOLVER_CG && c->solver != SLPIC2D_SOLVER_FFT)
+        why = "unknown solver";
+    else if (c->solver == SLPIC2D_SOLVER_FFT && (c->nx & (c->nx - 1) || c->nx > 8192))
+        why = "the FFT solver needs nx a power of two, at most 8192";
     else if (c->src_mode < SLPIC_SRC_NONE || c->src_mode > SLPIC_SRC_RATE ||
              (c->src_mode == SLPIC_SRC_LOSS_MATCHED &&
               (c->src_ref_species < 0 || c->src_ref_species >= c->n_species)))
@@ -1026,6 +1280,41 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
     h->ctas = sms * 4;
     if (!alloc((void **)&p.part, sizeof(double) * 3 * h->cg_ctas))
         return bail(SLPIC_ERR_OOM, "device allocation failed");
+    p.solver = c->solver;
+    if (p.solver == SLPIC2D_SOLVER_FFT) {
+        // twiddles and the Thomas multipliers of every (row, mode), in FP64 on the host
+        p.log2nx = 0;
+        while ((1 << p.log2nx) < p.nx)
+            ++p.log2nx;
+        if (!alloc((void **)&p.tw, sizeof(double2) * std::max(1, p.nx / 2)) ||
+            !alloc((void **)&p.spec, sizeof(double2) * nn) ||
+            !alloc((void **)&p.inv_m, sizeof(double) * nn) ||
+            !alloc((void **)&p.rpart, sizeof(double) * 2 * (p.ny + 1)))
+            return bail(SLPIC_ERR_OOM, "device allocation failed");
+        const double two_pi = 6.283185307179586;
+        std::vector<double2> tw((size_t)std::max(1, p.nx / 2));
+        for (int m = 0; m < p.nx / 2; ++m)
+            tw[m] = make_double2(std::cos(two_pi * m / p.nx), std::sin(two_pi * m / p.nx));
+        std::vector<double> inv_m(nn, 0.0);
+        for (int k = 0; k < p.nx; ++k) {
+            const double a = 4.0 - 2.0 * std::cos(two_pi * k / p.nx);
+            double prev = 0.0;  // 1/m_{j-1}
+            for (int j = 1; j < p.ny; ++j) {
+                prev = 1.0 / (a - prev);
+                inv_m[(size_t)j * p.nx + k] = prev;
+            }
+        }
+        cudaError_t e2 = cudaMemcpy(p.tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice);
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpy(p.inv_m, inv_m.data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
+        const int smem = 16 * p.nx;
+        if (e2 == cudaSuccess && smem > 48 * 1024)
+            e2 = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e2 == cudaSuccess && smem > 48 * 1024)
+            e2 = cudaFuncSetAttribute(k_ifft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e2 != cudaSuccess)
+            return bail(SLPIC_ERR_CUDA, cudaGetErrorString(e2));
+    }
     cudaError_t e = cudaMemset(h->d_state, 0, sizeof(State2D));
     if (e == cudaSuccess)
         e = cudaMemset(p.acc, 0, sizeof(unsigned long long) * nn * p.ns);
@@ -1130,7 +1419,7 @@ extern "C" int slpic2d_prepare(slpic2d_t *h)
     CK2(h, cudaMemsetAsync(p.acc, 0, sizeof(unsigned long long) * p.nn * p.ns, h->stream));
     k_deposit2d<<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
     CK2(h, cudaGetLastError());
-    int rc = launch_cg(h, 0);
+    int rc = launch_solve(h, 0);
     if (rc)
         return rc;
     h->prepared = true;
@@ -1175,9 +1464,9 @@ extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
         CK2(h, cudaGetLastError());
         if (ev)
             CK2(h, cudaEventRecord(ev[2], h->stream));
-        if ((rc = warm_start(h)))
+        if (h->p.solver == SLPIC2D_SOLVER_CG && (rc = warm_start(h)))
             return rc;
-        rc = launch_cg(h, 0);
+        rc = launch_solve(h, 0);
         if (rc)
             return rc;
         if (ev)
@@ -1392,7 +1681,7 @@ extern "C" int slpic2d_solve_poisson(slpic2d_t *h, const double *rho, double *ph
         return fail2(h, SLPIC_ERR_CUDA, cudaGetErrorString(e));
     }
     p.phi = d_phi;
-    rc = launch_cg(h, 1);
+    rc = launch_solve(h, 1);
     h->p = saved;
     if (rc == SLPIC_OK)
         rc = device_status(h);

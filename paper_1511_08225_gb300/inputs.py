@@ -244,11 +244,13 @@ def random_state(rng, n: int, n_cells: int, vscale: float = 1.0):
 # ------------------------------------------------------------------ 2D problems
 def plasma2d_problem(nx=1024, ny=1024, dx=1.0, v0=0.1, ppc=64, mass_ratio=1836.0, T_e=1.0,
                      T_i=0.1, kind=BETA_HEAVISIDE, dt=None, seed=SEED, capacity_factor=1.25,
-                     source_mode=SRC_LOSS_MATCHED, rate=0.0, cg_rtol=1e-8, cg_maxit=20000):
+                     source_mode=SRC_LOSS_MATCHED, rate=0.0, cg_rtol=1e-8, cg_maxit=20000,
+                     solver="cg"):
     """2D3V electron-ion plasma between two absorbing plates at phi = 0 (y = 0 and
     y = ny dx), periodic in x, loaded uniformly (ppc per species per cell), with a
     central source band (45%..55% of y) re-injecting physical Maxwellian pairs.
-    dt defaults to dx / v0.  Weights are per unit length in z: w = n0 dx^2 <1/beta> / ppc."""
+    dt defaults to dx / v0.  Weights are per unit length in z: w = n0 dx^2 <1/beta> / ppc.
+    solver: "cg" (Jacobi-PCG, warm-started) or "fft" (direct, nx a power of two)."""
     dt = dx / v0 if dt is None else dt
     sp = []
     for name, q, m, T in (("e", -1.0, 1.0, T_e), ("i", 1.0, mass_ratio, T_i)):
@@ -260,7 +262,7 @@ def plasma2d_problem(nx=1024, ny=1024, dx=1.0, v0=0.1, ppc=64, mass_ratio=1836.0
             "phi_lo": 0.0, "phi_hi": 0.0, "eps0": 1.0, "seed": int(seed), "species": sp,
             "source": {"mode": int(source_mode), "lo_cells": 0.45 * ny, "len_cells": 0.10 * ny,
                        "rate": float(rate), "ref_species": 1},
-            "cg_rtol": float(cg_rtol), "cg_maxit": int(cg_maxit)}
+            "cg_rtol": float(cg_rtol), "cg_maxit": int(cg_maxit), "solver": solver}
 
 
 def load_state2d(prob: dict, seed: int | None = None):

@@ -264,3 +264,73 @@ def test_load2d_rejects_bad_particles_and_capacity():
                np.zeros((cap + 1, 3), np.float32))
     assert ei.value.code == binding2d.binding.SLPIC_ERR_CAPACITY
     g.close()
+
+
+# ------------------------------------------------------------------ direct (FFT) solver
+@pytest.mark.parametrize("nx,ny", [(64, 48), (128, 2), (2, 9), (1024, 33)])
+def test_fft_solve_matches_direct_oracle(nx, ny):
+    """SLPIC2D_SOLVER_FFT (radix-2 FFT along x, Thomas per mode along y, FP64)
+    against the oracle's direct solve (plain DFT along x, Thomas per mode): biased
+    plates, random rho, one interior row (ny = 2), a two-point period (nx = 2)."""
+    prob = _prob(nx=nx, ny=ny, ppc=1, phi_hi=-0.7)
+    prob["phi_lo"] = 0.3
+    prob["solver"] = "fft"
+    g = binding2d.Simulation2D(prob)
+    rho = np.random.default_rng(nx + ny).normal(size=(ny + 1, nx))
+    phi, it, res = g.solve_poisson(rho)
+    exact = orc.poisson2d_direct(rho, prob["dx"], 0.3, -0.7)
+    assert it == 0 and res <= 1e-13
+    assert np.abs(phi - exact).max() <= 1e-12 * np.abs(exact).max()
+    assert np.all(phi[0] == 0.3) and np.all(phi[-1] == -0.7)
+    g.close()
+
+
+def test_fft_solver_needs_a_power_of_two_period():
+    prob = _prob(nx=48, ny=16, ppc=1)
+    prob["solver"] = "fft"
+    with pytest.raises(binding2d.SlpicError) as ei:
+        binding2d.Simulation2D(prob)
+    assert ei.value.code == binding2d.binding.SLPIC_ERR_INVALID
+
+
+@pytest.mark.parametrize("kind", [inputs.BETA_ONE, inputs.BETA_HEAVISIDE])
+def test_single_step2d_with_fft_solver_matches_oracle(kind):
+    """The step of the parity test above with the direct solver: the potential is
+    the direct solve of the GPU's own rho to roundoff, and the step matches the
+    oracle's."""
+    v0 = 0.35
+    prob = _prob(nx=64, ny=36, ppc=10, kind=kind, v0=v0, dx=0.5,
+                 dt=0.5 / (v0 if kind != inputs.BETA_ONE else 4.0), phi_hi=1.5)
+    prob["solver"] = "fft"
+    st = _unique_vz(_nonneutral(inputs.load_state2d(prob, seed=31 + kind)))
+    g = _sim(prob, st)
+    o = _oracle(prob, st)
+    rho_g, phi_g, _, _ = g.fields()
+    ref = orc.poisson2d_direct(rho_g, prob["dx"], prob["phi_lo"], prob["phi_hi"])
+    assert np.abs(phi_g - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    g.step(1)
+    g.synchronize()
+    o.step(1)
+    stats = _compare_step2d(prob, st, g, o)
+    print("parity2d fft", kind, stats)
+    d = g.diagnostics()
+    assert d["cg_iterations"] == 0 and d["cg_rel_residual"] <= 1e-13
+    for s in range(2):
+        assert abs(d["count"][s] - o.x[s].size) <= 2
+    g.close()
+
+
+def test_fft_and_cg_steps_agree():
+    """Twenty steps (a compacting step among them) with each solver from one load:
+    the potentials agree to the CG's tolerance."""
+    prob = _prob(nx=64, ny=40, ppc=8, v0=0.3, dt=1.5, cg_rtol=1e-12)
+    st = inputs.load_state2d(prob, seed=41)
+    pf = dict(prob, solver="fft")
+    g1, g2 = _sim(prob, st), _sim(pf, st)
+    g1.step(20)
+    g2.step(20)
+    p1, p2 = g1.fields()[1], g2.fields()[1]
+    assert np.abs(p1 - p2).max() <= 1e-6 * max(1e-6, np.abs(p2).max())
+    assert g2.diagnostics()["cg_iterations_total"] == 0
+    g1.close()
+    g2.close()
