@@ -215,6 +215,13 @@ int slpic_synchronize(slpic_t *h);
  * divided by dx), phi, E (the FP32 copy the particles gather).  Any pointer
  * may be NULL. */
 int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, float *E);
+/* The same read-back without waiting: the potential kernel and the three copies
+ * are queued on the handle's stream behind the steps already queued, and the
+ * arrays are filled when the stream gets there (slpic_synchronize, or a CUDA event
+ * on the stream, tells when).  The arrays must stay valid until then; page-locked
+ * (pinned) host memory makes the copies overlap the following steps.  Errors of the
+ * queued work are reported by the next synchronising call. */
+int slpic_fields_async(slpic_t *h, int instance, double *rho, double *phi, float *E);
 
 /* Physical number density sum(w beta S)/dx of one species, nodal. */
 int slpic_density(slpic_t *h, int instance, int species, double *n);

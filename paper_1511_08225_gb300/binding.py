@@ -41,7 +41,7 @@ EXPORTS = (
     "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernels_per_step",
     "slpic_particle_step_noalloc", "slpic_create_batch", "slpic_set_speed_limit",
     "slpic_set_timestep", "slpic_set_wave", "slpic_get_tuning", "slpic_set_tuning",
-    "slpic_autotune",
+    "slpic_autotune", "slpic_fields_async",
 )
 
 
@@ -123,6 +123,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "slpic_step": (I, [P, I64]),
         "slpic_synchronize": (I, [P]),
         "slpic_fields": (I, [P, I, P, P, P]),
+        "slpic_fields_async": (I, [P, I, P, P, P]),
         "slpic_density": (I, [P, I, I, P]),
         "slpic_charge_raw": (I, [P, I, I, P]),
         "slpic_particle_count": (I, [P, I, I, ctypes.POINTER(I64)]),

@@ -64,6 +64,14 @@ struct slpic_sim {
     // a batch of independent simulations (slpic_create_batch): each member does its
     // own per-instance work (loads, read-back, diagnostics); the batch advances all
     // of them together with the batched kernels, captured in g1 / gc / gK
+    // slpic_fields_async: the latest deposit and E copied on the step stream, the
+    // potential and the host copies on a private read-back stream
+    cudaStream_t rb_stream = nullptr;
+    cudaEvent_t ev_snap = nullptr, ev_rb = nullptr;
+    unsigned long long *d_snap_acc = nullptr;
+    float *d_snap_E = nullptr;
+    bool rb_used = false;
+
     std::vector<slpic_sim *> members;
     StepParams *d_params = nullptr;  // [members] on the device
     int4 *d_work = nullptr;          // particle-kernel work items
@@ -217,6 +225,16 @@ static void free_all(slpic_t *h)
         cudaGraphExecDestroy(h->gt);
     for (cudaEvent_t e : h->events)
         cudaEventDestroy(e);
+    if (h->rb_stream) {
+        cudaStreamSynchronize(h->rb_stream);
+        cudaStreamDestroy(h->rb_stream);
+    }
+    if (h->ev_snap)
+        cudaEventDestroy(h->ev_snap);
+    if (h->ev_rb)
+        cudaEventDestroy(h->ev_rb);
+    cudaFree(h->d_snap_acc);
+    cudaFree(h->d_snap_E);
     cudaFree(h->d_state);
     cudaFree(h->d_acc);
     cudaFree(h->d_E);
@@ -676,6 +694,8 @@ extern "C" int slpic_synchronize(slpic_t *h)
         return SLPIC_OK;
     }
     CK(h, cudaStreamSynchronize(h->stream));
+    if (h->rb_stream)
+        CK(h, cudaStreamSynchronize(h->rb_stream));
     int e = 0;
     CK(h, cudaMemcpy(&e, &h->d_state->error, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
@@ -706,7 +726,8 @@ extern "C" int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, 
         return rc;
     if (rho || phi) {
         // the step computes E only; rho and phi of the latest deposit on demand
-        launch_potential(h->p, h->stream);
+        launch_potential(h->p, h->d_acc + (size_t)(h->step & 1) * h->ns * h->nn, h->step,
+                         h->stream);
         CK(h, cudaGetLastError());
         CK(h, cudaStreamSynchronize(h->stream));
     }
@@ -716,6 +737,47 @@ extern "C" int slpic_fields(slpic_t *h, int instance, double *rho, double *phi, 
         CK(h, cudaMemcpy(phi, h->d_phi, sizeof(double) * h->nn, cudaMemcpyDeviceToHost));
     if (E)
         CK(h, cudaMemcpy(E, h->d_E, sizeof(float) * h->nn, cudaMemcpyDeviceToHost));
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_fields_async(slpic_t *h, int instance, double *rho, double *phi, float *E)
+{
+    BATCH_FORWARD(h, instance, slpic_fields_async(m_, 0, rho, phi, E));
+    int rc = check_handle(h, instance);
+    if (rc)
+        return rc;
+    if (h->dirty && (rc = slpic_prepare(h)))
+        return rc;
+    if (!h->rb_stream) {
+        CK(h, cudaStreamCreateWithFlags(&h->rb_stream, cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->ev_snap, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_rb, cudaEventDisableTiming));
+        CK(h, cudaMalloc(&h->d_snap_acc, sizeof(unsigned long long) * h->ns * h->nn));
+        CK(h, cudaMalloc(&h->d_snap_E, sizeof(float) * h->nn));
+    }
+    // the previous read-back has finished with the snapshot before it is replaced
+    if (h->rb_used)
+        CK(h, cudaStreamWaitEvent(h->stream, h->ev_rb, 0));
+    launch_snapshot(h->d_acc + (size_t)(h->step & 1) * h->ns * h->nn, h->d_snap_acc,
+                    (size_t)h->ns * h->nn, h->d_E, h->d_snap_E, h->nn, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaEventRecord(h->ev_snap, h->stream));
+    CK(h, cudaStreamWaitEvent(h->rb_stream, h->ev_snap, 0));
+    if (rho || phi) {
+        launch_potential(h->p, h->d_snap_acc, h->step, h->rb_stream);
+        CK(h, cudaGetLastError());
+    }
+    if (rho)
+        CK(h, cudaMemcpyAsync(rho, h->d_rho, sizeof(double) * h->nn, cudaMemcpyDeviceToHost,
+                              h->rb_stream));
+    if (phi)
+        CK(h, cudaMemcpyAsync(phi, h->d_phi, sizeof(double) * h->nn, cudaMemcpyDeviceToHost,
+                              h->rb_stream));
+    if (E)
+        CK(h, cudaMemcpyAsync(E, h->d_snap_E, sizeof(float) * h->nn, cudaMemcpyDeviceToHost,
+                              h->rb_stream));
+    CK(h, cudaEventRecord(h->ev_rb, h->rb_stream));
+    h->rb_used = true;
     return SLPIC_OK;
 }
 

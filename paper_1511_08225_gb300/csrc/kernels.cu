@@ -8,6 +8,7 @@
 //   k_validate   range checks of device-side particle loads
 //
 // Citations: Werner et al., arXiv 1511.08225, Appendix A, Eq. (slpicIntegration).
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cstdint>
 #include <mutex>
@@ -870,15 +871,16 @@ __device__ __forceinline__ double wave_E(const StepParams &p, int j, double t)
     return -wave_amplitude(p, t) * p.wave_k * cos(p.wave_k * ((double)j * p.dx - p.wave_vphi * t));
 }
 
-__global__ void __launch_bounds__(kFT) k_potential(StepParams p)
+// dep: the deposit to solve from, [species][nn] (the latest level's, or a copy of it);
+// step: its time level (for a prescribed wave)
+__global__ void __launch_bounds__(kFT) k_potential(StepParams p, const unsigned long long *dep,
+                                                   long long step)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     double *s_P = reinterpret_cast<double *>(smem);  // [nn]
     __shared__ double s_w[32];
     __shared__ double s_D0, s_shift;
 
-    const long long step = p.st->step;
-    const int Q = (int)(step & 1);
     const int N = p.n_cells, nn = p.nn;
 
     // ---- rho_j from the fixed-point deposits (FP64)
@@ -889,7 +891,7 @@ __global__ void __launch_bounds__(kFT) k_potential(StepParams p)
     for (int j = j0; j < j1; ++j) {
         double r = 0.0;
         for (int s = 0; s < p.ns; ++s) {
-            long long a = (long long)__ldcg(p.acc + ((size_t)Q * p.ns + s) * nn + j);
+            long long a = (long long)__ldcg(dep + (size_t)s * nn + j);
             r += p.sp[s].qw_dx * ((double)a * scale);
         }
         p.rho[j] = r;
@@ -1495,9 +1497,32 @@ void launch_field(const StepParams &p, int mode, cudaStream_t st)
     k_field<<<kFC, kFCT, field_cluster_smem_bytes(p.nn, p.ns), st>>>(p, mode);
 }
 
-void launch_potential(const StepParams &p, cudaStream_t st)
+// the latest deposit ([species][nn]) and E copied for a read-back that runs beside
+// the following steps
+__global__ void k_snapshot(const unsigned long long *__restrict__ dep, unsigned long long *__restrict__ dep_out,
+                           size_t ndep, const float *__restrict__ E, float *__restrict__ E_out, int nn)
 {
-    k_potential<<<1, kFT, field_smem_bytes(p.nn), st>>>(p);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < ndep + nn;
+         t += (size_t)gridDim.x * blockDim.x) {
+        if (t < ndep)
+            dep_out[t] = dep[t];
+        else
+            E_out[t - ndep] = E[t - ndep];
+    }
+}
+
+void launch_snapshot(const unsigned long long *dep, unsigned long long *dep_out, size_t ndep,
+                     const float *E, float *E_out, int nn, cudaStream_t st)
+{
+    const size_t n = ndep + (size_t)nn;
+    k_snapshot<<<(unsigned)std::min<size_t>((n + 255) / 256, 1024), 256, 0, st>>>(dep, dep_out, ndep,
+                                                                                  E, E_out, nn);
+}
+
+void launch_potential(const StepParams &p, const unsigned long long *dep, long long step,
+                      cudaStream_t st)
+{
+    k_potential<<<1, kFT, field_smem_bytes(p.nn), st>>>(p, dep, step);
 }
 
 void launch_deposit(const StepParams &p, int ctas_per_species, cudaStream_t st)

@@ -38,7 +38,12 @@ cudaError_t configure_particles_tma(int nn, int *stages);
 void launch_particles_tma(const StepParams &p, int ctas, int stages, cudaStream_t st);
 void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st);
 void launch_field(const StepParams &p, int mode, cudaStream_t st);
-void launch_potential(const StepParams &p, cudaStream_t st);
+// copy of a deposit ([species][nn], ndep words) and of E, for an overlapped read-back
+void launch_snapshot(const unsigned long long *dep, unsigned long long *dep_out, size_t ndep,
+                     const float *E, float *E_out, int nn, cudaStream_t st);
+// rho and phi (p.rho, p.phi) from the deposit dep ([species][nn]) of time level step
+void launch_potential(const StepParams &p, const unsigned long long *dep, long long step,
+                      cudaStream_t st);
 // batched forms over many instances: d_params[m] on the device; the particle
 // kernels take one CTA per work item (instance, species, share, shares)
 cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compact_per_sm);
