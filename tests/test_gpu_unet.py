@@ -4,7 +4,7 @@
 The GPU multiplies by BF16 copies of the FP32 weights and accumulates in FP32;
 the oracle is given the same BF16-rounded weights and runs in FP64, so the
 difference is FP32 accumulation alone: the bar is 1e-3 of each tensor's largest
-entry (the survey's P11 asks for 1e-2)."""
+entry, tighter than the 1e-2 a BF16 network calls for."""
 import numpy as np
 import pytest
 
@@ -138,7 +138,7 @@ def test_tensor_core_forward_matches_oracle(levels, base, n, nb):
     """tcgen05 implicit-GEMM convolutions (BF16 operands, FP32 accumulation in
     tensor memory) against the oracle with every conv input rounded to BF16: a
     ragged last pixel tile (40 x 40), a grid smaller than one tile (8 x 8), 3 and
-    256 output channels.  The bar is the survey's 1e-2 of the largest output: a
+    256 output channels.  The bar is 1e-2 of the largest output: a
     conv input whose FP32 and FP64 values straddle a BF16 rounding boundary rounds
     differently on the two sides, and with 256 channels a few hundred of the
     ~700k activations do.  The mean error is less than half that against the

@@ -1,7 +1,7 @@
 """Pins of the U-Net oracle (no GPU), each resting on something other than the
 oracle: a library correlation, adjoint identities, bfloat16 values worked out by
 hand, and central finite differences of the loss for parameters of every layer
-(2-level, 8-channel nets at 32 x 32)."""
+(2-level, 8-channel nets at 32 x 32 among them)."""
 import numpy as np
 import pytest
 from scipy import signal
