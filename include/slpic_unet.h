@@ -25,11 +25,13 @@
  * Precision: activations and gradients FP32; the convolutions multiply by a
  * BF16 copy (round to nearest even) of the FP32 master weights and accumulate in
  * FP32; biases FP32; weight-gradient sums FP64 across threads; loss sums FP64.
- * With tensor_cores = 1 the forward convolutions (output channels up to 256) run
- * as implicit GEMMs on the tensor cores (tcgen05, BF16 x BF16, FP32 accumulate in
- * tensor memory): each conv's input is also rounded to BF16 (nearest even), and
- * the weight gradient multiplies by that rounded input; the input gradient passes
- * the rounding through unchanged.
+ * With tensor_cores = 1 the forward convolutions and the input-gradient
+ * convolutions run as implicit GEMMs on the tensor cores (tcgen05, BF16 x BF16,
+ * FP32 accumulate in tensor memory, output channels in slices of 256): each
+ * forward conv's input is rounded to BF16 (nearest even), and the weight gradient
+ * multiplies by that rounded input; the input gradient is the transposed conv of
+ * the output gradient rounded to BF16, and passes the forward rounding through
+ * unchanged.  The weight gradients stay on the CUDA cores (FP32 output gradient).
  *
  * Parameters: one flat FP32 array, conv by conv in the order encoder
  * l = 0..L-1, decoder l = L-2..0, output; each conv its weights

@@ -134,18 +134,26 @@ def forward(params, x, levels: int, act_bf16: bool = False):
     return y[0], cache
 
 
-def backward(params, cache, dy, levels: int):
-    """Parameter gradients [(dW, db)] for the loss gradient dy = dL/dy (H, W)."""
+def backward(params, cache, dy, levels: int, act_bf16: bool = False):
+    """Parameter gradients [(dW, db)] for the loss gradient dy = dL/dy (H, W).  With
+    act_bf16 (tensor-core operands) each conv's input gradient is formed from its
+    output gradient rounded to bfloat16; the weight gradients use it unrounded."""
+    def cb(x, w, gz):
+        gx, dw, db = conv_backward(x, w, gz)
+        if act_bf16:
+            gx = conv_backward(x, w, bf16(gz))[0]
+        return gx, dw, db
+
     grads = [None] * len(params)
     k = len(params) - 1
-    g, dw, db = conv_backward(cache["in"][k], params[k][0], dy[None])
+    g, dw, db = cb(cache["in"][k], params[k][0], dy[None])
     grads[k] = (dw, db)
     d_enc = [np.zeros_like(cache["pre"][l]) for l in range(levels)]
     g_d = g  # gradient at the output of the current decoder level (d_l)
     for l in range(0, levels - 1):
         k -= 1
         gz = g_d * (cache["pre"][k] > 0)
-        gc, dw, db = conv_backward(cache["in"][k], params[k][0], gz)
+        gc, dw, db = cb(cache["in"][k], params[k][0], gz)
         grads[k] = (dw, db)
         c_up = cache["in"][k].shape[0] - d_enc[l].shape[0]
         d_enc[l] += gc[c_up:]
@@ -155,7 +163,7 @@ def backward(params, cache, dy, levels: int):
     for l in range(levels - 1, -1, -1):
         k = l
         gz = d_enc[l] * (cache["pre"][k] > 0)
-        gi, dw, db = conv_backward(cache["in"][k], params[k][0], gz)
+        gi, dw, db = cb(cache["in"][k], params[k][0], gz)
         grads[k] = (dw, db)
         if l > 0:
             d_enc[l - 1] += pool_backward(gi)

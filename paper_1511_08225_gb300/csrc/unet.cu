@@ -172,9 +172,32 @@ __global__ void k_pack_tc(const __nv_bfloat16 *__restrict__ w, int cout, int cin
     }
 }
 
+// The transposed conv of the input gradient, dx = conv^T(dz), is the same conv of dz
+// with the weights' channels swapped and taps mirrored: W'[c][o][t] = W[o][c][8 - t].
+// packed[kc][c/8][j][c%8][kk] = W[o][c][8 - t] for k = t cpo + o (cpo = cout padded to 16)
+__global__ void k_pack_tc_t(const __nv_bfloat16 *__restrict__ w, int cout, int cin, int Np, int nkc,
+                            __nv_bfloat16 *__restrict__ packed)
+{
+    const int cp = (cout + 15) / 16 * 16;
+    const size_t total = (size_t)nkc * Np * kTcKC;
+    for (size_t e = blockIdx.x * (size_t)kT + threadIdx.x; e < total; e += (size_t)gridDim.x * kT) {
+        const int kc = (int)(e / ((size_t)Np * kTcKC));
+        const int r = (int)(e - (size_t)kc * Np * kTcKC);
+        const int g = r / (8 * kTcKC);
+        const int rem = r - g * 8 * kTcKC;
+        const int j = rem / 64, rr = (rem / 8) % 8, kk = rem % 8;
+        const int c = g * 8 + rr, k = kc * kTcKC + j * 8 + kk;
+        const int t = k / cp, o = k - t * cp;
+        packed[e] = (c < cin && t < 9 && o < cout) ? w[((size_t)o * cin + c) * 9 + (8 - t)]
+                                                   : __float2bfloat16_rn(0.0f);
+    }
+}
+
+// wp: the packed B of this launch's output channels (a slice of at most 256 rows of a
+// packed image whose chunks lie bstride elements apart); b: their biases
 __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(TV x, int cin, const __nv_bfloat16 *__restrict__ wp,
-                                                    const float *__restrict__ b, int cout, int Np,
-                                                    TV a, int relu, int H, int W, int *flag)
+                                                    size_t bstride, const float *__restrict__ b, int cout,
+                                                    int Np, TV a, int relu, int H, int W, int *flag)
 {
     extern __shared__ __align__(1024) unsigned char tsm[];
     const int chunkB = Np * kTcKC * 2;
@@ -259,7 +282,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(TV x, int cin, const
             }
         }
         // B: the packed chunk image, 16 bytes per thread and step
-        const uint4 *src = reinterpret_cast<const uint4 *>(wp + (size_t)kc * Np * kTcKC);
+        const uint4 *src = reinterpret_cast<const uint4 *>(wp + (size_t)kc * bstride);
         uint4 *dst = reinterpret_cast<uint4 *>(bufB);
         for (int e = tid; e < chunkB / 16; e += kTcThreads)
             dst[e] = __ldg(src + e);
@@ -675,6 +698,8 @@ struct ConvSpec {
     size_t w_off, b_off;    // into the flat parameter array
     int Np = 0, nkc = 0;    // tensor-core form: padded N, K chunks
     size_t tc_off = 0;      // its packed weights in wtc
+    int Npt = 0, nkct = 0;  // the transposed conv (input gradient): padded N, K chunks
+    size_t tct_off = 0;     // its packed weights in wtct
 };
 
 struct slpic_unet {
@@ -696,7 +721,8 @@ struct slpic_unet {
     long long adam_t = 0;
     // tensor-core forward (cfg.tensor_cores): packed BF16 weights, stale after a
     // parameter change until the next forward repacks them
-    __nv_bfloat16 *wtc = nullptr;
+    __nv_bfloat16 *wtc = nullptr, *wtct = nullptr;
+    float *zeros = nullptr;  // zero biases of the transposed convs
     bool tc_dirty = true;
     int *d_flag = nullptr;  // a bounded wait of a tensor-core kernel ran out
     cudaStream_t stream = nullptr;
@@ -782,15 +808,29 @@ constexpr int kTcMaxN = 256;
 
 size_t tc_smem_bytes(int Np) { return 2 * (size_t)kTcChunkA + 2 * (size_t)Np * kTcKC * 2; }
 
+// a tensor-core conv at `level` over all Np packed output channels, in slices of at
+// most kTcMaxN (one launch each)
+void conv_tc(slpic_unet_t *h, TV x, int cin, const __nv_bfloat16 *wp, int Np, const float *bias,
+             int cout, TV a, int relu, int level, int nb, cudaStream_t st)
+{
+    const int H = hl(h, level), W = wl(h, level);
+    dim3 g((unsigned)((H * W + kTcM - 1) / kTcM), (unsigned)nb);
+    for (int o0 = 0; o0 < Np; o0 += kTcMaxN) {
+        const int n = std::min(kTcMaxN, Np - o0);
+        TV as = a;
+        as.coff += o0;
+        k_conv_fwd_tc<<<g, kTcThreads, tc_smem_bytes(n), st>>>(
+            x, cin, wp + (size_t)o0 * kTcKC, (size_t)Np * kTcKC, bias + o0, std::min(cout - o0, n), n,
+            as, relu, H, W, h->d_flag);
+    }
+}
+
 void conv_fwd(slpic_unet_t *h, int k, TV x, TV a, int relu, int nb, cudaStream_t st)
 {
     const ConvSpec &c = h->conv[k];
     const int H = hl(h, c.level), W = wl(h, c.level);
-    if (h->cfg.tensor_cores && c.Np <= kTcMaxN) {
-        dim3 g((unsigned)((H * W + kTcM - 1) / kTcM), (unsigned)nb);
-        k_conv_fwd_tc<<<g, kTcThreads, tc_smem_bytes(c.Np), st>>>(x, c.cin, h->wtc + c.tc_off,
-                                                             h->p + c.b_off, c.cout, c.Np, a, relu,
-                                                             H, W, h->d_flag);
+    if (h->cfg.tensor_cores) {
+        conv_tc(h, x, c.cin, h->wtc + c.tc_off, c.Np, h->p + c.b_off, c.cout, a, relu, c.level, nb, st);
         return;
     }
     dim3 grid((unsigned)((H * W + kT - 1) / kT), (unsigned)((c.cout + kOCB - 1) / kOCB), (unsigned)nb);
@@ -802,9 +842,10 @@ void conv_bwd(slpic_unet_t *h, int k, TV x, TV dz, TV *dx, int nb, cudaStream_t 
     const ConvSpec &c = h->conv[k];
     const int H = hl(h, c.level), W = wl(h, c.level);
     k_conv_bwd_w<<<dim3((unsigned)c.cin, (unsigned)c.cout), kT, 0, st>>>(
-        x, c.cin, dz, c.cout, h->g + c.w_off, h->g + c.b_off, H, W, nb,
-        (h->cfg.tensor_cores && c.Np <= kTcMaxN) ? 1 : 0);
-    if (dx) {
+        x, c.cin, dz, c.cout, h->g + c.w_off, h->g + c.b_off, H, W, nb, h->cfg.tensor_cores ? 1 : 0);
+    if (dx && h->cfg.tensor_cores) {
+        conv_tc(h, dz, c.cout, h->wtct + c.tct_off, c.Npt, h->zeros, c.cin, *dx, 0, c.level, nb, st);
+    } else if (dx) {
         dim3 grid((unsigned)((H * W + kT - 1) / kT), (unsigned)((c.cin + kOCB - 1) / kOCB),
                   (unsigned)nb);
         k_conv_bwd_x<<<grid, kT, 0, st>>>(dz, c.cout, h->pb + c.w_off, c.cin, *dx, H, W);
@@ -830,10 +871,12 @@ void forward_net(slpic_unet_t *h, int nb, cudaStream_t st)
 {
     const int L = h->L;
     if (h->cfg.tensor_cores && h->tc_dirty) {
-        for (const ConvSpec &c : h->conv)
-            if (c.Np <= kTcMaxN)
-                k_pack_tc<<<grid_for((size_t)c.nkc * c.Np * kTcKC), kT, 0, st>>>(
-                    h->pb + c.w_off, c.cout, c.cin, c.Np, c.nkc, h->wtc + c.tc_off);
+        for (const ConvSpec &c : h->conv) {
+            k_pack_tc<<<grid_for((size_t)c.nkc * c.Np * kTcKC), kT, 0, st>>>(
+                h->pb + c.w_off, c.cout, c.cin, c.Np, c.nkc, h->wtc + c.tc_off);
+            k_pack_tc_t<<<grid_for((size_t)c.nkct * c.Npt * kTcKC), kT, 0, st>>>(
+                h->pb + c.w_off, c.cout, c.cin, c.Npt, c.nkct, h->wtct + c.tct_off);
+        }
         h->tc_dirty = false;
     }
     for (int l = 0; l < L; ++l) {
@@ -1002,13 +1045,18 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
     for (int l = L - 2; l >= 0; --l)
         add(ch(h, l + 1) + ch(h, l), ch(h, l), l);
     add(ch(h, 0), 1, 0);
-    size_t ntc = 0;  // packed tensor-core weights
+    size_t ntc = 0, ntct = 0;  // packed tensor-core weights: forward, transposed
+    int maxc = 1;
     for (ConvSpec &s : h->conv) {
         s.Np = (s.cout + 15) / 16 * 16;
         s.nkc = (9 * ((s.cin + 15) / 16 * 16) + kTcKC - 1) / kTcKC;
         s.tc_off = ntc;
-        if (s.Np <= kTcMaxN)
-            ntc += (size_t)s.nkc * s.Np * kTcKC;
+        ntc += (size_t)s.nkc * s.Np * kTcKC;
+        s.Npt = (s.cin + 15) / 16 * 16;
+        s.nkct = (9 * ((s.cout + 15) / 16 * 16) + kTcKC - 1) / kTcKC;
+        s.tct_off = ntct;
+        ntct += (size_t)s.nkct * s.Npt * kTcKC;
+        maxc = std::max(maxc, std::max(s.Np, s.Npt));
     }
 
     const int nb = h->nbmax;
@@ -1019,11 +1067,17 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
     if (!rc) rc = alloc_f(h, &h->p, h->nparam);
     if (!rc) rc = alloc(h, (void **)&h->pb, sizeof(__nv_bfloat16) * h->nparam);
     if (!rc && c.tensor_cores) {
-        rc = alloc(h, (void **)&h->wtc, sizeof(__nv_bfloat16) * (ntc ? ntc : 1));
+        rc = alloc(h, (void **)&h->wtc, sizeof(__nv_bfloat16) * ntc);
+        if (!rc)
+            rc = alloc(h, (void **)&h->wtct, sizeof(__nv_bfloat16) * ntct);
+        if (!rc)
+            rc = alloc_f(h, &h->zeros, (size_t)maxc);
         if (!rc)
             rc = alloc(h, (void **)&h->d_flag, sizeof(int));
         if (!rc) {
             cudaError_t e = cudaMemset(h->d_flag, 0, sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaMemset(h->zeros, 0, sizeof(float) * maxc);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tc_smem_bytes(kTcMaxN));

@@ -52,7 +52,7 @@ def _oracle_grads(params, xs, ts, levels, energy=False, act_bf16=False):
             r = y - t
             loss += float((r * r).sum())
             dy = 2.0 * r / count
-        g = ounet.backward(pb, cache, dy, levels)
+        g = ounet.backward(pb, cache, dy, levels, act_bf16=act_bf16)
         grads = g if grads is None else [(a + c, b + d) for (a, b), (c, d) in zip(grads, g)]
     return loss / count, grads
 
@@ -162,8 +162,10 @@ def test_tensor_core_forward_matches_oracle(levels, base, n, nb):
     net.close()
 
 
-@pytest.mark.parametrize("levels,base,n,nb", [(2, 8, 32, 2), (3, 4, 16, 1)])
+@pytest.mark.parametrize("levels,base,n,nb", [(2, 8, 32, 2), (3, 4, 16, 1), (4, 32, 32, 1)])
 def test_tensor_core_gradients_match_oracle(levels, base, n, nb):
+    """Forward and input-gradient convolutions on the tensor cores; (4, 32, 32) has a
+    transposed conv of 384 output channels, done in two slices."""
     params = _params(levels, base, seed=31 + levels)
     rng = np.random.default_rng(32 + levels)
     xs, ts = rng.normal(size=(nb, n, n)), rng.normal(size=(nb, n, n))
