@@ -98,6 +98,7 @@ struct Params2D {
     double2 *spec;            // [nn] Fourier coefficients along x, row by row
     double *inv_m;            // [nn] Thomas multipliers 1/m_j per (row j, mode k)
     double *rpart;            // [2 (ny+1)] per-row sums of r^2 and b^2
+    int *hist, *cursor, *bsum;  // cell sort: counts per cell, then slots; block sums
 };
 
 // ---------------------------------------------------------------------------------
@@ -950,6 +951,160 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_report(Params2D p)
         atomicCAS(&st->error, 0, SLPIC_ERR_NOCONVERGE);
 }
 
+// ---- counting sort of the particles by cell ------------------------------------------
+// Particles in cell order make the gather of E and the deposit atomics of
+// neighbouring threads land on neighbouring nodes.  Three passes over the live
+// particles of buffer `src`: a histogram per cell (lanes of a warp in the same cell
+// add once, __match_any_sync), an exclusive scan of the histogram into each cell's
+// first slot, and a scatter into buffer `dst` (a slot per particle by an atomic on
+// its cell's cursor, again once per warp group).  The order within a cell is
+// whatever the atomics give; nothing computed depends on it.
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanBlock = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kThreads) k_sort_count2d(Params2D p, int s, int src)
+{
+    const Species2D &sp = p.sp[s];
+    const long long n = (long long)p.st->count[s][src];
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long base = ((long long)blockIdx.x * kThreads + threadIdx.x) & ~31LL; base < n;
+         base += stride) {
+        const long long i = base + lane;
+        const int c = i < n ? sp.cell[src][i] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, c);
+        if (c >= 0 && lane == __ffs(grp) - 1)
+            atomicAdd(&p.hist[c], __popc(grp));
+    }
+}
+
+// exclusive scan of hist[0..nn) into cursor: per block of kScanBlock entries, then
+// the block totals, then their offsets added
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(Params2D p)
+{
+    __shared__ int s_w[kScanThreads / 32];
+    const long long b0 = (long long)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    int v[kScanPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = b0 + k < p.nn ? p.hist[b0 + k] : 0;
+        sum += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += y;
+    }
+    if (lane == 31)
+        s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = s_w[lane];
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o)
+                wi += y;
+        }
+        s_w[lane] = wi - w;  // exclusive over warps
+        if (lane == 31)
+            p.bsum[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    int run = s_w[warp] + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (b0 + k < p.nn)
+            p.cursor[b0 + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(Params2D p, int nb)
+{
+    __shared__ int s_carry;
+    __shared__ int s_w[kScanThreads / 32];
+    if (threadIdx.x == 0)
+        s_carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nb ? p.bsum[i] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            s_w[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int w = s_w[lane];
+            int wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o)
+                    wi += y;
+            }
+            s_w[lane] = wi - w;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        if (i < nb)
+            p.bsum[i] = carry + s_w[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1)
+            s_carry = carry + s_w[warp] + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(Params2D p)
+{
+    const long long i0 = (long long)blockIdx.x * kScanBlock;
+    const int add = p.bsum[blockIdx.x];
+    for (int k = threadIdx.x; k < kScanBlock; k += kScanThreads)
+        if (i0 + k < p.nn)
+            p.cursor[i0 + k] += add;
+}
+
+// the sorted buffer's slots: the end of the last cell's run; no holes
+__global__ void k_sort_count_set(Params2D p, int s, int b)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        p.st->count[s][b] = (unsigned long long)p.cursor[p.nn - 1];
+        p.st->holes[s][b] = 0ULL;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sort_scatter2d(Params2D p, int s, int src, int dst)
+{
+    const Species2D &sp = p.sp[s];
+    const long long n = (long long)p.st->count[s][src];
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long base = ((long long)blockIdx.x * kThreads + threadIdx.x) & ~31LL; base < n;
+         base += stride) {
+        const long long i = base + lane;
+        const int c = i < n ? sp.cell[src][i] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(grp) - 1;
+        int slot = 0;
+        if (c >= 0 && lane == leader)
+            slot = atomicAdd(&p.cursor[c], __popc(grp));
+        slot = __shfl_sync(0xffffffffu, slot, leader);
+        if (c >= 0) {
+            const int o = slot + __popc(grp & ((1u << lane) - 1u));
+            sp.cell[dst][o] = c;
+            sp.pv[dst][o] = sp.pv[src][i];
+            sp.vz[dst][o] = sp.vz[src][i];
+        }
+    }
+}
+
 // ---- initial guess of the CG (slpic2d_set_warm_start) ------------------------------
 // rho of rows 0..ny-1 as FP32 from the deposits (left in place for the CG kernel);
 // row 0, a plate, is zero.  The layout is the nodal one, so the array is the
@@ -1136,6 +1291,30 @@ extern "C" int slpic2d_set_warm_start(slpic2d_t *h, int32_t mode, slpic_unet_t *
     return SLPIC_OK;
 }
 
+// Sort every species' particles of buffer `src` by cell into buffer `dst` (holes
+// dropped, the count set to the live particles), then swap the two buffers' roles,
+// so that buffer index `src` names the sorted particles.
+static int sort_particles(slpic2d_t *h, int src)
+{
+    Params2D &p = h->p;
+    const int dst = src ^ 1;
+    const unsigned nblk = (unsigned)((p.nn + kScanBlock - 1) / kScanBlock);
+    for (int s = 0; s < p.ns; ++s) {
+        CK2(h, cudaMemsetAsync(p.hist, 0, sizeof(int) * p.nn, h->stream));
+        k_sort_count2d<<<h->ctas, kThreads, 0, h->stream>>>(p, s, src);
+        k_scan_blocks<<<nblk, kScanThreads, 0, h->stream>>>(p);
+        k_scan_top<<<1, kScanThreads, 0, h->stream>>>(p, (int)nblk);
+        k_scan_add<<<nblk, kScanThreads, 0, h->stream>>>(p);
+        k_sort_scatter2d<<<h->ctas, kThreads, 0, h->stream>>>(p, s, src, dst);
+        k_sort_count_set<<<1, 32, 0, h->stream>>>(p, s, src);
+        CK2(h, cudaGetLastError());
+        std::swap(p.sp[s].cell[src], p.sp[s].cell[dst]);
+        std::swap(p.sp[s].pv[src], p.sp[s].pv[dst]);
+        std::swap(p.sp[s].vz[src], p.sp[s].vz[dst]);
+    }
+    return SLPIC_OK;
+}
+
 // The field solve of the configured solver (mode as for k_cg2d).
 static int launch_solve(slpic2d_t *h, int mode)
 {
@@ -1280,6 +1459,9 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
     h->ctas = sms * 4;
     if (!alloc((void **)&p.part, sizeof(double) * 3 * h->cg_ctas))
         return bail(SLPIC_ERR_OOM, "device allocation failed");
+    if (!alloc((void **)&p.hist, sizeof(int) * nn) || !alloc((void **)&p.cursor, sizeof(int) * nn) ||
+        !alloc((void **)&p.bsum, sizeof(int) * ((nn + kScanBlock - 1) / kScanBlock + 1)))
+        return bail(SLPIC_ERR_OOM, "device allocation failed");
     p.solver = c->solver;
     if (p.solver == SLPIC2D_SOLVER_FFT) {
         // twiddles and the Thomas multipliers of every (row, mode), in FP64 on the host
@@ -1416,10 +1598,16 @@ extern "C" int slpic2d_prepare(slpic2d_t *h)
     if (!h)
         return SLPIC_ERR_INVALID;
     Params2D &p = h->p;
+    State2D st;
+    int rc = read_state(h, st);
+    if (rc)
+        return rc;
+    if ((rc = sort_particles(h, (int)(st.step & 1))))  // the load in cell order
+        return rc;
     CK2(h, cudaMemsetAsync(p.acc, 0, sizeof(unsigned long long) * p.nn * p.ns, h->stream));
     k_deposit2d<<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
     CK2(h, cudaGetLastError());
-    int rc = launch_solve(h, 0);
+    rc = launch_solve(h, 0);
     if (rc)
         return rc;
     h->prepared = true;
@@ -1462,6 +1650,9 @@ extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
             CK2(h, cudaEventRecord(ev[1], h->stream));
         k_inject2d<<<1, 1024, 0, h->stream>>>(p, compact ? 1 : 0);
         CK2(h, cudaGetLastError());
+        // after the compacting step (holes dropped, sources appended): particles by cell
+        if (compact && (rc = sort_particles(h, (int)((step + 1) & 1))))
+            return rc;
         if (ev)
             CK2(h, cudaEventRecord(ev[2], h->stream));
         if (h->p.solver == SLPIC2D_SOLVER_CG && (rc = warm_start(h)))

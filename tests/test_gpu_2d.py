@@ -334,3 +334,21 @@ def test_fft_and_cg_steps_agree():
     assert g2.diagnostics()["cg_iterations_total"] == 0
     g1.close()
     g2.close()
+
+
+def test_particles_are_sorted_by_cell_after_load_and_compaction():
+    """The counting sort by cell (after slpic2d_prepare and after every compacting
+    step): particles come back in non-decreasing cell order, none lost."""
+    prob = _prob(nx=32, ny=24, ppc=6, v0=0.3, dt=1.5)
+    st = inputs.load_state2d(prob, seed=51)
+    g = _sim(prob, st)
+    for s in range(2):
+        c, _, _ = g.particles(s)
+        assert c.size == st[s][0].size and np.all(np.diff(c) >= 0)
+        assert np.array_equal(np.sort(c), np.sort(st[s][0]))
+    g.step(16)  # step 15 compacts, then sorts
+    d = g.diagnostics()
+    for s in range(2):
+        c, _, _ = g.particles(s)
+        assert c.size == d["count"][s] and np.all(np.diff(c) >= 0)
+    g.close()
