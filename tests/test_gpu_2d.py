@@ -352,3 +352,21 @@ def test_particles_are_sorted_by_cell_after_load_and_compaction():
         c, _, _ = g.particles(s)
         assert c.size == d["count"][s] and np.all(np.diff(c) >= 0)
     g.close()
+
+
+def test_warp_summed_deposit_is_the_per_particle_deposit():
+    """The step's deposit adds the lanes of a warp that share a cell before its
+    atomics.  With the direct solver (exact to roundoff), the potential each step
+    leaves equals the direct solve of the charge recomputed particle by particle
+    (slpic2d_fields) at the same positions: a lost, doubled or misplaced sum would
+    show at once.  Sorted particles (after the load) make the groups long."""
+    prob = _prob(nx=64, ny=40, ppc=16, v0=0.3, dt=1.5, phi_hi=0.5)
+    prob["solver"] = "fft"
+    st = inputs.load_state2d(prob, seed=61)
+    g = _sim(prob, st)
+    for n in (1, 4, 16):  # the 16th step compacts and sorts again
+        g.step(n)
+        rho, phi, _, _ = g.fields()
+        ref = orc.poisson2d_direct(rho, prob["dx"], prob["phi_lo"], prob["phi_hi"])
+        assert np.abs(phi - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), n
+    g.close()
