@@ -31,7 +31,9 @@
  * forward conv's input is rounded to BF16 (nearest even), and the weight gradient
  * multiplies by that rounded input; the input gradient is the transposed conv of
  * the output gradient rounded to BF16, and passes the forward rounding through
- * unchanged.  The weight gradients stay on the CUDA cores (FP32 output gradient).
+ * unchanged; the weight gradient is a GEMM over the pixels (split over CTAs, the
+ * parts added in a fixed order) of the rounded input and the rounded output
+ * gradient; the bias gradient sums the unrounded output gradient in FP64.
  *
  * Parameters: one flat FP32 array, conv by conv in the order encoder
  * l = 0..L-1, decoder l = L-2..0, output; each conv its weights

@@ -136,12 +136,13 @@ def forward(params, x, levels: int, act_bf16: bool = False):
 
 def backward(params, cache, dy, levels: int, act_bf16: bool = False):
     """Parameter gradients [(dW, db)] for the loss gradient dy = dL/dy (H, W).  With
-    act_bf16 (tensor-core operands) each conv's input gradient is formed from its
-    output gradient rounded to bfloat16; the weight gradients use it unrounded."""
+    act_bf16 (tensor-core operands) each conv's input and weight gradients are formed
+    from its output gradient rounded to bfloat16; the bias gradients from it
+    unrounded."""
     def cb(x, w, gz):
         gx, dw, db = conv_backward(x, w, gz)
         if act_bf16:
-            gx = conv_backward(x, w, bf16(gz))[0]
+            gx, dw, _ = conv_backward(x, w, bf16(gz))
         return gx, dw, db
 
     grads = [None] * len(params)

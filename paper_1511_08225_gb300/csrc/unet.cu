@@ -342,6 +342,212 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_fwd_tc(TV x, int cin, const
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
+// ---- weight gradient on the tensor cores ---------------------------------------------
+// dW[o][c][t] = sum over samples and pixels of dz[o][p] x[c][p + off_t]: a GEMM with
+// M = (tap t, channel c) rows r = t cp + c (cp = cin padded to 16), N = output
+// channels (padded to 16), K = the nb * HW pixels, split over CTAs (blockIdx.y) and
+// added afterwards in a fixed order (k_wgrad_reduce).  A[r][k] = x of the pixel k
+// shifted by tap t (zero off the image), B[o][k] = dz[o] at pixel k, both rounded to
+// BF16, built by the threads in the K-major core-matrix layout of the forward conv
+// (thread: a pair of adjacent pixels, a stripe of rows).  Partial sums FP32 in TMEM.
+__global__ void __launch_bounds__(kTcThreads) k_conv_wgrad_tc(TV x, int cin, TV dz, int cout, int Np,
+                                                            int H, int W, int nb, int chunks_per,
+                                                            float *__restrict__ part, int *flag)
+{
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const int chunkB = Np * kTcKC * 2;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int HW = H * W;
+    const long long npix = (long long)nb * HW;
+    const int cp = (cin + 15) / 16 * 16, nrows = 9 * cp;
+    const int r0 = blockIdx.x * kTcM;  // this CTA's first row
+    const long long c0 = (long long)blockIdx.y * chunks_per;
+    const long long nchunk = (npix + kTcKC - 1) / kTcKC;
+    const int nkc = (int)max(0LL, min((long long)chunks_per, nchunk - c0));
+    const uint32_t ncols = Np <= 32 ? 32u : Np <= 64 ? 64u : Np <= 128 ? 128u : 256u;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc_smem(&s_tmem)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&s_bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&s_bar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const int kp = tid & 31;         // pixel pair of the chunk: k = 2 kp, 2 kp + 1
+    const int stripe = tid >> 5;     // rows stripe, 8 and 8 rows apart
+    for (int kc = 0; kc < nkc; ++kc) {
+        const int buf = kc & 1;
+        unsigned char *bufA = tsm + buf * kTcChunkA;
+        unsigned char *bufB = tsm + 2 * kTcChunkA + buf * chunkB;
+        if (kc >= 2 && !s_fail) {
+            if (!tc_wait(&s_bar[buf], (unsigned)(((kc - 2) >> 1) & 1), flag))
+                s_fail = 1;
+        }
+        __syncthreads();
+        if (s_fail)
+            break;
+        // this thread's two pixels
+        const long long P0 = (c0 + kc) * kTcKC + 2 * kp;
+        int pn[2], pp[2], pi[2], pj[2];
+        unsigned tap_ok[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long long P = P0 + u;
+            tap_ok[u] = 0u;
+            pn[u] = 0;
+            pp[u] = 0;
+            pi[u] = 0;
+            pj[u] = 0;
+            if (P < npix) {
+                pn[u] = (int)(P / HW);
+                pp[u] = (int)(P - (long long)pn[u] * HW);
+                pi[u] = pp[u] / W;
+                pj[u] = pp[u] - pi[u] * W;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const int ii = pi[u] + t / 3 - 1, jj = pj[u] + t % 3 - 1;
+                    if (ii >= 0 && ii < H && jj >= 0 && jj < W)
+                        tap_ok[u] |= 1u << t;
+                }
+            }
+        }
+        // A: rows r0 + stripe + 8 q, q = 0..15
+        const int koff = (kp >> 2) * 128 + (kp & 3) * 4;  // byte offset of k = 2 kp in a row
+#pragma unroll 4
+        for (int q = 0; q < 16; ++q) {
+            const int rl = stripe + 8 * q;  // row within the tile
+            const int r = r0 + rl;
+            float v2[2] = {0.0f, 0.0f};
+            if (r < nrows) {
+                const int t = r / cp, c = r - t * cp;
+                if (c < cin) {
+                    const int off = (t / 3 - 1) * W + (t % 3 - 1);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        if ((tap_ok[u] >> t) & 1u)
+                            v2[u] = __ldg(at(x, pn[u], c, HW) + pp[u] + off);
+                }
+            }
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v2[0], v2[1]);
+            *reinterpret_cast<__nv_bfloat162 *>(bufA + (rl >> 3) * 1024 + (rl & 7) * 16 + koff) = h2;
+        }
+        // B: rows o = stripe + 8 q
+        for (int o = stripe; o < Np; o += 8) {
+            float v2[2] = {0.0f, 0.0f};
+            if (o < cout) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (P0 + u < npix)
+                        v2[u] = __ldg(at(dz, pn[u], o, HW) + pp[u]);
+            }
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v2[0], v2[1]);
+            *reinterpret_cast<__nv_bfloat162 *>(bufB + (o >> 3) * 1024 + (o & 7) * 16 + koff) = h2;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = tc_idesc(Np);
+#pragma unroll
+            for (int kk = 0; kk < kTcKC / 16; ++kk) {
+                const uint64_t da = tc_desc(tc_smem(bufA) + kk * 256);
+                const uint64_t db = tc_desc(tc_smem(bufB) + kk * 256);
+                const uint32_t accum = (kc > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(accum));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_smem(&s_bar[buf]))
+                : "memory");
+        }
+    }
+    bool ok = !s_fail && nkc > 0;
+    if (ok)
+        ok = tc_wait(&s_bar[(nkc - 1) & 1], (unsigned)(((nkc - 1) >> 1) & 1), flag);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncwarp();
+    // partial sums of this K range: part[blockIdx.y][r][o] (zero when nothing was summed)
+    const int half = tid >> 7, rl = (warp & 3) * 32 + (tid & 31);
+    const int r = r0 + rl;
+    float *dst = part + ((size_t)blockIdx.y * gridDim.x * kTcM + r) * Np;
+    const bool all_ok = __all_sync(0xffffffffu, ok);
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    for (int o0 = half * (Np / 2); o0 < (half + 1) * (Np / 2); o0 += 8) {
+        uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (all_ok) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7])
+                : "r"(lane_base + (uint32_t)o0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            dst[o0 + q] = __uint_as_float(v[q]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+// dW[o][c][t] = sum over the K splits, in split order, of part[s][t cp + c][o]
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int splits, int mrows, int Np, int cin,
+                               int cout, float *__restrict__ dw)
+{
+    const int cp = (cin + 15) / 16 * 16;
+    const size_t total = (size_t)cout * cin * 9;
+    for (size_t e = blockIdx.x * (size_t)kT + threadIdx.x; e < total; e += (size_t)gridDim.x * kT) {
+        const int o = (int)(e / ((size_t)cin * 9));
+        const int rem = (int)(e - (size_t)o * cin * 9);
+        const int c = rem / 9, t = rem - c * 9;
+        const int r = t * cp + c;
+        double acc = 0.0;
+        for (int sp = 0; sp < splits; ++sp)
+            acc += (double)part[((size_t)sp * mrows + r) * Np + o];
+        dw[e] = (float)acc;
+    }
+}
+
+// db[o] = sum of dz[o] over samples and pixels (FP64, one CTA per output channel)
+__global__ void __launch_bounds__(kT) k_bias_grad(TV dz, int cout, int HW, int nb, float *__restrict__ db)
+{
+    __shared__ double s_red[kT / 32];
+    const int o = blockIdx.x;
+    double acc = 0.0;
+    for (int n = 0; n < nb; ++n) {
+        const float *g = at(dz, n, o, HW);
+        for (int p = threadIdx.x; p < HW; p += kT)
+            acc += g[p];
+    }
+    for (int off = 16; off; off >>= 1)
+        acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0)
+        s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < kT / 32; ++k)
+            v += s_red[k];
+        db[o] = (float)v;
+    }
+}
+
 // ---- gradient of the convolution's input: dx = conv^T(dz) ------------------------
 // dx[c,i,j] = sum_{o,di,dj} w[o,c,di,dj] dz[o, i-di+1, j-dj+1]
 __global__ void __launch_bounds__(kT) k_conv_bwd_x(TV dz, int cout, const __nv_bfloat16 *__restrict__ w,
@@ -723,6 +929,8 @@ struct slpic_unet {
     // parameter change until the next forward repacks them
     __nv_bfloat16 *wtc = nullptr, *wtct = nullptr;
     float *zeros = nullptr;  // zero biases of the transposed convs
+    float *wpart = nullptr;  // K-split partial weight gradients
+    size_t wpart_n = 0;
     bool tc_dirty = true;
     int *d_flag = nullptr;  // a bounded wait of a tensor-core kernel ran out
     cudaStream_t stream = nullptr;
@@ -837,12 +1045,33 @@ void conv_fwd(slpic_unet_t *h, int k, TV x, TV a, int relu, int nb, cudaStream_t
     k_conv_fwd<<<grid, kT, 0, st>>>(x, c.cin, h->pb + c.w_off, h->p + c.b_off, c.cout, a, relu, H, W);
 }
 
+// K split of the tensor-core weight gradient: (M tiles, splits, 64-pixel chunks per split)
+void wgrad_split(const slpic_unet_t *h, const ConvSpec &c, int nb, int *mt, int *splits, int *per)
+{
+    const long long npix = (long long)nb * hwl(h, c.level);
+    const long long nchunk = (npix + kTcKC - 1) / kTcKC;
+    *mt = (9 * ((c.cin + 15) / 16 * 16) + kTcM - 1) / kTcM;
+    long long sp = std::max(1LL, std::min(nchunk, (long long)(2 * 152 + *mt - 1) / *mt));
+    *per = (int)((nchunk + sp - 1) / sp);
+    *splits = (int)((nchunk + *per - 1) / *per);
+}
+
 void conv_bwd(slpic_unet_t *h, int k, TV x, TV dz, TV *dx, int nb, cudaStream_t st)
 {
     const ConvSpec &c = h->conv[k];
     const int H = hl(h, c.level), W = wl(h, c.level);
-    k_conv_bwd_w<<<dim3((unsigned)c.cin, (unsigned)c.cout), kT, 0, st>>>(
-        x, c.cin, dz, c.cout, h->g + c.w_off, h->g + c.b_off, H, W, nb, h->cfg.tensor_cores ? 1 : 0);
+    if (h->cfg.tensor_cores && c.Np <= kTcMaxN) {
+        int mt, splits, per;
+        wgrad_split(h, c, nb, &mt, &splits, &per);
+        k_conv_wgrad_tc<<<dim3((unsigned)mt, (unsigned)splits), kTcThreads, tc_smem_bytes(c.Np), st>>>(
+            x, c.cin, dz, c.cout, c.Np, H, W, nb, per, h->wpart, h->d_flag);
+        k_wgrad_reduce<<<grid_for((size_t)c.cout * c.cin * 9), kT, 0, st>>>(
+            h->wpart, splits, mt * kTcM, c.Np, c.cin, c.cout, h->g + c.w_off);
+        k_bias_grad<<<c.cout, kT, 0, st>>>(dz, c.cout, H * W, nb, h->g + c.b_off);
+    } else {
+        k_conv_bwd_w<<<dim3((unsigned)c.cin, (unsigned)c.cout), kT, 0, st>>>(
+            x, c.cin, dz, c.cout, h->g + c.w_off, h->g + c.b_off, H, W, nb, h->cfg.tensor_cores ? 1 : 0);
+    }
     if (dx && h->cfg.tensor_cores) {
         conv_tc(h, dz, c.cout, h->wtct + c.tct_off, c.Npt, h->zeros, c.cin, *dx, 0, c.level, nb, st);
     } else if (dx) {
@@ -952,6 +1181,21 @@ int ensure_grads(slpic_unet_t *h)
             return rc;
         if (l >= 1 && (rc = alloc_f(h, &h->dpool[l], (size_t)nb * ch(h, l - 1) * hwl(h, l))))
             return rc;
+    }
+    if (h->cfg.tensor_cores) {
+        size_t need = 1;
+        for (const ConvSpec &c : h->conv) {
+            if (c.Np > kTcMaxN)
+                continue;
+            for (int b = 1; b <= nb; ++b) {  // the split depends on the batch of the call
+                int mt, splits, per;
+                wgrad_split(h, c, b, &mt, &splits, &per);
+                need = std::max(need, (size_t)splits * mt * kTcM * c.Np);
+            }
+        }
+        if ((rc = alloc_f(h, &h->wpart, need)))
+            return rc;
+        h->wpart_n = need;
     }
     CKU(h, cudaMemsetAsync(h->m, 0, sizeof(float) * h->nparam, h->stream));
     CKU(h, cudaMemsetAsync(h->v, 0, sizeof(float) * h->nparam, h->stream));
@@ -1080,6 +1324,9 @@ extern "C" int slpic_unet_create(const slpic_unet_config *cfg, slpic_unet_t **ou
                 e = cudaMemset(h->zeros, 0, sizeof(float) * maxc);
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes(kTcMaxN));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tc_smem_bytes(kTcMaxN));
             if (e != cudaSuccess)
                 rc = failu(h, SLPIC_ERR_CUDA, cudaGetErrorString(e));
