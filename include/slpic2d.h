@@ -125,8 +125,10 @@ int slpic2d_fields(slpic2d_t *h, double *rho, double *phi, float *Ex, float *Ey)
 /* The int64 deposit of species s for the current time level ((ny+1)*nx). */
 int slpic2d_charge_raw(slpic2d_t *h, int s, int64_t *acc);
 int slpic2d_particle_count(slpic2d_t *h, int s, int64_t *n);
-/* Copy out species s (capacity *n on entry, count on return; order is not
- * preserved across steps). */
+/* Copy out species s (capacity *n on entry, count on return).  Order: by cell
+ * after slpic2d_prepare and after every compacting step (every 16th), when the
+ * particles are sorted by cell (a counting sort; holes dropped); in between, each
+ * particle keeps its slot; within a cell the order is arbitrary. */
 int slpic2d_get_particles(slpic2d_t *h, int s, int32_t *cell, float *offset, float *v,
                           int64_t *n);
 int slpic2d_diagnostics(slpic2d_t *h, slpic2d_diag *out);

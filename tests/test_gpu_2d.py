@@ -370,3 +370,23 @@ def test_warp_summed_deposit_is_the_per_particle_deposit():
         ref = orc.poisson2d_direct(rho, prob["dx"], prob["phi_lo"], prob["phi_hi"])
         assert np.abs(phi - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), n
     g.close()
+
+
+def test_sort_drops_holes_when_particles_are_added_later():
+    """In-place steps leave holes; particles loaded afterwards are appended behind
+    them; slpic2d_prepare sorts again: the holes go, the live particles stay."""
+    prob = _prob(nx=32, ny=24, ppc=6, v0=0.3, dt=1.5)
+    st = inputs.load_state2d(prob, seed=71)
+    g = _sim(prob, st)
+    g.step(5)  # in-place steps: absorbed particles leave holes
+    d = g.diagnostics()
+    before = [g.particles(s)[0].size for s in range(2)]
+    assert before == d["count"][:2]
+    extra = inputs.load_state2d(dict(prob, species=[dict(sp, ppc=1) for sp in prob["species"]]), seed=72)
+    g.load_state(extra)
+    g.prepare()
+    for s in range(2):
+        c, _, _ = g.particles(s)
+        assert c.size == before[s] + extra[s][0].size
+        assert np.all(c >= 0) and np.all(np.diff(c) >= 0)
+    g.close()
