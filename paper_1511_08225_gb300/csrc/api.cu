@@ -612,8 +612,11 @@ static int capture(slpic_t *h, long long first_step, int nsteps, bool timed,
         // record inside a capture only orders streams)
         if (timed)
             cudaEventRecordWithFlags(h->events[4 * k], h->cap_stream, cudaEventRecordExternal);
+        // one SM left free: the TMA kernel holds a whole SM per CTA, so other work
+        // on the GPU (the overlapped read-back's potential kernel) would otherwise
+        // delay one of its CTAs, and with it the kernel, by that work's length
         if (!compact && h->tma_stages && h->particle_kernel == 0)
-            launch_particles_tma(h->p, h->num_sms, h->tma_stages, h->cap_stream);
+            launch_particles_tma(h->p, std::max(1, h->num_sms - 1), h->tma_stages, h->cap_stream);
         else
             launch_particles(h->p, compact ? h->ctas_c : h->ctas, compact, h->cap_stream);
         if (timed)
