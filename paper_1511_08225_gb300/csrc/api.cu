@@ -351,7 +351,10 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     h->ctas = std::max(1, sms * occ / ns);
     h->ctas_c = std::max(1, sms * occ_c / ns);
     h->small_ctas = std::max(1, sms * 2 / ns);
-    h->hard_ctas = sms * 8;
+    // k_hard: 2 CTAs of 256 threads per SM, one lane per listed particle for the
+    // ~20k-80k a step lists here (a grid-stride loop beyond); measured against 4 and 8
+    // per SM, whose idle CTAs cost about a microsecond
+    h->hard_ctas = sms * 2;
     CKC(configure_particles_tma(nn, &h->tma_stages));
 
     StepParams &p = h->p;
