@@ -19,6 +19,12 @@ Readings of the paper that this file takes (the paper is silent on them):
 the loaded velocity is v^{-1/2}; rho^0 is deposited with beta(|v^{-1/2}|);
 injected particles are deposited into rho^{n+1} with beta of their initial
 velocity and take their first push in the next step.
+
+A speed limit that varies in space (Sec. II) is given as prob["v0_profile"]:
+one factor lam_c > 0 per cell, so that a particle in cell c has the limit
+v0_s lam_c.  The push of a step takes the factor of the cell the particle starts
+in, the deposit that of the cell it is deposited from, the wall source that of
+the last cell (the one the entering particles are placed in).
 """
 from __future__ import annotations
 
@@ -81,14 +87,14 @@ def lib():
         L.orc_efield1d.restype = None
         L.orc_efield1d.argtypes = [_I, _I, _D, _P, _P]
         L.orc_deposit1d.restype = None
-        L.orc_deposit1d.argtypes = [_I, _I, _D, _L, _P, _P, _P, _I, _D, _D, _P]
+        L.orc_deposit1d.argtypes = [_I, _I, _D, _L, _P, _P, _P, _I, _D, _P, _D, _P]
         L.orc_beta_f32.restype = ctypes.c_float
         L.orc_beta_f32.argtypes = [_I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float]
         L.orc_deposit_q40.restype = None
-        L.orc_deposit_q40.argtypes = [_I, _I, _L, _P, _P, _P, _I, ctypes.c_float, _P]
+        L.orc_deposit_q40.argtypes = [_I, _I, _L, _P, _P, _P, _I, ctypes.c_float, _P, _P]
         L.orc_push1d.restype = None
-        L.orc_push1d.argtypes = [_I, _I, _D, _D, _P, _L, _P, _P, _P, _D, _I, _D, _P]
+        L.orc_push1d.argtypes = [_I, _I, _D, _D, _P, _L, _P, _P, _P, _D, _I, _D, _P, _P]
         L.orc_splitmix64_at.restype = ctypes.c_uint64
         L.orc_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         L.orc_stream_key.restype = ctypes.c_uint64
@@ -197,15 +203,21 @@ def efield1d(phi: np.ndarray, dx: float, periodic: bool) -> np.ndarray:
     return E
 
 
-def deposit_q40(n_cells, periodic, cell, offset, v, kind, v0) -> np.ndarray:
-    """The quantised int64 deposit rule (bit-exact contract, see the C file)."""
+def deposit_q40(n_cells, periodic, cell, offset, v, kind, v0, lam=None) -> np.ndarray:
+    """The quantised int64 deposit rule (bit-exact contract, see the C file);
+    lam: per-cell FP32 factors of v0, or None."""
     cell = np.ascontiguousarray(cell, dtype=np.int32)
     offset = np.ascontiguousarray(offset, dtype=np.float32)
     v = np.ascontiguousarray(v, dtype=np.float32).reshape(-1, 3)
     nn = n_cells if periodic else n_cells + 1
     acc = np.zeros(nn, dtype=np.int64)
+    lam_p = None
+    if lam is not None:
+        lam = np.ascontiguousarray(lam, dtype=np.float32)
+        assert lam.size == n_cells
+        lam_p = _ptr(lam)
     lib().orc_deposit_q40(n_cells, int(periodic), cell.size, _ptr(cell), _ptr(offset),
-                          _ptr(v), kind, np.float32(v0), _ptr(acc))
+                          _ptr(v), kind, np.float32(v0), lam_p, _ptr(acc))
     return acc
 
 
@@ -284,6 +296,7 @@ class OracleSim:
         self.nn = self.N if self.periodic else self.N + 1
         self.sp = prob["species"]
         ns = len(self.sp)
+        self.set_profile(prob.get("v0_profile"))
         self.x = [np.zeros(0) for _ in range(ns)]
         self.v = [np.zeros((0, 3)) for _ in range(ns)]
         self.step_index = 0
@@ -295,6 +308,27 @@ class OracleSim:
         self.rho = np.zeros(self.nn)
         self.phi = np.zeros(self.nn)
         self.E = np.zeros(self.nn)
+
+    def set_profile(self, lam):
+        """Per-cell factors of every species' v0 (FP32 numbers, > 0), or None
+        for a uniform limit; takes effect from the next push or deposit."""
+        if lam is None:
+            self.lam = None
+            return
+        lam = np.asarray(lam, dtype=np.float32).astype(np.float64)
+        assert lam.shape == (self.N,) and (lam > 0).all()
+        self.lam = np.ascontiguousarray(lam)
+
+    def _lam_ptr(self):
+        return None if self.lam is None else _ptr(self.lam)
+
+    def v0_of_cells(self, s: int, cells) -> np.ndarray:
+        """The FP64 limit of species s in the given cells."""
+        v0 = float(self.sp[s]["v0"])
+        cells = np.asarray(cells, dtype=np.int64)
+        if self.lam is None:
+            return np.full(cells.shape, v0)
+        return v0 * self.lam[cells]
 
     # --- loading -----------------------------------------------------------
     def load(self, s: int, x: np.ndarray, v: np.ndarray):
@@ -320,8 +354,8 @@ class OracleSim:
             x = np.ascontiguousarray(self.x[s])
             v = np.ascontiguousarray(self.v[s])
             L.orc_deposit1d(self.N, int(self.periodic), self.dx, x.size, _ptr(x), _ptr(v),
-                            None, int(sp["kind"]), float(sp["v0"]), float(sp["w"]),
-                            _ptr(self.dens[s]))
+                            None, int(sp["kind"]), float(sp["v0"]), self._lam_ptr(),
+                            float(sp["w"]), _ptr(self.dens[s]))
         self.rho = sum(float(sp["q"]) * self.dens[s] for s, sp in enumerate(self.sp))
 
     def solve(self, t=None):
@@ -356,7 +390,7 @@ class OracleSim:
             flux = np.zeros(2, dtype=np.int64)
             L.orc_push1d(self.N, int(self.periodic), self.dx, self.dt, _ptr(E), n, _ptr(x),
                          _ptr(v), _ptr(alive), float(sp["q"]) / float(sp["m"]),
-                         int(sp["kind"]), float(sp["v0"]), _ptr(flux))
+                         int(sp["kind"]), float(sp["v0"]), self._lam_ptr(), _ptr(flux))
             keep = alive.astype(bool)
             self.x[s] = x[keep]
             self.v[s] = v[keep]
@@ -407,8 +441,8 @@ class OracleSim:
             vth = np.sqrt(float(sp["T"]) / float(sp["m"]))
             if int(src.get("mode", SRC_NONE)) == SRC_WALL:
                 L.orc_inject_wall(int(self.prob["seed"]), self.step_index, s, k, self.N,
-                                  self.dx, self.dt, vth, int(sp["kind"]), float(sp["v0"]),
-                                  _ptr(x), _ptr(v))
+                                  self.dx, self.dt, vth, int(sp["kind"]),
+                                  float(self.v0_of_cells(s, [self.N - 1])[0]), _ptr(x), _ptr(v))
             else:
                 L.orc_inject(int(self.prob["seed"]), self.step_index, s, k,
                              np.float32(src["lo_cells"]), np.float32(src["len_cells"]),
@@ -431,7 +465,8 @@ class OracleSim:
         for s, sp in enumerate(self.sp):
             v = self.v[s]
             r = np.sqrt((v * v).sum(axis=1))
-            b = _beta_vec(int(sp["kind"]), r, float(sp["v0"]))
+            cells = np.minimum(np.floor(self.x[s] / self.dx).astype(np.int64), self.N - 1)
+            b = _beta_vec(int(sp["kind"]), r, self.v0_of_cells(s, cells))
             w = float(sp["w"])
             out["count"].append(int(v.shape[0]))
             out["sum_w"].append(w * v.shape[0])

@@ -362,14 +362,28 @@ void orc_efield1d(int n_cells, int periodic, double dx, const double *phi, doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* A speed limit that varies in space (Sec. II: beta, and so v0, may depend */
+/* on position).  Reading: one factor lam[c] > 0 per cell, shared by the    */
+/* species, so that the limit of a particle in cell c is v0 lam[c]; with    */
+/* lam NULL the limit is v0 everywhere.  beta(x, v) is evaluated where the  */
+/* particle is: the push of a step takes the limit of the cell it starts    */
+/* the step in (where E is gathered), the charge assignment the limit of    */
+/* the cell it is deposited from.                                           */
+/* ------------------------------------------------------------------------ */
+static double v0_at(double v0, const double *lam, int c)
+{
+    return lam ? v0 * lam[c] : v0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Charge assignment, Appendix A: rho^{n+1} = sum_p w_p beta(|v^{n+1/2}|)    */
 /* S(x - x_p^{n+1}), with linear (cloud-in-cell) S as the PIC scatter of    */
 /* Sec. II.  Output: number density n_j += w beta S_j / dx (the caller      */
 /* multiplies by the species charge).                                       */
 /* ------------------------------------------------------------------------ */
 void orc_deposit1d(int n_cells, int periodic, double dx, long n, const double *x,
-                   const double *v, const uint8_t *alive, int kind, double v0, double w,
-                   double *dens)
+                   const double *v, const uint8_t *alive, int kind, double v0,
+                   const double *lam, double w, double *dens)
 {
     int N = n_cells;
     for (long p = 0; p < n; ++p) {
@@ -381,7 +395,7 @@ void orc_deposit1d(int n_cells, int periodic, double dx, long n, const double *x
         double d = xi - cf;
         double r = sqrt(v[3 * p] * v[3 * p] + v[3 * p + 1] * v[3 * p + 1] +
                         v[3 * p + 2] * v[3 * p + 2]);
-        double b = orc_beta(kind, r, v0);
+        double b = orc_beta(kind, r, v0_at(v0, lam, c));
         int c1 = periodic ? (c + 1) % N : c + 1;
         dens[c] += w * b * (1.0 - d) / dx;
         dens[c1] += w * b * d / dx;
@@ -398,6 +412,8 @@ void orc_deposit1d(int n_cells, int periodic, double dx, long n, const double *x
 /*   qT = rint(beta * 2^40), qR = rint((beta*d) * 2^40), qL = qT - qR       */
 /*   acc[c] += qL, acc[c+1 (mod N if periodic)] += qR   (int64)             */
 /* Integer sums are exact and order-free, so sum_j acc_j = sum_p qT_p.       */
+/* With a per-cell factor lam (FP32), the limit in cell c is the FP32        */
+/* product v0 * lam[c], rounded to nearest.                                  */
 /* ------------------------------------------------------------------------ */
 float orc_beta_f32(int kind, float vx, float vy, float vz, float v0)
 {
@@ -413,7 +429,7 @@ float orc_beta_f32(int kind, float vx, float vy, float vz, float v0)
 
 void orc_deposit_q40(int n_cells, int periodic, long n, const int32_t *cell,
                      const float *offset, const float *v, int kind, float v0,
-                     int64_t *acc)
+                     const float *lam, int64_t *acc)
 {
     int N = n_cells;
     const float scale = 1099511627776.0f; /* 2^40 */
@@ -421,7 +437,8 @@ void orc_deposit_q40(int n_cells, int periodic, long n, const int32_t *cell,
         int c = cell[p];
         if (c < 0)
             continue;
-        float b = orc_beta_f32(kind, v[3 * p], v[3 * p + 1], v[3 * p + 2], v0);
+        float v0c = lam ? v0 * lam[c] : v0;
+        float b = orc_beta_f32(kind, v[3 * p], v[3 * p + 1], v[3 * p + 2], v0c);
         float bd = b * offset[p];
         int64_t qR = llrintf(bd * scale);
         int64_t qT = llrintf(b * scale);
@@ -440,10 +457,12 @@ void orc_deposit_q40(int n_cells, int periodic, long n, const int32_t *cell,
 /* Walls (Sec. IV): a particle with x < 0 or x >= L is absorbed; on a      */
 /* periodic grid x wraps into [0, L).                                       */
 /* alive[p]: in/out.  flux[0] / flux[1] count absorptions at x=0 / x=L.    */
+/* lam: per-cell factors of v0 (see v0_at) or NULL; both the integral and   */
+/* the move take the limit of the cell the particle starts the step in.     */
 /* ------------------------------------------------------------------------ */
 void orc_push1d(int n_cells, int periodic, double dx, double dt, const double *E, long n,
                 double *x, double *v, uint8_t *alive, double qm, int kind, double v0,
-                long *flux)
+                const double *lam, long *flux)
 {
     int N = n_cells;
     double L = dx * N;
@@ -458,11 +477,12 @@ void orc_push1d(int n_cells, int periodic, double dx, double dt, const double *E
         double Ep = (1.0 - d) * E[c] + d * E[c1];
         double a[3] = {qm * Ep, 0.0, 0.0};
         double *vp = v + 3 * p;
-        double tau = orc_beta_integral(kind, vp, a, dt, v0);
+        double v0p = v0_at(v0, lam, c);
+        double tau = orc_beta_integral(kind, vp, a, dt, v0p);
         for (int i = 0; i < 3; ++i)
             vp[i] += a[i] * tau;
         double r = sqrt(vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2]);
-        double b = orc_beta(kind, r, v0);
+        double b = orc_beta(kind, r, v0p);
         double xn = x[p] + b * vp[0] * dt;
         if (periodic) {
             xn -= L * floor(xn / L);

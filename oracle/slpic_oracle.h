@@ -38,17 +38,18 @@ void orc_efield1d(int n_cells, int periodic, double dx, const double *phi, doubl
 
 /* Appendix A charge assignment (FP64) and the quantised FP32 -> int64 rule */
 void orc_deposit1d(int n_cells, int periodic, double dx, long n, const double *x,
-                   const double *v, const uint8_t *alive, int kind, double v0, double w,
-                   double *dens);
+                   const double *v, const uint8_t *alive, int kind, double v0,
+                   const double *lam, double w, double *dens);
 float orc_beta_f32(int kind, float vx, float vy, float vz, float v0);
 void orc_deposit_q40(int n_cells, int periodic, long n, const int32_t *cell,
                      const float *offset, const float *v, int kind, float v0,
-                     int64_t *acc);
+                     const float *lam, int64_t *acc);
 
-/* Appendix A gather/push/move with Sec. IV walls */
+/* Appendix A gather/push/move with Sec. IV walls; lam (per-cell factors of  */
+/* v0, Sec. II: the limit may vary in space) or NULL in all three            */
 void orc_push1d(int n_cells, int periodic, double dx, double dt, const double *E, long n,
                 double *x, double *v, uint8_t *alive, double qm, int kind, double v0,
-                long *flux);
+                const double *lam, long *flux);
 
 /* counter-based SplitMix64 and the volume source */
 uint64_t orc_splitmix64_at(uint64_t key, uint64_t i);

@@ -200,7 +200,7 @@ def test_q40_sum_equals_particle_total_and_fp64_deposit():
         x = (cell.astype(np.float64) + off.astype(np.float64)) * 1.0
         orc.lib().orc_deposit1d(N, int(periodic), 1.0, x.size, orc._ptr(x),
                                 orc._ptr(np.ascontiguousarray(v, dtype=np.float64)), None,
-                                HEAV, 0.3, 1.0, orc._ptr(dens))
+                                HEAV, 0.3, None, 1.0, orc._ptr(dens))
         np.testing.assert_allclose(acc / 2.0 ** 40, dens, rtol=1e-5, atol=1e-5)
 
 
