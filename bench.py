@@ -39,11 +39,23 @@ PPC = 1000
 N_CELLS = 4096
 
 
-def workload_config(n_gpus):
+def v0_profile(kind, n_cells):
+    """Per-cell factors of v0 for --v0-profile: 'sine' is 1/2 at the walls and 1
+    at the centre, lam_c = 1/2 + 1/2 sin(pi x_c / L) at the cell centres."""
+    if kind == "none":
+        return None
+    x = (np.arange(n_cells) + 0.5) / n_cells
+    return (0.5 + 0.5 * np.sin(np.pi * x)).astype(np.float32)
+
+
+def workload_config(n_gpus, profile="none"):
+    limit = ("v0=0.02 v_te" if profile == "none" else
+             "v0=0.02 v_te x lam(x), lam = 1/2 + 1/2 sin(pi x/L) per cell (speed limit varying "
+             "in space)")
     return {
         "workload": "1D bounded argon-like sheath (1D3V): 4096 cells, dx=0.5 lambda_De, "
                     "m_i/m_e=73440, T_e/T_i=10, 1000 ppc/species (8.19M particles at load), "
-                    "Heaviside beta, v0=0.02 v_te, dt=dx/v0, phi=0 absorbing walls, "
+                    f"Heaviside beta, {limit}, dt=dx/v0, phi=0 absorbing walls, "
                     "central LOSS_MATCHED source",
         "n_cells": N_CELLS, "ppc_per_species": PPC, "v0": V0, "species": 2,
         "precision": "FP32 push, int64 fixed-point deposit, FP64 Poisson",
@@ -202,6 +214,9 @@ def run_reference(args):
     from oracle import oracle as orc
     orc.build()
     prob = make_problem(inputs.SEED)
+    lam = v0_profile(args.v0_profile, prob["n_cells"])
+    if lam is not None:
+        prob["v0_profile"] = lam
     state = inputs.load_state(prob)
     # calibrate the per-particle cost, then size each step's sample so that
     # warmup + steps end in about two minutes
@@ -232,7 +247,8 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "impl": "reference", "config": workload_config(args.gpus),
+        "data": "synthetic", "impl": "reference",
+        "config": workload_config(args.gpus, args.v0_profile),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -275,6 +291,9 @@ def run_gpu(args):
 
     seed = inputs.SEED + rank
     prob = make_problem(seed)
+    lam = v0_profile(args.v0_profile, prob["n_cells"])
+    if lam is not None:
+        prob["v0_profile"] = lam
     state = inputs.load_state(prob)
     n_load = sum(s[0].size for s in state)
 
@@ -337,8 +356,10 @@ def run_gpu(args):
         push_ms = t_max / args.steps
     achieved = BYTES_PER_PARTICLE_STEP * n_mean / (push_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": profiled_traffic(n_mean),
-            "kernel": (f"{'k_particles_tma' if tuning['particle_kernel'] == 0 else 'k_particles'} "
+            "frac": achieved / peak,
+            "traffic": profiled_traffic(n_mean) if lam is None else None,
+            "kernel": (f"{'k_particles_tma' if tuning['particle_kernel'] == 0 else 'k_particles'}"
+                       f"{'' if lam is None else ' (speed-limit profile variant)'} "
                        f"(in-place steps; k_particles_compact every {tuning['compact_every']})"),
             "kernel_ms": push_ms, "hard_kernel_ms": hard_ms,
             "field_kernel_ms": field_ms, "iterative_pushes_per_step": iterative_per_step,
@@ -355,7 +376,7 @@ def run_gpu(args):
     # the plain FP64 form of the same step on the same workload (the comparison
     # point of the metric), after the same warm-up
     fp64 = None
-    if rank == 0 and not args.no_fp64:
+    if rank == 0 and not args.no_fp64 and lam is None:  # the FP64 form has no profile
         fp64 = run_fp64(prob, state, args, binding, torch, stream, value)
 
     cpu = None
@@ -370,7 +391,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "impl": "gb300", "config": workload_config(world),
+            "data": "synthetic", "impl": "gb300",
+            "config": workload_config(world, args.v0_profile),
             "particles_at_load": n_load, "particles_timed_mean": n_mean,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_form": fp64,
             "gpu_launches": kps * args.steps, "clocks": clocks.summary(),
@@ -917,6 +939,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--v0-profile", default="none", choices=["none", "sine"],
+                    help="sheath1d: a speed limit varying in space (per-cell factors of v0)")
     ap.add_argument("--workload", default="sheath1d",
                     choices=["sheath1d", "plasma2d", "batch", "paper_sheath", "unet2d"],
                     help="sheath1d (the headline), plasma2d (2D3V + CG), batch (many "

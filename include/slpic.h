@@ -252,8 +252,9 @@ int slpic_diagnostics(slpic_t *h, int instance, slpic_diag *out);
  * remainders, step index) into a host buffer.  With buf == NULL, *size
  * receives the bytes needed.  Restoring into a handle created from the same
  * config continues bit for bit.  Settings changed after creation
- * (slpic_set_speed_limit, slpic_set_timestep, slpic_set_wave) are not part of
- * the checkpoint: set them again on the restored handle. */
+ * (slpic_set_speed_limit, slpic_set_speed_limit_profile, slpic_set_timestep,
+ * slpic_set_wave) are not part of the checkpoint: set them again on the
+ * restored handle. */
 int slpic_save(slpic_t *h, void *buf, size_t *size);
 int slpic_restore(slpic_t *h, const void *buf, size_t size);
 
@@ -313,7 +314,7 @@ int slpic_get_tuning(slpic_t *h, slpic_tuning *out);
 int slpic_set_tuning(slpic_t *h, const slpic_tuning *t);
 int slpic_autotune(slpic_t *h, int32_t steps_per_trial, slpic_tuning *chosen, double *ms_per_step);
 
-/* ---- a speed limit that changes in time (Sec. II; the Summary) -------------- */
+/* ---- a speed limit that changes in time or space (Sec. II; the Summary) ----- */
 
 /* Change the speed limit v0 of a speed-limited species from the next step on
  * (the paper notes that v0 may vary in time, e.g. raised mid-run to tighten or
@@ -336,8 +337,28 @@ int slpic_set_wave(slpic_t *h, double phi0, double k, double vphi, double t_ramp
 /* Change the timestep from the next step on, with the CFL checks of
  * slpic_create.  The stored velocities are taken as v^{n+1/2} of the new step
  * (the usual first-order restart of a leapfrog); the wall source's rate per step
- * follows dt.  Not available on a batch handle. */
+ * follows dt.  With a speed-limit profile, dt * v0 * (its largest factor) <= dx.
+ * Not available on a batch handle. */
 int slpic_set_timestep(slpic_t *h, double dt);
+
+/* A speed limit that varies in space (Sec. II: beta, and so v0, may depend on
+ * position, e.g. on a grid whose spacing varies).  lambda: n_cells factors
+ * (host, FP64, copied; converted to FP32, each finite and > 0 there), one per
+ * cell, shared by the species: a speed-limited species s in cell c has the limit
+ * v0_s * lambda_c, the FP32 product of its FP32 v0 and factor rounded to
+ * nearest.  The push of a step (the integral of beta and the move) takes the
+ * limit of the cell the particle starts the step in, where E is gathered; every
+ * deposit (the particle step's, the loaded state's, the source's) takes the limit
+ * of the cell the particle is deposited from; the wall source places entering
+ * particles with the limit of cell n_cells - 1.  slpic_charge_raw's rule holds
+ * with that limit.  lambda == NULL returns to the uniform limit.  Applies from
+ * the next step (or prepare); the particles and their g-weights are kept.
+ * Errors: SLPIC_ERR_INVALID for a batch handle, n_cells other than the grid's,
+ * or a factor that is not finite and > 0; SLPIC_ERR_CFL if dt * v0_s * (largest
+ * factor) > dx for a speed-limited species.  Every particle kernel has a
+ * variant that reads the profile (compiled apart, so that the uniform limit
+ * pays nothing for it); results do not depend on which kernel runs. */
+int slpic_set_speed_limit_profile(slpic_t *h, const double *lambda, int n_cells);
 
 /* ---- allocation-free particle step ------------------------------------------ */
 

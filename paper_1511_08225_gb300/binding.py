@@ -41,7 +41,7 @@ EXPORTS = (
     "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernels_per_step",
     "slpic_particle_step_noalloc", "slpic_create_batch", "slpic_set_speed_limit",
     "slpic_set_timestep", "slpic_set_wave", "slpic_get_tuning", "slpic_set_tuning",
-    "slpic_autotune", "slpic_fields_async",
+    "slpic_autotune", "slpic_fields_async", "slpic_set_speed_limit_profile",
 )
 
 
@@ -106,6 +106,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "slpic_create": (I, [ctypes.POINTER(slpic_config), ctypes.POINTER(P)]),
         "slpic_create_batch": (I, [ctypes.POINTER(slpic_config), I, ctypes.POINTER(P)]),
         "slpic_set_speed_limit": (I, [P, I, I, D]),
+        "slpic_set_speed_limit_profile": (I, [P, P, I]),
         "slpic_set_timestep": (I, [P, D]),
         "slpic_set_wave": (I, [P, D, D, D, D]),
         "slpic_get_tuning": (I, [P, ctypes.POINTER(slpic_tuning)]),
@@ -363,6 +364,12 @@ class Simulation:
         self.nn = int(prob["n_cells"]) + (0 if prob["periodic"] else 1)
         self.ns = len(prob["species"])
         self.h = slpic_create(self.cfg)
+        if prob.get("v0_profile") is not None:
+            try:
+                slpic_set_speed_limit_profile(self.h, prob["v0_profile"])
+            except SlpicError:
+                self.close()
+                raise
 
     def close(self):
         if self.h:
@@ -425,6 +432,17 @@ class Simulation:
 def slpic_set_speed_limit(h, instance, species, v0):
     _check(h, load_library().slpic_set_speed_limit(h, instance, species, v0),
            "slpic_set_speed_limit")
+
+
+def slpic_set_speed_limit_profile(h, lam):
+    """Per-cell factors of v0 (one per cell), or None for a uniform limit."""
+    if lam is None:
+        rc = load_library().slpic_set_speed_limit_profile(h, None, 0)
+    else:
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        rc = load_library().slpic_set_speed_limit_profile(
+            h, lam.ctypes.data_as(ctypes.c_void_p), int(lam.size))
+    _check(h, rc, "slpic_set_speed_limit_profile")
 
 
 def slpic_set_timestep(h, dt):

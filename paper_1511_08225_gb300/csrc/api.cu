@@ -50,6 +50,8 @@ struct slpic_sim {
     int32_t *d_hard[kMaxSpecies] = {};
     double *d_diag = nullptr;
     int *d_bad = nullptr;
+    float *d_lam = nullptr;  // speed-limit profile (slpic_set_speed_limit_profile)
+    double lam_max = 1.0;    // its largest factor (1 without a profile)
     void *d_stage = nullptr;  // load/read-back staging
     size_t stage_bytes = 0;
 
@@ -243,6 +245,7 @@ static void free_all(slpic_t *h)
     cudaFree(h->d_rho);
     cudaFree(h->d_diag);
     cudaFree(h->d_bad);
+    cudaFree(h->d_lam);
     cudaFree(h->d_stage);
     for (int s = 0; s < kMaxSpecies; ++s) {
         for (int b = 0; b < 2; ++b) {
@@ -1149,11 +1152,52 @@ extern "C" int slpic_set_speed_limit(slpic_t *h, int instance, int species, doub
         return fail(h, SLPIC_ERR_INVALID, "species has no speed limit (beta == 1)");
     if (!(v0 > 0) || !std::isfinite(v0))
         return fail(h, SLPIC_ERR_INVALID, "v0 must be > 0");
-    if (h->cfg.dt * v0 > h->cfg.dx)
-        return fail(h, SLPIC_ERR_CFL, "dt * v0 > dx: lower the timestep first");
+    if (h->cfg.dt * v0 * h->lam_max > h->cfg.dx)
+        return fail(h, SLPIC_ERR_CFL, "dt * v0 * (largest profile factor) > dx: lower the timestep first");
     CK(h, cudaStreamSynchronize(h->stream));
     h->cfg.species[species].v0 = v0;
     h->p.sp[species].v0 = (float)v0;
+    drop_graphs(h);
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_set_speed_limit_profile(slpic_t *h, const double *lambda, int n_cells)
+{
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (!lambda) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->p.lam = nullptr;
+        h->lam_max = 1.0;
+        drop_graphs(h);
+        return SLPIC_OK;
+    }
+    if (n_cells != h->cfg.n_cells)
+        return fail(h, SLPIC_ERR_INVALID, "the profile needs one factor per cell");
+    std::vector<float> lam32(n_cells);
+    double mx = 0.0;
+    for (int c = 0; c < n_cells; ++c) {
+        lam32[c] = (float)lambda[c];
+        if (!(lambda[c] > 0) || !std::isfinite(lambda[c]) || !(lam32[c] > 0.0f) ||
+            !std::isfinite(lam32[c]))
+            return fail(h, SLPIC_ERR_INVALID, "profile factors must be finite and > 0 in FP32");
+        mx = std::max(mx, (double)lam32[c]);
+    }
+    for (int s = 0; s < h->ns; ++s) {
+        const slpic_species &sp = h->cfg.species[s];
+        if (sp.beta_kind != SLPIC_BETA_ONE && h->cfg.dt * sp.v0 * mx > h->cfg.dx)
+            return fail(h, SLPIC_ERR_CFL, "dt * v0 * (largest factor) > dx for species " +
+                                              std::to_string(s));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!h->d_lam)
+        CK(h, cudaMalloc(&h->d_lam, sizeof(float) * n_cells));
+    CK(h, cudaMemcpy(h->d_lam, lam32.data(), sizeof(float) * n_cells, cudaMemcpyHostToDevice));
+    h->p.lam = h->d_lam;
+    h->lam_max = mx;
     drop_graphs(h);
     return SLPIC_OK;
 }
@@ -1197,8 +1241,9 @@ extern "C" int slpic_set_timestep(slpic_t *h, double dt)
         return fail(h, SLPIC_ERR_INVALID, "dt must be > 0");
     for (int s = 0; s < h->ns; ++s) {
         const slpic_species &sp = h->cfg.species[s];
-        if (sp.beta_kind != SLPIC_BETA_ONE && dt * sp.v0 > h->cfg.dx)
-            return fail(h, SLPIC_ERR_CFL, "dt * v0 > dx for species " + std::to_string(s));
+        if (sp.beta_kind != SLPIC_BETA_ONE && dt * sp.v0 * h->lam_max > h->cfg.dx)
+            return fail(h, SLPIC_ERR_CFL, "dt * v0 > dx for species " + std::to_string(s) +
+                                              " (v0 times the largest profile factor)");
         if (sp.beta_kind == SLPIC_BETA_ONE && h->cfg.max_speed > 0 &&
             dt * h->cfg.max_speed > h->cfg.dx)
             return fail(h, SLPIC_ERR_CFL, "dt * max_speed > dx");

@@ -114,6 +114,7 @@ __device__ __forceinline__ void list_hard(bool hard, long long i, const SpeciesD
 
 // Bodies of the kernels take the parameters by reference (kernel parameter space
 // for one simulation, shared memory for a batch) and the CTA's share of the work.
+template <bool kProf>
 __device__ __forceinline__ void particles_compact(const StepParams &p, int s, int cta, int nctas)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -169,10 +170,11 @@ __device__ __forceinline__ void particles_compact(const StepParams &p, int s, in
             bool hard = false;
             if (live[k]) {
                 float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
+                const float v0n = v0_at<kProf>(p, sp, c[k]);
                 float vx;
-                if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, sp.v0, vx)) {
+                if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, v0n, vx)) {
                     int wall = 0;
-                    live[k] = move_and_deposit(p, sp, dep, c[k], q[k], vx, wall);
+                    live[k] = move_and_deposit<kProf>(p, sp, dep, c[k], q[k], vx, wall, v0n);
                     if (!live[k])
                         atomicAdd(&s_abs[wall], 1u);
                 } else {
@@ -199,6 +201,7 @@ constexpr int kWT = 32 * kWI;    // particles per warp-tile
 
 size_t particle_inplace_smem_bytes(int nn) { return (size_t)nn * 3 * sizeof(unsigned); }
 
+template <bool kProf>
 __device__ __forceinline__ void particles_inplace(const StepParams &p, int s, int cta, int nctas)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -261,10 +264,11 @@ __device__ __forceinline__ void particles_inplace(const StepParams &p, int s, in
                     __stcs(cout + i, -1);  // a hole stays a hole
                 } else {
                     float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
+                    const float v0n = v0_at<kProf>(p, sp, c[k]);
                     float vx;
-                    if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, sp.v0, vx)) {
+                    if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, v0n, vx)) {
                         int wall = 0;
-                        if (move_and_deposit(p, sp, dep, c[k], q[k], vx, wall)) {
+                        if (move_and_deposit<kProf>(p, sp, dep, c[k], q[k], vx, wall, v0n)) {
                             __stcs(cout + i, c[k]);
                             __stcs(vout + i, q[k]);
                         } else {
@@ -396,6 +400,7 @@ __device__ __forceinline__ void tma_share(long long n, int cta, int nctas, long 
     t1 = nt * (cta + 1) / nctas;
 }
 
+template <bool kProf>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_constant__ StepParams p,
                                                                  int stages)
 {
@@ -504,10 +509,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
                             __stcs(cout + i, -1);  // a hole stays a hole
                         } else {
                             float ax = gather_ax(p, sp, s_E, c[m], q[m].x);
+                            const float v0n = v0_at<kProf>(p, sp, c[m]);
                             float vx;
-                            if (push_vx_easy(sp.kind, q[m].y, q[m].z, q[m].w, ax, p.dt, sp.v0, vx)) {
+                            if (push_vx_easy(sp.kind, q[m].y, q[m].z, q[m].w, ax, p.dt, v0n, vx)) {
                                 int wall = 0;
-                                if (move_and_deposit(p, sp, dep, c[m], q[m], vx, wall)) {
+                                if (move_and_deposit<kProf>(p, sp, dep, c[m], q[m], vx, wall, v0n)) {
                                     __stcs(cout + i, c[m]);
                                     __stcs(vout + i, q[m]);
                                 } else {
@@ -566,14 +572,17 @@ __device__ __forceinline__ void load_params(StepParams &dst, const StepParams *s
     __syncthreads();
 }
 
+// kProf: the speed-limit profile p.lam is set
+template <bool kProf>
 __global__ void __launch_bounds__(kPB, 3) k_particles_compact(const __grid_constant__ StepParams p)
 {
-    particles_compact(p, blockIdx.y, blockIdx.x, gridDim.x);
+    particles_compact<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
+template <bool kProf>
 __global__ void __launch_bounds__(kPB, 4) k_particles(const __grid_constant__ StepParams p)
 {
-    particles_inplace(p, blockIdx.y, blockIdx.x, gridDim.x);
+    particles_inplace<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // Batched forms: CTA b works on (instance, species, share, shares) = work[b].
@@ -583,7 +592,7 @@ __global__ void __launch_bounds__(kPB, 3)
     __shared__ StepParams s_p;
     const int4 w = work[blockIdx.x];
     load_params(s_p, ps + w.x);
-    particles_compact(s_p, w.y, w.z, w.w);
+    particles_compact<false>(s_p, w.y, w.z, w.w);
 }
 
 __global__ void __launch_bounds__(kPB, 4)
@@ -592,7 +601,7 @@ __global__ void __launch_bounds__(kPB, 4)
     __shared__ StepParams s_p;
     const int4 w = work[blockIdx.x];
     load_params(s_p, ps + w.x);
-    particles_inplace(s_p, w.y, w.z, w.w);
+    particles_inplace<false>(s_p, w.y, w.z, w.w);
 }
 
 // ---------------------------------------------------------------------------------
@@ -604,6 +613,7 @@ __global__ void __launch_bounds__(kPB, 4)
 // int64 accumulator.  After an in-place step a particle returns to its slot (a hole
 // if absorbed); after a compacting step survivors are appended to the output.
 // ---------------------------------------------------------------------------------
+template <bool kProf>
 __device__ __forceinline__ void hard_body(const StepParams &p, int compact, long long gwarp,
                                           long long nwarps)
 {
@@ -642,9 +652,10 @@ __device__ __forceinline__ void hard_body(const StepParams &p, int compact, long
             c = sp.cell[P][slot];
             q = sp.pv[P][slot];
             float ax = gather_ax(p, sp, p.E, c, q.x);
-            float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
+            const float v0n = v0_at<kProf>(p, sp, c);
+            float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, v0n);
             int wall = 0;
-            live = move_and_deposit(p, sp, dep, c, q, vx, wall);
+            live = move_and_deposit<kProf>(p, sp, dep, c, q, vx, wall, v0n);
             if (!live)
                 atomicAdd(&s_abs[s][wall], 1u);
         }
@@ -680,9 +691,10 @@ __device__ __forceinline__ void hard_body(const StepParams &p, int compact, long
     }
 }
 
+template <bool kProf>
 __global__ void __launch_bounds__(256) k_hard(const __grid_constant__ StepParams p, int compact)
 {
-    hard_body(p, compact, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+    hard_body<kProf>(p, compact, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
               (long long)gridDim.x * (blockDim.x >> 5));
 }
 
@@ -691,7 +703,7 @@ __global__ void __launch_bounds__(256) k_hard_batch(const StepParams *__restrict
 {
     __shared__ StepParams s_p;
     load_params(s_p, ps + blockIdx.y);
-    hard_body(s_p, compact, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+    hard_body<false>(s_p, compact, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
               (long long)gridDim.x * (blockDim.x >> 5));
 }
 
@@ -720,7 +732,7 @@ __global__ void __launch_bounds__(256) k_deposit(StepParams p)
         int c1 = c + 1;
         if (p.periodic && c1 == N)
             c1 = 0;
-        deposit_node(s_hist, c, c1, beta_q(sp.kind, q.y, q.z, q.w, sp.v0), q.x);
+        deposit_node(s_hist, c, c1, beta_q(sp.kind, q.y, q.z, q.w, v0_cell(p, sp, c)), q.x);
     }
     __syncthreads();
     unsigned long long *acc = p.acc + ((size_t)P * p.ns + s) * p.nn;
@@ -821,7 +833,7 @@ __device__ void inject_species(const StepParams &p, int s, long long step, long 
             float sw, cw;
             sincospif(2.0f * u3, &sw, &cw);
             const float vy = rw * cw, vz = rw * sw;
-            const float b = beta_q(sp.kind, -vxm, vy, vz, sp.v0);
+            const float b = beta_q(sp.kind, -vxm, vy, vz, v0_cell(p, sp, N - 1));
             float xc = __fsub_rn((float)N, __fmul_rn(u0, __fmul_rn(__fmul_rn(b, vxm), p.dt_dx)));
             if (!(xc < (float)N))
                 xc = __int_as_float(__float_as_int((float)N) - 1);
@@ -848,7 +860,7 @@ __device__ void inject_species(const StepParams &p, int s, long long step, long 
         if (p.periodic && c1 == N)
             c1 = 0;
         unsigned long long qL, qR;
-        quantise(beta_q(sp.kind, q.y, q.z, q.w, sp.v0), off, qL, qR);
+        quantise(beta_q(sp.kind, q.y, q.z, q.w, v0_cell(p, sp, c)), off, qL, qR);
         atomicAdd(acc + c, qL);
         atomicAdd(acc + c1, qR);
     }
@@ -1287,10 +1299,11 @@ __global__ void __launch_bounds__(256) k_diag(StepParams p, double *out)
     double a = 0.0, b = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        if (sp.cell[P][i] < 0)
+        const int c = sp.cell[P][i];
+        if (c < 0)
             continue;  // hole
         float4 q = sp.pv[P][i];
-        double bt = (double)beta_q(sp.kind, q.y, q.z, q.w, sp.v0);
+        double bt = (double)beta_q(sp.kind, q.y, q.z, q.w, v0_cell(p, sp, c));
         double v2 = (double)q.y * q.y + (double)q.z * q.z + (double)q.w * q.w;
         a += bt;
         b += bt * v2;
@@ -1374,15 +1387,19 @@ cudaError_t configure_kernels(int nn)
     if (nn <= configured)
         return cudaSuccess;
     configured = nn;
-    cudaError_t e = cudaFuncSetAttribute(k_particles_compact,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)particle_kernel_smem_bytes(nn));
-    if (e != cudaSuccess)
-        return e;
-    e = cudaFuncSetAttribute(k_particles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)particle_inplace_smem_bytes(nn));
-    if (e != cudaSuccess)
-        return e;
+    cudaError_t e = cudaSuccess;
+    for (auto f : {k_particles_compact<false>, k_particles_compact<true>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)particle_kernel_smem_bytes(nn));
+        if (e != cudaSuccess)
+            return e;
+    }
+    for (auto f : {k_particles<false>, k_particles<true>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)particle_inplace_smem_bytes(nn));
+        if (e != cudaSuccess)
+            return e;
+    }
     e = cudaFuncSetAttribute(k_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(nn * sizeof(unsigned long long)));
     if (e != cudaSuccess)
@@ -1397,21 +1414,22 @@ cudaError_t configure_kernels(int nn)
 
 cudaError_t particle_ctas_per_sm(int nn, int *inplace, int *compacting)
 {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(inplace, k_particles, kPB,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(inplace, k_particles<false>, kPB,
                                                                   particle_inplace_smem_bytes(nn));
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(compacting, k_particles_compact, kPB,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(compacting, k_particles_compact<false>, kPB,
                                                          particle_kernel_smem_bytes(nn));
 }
 
 void launch_particles(const StepParams &p, int ctas_per_species, bool compact, cudaStream_t st)
 {
     dim3 grid(ctas_per_species, p.ns);
+    const size_t smem = compact ? particle_kernel_smem_bytes(p.nn) : particle_inplace_smem_bytes(p.nn);
     if (compact)
-        k_particles_compact<<<grid, kPB, particle_kernel_smem_bytes(p.nn), st>>>(p);
+        (p.lam ? k_particles_compact<true> : k_particles_compact<false>)<<<grid, kPB, smem, st>>>(p);
     else
-        k_particles<<<grid, kPB, particle_inplace_smem_bytes(p.nn), st>>>(p);
+        (p.lam ? k_particles<true> : k_particles<false>)<<<grid, kPB, smem, st>>>(p);
 }
 
 cudaError_t configure_particles_tma(int nn, int *stages)
@@ -1429,7 +1447,10 @@ cudaError_t configure_particles_tma(int nn, int *stages)
         --k;
     if (k < 2)
         return cudaSuccess;
-    e = cudaFuncSetAttribute(k_particles_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
+    e = cudaFuncSetAttribute(k_particles_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_particles_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)room);
     if (e == cudaSuccess)
         *stages = k;
     return e;
@@ -1437,12 +1458,14 @@ cudaError_t configure_particles_tma(int nn, int *stages)
 
 void launch_particles_tma(const StepParams &p, int ctas, int stages, cudaStream_t st)
 {
-    k_particles_tma<<<ctas, kTmaThreads, particle_tma_smem_bytes(p.nn, stages), st>>>(p, stages);
+    (p.lam ? k_particles_tma<true> : k_particles_tma<false>)<<<ctas, kTmaThreads,
+                                                               particle_tma_smem_bytes(p.nn, stages),
+                                                               st>>>(p, stages);
 }
 
 void launch_hard(const StepParams &p, int ctas, bool compact, cudaStream_t st)
 {
-    k_hard<<<ctas, 256, 0, st>>>(p, compact ? 1 : 0);
+    (p.lam ? k_hard<true> : k_hard<false>)<<<ctas, 256, 0, st>>>(p, compact ? 1 : 0);
 }
 
 void launch_particles_batch(const StepParams *d_params, const int4 *d_work, int n_work,

@@ -28,15 +28,36 @@ __device__ __forceinline__ float gather_ax(const StepParams &p, const SpeciesDev
     return __fmul_rn(sp.qm, Ep);
 }
 
+// The speed limit of species sp in cell c (Sec. II: v0 may vary with position).
+// kProf: a per-cell profile is set (p.lam), and the limit is the FP32 product
+// v0 * lam[c] rounded to nearest; otherwise the species' uniform v0.
+template <bool kProf>
+__device__ __forceinline__ float v0_at(const StepParams &p, const SpeciesDev &sp, int c)
+{
+    if (!kProf)
+        return sp.v0;
+    return __fmul_rn(sp.v0, __ldg(p.lam + c));
+}
+
+// The same where a kernel serves both cases at run time (p.lam may be null).
+__device__ __forceinline__ float v0_cell(const StepParams &p, const SpeciesDev &sp, int c)
+{
+    return p.lam ? __fmul_rn(sp.v0, __ldg(p.lam + c)) : sp.v0;
+}
+
 // After the velocity push (new vx): x^{n+1} = x^n + beta(|v^{n+1/2}|) v^{n+1/2} dt in
 // cell units, walls or wrap, and rho^{n+1} += q w beta S(x - x^{n+1}) through
 // dep(c, c+1, beta, offset).  Returns false if absorbed (wall = 0 at x=0, 1 at x=L).
-template <typename Dep>
+// v0n is the limit of the start cell (that of the push); with kProf the deposit
+// takes beta with the limit of the cell the particle ends in (the same beta if it
+// stayed in its cell: a warp whose particles all stay skips the second division).
+template <bool kProf = false, typename Dep>
 __device__ __forceinline__ bool move_and_deposit(const StepParams &p, const SpeciesDev &sp,
-                                                 Dep &dep, int &c, float4 &q, float vx, int &wall)
+                                                 Dep &dep, int &c, float4 &q, float vx, int &wall,
+                                                 float v0n)
 {
     const int N = p.n_cells;
-    float b = beta_q(sp.kind, vx, q.z, q.w, sp.v0);
+    float b = beta_q(sp.kind, vx, q.z, q.w, v0n);
     float xn = __fmaf_rn(__fmul_rn(b, vx), p.dt_dx, q.x);
     float fl = floorf(xn);
     int cn = c + (int)fl;
@@ -59,6 +80,8 @@ __device__ __forceinline__ bool move_and_deposit(const StepParams &p, const Spec
     int cn1 = cn + 1;
     if (p.periodic && cn1 == N)
         cn1 = 0;
+    if (kProf && cn != c)
+        b = beta_q(sp.kind, vx, q.z, q.w, v0_at<true>(p, sp, cn));
     dep(cn, cn1, b, dn);
     c = cn;
     q.x = dn;
@@ -107,7 +130,7 @@ __device__ __forceinline__ bool advance(const StepParams &p, const SpeciesDev &s
     // v^{n+1/2} = v^{n-1/2} + a int beta dt
     float vx = push_vx(sp.kind, q.y, q.z, q.w, ax, p.dt, sp.v0);
     DepositU64 dep{hist};
-    return move_and_deposit(p, sp, dep, c, q, vx, wall);
+    return move_and_deposit(p, sp, dep, c, q, vx, wall, sp.v0);
 }
 
 }  // namespace slpic

@@ -90,6 +90,9 @@ struct StepParams {
     double *phi;              // [nn]
     double *rho;              // [nn]
     DevState *st;
+    // speed limit that varies in space: the limit of species s in cell c is
+    // sp[s].v0 * lam[c] (FP32 product); nullptr = uniform
+    const float *lam;         // [n_cells]
 };
 
 }  // namespace slpic

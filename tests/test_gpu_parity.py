@@ -109,12 +109,13 @@ def test_field_solve_matches_thomas(periodic, phi_hi):
 
 
 # ------------------------------------------------------------------ one step
-def _compare_step(prob, st, gpu, o, rel=1e-5, stats=None):
+def _compare_step(prob, st, gpu, o, rel=1e-5, stats=None, lam=None):
     """Per-particle bars of the module docstring, matched by (vy, vz).
 
     Velocity: |v_gpu - v_orc| <= rel |v|.  Position: the move is
     beta(|v|) v_x dt, so a velocity error of rel |v| moves x by at most
-    rel beta(|v|) |v| dt; the bar is that plus 8 ulp of the FP32 offset."""
+    rel beta(|v|) |v| dt; the bar is that plus 8 ulp of the FP32 offset.
+    lam: per-cell factors of v0 (beta then takes v0 lam[start cell])."""
     dx, N = prob["dx"], prob["n_cells"]
     L = N * dx
     for s in range(len(st)):
@@ -151,7 +152,9 @@ def _compare_step(prob, st, gpu, o, rel=1e-5, stats=None):
         dxp = periodic_diff(xg, xo[ia], L) if prob["periodic"] else xg - xo[ia]
         sp = prob["species"][s]
         r = np.linalg.norm(vref, axis=1)
-        b = orc._beta_vec(int(sp["kind"]), r, float(sp["v0"]))
+        v0p = float(sp["v0"]) if lam is None else \
+            float(sp["v0"]) * np.asarray(lam, np.float64)[st[s][0][jb]]
+        b = orc._beta_vec(int(sp["kind"]), r, v0p)
         tol = rel * b * r * prob["dt"] + 8 * 2.0 ** -24 * dx
         if stats is not None:
             stats.append({"species": s, "max_dv_rel": float(np.max(dv / np.maximum(vnorm, 1e-30))),
