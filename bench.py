@@ -222,7 +222,9 @@ def run_reference(args):
     # warmup + steps end in about two minutes
     rate, _, _, _ = oracle_rate(prob, state, 0.5, max_particles=20_000)
     total_steps = max(1, args.steps + args.warmup)
-    per_step_particles = int(max(200, min(8_192_000, rate * 120.0 / total_steps)))
+    # at most 250k particles a step: far above the calibration sample the oracle's cost
+    # per particle grows (a whole 8.19M-particle step ran about 7x slower per particle)
+    per_step_particles = int(max(200, min(250_000, rate * 120.0 / total_steps)))
     rng = np.random.default_rng(1)
     o = orc.OracleSim(prob)
     n_total = sum(s[0].size for s in state)
