@@ -6,8 +6,9 @@ Bars (written into each test):
     same charge (relative to max|phi|), E within FP32 rounding;
   * one push: |v_gpu - v_orc| <= 1e-5 |v| and positions within 1e-5 of the
     displacement plus 4 ulp of the FP32 in-cell offset;
-  * sampled full-size step: the same per-particle bars at 4,096 cells and
-    8.2M particles in the launch configuration the benchmark times.
+  * sampled full-size step (test_gpu_fullsize): the same per-particle bars at
+    4,096 cells and 8.2M particles in the launch configuration the benchmark
+    times.
 """
 import numpy as np
 import pytest
