@@ -173,3 +173,29 @@ def test_steady_free_streaming_density_does_not_depend_on_the_profile():
     assert np.abs(crat * lam[:-1] - 1.0).max() < 0.06, crat
     wrong = out[True][2][inner] / out[False][0][inner]
     assert wrong.max() > 1.5
+
+
+def test_diagnostics_weight_agrees_with_the_deposit_under_a_profile():
+    """The physical weight sum(w beta) of the diagnostics and the integral of the
+    deposit, sum_j n_j dx, are the same sum (linear weighting conserves it): with a
+    random profile both must take beta at each particle's own cell."""
+    N, dx, v0 = 24, 0.5, 0.3
+    lam = np.random.default_rng(6).uniform(0.3, 1.0, N).astype(np.float32)
+    sp = [{"name": "e", "q": -1.0, "m": 1.0, "w": 0.01, "v0": v0, "kind": HEAV, "T": 0.0},
+          {"name": "i", "q": 1.0, "m": 50.0, "w": 0.02, "v0": v0, "kind": REL, "T": 0.0}]
+    prob = {"n_cells": N, "dx": dx, "dt": dx / v0, "periodic": False, "phi_lo": 0.0,
+            "phi_hi": 0.0, "eps0": 1.0, "seed": 1, "species": sp,
+            "source": {"mode": orc.SRC_NONE}, "v0_profile": lam}
+    o = orc.OracleSim(prob)
+    for s in range(2):
+        x, v, _ = _particles(N, dx, 3000, 10 + s)
+        o.load(s, x, v)
+    o.start()
+    d = o.diagnostics()
+    for s in range(2):
+        assert o.dens[s].sum() * dx == pytest.approx(d["sum_wbeta"][s], rel=1e-12)
+    # the uniform limit gives another total: the check sees the profile
+    u = orc.OracleSim(dict(prob, v0_profile=None))
+    for s in range(2):
+        u.load(s, o.x[s], o.v[s])
+    assert abs(u.diagnostics()["sum_wbeta"][0] - d["sum_wbeta"][0]) > 1e-3 * d["sum_wbeta"][0]
