@@ -44,3 +44,14 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch):
     with contextlib.redirect_stdout(out):
         assert bench.run_reference(args) == 0
     assert out.getvalue() == ""
+
+
+def test_oracle_on_all_cores_sums_independent_copies():
+    from paper_1511_08225_gb300 import inputs
+    prob = inputs.sheath_problem(n_cells=64, ppc=50, v0=0.05)
+    state = inputs.load_state(prob)
+    rate, workers, per = bench.oracle_rate_all_cores(prob, state, 3.0, per_worker=2000,
+                                                     workers=2)
+    assert workers == 2 and per == 1.5 and rate > 0
+    one, _, _, _ = bench.oracle_rate(prob, state, 1.5, max_particles=2000)
+    assert 0.8 * one < rate < 3.0 * one  # two cores, not a fluke
