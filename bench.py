@@ -233,7 +233,7 @@ def oracle_rate_all_cores(prob, state, cpu_seconds, per_worker=40_000, workers=N
         jobs.append((prob, sub, budget))
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        res = pool.map_async(_oracle_rate_job, jobs, chunksize=1).get(timeout=4 * budget + 120)
+        res = pool.map_async(_oracle_rate_job, jobs, chunksize=1).get(timeout=4 * budget + 60)
     return sum(r for r, _, _ in res), workers, budget
 
 
