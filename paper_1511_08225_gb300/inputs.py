@@ -234,6 +234,31 @@ def load_state(prob: dict, seed: int | None = None, quiet: bool = False):
     return out
 
 
+def quiet_symmetric_state(prob: dict, seed: int | None = None):
+    """A quiet start whose velocity set is symmetric: every cell holds the same ppc
+    velocities, ppc/2 draws of g0 and their negatives side by side, at offsets
+    (k+1/2)/ppc, and each species' weight w is reset so that sum(w beta) over a cell
+    is exactly n0 dx.  The load is neutral cell by cell and carries no net flux or
+    net d(beta)/dv, so nothing but the walls and the source disturbs it."""
+    rng = make_rng(prob["seed"] if seed is None else seed)
+    out = []
+    N = int(prob["n_cells"])
+    for sp in prob["species"]:
+        ppc = int(sp["ppc"])
+        h = g_velocities(rng, ppc // 2, sp["vth"], sp["v0"], sp["kind"], sp.get("vdim", 3))
+        v = np.empty((2 * (ppc // 2), 3), dtype=np.float32)
+        v[0::2] = h
+        v[1::2] = -v[0::2]
+        v64 = v.astype(np.float64)  # the weight is set from the stored FP32 velocities
+        r = np.sqrt((v64 * v64).sum(1))
+        sp["w"] = float(prob["dx"] / (1.0 / _g_factor(sp["kind"], r, sp["v0"])).sum())
+        n = v.shape[0]
+        cell = np.repeat(np.arange(N, dtype=np.int32), n)
+        off = np.tile(((np.arange(n) + 0.5) / n).astype(np.float32), N)
+        out.append((cell, off, np.tile(v, (N, 1))))
+    return out
+
+
 def random_state(rng, n: int, n_cells: int, vscale: float = 1.0):
     """Generic FP32 state for parity cases: uniform cells, Gaussian velocities."""
     cell, off = uniform_cells(rng, n, n_cells)
