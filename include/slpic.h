@@ -260,12 +260,13 @@ int slpic_restore(slpic_t *h, const void *buf, size_t size);
 
 /* ---- timing --------------------------------------------------------------- */
 
-/* From now on slpic_step runs its steps as graphs of `steps_per_graph` steps
- * (1..4096, rounded up to a multiple of 16, the interval of the compacting
- * particle step; 0 turns timing off) in which CUDA events bracket the kernels of
- * every step.  The events are recorded
- * on the handle's stream, the stream the kernels run on; each graph replay
- * re-records them.  Steps beyond a multiple of steps_per_graph run untimed. */
+/* From now on slpic_step runs its steps in blocks of `steps_per_graph` (1..4096;
+ * 0 turns timing off), each block one graph in which CUDA events bracket the
+ * kernels of every step, starting at whatever step the run has reached.  The
+ * events are recorded on the handle's stream, the stream the kernels run on; each
+ * graph replay re-records them.  The steps of a call beyond a whole number of
+ * blocks run untimed.  The event nodes separate the kernels, which adds a few
+ * microseconds of launch latency to each bracketed interval. */
 int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph);
 
 /* Mean device time (ms) per step of the streaming particle kernel, of the kernel
@@ -274,6 +275,30 @@ int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph);
  * ran); synchronising.  Any pointer may be NULL. */
 int slpic_kernel_times(slpic_t *h, double *particle_ms, double *hard_ms, double *field_ms,
                        int64_t *steps);
+
+/* The particle kernel's pipeline waits (for a tile's bulk copy to land, for the
+ * consumer warps to free a stage) give up after `cycles` SM clock cycles (default
+ * 2e9, about a second; 0 restores the default).  A wait that gives up records
+ * SLPIC_ERR_TIMEOUT, which the next synchronising call reports; the kernel then
+ * skips its remaining tiles, waits for its own copies still in flight (with the
+ * default limit, whatever `cycles` is) and returns, so the GPU context stays
+ * usable.  The step it cut short leaves the handle's particles and fields no longer
+ * those of the method: destroy the handle (reading it back stays safe).  A limit far
+ * below a copy's latency exercises that path.  Below the default the waits poll the
+ * barrier without suspending the thread (which costs issue slots), so that a short
+ * limit can run out.  Takes effect from the next step (the step graphs are captured
+ * again).  SLPIC_ERR_INVALID for cycles < 0 or a batch. */
+int slpic_set_wait_limit(slpic_t *h, int64_t cycles);
+
+/* Device time of the step's kernels, always recorded: for kind 0 (the particle
+ * kernel, in-place or compacting), 1 (the kernel for the particles that need the
+ * iterative push) and 2 (the source and field kernel), ms[kind] is the summed
+ * device time of its launches since the handle was created, each launch counted
+ * from the start of its first CTA to the end of its last on the GPU's global timer,
+ * and launches[kind] the number of launches.  Differences of two calls give the
+ * time of the steps between them.  Synchronising; either pointer may be NULL;
+ * SLPIC_ERR_INVALID for a batch handle. */
+int slpic_kernel_spans(slpic_t *h, double *ms, int64_t *launches);
 
 /* Number of kernels one slpic_step(h, 1) launches. */
 int slpic_kernels_per_step(slpic_t *h, int *n);

@@ -38,7 +38,9 @@ EXPORTS = (
     "slpic_load_particles_f64", "slpic_prepare", "slpic_step", "slpic_synchronize",
     "slpic_fields", "slpic_density", "slpic_charge_raw", "slpic_particle_count",
     "slpic_get_particles", "slpic_diagnostics", "slpic_save", "slpic_restore",
-    "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernels_per_step",
+    "slpic_enable_kernel_timing", "slpic_kernel_times", "slpic_kernel_spans",
+    "slpic_set_wait_limit",
+    "slpic_kernels_per_step",
     "slpic_particle_step_noalloc", "slpic_create_batch", "slpic_set_speed_limit",
     "slpic_set_timestep", "slpic_set_wave", "slpic_get_tuning", "slpic_set_tuning",
     "slpic_autotune", "slpic_fields_async", "slpic_set_speed_limit_profile",
@@ -135,6 +137,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "slpic_enable_kernel_timing": (I, [P, I64]),
         "slpic_kernel_times": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                    ctypes.POINTER(I64)]),
+        "slpic_kernel_spans": (I, [P, P, P]),
+        "slpic_set_wait_limit": (I, [P, I64]),
         "slpic_kernels_per_step": (I, [P, ctypes.POINTER(I)]),
         "slpic_particle_step_noalloc": (I, [ctypes.POINTER(slpic_config), I, I64, P, P, P, P, P,
                                             P, ctypes.POINTER(I64), P, P]),
@@ -328,6 +332,21 @@ def slpic_kernel_times(h):
                                                 ctypes.byref(c), ctypes.byref(n)),
            "slpic_kernel_times")
     return a.value, b.value, c.value, n.value
+
+
+def slpic_kernel_spans(h):
+    """(ms[3], launches[3]): summed device time and launch count of the particle
+    kernel, the iterative-push kernel and the field kernel since creation."""
+    ms = np.zeros(3)
+    n = np.zeros(3, dtype=np.int64)
+    _check(h, load_library().slpic_kernel_spans(h, _ptr(ms), _ptr(n)), "slpic_kernel_spans")
+    return ms, n
+
+
+def slpic_set_wait_limit(h, cycles: int):
+    """Spin limit of the particle kernel's pipeline waits, in SM clock cycles (0 =
+    the default, about a second)."""
+    _check(h, load_library().slpic_set_wait_limit(h, int(cycles)), "slpic_set_wait_limit")
 
 
 def slpic_kernels_per_step(h) -> int:

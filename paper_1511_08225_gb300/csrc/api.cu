@@ -58,9 +58,10 @@ struct slpic_sim {
     cudaGraphExec_t g1 = nullptr;   // one in-place step
     cudaGraphExec_t gc = nullptr;   // one compacting step
     cudaGraphExec_t gK = nullptr;   // one cycle: compact_every - 1 in-place steps, 1 compacting
-    cudaGraphExec_t gt = nullptr;   // timed graph: t_len steps (whole cycles) with their own events
+    cudaGraphExec_t gt = nullptr;   // timed graph: t_len steps from phase t_phase, with events
     std::vector<cudaEvent_t> events; // 3 per step of the timed graph
     long long t_len = 0;             // steps per timed graph (0 = timing off)
+    long long t_phase = -1;          // step % compact_every at which gt starts
     long long t_launched = 0;        // timed-graph launches since timing was enabled
 
     // a batch of independent simulations (slpic_create_batch): each member does its
@@ -336,6 +337,9 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
         for (int b = 0; b < 2; ++b) {
             CKC(cudaMalloc(&h->d_cell[s][b], sizeof(int32_t) * cfg->species[s].capacity));
             CKC(cudaMalloc(&h->d_pv[s][b], sizeof(float4) * cfg->species[s].capacity));
+            // every slot starts as a hole (cell -1): a step cut short by a wait that
+            // gave up leaves slots unwritten, and a later step must find them valid
+            CKC(cudaMemset(h->d_cell[s][b], 0xFF, sizeof(int32_t) * cfg->species[s].capacity));
         }
         CKC(cudaMalloc(&h->d_hard[s], sizeof(int32_t) * cfg->species[s].capacity));
     }
@@ -410,6 +414,7 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     p.phi = h->d_phi;
     p.rho = h->d_rho;
     p.st = h->d_state;
+    p.wait_cycles = kWaitCycles;
 #undef CKC
     *out = h;
     return SLPIC_OK;
@@ -666,9 +671,14 @@ extern "C" int slpic_step(slpic_t *h, int64_t nsteps)
     int64_t left = nsteps;
     while (left > 0) {
         const long long phase = h->step % h->compact_every;
-        if (phase == 0 && h->t_len > 0 && left >= h->t_len) {
-            if (!h->gt && (rc = capture(h, 0, (int)h->t_len, true, &h->gt)))
+        if (h->t_len > 0 && left >= h->t_len) {
+            if (h->gt && h->t_phase != phase) {
+                cudaGraphExecDestroy(h->gt);
+                h->gt = nullptr;
+            }
+            if (!h->gt && (rc = capture(h, phase, (int)h->t_len, true, &h->gt)))
                 return rc;
+            h->t_phase = phase;
             CK(h, cudaGraphLaunch(h->gt, h->stream));
             h->t_launched++;
             h->step += h->t_len;
@@ -1049,7 +1059,6 @@ extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
         return rc;
     if (steps_per_graph < 0 || steps_per_graph > 4096)
         return fail(h, SLPIC_ERR_INVALID, "steps_per_graph must be in 0..4096");
-    steps_per_graph = (steps_per_graph + h->compact_every - 1) / h->compact_every * h->compact_every;
     CK(h, cudaStreamSynchronize(h->stream));
     if (h->gt) {
         cudaGraphExecDestroy(h->gt);
@@ -1059,6 +1068,7 @@ extern "C" int slpic_enable_kernel_timing(slpic_t *h, int64_t steps_per_graph)
         cudaEventDestroy(e);
     h->events.clear();
     h->t_launched = 0;
+    h->t_phase = -1;
     h->t_len = steps_per_graph;
     h->events.resize(4 * steps_per_graph);
     for (auto &e : h->events)
@@ -1094,6 +1104,43 @@ extern "C" int slpic_kernel_times(slpic_t *h, double *particle_ms, double *hard_
         *field_ms = n ? c / n : 0.0;
     if (steps)
         *steps = n;
+    return SLPIC_OK;
+}
+
+static void drop_graphs(slpic_t *h);
+
+extern "C" int slpic_set_wait_limit(slpic_t *h, int64_t cycles)
+{
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    if (cycles < 0)
+        return fail(h, SLPIC_ERR_INVALID, "cycles < 0");
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->p.wait_cycles = cycles ? (long long)cycles : kWaitCycles;
+    drop_graphs(h);
+    return SLPIC_OK;
+}
+
+extern "C" int slpic_kernel_spans(slpic_t *h, double *ms, int64_t *launches)
+{
+    if (is_batch(h))
+        return fail(h, SLPIC_ERR_INVALID, "not available for a batch handle");
+    int rc = check_handle(h, 0);
+    if (rc)
+        return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    DevState st;
+    if ((rc = read_state(h, &st)))
+        return rc;
+    for (int k = 0; k < 3; ++k) {
+        if (ms)
+            ms[k] = 1e-6 * (double)st.span_ns[k];
+        if (launches)
+            launches[k] = (int64_t)st.span_launches[k];
+    }
     return SLPIC_OK;
 }
 

@@ -40,6 +40,43 @@ namespace slpic {
 // atomicAdd to reserve the batch's output range (order inside a batch is kept;
 // batch order is not).
 // ---------------------------------------------------------------------------------
+// ---------------------------------------------------------------------------------
+// Device time of each kernel of the step (slpic_kernel_spans): thread 0 of every CTA
+// takes the earliest start with an atomic, and the last CTA to finish adds the span
+// from that start to its own end.  A few atomics per CTA; the next launch of the
+// same kernel follows on the stream, so the reset cannot race it.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void span_enter(DevState *st, int k)
+{
+    if (threadIdx.x == 0)
+        atomicMax(&st->span_t0n[k], ~gtimer());
+}
+
+// every thread of the CTA calls it, after the CTA's last work
+__device__ __forceinline__ void span_exit(DevState *st, int k)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned n = gridDim.x * gridDim.y * gridDim.z;
+        if (atomicAdd(&st->span_done[k], 1u) == n - 1u) {
+            const unsigned long long t1 = gtimer();
+            const unsigned long long t0 = ~atomicExch(&st->span_t0n[k], 0ULL);
+            st->span_ns[k] += t1 > t0 ? t1 - t0 : 0ULL;
+            st->span_launches[k] += 1ULL;
+            st->span_done[k] = 0u;
+            __threadfence();
+        }
+    }
+}
+
 constexpr int kPB = kParticleThreads;  // threads per CTA
 constexpr int kPI = 4;                 // particles per thread per tile
 constexpr int kPT = kPB * kPI;         // particles per tile
@@ -354,17 +391,49 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity)
     return done != 0;
 }
 
-// true once the phase of `parity` has completed; false after ~1 s or once another
-// wait of the CTA has failed (*fail set), recording SLPIC_ERR_TIMEOUT
+// non-blocking test: try_wait may suspend the thread for a while before it returns
+// false, long enough for a copy to land, so a limit shorter than that suspension
+// needs this form to be able to run out
+__device__ __forceinline__ bool mbar_poll(uint64_t *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// true once the phase of `parity` has completed; false after `limit` cycles (about
+// a second by default) or once another wait of the CTA has failed (*fail set),
+// recording SLPIC_ERR_TIMEOUT
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, volatile int *fail,
-                                          int *error)
+                                          int *error, long long limit)
+{
+    const long long t0 = clock64();
+    const bool poll = limit < kWaitCycles;  // uniform: a kernel parameter
+    while (!(poll ? mbar_poll(bar, parity) : mbar_test(bar, parity))) {
+        if (*fail)
+            return false;
+        if (clock64() - t0 > limit) {
+            *fail = 1;
+            atomicCAS(error, 0, SLPIC_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// The wait for a copy this CTA issued, before the CTA exits: copies of valid
+// memory always land, so it ignores *fail and the wait limit of the pipeline and
+// gives up only after kDrainCycles (recording SLPIC_ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, unsigned parity, int *error)
 {
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {
-        if (*fail)
-            return false;
-        if (clock64() - t0 > 2000000000LL) {
-            *fail = 1;
+        if (clock64() - t0 > kDrainCycles) {
             atomicCAS(error, 0, SLPIC_ERR_TIMEOUT);
             return false;
         }
@@ -415,6 +484,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
     __shared__ unsigned s_abs[2];
     __shared__ int s_fail;
 
+    span_enter(p.st, 0);
     const long long step = *(volatile long long *)&p.st->step;
     const int P = (int)(step & 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -447,7 +517,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
                 for (long long t = t0; t < t1; ++t, ++k) {
                     const int st = (int)(k % stages);
                     const unsigned ph = (unsigned)((k / stages) & 1);
-                    if (k >= stages && !mbar_wait(&empty[st], ph ^ 1u, fail, &p.st->error))
+                    if (k >= stages &&
+                        !mbar_wait(&empty[st], ph ^ 1u, fail, &p.st->error, p.wait_cycles))
                         break;
                     const long long i0 = t * kTmaTile;
                     const int cnt = (int)min((long long)kTmaTile, n - i0);
@@ -459,9 +530,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
                                   &full[st]);
                 }
             }
-            // every copy issued has landed before the CTA may exit
+            // every copy issued has landed before the CTA may exit (also after a wait
+            // of the pipeline gave up)
             for (long long j = (k > stages ? k - stages : 0); j < k; ++j)
-                if (!mbar_wait(&full[j % stages], (unsigned)((j / stages) & 1), fail, &p.st->error))
+                if (!mbar_drain(&full[j % stages], (unsigned)((j / stages) & 1), &p.st->error))
                     break;
         }
     } else {
@@ -480,7 +552,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
             for (long long t = t0; t < t1; ++t, ++k) {
                 const int st = (int)(k % stages);
                 const unsigned ph = (unsigned)((k / stages) & 1);
-                const bool ok = !*fail && mbar_wait(&full[st], ph, fail, &p.st->error);
+                const bool ok = !*fail && mbar_wait(&full[st], ph, fail, &p.st->error,
+                                                    p.wait_cycles);
                 const long long i0 = t * kTmaTile;
                 const int cnt = (int)min((long long)kTmaTile, n - i0);
                 const int cb = cnt & ~3;
@@ -558,7 +631,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
             consumers_sync();
         }
     }
-    __syncthreads();
+    span_exit(p.st, 0);
 }
 
 // Copy one instance's parameters into shared memory (batched kernels).
@@ -576,13 +649,17 @@ __device__ __forceinline__ void load_params(StepParams &dst, const StepParams *s
 template <bool kProf>
 __global__ void __launch_bounds__(kPB, 3) k_particles_compact(const __grid_constant__ StepParams p)
 {
+    span_enter(p.st, 0);
     particles_compact<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
+    span_exit(p.st, 0);
 }
 
 template <bool kProf>
 __global__ void __launch_bounds__(kPB, 4) k_particles(const __grid_constant__ StepParams p)
 {
+    span_enter(p.st, 0);
     particles_inplace<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
+    span_exit(p.st, 0);
 }
 
 // Batched forms: CTA b works on (instance, species, share, shares) = work[b].
@@ -694,8 +771,10 @@ __device__ __forceinline__ void hard_body(const StepParams &p, int compact, long
 template <bool kProf>
 __global__ void __launch_bounds__(256) k_hard(const __grid_constant__ StepParams p, int compact)
 {
+    span_enter(p.st, 1);
     hard_body<kProf>(p, compact, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
               (long long)gridDim.x * (blockDim.x >> 5));
+    span_exit(p.st, 1);
 }
 
 // batched: grid (CTAs per instance, instances)
@@ -1273,7 +1352,9 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
 __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
     k_field(const __grid_constant__ StepParams p, int mode)
 {
+    span_enter(p.st, 2);
     field_body(p, mode);
+    span_exit(p.st, 2);
 }
 
 // batched: one cluster per instance

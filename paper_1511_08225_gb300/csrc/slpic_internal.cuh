@@ -38,6 +38,13 @@ struct DevState {
     unsigned long long hard_n[kMaxSpecies];        // particles listed for k_hard this step
     int error;                                     // first SLPIC_ERR_* raised on the device
     int pad;
+    // device time of the step's kernels (0 particle, 1 k_hard, 2 k_field): per launch
+    // the span from the first CTA's start to the last CTA's end (globaltimer, ns)
+    unsigned long long span_t0n[3];       // ~(earliest start) of the running launch; 0 = none
+    unsigned long long span_ns[3];        // summed spans
+    unsigned long long span_launches[3];  // launches summed
+    unsigned int span_done[3];            // CTAs of the running launch that have finished
+    unsigned int pad2;
 };
 
 struct SpeciesDev {
@@ -93,6 +100,13 @@ struct StepParams {
     // speed limit that varies in space: the limit of species s in cell c is
     // sp[s].v0 * lam[c] (FP32 product); nullptr = uniform
     const float *lam;         // [n_cells]
+    // longest spin of a pipeline wait in the particle kernel, in SM clock cycles
+    // (slpic_set_wait_limit); the wait for the CTA's own copies in flight before it
+    // exits keeps kDrainCycles whatever this is
+    long long wait_cycles;
 };
+
+constexpr long long kWaitCycles = 2000000000LL;   // default wait limit, about a second
+constexpr long long kDrainCycles = 2000000000LL;  // limit of the drain of copies in flight
 
 }  // namespace slpic

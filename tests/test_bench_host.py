@@ -50,8 +50,32 @@ def test_oracle_on_all_cores_sums_independent_copies():
     from paper_1511_08225_gb300 import inputs
     prob = inputs.sheath_problem(n_cells=64, ppc=50, v0=0.05)
     state = inputs.load_state(prob)
-    rate, workers, per = bench.oracle_rate_all_cores(prob, state, 3.0, per_worker=2000,
-                                                     workers=2)
-    assert workers == 2 and per == 1.5 and rate > 0
-    one, _, _, _ = bench.oracle_rate(prob, state, 1.5, max_particles=2000)
-    assert 0.8 * one < rate < 3.0 * one  # two cores, not a fluke
+    one, done, dt, nst = bench.oracle_rate(prob, state, budget_s=1.0, max_particles=2000)
+    assert nst >= 1 and done > 0 and one > 0
+    # the copies run the one-core run's step range, each on its own subsample
+    rate, workers, slow = bench.oracle_rate_all_cores(prob, state, nst, per_worker=2000,
+                                                      workers=2, timeout=120)
+    assert workers == 2 and rate > 0 and slow > 0
+    assert 0.8 * one < rate < 2.6 * one  # two cores, not a fluke
+
+
+def test_oracle_rate_runs_exact_step_count():
+    from paper_1511_08225_gb300 import inputs
+    prob = inputs.sheath_problem(n_cells=64, ppc=20, v0=0.05)
+    state = inputs.load_state(prob)
+    _, done, _, nst = bench.oracle_rate(prob, state, n_steps=3, max_particles=500)
+    assert nst == 3 and done > 0
+
+
+def test_cpu_baseline_line_fields():
+    from paper_1511_08225_gb300 import inputs
+    prob = inputs.sheath_problem(n_cells=64, ppc=50, v0=0.05)
+    state = inputs.load_state(prob)
+    cpu = bench.cpu_baseline(prob, state, 1.0, per_worker=2000)
+    assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["unit"] == bench.UNIT
+    assert cpu["cores"] >= 1 and "steps 1.." in cpu["sample"]
+    if cpu["cores"] > 1:
+        assert cpu["single_core"]["cores"] == 1
+        # independent copies cannot beat cores x the one-core rate (beyond the timing
+        # noise of runs this short)
+        assert cpu["value"] <= 1.5 * cpu["cores_x_single_core"]

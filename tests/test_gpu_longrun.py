@@ -84,8 +84,8 @@ def test_mixed_form_sheath_profiles_match_oracle_ensemble(golden):
     runs = [_mixed_run(GPU_SEED0 + k, golden["ppc"]) for k in range(N_SEEDS)]
     mine = ens.summarise([r[0] for r in runs], [r[1] for r in runs])
     zp, zf = ens.compare(mine, golden)
-    # the plates hold their potentials exactly
-    assert np.allclose(mine["mean"][0, [0, -1]], golden["mean"][0, [0, -1]], rtol=0, atol=1e-12)
+    # the plates hold their potentials (the stored file keeps 11 significant digits)
+    assert np.allclose(mine["mean"][0, [0, -1]], golden["mean"][0, [0, -1]], rtol=0, atol=1e-9)
     assert np.abs(zp).max() <= ens.Z_MAX, f"profiles: max |z| = {np.abs(zp).max():.2f}"
     assert (zp ** 2).mean() <= ens.CHI2_MAX, f"profiles: mean z^2 = {(zp ** 2).mean():.2f}"
     assert np.abs(zf).max() <= ens.Z_MAX, f"fluxes: z = {zf}"

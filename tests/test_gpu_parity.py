@@ -12,6 +12,7 @@ Bars (written into each test):
 """
 import numpy as np
 import pytest
+import torch
 
 from oracle import oracle as orc
 from paper_1511_08225_gb300 import binding, inputs
@@ -419,9 +420,34 @@ def test_empty_species_and_device_load():
 def test_kernel_timing_records_both_kernels():
     prob = _problem(N=64)
     sim = _sim(prob, _state(prob, (10_000, 10_000)))
-    binding.slpic_enable_kernel_timing(sim.h, 4)  # rounded up to one 16-step cycle
-    sim.step(40)  # two timed replays of 16 steps, then 8 untimed steps
-    pm, hm, fm, n = binding.slpic_kernel_times(sim.h)
-    assert n == 16 and pm > 0 and hm > 0 and fm > 0
+    sim.step(5)  # timed blocks start wherever the run is, not only at a cycle start
+    binding.slpic_enable_kernel_timing(sim.h, 12)
+    sim.step(30)  # two timed replays of 12 steps (the second crosses a compacting step),
+    pm, hm, fm, n = binding.slpic_kernel_times(sim.h)  # then 6 untimed steps
+    assert n == 12 and pm > 0 and hm > 0 and fm > 0
     assert binding.slpic_kernels_per_step(sim.h) == 3
+    assert sim.diagnostics()["step"] == 35
+    sim.close()
+
+
+def test_kernel_spans_count_every_launch_of_the_steps():
+    """slpic_kernel_spans: one launch of each kernel per step, device time > 0, and
+    for a block of steps the summed spans fit inside the stream's elapsed time."""
+    prob = _problem(N=64)
+    sim = _sim(prob, _state(prob, (20_000, 20_000)))
+    sim.step(3)
+    sim.synchronize()
+    ms0, n0 = binding.slpic_kernel_spans(sim.h)
+    stream = torch.cuda.current_stream()
+    binding.slpic_set_stream(sim.h, stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(40)
+    e1.record(stream)
+    e1.synchronize()
+    ms1, n1 = binding.slpic_kernel_spans(sim.h)
+    assert list(n1 - n0) == [40, 40, 40]
+    d = ms1 - ms0
+    assert (d > 0).all()
+    assert d.sum() <= e0.elapsed_time(e1) * 1.02  # two clocks: allow 2 %
     sim.close()

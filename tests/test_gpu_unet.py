@@ -254,3 +254,56 @@ def test_training_fits_a_fixed_linear_map():
                               want_loss=(it == 399))
     assert last < 0.1 * first, (first, last)
     net.close()
+
+
+# ---------------------------------------------------------------- against the plain oracle
+@pytest.mark.parametrize("levels,base,n,nb", [(2, 8, 32, 2), (3, 4, 16, 3), (4, 8, 40, 2),
+                                              (1, 3, 8, 1), (4, 32, 64, 1)])
+def test_tensor_core_forward_within_bf16_bar_of_plain_oracle(levels, base, n, nb):
+    """The tensor-core forward against the plain FP64 oracle, which rounds nothing but
+    the weights (the BF16 weights are the network's parameters as stored): within
+    1e-2 of the largest output, the bar a BF16 network is held to.  The BF16-input
+    oracle mode above states where the kernels round; this bar does not depend on
+    that mode."""
+    assert _tc_available()
+    params = _params(levels, base, seed=levels * 7 + base)
+    rng = np.random.default_rng(17)
+    xs = rng.normal(size=(nb, n, n))
+    net = binding_unet.UNet(levels, base, n, n, max_batch=nb, normalise=False, tensor_cores=True)
+    net.set_params(params)
+    y = torch.zeros((nb, n, n), device="cuda")
+    net.forward(_dev(xs), y)
+    got = y.cpu().numpy()
+    for k in range(nb):
+        ref = ounet.forward(_bf(params), xs[k].astype(np.float32).astype(np.float64), levels)[0]
+        assert np.abs(got[k] - ref).max() <= 1e-2 * np.abs(ref).max(), k
+    net.close()
+
+
+@pytest.mark.parametrize("levels,base,n,nb", [(2, 8, 32, 2), (3, 4, 16, 1), (4, 32, 32, 1)])
+def test_tensor_core_gradients_against_plain_oracle(levels, base, n, nb):
+    """Loss and parameter gradients of the tensor-core path against the plain FP64
+    oracle's (BF16 weights, nothing else rounded).  BF16 activations alone move a
+    small random network's weight gradients: by up to ~14 % of a layer's largest
+    entry at (3, 4, 16), oracle against oracle, through flipped ReLU masks and
+    cancelling sums.  So the bar is that deviation, measured here by the oracle
+    alone (its BF16-operand mode against its plain mode), plus 1e-2 of the layer's
+    largest entry, and every layer's gradient must point the same way as the plain
+    one (cosine >= 0.99)."""
+    params = _params(levels, base, seed=31 + levels)
+    rng = np.random.default_rng(32 + levels)
+    xs, ts = rng.normal(size=(nb, n, n)), rng.normal(size=(nb, n, n))
+    net = binding_unet.UNet(levels, base, n, n, max_batch=nb, normalise=False, tensor_cores=True)
+    net.set_params(params)
+    loss, grads = net.gradients(_dev(xs), _dev(ts))
+    ref_loss, ref = _oracle_grads(params, xs, ts, levels, act_bf16=False)
+    _, ref16 = _oracle_grads(params, xs, ts, levels, act_bf16=True)
+    assert loss == pytest.approx(ref_loss, rel=1e-2)
+    for k, ((dw, db), (rw, rb), (qw, qb)) in enumerate(zip(grads, ref, ref16)):
+        assert np.abs(dw - rw).max() <= np.abs(qw - rw).max() + 1e-2 * np.abs(rw).max(), ("W", k)
+        cos = float((dw.astype(np.float64) * rw).sum() /
+                    np.sqrt((dw.astype(np.float64) ** 2).sum() * (rw * rw).sum()))
+        assert cos >= 0.99, ("W", k, cos)
+        assert np.abs(db - rb).max() <= np.abs(qb - rb).max() + \
+            1e-2 * max(np.abs(rb).max(), 1e-12), ("b", k)
+    net.close()
