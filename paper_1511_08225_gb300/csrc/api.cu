@@ -47,7 +47,8 @@ struct slpic_sim {
     double *d_E64 = nullptr, *d_phi = nullptr, *d_rho = nullptr;
     int32_t *d_cell[kMaxSpecies][2] = {};
     float4 *d_pv[kMaxSpecies][2] = {};
-    int32_t *d_hard[kMaxSpecies] = {};
+    HardRec *d_hard[kMaxSpecies] = {};
+    int32_t *d_hard_slot[kMaxSpecies] = {};
     double *d_diag = nullptr;
     int *d_bad = nullptr;
     float *d_lam = nullptr;  // speed-limit profile (slpic_set_speed_limit_profile)
@@ -98,6 +99,14 @@ static int fail(slpic_t *h, int code, const std::string &msg)
 {
     h->err = msg;
     return code;
+}
+
+// Records for the particles needing the iterative push: an eighth of the capacity
+// (a step lists well under 1 % on the headline sheath), at least 64k; beyond that
+// the list continues as bare slots.
+static long long hard_records(long long capacity)
+{
+    return std::min(capacity, std::max(capacity / 8, 65536LL));
 }
 
 // A batch handle forwards a per-instance call to its member (as instance 0).
@@ -254,6 +263,7 @@ static void free_all(slpic_t *h)
             cudaFree(h->d_pv[s][b]);
         }
         cudaFree(h->d_hard[s]);
+        cudaFree(h->d_hard_slot[s]);
     }
     if (h->own_stream)
         cudaStreamDestroy(h->own_stream);
@@ -341,7 +351,8 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
             // gave up leaves slots unwritten, and a later step must find them valid
             CKC(cudaMemset(h->d_cell[s][b], 0xFF, sizeof(int32_t) * cfg->species[s].capacity));
         }
-        CKC(cudaMalloc(&h->d_hard[s], sizeof(int32_t) * cfg->species[s].capacity));
+        CKC(cudaMalloc(&h->d_hard[s], sizeof(HardRec) * hard_records(cfg->species[s].capacity)));
+        CKC(cudaMalloc(&h->d_hard_slot[s], sizeof(int32_t) * cfg->species[s].capacity));
     }
     CKC(cudaMemset(h->d_state, 0, sizeof(DevState)));
     CKC(cudaMemset(h->d_acc, 0, sizeof(unsigned long long) * 2 * ns * nn));
@@ -393,6 +404,8 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
             d.pv[b] = h->d_pv[s][b];
         }
         d.hard = h->d_hard[s];
+        d.hard_slot = h->d_hard_slot[s];
+        d.hard_recs = hard_records(cfg->species[s].capacity);
         d.capacity = sp.capacity;
         d.qm = (float)(sp.q / sp.m);
         d.v0 = sp.beta_kind == SLPIC_BETA_ONE ? INFINITY : (float)sp.v0;

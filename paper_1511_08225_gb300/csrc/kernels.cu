@@ -132,9 +132,10 @@ __device__ __forceinline__ void compact_store(const bool (&live)[NI], const int 
 
 size_t particle_kernel_smem_bytes(int nn) { return (size_t)nn * 3 * sizeof(unsigned); }
 
-// Append the slots of this warp's hard particles to the species' list for k_hard
-// (one atomicAdd per warp).
-__device__ __forceinline__ void list_hard(bool hard, long long i, const SpeciesDev &sp,
+// Append this warp's hard particles (slot i, cell c, state q, the gathered ax) to
+// the species' list for k_hard (one atomicAdd per warp).
+__device__ __forceinline__ void list_hard(bool hard, long long i, int c, const float4 &q,
+                                          float ax, const SpeciesDev &sp,
                                           unsigned long long *hard_n)
 {
     const unsigned hm = __ballot_sync(0xffffffffu, hard);
@@ -145,8 +146,17 @@ __device__ __forceinline__ void list_hard(bool hard, long long i, const SpeciesD
     if (lane == 0)
         b = atomicAdd(hard_n, (unsigned long long)__popc(hm));
     b = __shfl_sync(0xffffffffu, b, 0);
-    if (hard)
-        sp.hard[b + __popc(hm & ((1u << lane) - 1u))] = (int32_t)i;
+    if (hard) {
+        const long long k = (long long)b + __popc(hm & ((1u << lane) - 1u));
+        if (k < sp.hard_recs) {
+            int4 *r = reinterpret_cast<int4 *>(sp.hard + k);
+            r[0] = make_int4((int)i, c, __float_as_int(ax), 0);
+            r[1] = make_int4(__float_as_int(q.x), __float_as_int(q.y), __float_as_int(q.z),
+                             __float_as_int(q.w));
+        } else {
+            sp.hard_slot[k] = (int32_t)i;
+        }
+    }
 }
 
 // Bodies of the kernels take the parameters by reference (kernel parameter space
@@ -205,6 +215,7 @@ __device__ __forceinline__ void particles_compact(const StepParams &p, int s, in
 #pragma unroll
         for (int k = 0; k < kPI; ++k) {
             bool hard = false;
+            float axh = 0.0f;
             if (live[k]) {
                 float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
                 const float v0n = v0_at<kProf>(p, sp, c[k]);
@@ -216,10 +227,12 @@ __device__ __forceinline__ void particles_compact(const StepParams &p, int s, in
                         atomicAdd(&s_abs[wall], 1u);
                 } else {
                     hard = true;
+                    axh = ax;
                     live[k] = false;  // pushed, deposited and stored by k_hard
                 }
             }
-            list_hard(hard, base + k * kPB + threadIdx.x, sp, &p.st->hard_n[s]);
+            list_hard(hard, base + k * kPB + threadIdx.x, c[k], q[k], axh, sp,
+                      &p.st->hard_n[s]);
         }
         compact_store<kPI>(live, c, q, s_off, &s_base, cnt_out, cout, vout);
     }
@@ -296,6 +309,7 @@ __device__ __forceinline__ void particles_inplace(const StepParams &p, int s, in
         for (int k = 0; k < kWI; ++k) {
             const long long i = base + k * 32 + lane;
             bool hard = false;
+            float axh = 0.0f;
             if (act[k]) {
                 if (c[k] < 0) {
                     __stcs(cout + i, -1);  // a hole stays a hole
@@ -317,10 +331,11 @@ __device__ __forceinline__ void particles_inplace(const StepParams &p, int s, in
                         }
                     } else {
                         hard = true;  // k_hard pushes it and writes its slot
+                        axh = ax;
                     }
                 }
             }
-            list_hard(hard, i, sp, &p.st->hard_n[s]);
+            list_hard(hard, i, c[k], q[k], axh, sp, &p.st->hard_n[s]);
         }
     }
 
@@ -484,14 +499,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
     __shared__ unsigned s_abs[2];
     __shared__ int s_fail;
 
-    span_enter(p.st, 0);
-    const long long step = *(volatile long long *)&p.st->step;
-    const int P = (int)(step & 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = threadIdx.x; j < p.nn; j += kTmaThreads) {
         s_lo[j] = 0u;
         s_hi[j] = 0u;
-        s_E[j] = p.E[j];
     }
     if (threadIdx.x == 0) {
         for (int k = 0; k < stages; ++k) {
@@ -502,6 +513,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    span_enter(p.st, 0);
+    const long long step = *(volatile long long *)&p.st->step;
+    const int P = (int)(step & 1);
+    for (int j = threadIdx.x; j < p.nn; j += kTmaThreads)
+        s_E[j] = p.E[j];
     __syncthreads();
     volatile int *fail = &s_fail;
 
@@ -577,6 +593,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
                 for (int m = 0; m < kTmaPer; ++m) {
                     const long long i = i0 + m * kTmaConsumers + threadIdx.x;
                     bool hard = false;
+                    float axh = 0.0f;
                     if (act[m]) {
                         if (c[m] < 0) {
                             __stcs(cout + i, -1);  // a hole stays a hole
@@ -598,10 +615,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
                                 }
                             } else {
                                 hard = true;  // k_hard pushes it and writes its slot
+                                axh = ax;
                             }
                         }
                     }
-                    list_hard(hard, i, sp, &p.st->hard_n[s]);
+                    list_hard(hard, i, c[m], q[m], axh, sp, &p.st->hard_n[s]);
                 }
             }
             // species done: absorbed counts, histogram flush and clear
@@ -725,10 +743,22 @@ __device__ __forceinline__ void hard_body(const StepParams &p, int compact, long
                 }
             const SpeciesDev &sp = p.sp[s];
             DepositU64 dep{p.acc + ((size_t)(P ^ 1) * p.ns + s) * p.nn};
-            slot = sp.hard[t - base];
-            c = sp.cell[P][slot];
-            q = sp.pv[P][slot];
-            float ax = gather_ax(p, sp, p.E, c, q.x);
+            const long long k = t - base;
+            float ax;
+            if (k < sp.hard_recs) {
+                const int4 *rec = reinterpret_cast<const int4 *>(sp.hard + k);
+                const int4 r0 = __ldcs(rec), r1 = __ldcs(rec + 1);  // one record, no chain
+                slot = r0.x;
+                c = r0.y;
+                ax = __int_as_float(r0.z);
+                q = make_float4(__int_as_float(r1.x), __int_as_float(r1.y),
+                                __int_as_float(r1.z), __int_as_float(r1.w));
+            } else {  // past the records: the slot, then the particle and its field
+                slot = sp.hard_slot[k];
+                c = sp.cell[P][slot];
+                q = sp.pv[P][slot];
+                ax = gather_ax(p, sp, p.E, c, q.x);
+            }
             const float v0n = v0_at<kProf>(p, sp, c);
             float vx = push_vx_walk(sp.kind, q.y, q.z, q.w, ax, p.dt, v0n);
             int wall = 0;

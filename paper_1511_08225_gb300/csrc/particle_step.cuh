@@ -103,9 +103,8 @@ struct DepositU64 {
 // the old value the atomic returns and added to hi, so the sum stays exact.
 struct DepositSplit32 {
     unsigned *lo, *hi;
-    __device__ __forceinline__ void add(int c, unsigned long long v)
+    __device__ __forceinline__ void add(int c, unsigned vl, unsigned vh)
     {
-        unsigned vl = (unsigned)v, vh = (unsigned)(v >> 32);
         unsigned old = atomicAdd(lo + c, vl);
         vh += (old + vl < old) ? 1u : 0u;
         if (vh)
@@ -113,10 +112,10 @@ struct DepositSplit32 {
     }
     __device__ __forceinline__ void operator()(int c, int c1, float b, float off)
     {
-        unsigned long long qL, qR;
-        quantise(b, off, qL, qR);
-        add(c, qL);
-        add(c1, qR);
+        unsigned llo, lhi, rlo, rhi;
+        quantise_split(b, off, llo, lhi, rlo, rhi);
+        add(c, llo, lhi);
+        add(c1, rlo, rhi);
     }
 };
 

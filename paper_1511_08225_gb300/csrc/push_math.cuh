@@ -49,31 +49,55 @@ __device__ __forceinline__ float beta_q(int kind, float vx, float vy, float vz, 
     return __fdiv_rn(v0, __fsqrt_rn(__fadd_rn(s2, __fmul_rn(v0, v0))));
 }
 
-// rint(x) as an unsigned 64-bit integer, for 0 <= x < 2^41, from the bits of
-// rintf(x): the rounded value is an integer with at most 24 significant bits,
-// i.e. its mantissa (hidden bit included) shifted by exponent - 23.  Integer
-// shifts only: a float -> int64 conversion would run on the FP64 pipe, which is
-// narrow on this GPU.  Same value as llrintf (round to nearest, ties to even).
-__device__ __forceinline__ unsigned long long rint_u64(float x)
+// rint(x) (round to nearest, ties to even) for 0 <= x < 2^41 as two 32-bit words,
+// value = hi 2^32 + lo, with 32-bit integer operations only (a float -> int64
+// conversion would run on the FP64 pipe, which is narrow on this GPU, and a 64-bit
+// variable shift takes several instructions):
+//   x < 2^23:  x + 2^23 lies in [2^23, 2^24], where the float spacing is 1, so the
+//              sum is rounded to an integer exactly as rint rounds x, and its bits
+//              minus those of 2^23 are that integer (2^24 - 2^23 = 2^23 included);
+//   x >= 2^23: x is an integer already: its 24-bit significand shifted left by
+//              exponent - 23 (0..17), the words split off by a funnel shift.
+__device__ __forceinline__ void rint_split(float x, unsigned &lo, unsigned &hi)
 {
-    unsigned bits = __float_as_uint(rintf(x));
-    if (bits == 0u)
-        return 0ULL;
-    int e = (int)(bits >> 23) - 127;  // unbiased exponent, 0 <= e <= 40
-    unsigned long long m = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
-    return e >= 23 ? (m << (e - 23)) : (m >> (23 - e));
+    const unsigned bits = __float_as_uint(x);
+    const bool big = x >= 8388608.0f;
+    const unsigned sh = big ? (bits >> 23) - 150u : 0u;  // exponent - 23
+    const unsigned m = (bits & 0x7FFFFFu) | 0x800000u;
+    const unsigned small = __float_as_uint(__fadd_rn(x, 8388608.0f)) - 0x4B000000u;
+    lo = big ? (m << sh) : small;
+    hi = big ? __funnelshift_l(m, 0u, sh) : 0u;
 }
 
-// qT = rint(beta 2^40), qR = rint((beta*offset) 2^40); node c gets qT - qR,
-// node c+1 gets qR.
+// The same value as one unsigned 64-bit integer.
+__device__ __forceinline__ unsigned long long rint_u64(float x)
+{
+    unsigned lo, hi;
+    rint_split(x, lo, hi);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// qT = rint(beta 2^40), qR = rint((beta*offset) 2^40); node c gets qL = qT - qR,
+// node c+1 gets qR; each as two 32-bit words (value = hi 2^32 + lo).
+__device__ __forceinline__ void quantise_split(float beta, float offset, unsigned &qLlo,
+                                               unsigned &qLhi, unsigned &qRlo, unsigned &qRhi)
+{
+    const float two40 = 1099511627776.0f;
+    unsigned tlo, thi;
+    rint_split(__fmul_rn(__fmul_rn(beta, offset), two40), qRlo, qRhi);
+    rint_split(__fmul_rn(beta, two40), tlo, thi);
+    qLlo = tlo - qRlo;
+    qLhi = thi - qRhi - (tlo < qRlo ? 1u : 0u);
+}
+
+// The same as 64-bit integers.
 __device__ __forceinline__ void quantise(float beta, float offset, unsigned long long &qL,
                                          unsigned long long &qR)
 {
-    const float two40 = 1099511627776.0f;
-    unsigned long long r = rint_u64(__fmul_rn(__fmul_rn(beta, offset), two40));
-    unsigned long long t = rint_u64(__fmul_rn(beta, two40));
-    qR = r;
-    qL = t - r;
+    unsigned llo, lhi, rlo, rhi;
+    quantise_split(beta, offset, llo, lhi, rlo, rhi);
+    qL = ((unsigned long long)lhi << 32) | llo;
+    qR = ((unsigned long long)rhi << 32) | rlo;
 }
 
 // int_{wa}^{wa+d} sqrt(w^2 + D) dw for a segment that does not cross w = 0
@@ -109,27 +133,27 @@ constexpr float kSeriesMax = 0.12f;
 
 __device__ __forceinline__ float series_poly(float om, float k)
 {
-    // explicit fused multiply-adds: every kernel that inlines this gets the same bits
-    const float o2 = om * om;
-    const float b2 = -0.5f * om;
-    const float b3 = __fmaf_rn(4.0f, o2, -1.0f) * (1.0f / 6.0f);
-    const float b4 = -om * __fmaf_rn(28.0f, o2, -13.0f) * (1.0f / 24.0f);
-    const float b5 = __fmaf_rn(__fmaf_rn(280.0f, o2, -188.0f), o2, 13.0f) * (1.0f / 120.0f);
-    const float b6 = -om * __fmaf_rn(__fmaf_rn(3640.0f, o2, -3188.0f), o2, 493.0f) * (1.0f / 720.0f);
-    const float b7 =
-        __fmaf_rn(__fmaf_rn(__fmaf_rn(58240.0f, o2, -62832.0f), o2, 15480.0f), o2, -493.0f) *
-        (1.0f / 5040.0f);
-    const float b8 =
-        -om * __fmaf_rn(__fmaf_rn(__fmaf_rn(1106560.0f, o2, -1417584.0f), o2, 483528.0f), o2,
-                        -37369.0f) *
-        (1.0f / 40320.0f);
-    float poly = __fmaf_rn(b8, k, b7);
-    poly = __fmaf_rn(poly, k, b6);
-    poly = __fmaf_rn(poly, k, b5);
-    poly = __fmaf_rn(poly, k, b4);
-    poly = __fmaf_rn(poly, k, b3);
-    poly = __fmaf_rn(poly, k, b2);
-    return __fmaf_rn(poly, k, 1.0f);
+    // b_n is even in om for odd n and om times an even polynomial for even n, so the
+    // sum splits into two polynomials in k^2 whose coefficients are polynomials in
+    // om^2 (the divisors folded into them):
+    //   1 + b3 k^2 + b5 k^4 + b7 k^6  +  om k (d2 + d4 k^2 + d6 k^4 + d8 k^6),  b_n = om d_n.
+    // Explicit fused multiply-adds: every kernel that inlines this gets the same bits.
+    const float o2 = __fmul_rn(om, om);
+    const float k2 = __fmul_rn(k, k);
+    const float b3 = __fmaf_rn(4.0f / 6.0f, o2, -1.0f / 6.0f);
+    const float b5 = __fmaf_rn(__fmaf_rn(280.0f / 120.0f, o2, -188.0f / 120.0f), o2, 13.0f / 120.0f);
+    const float b7 = __fmaf_rn(__fmaf_rn(__fmaf_rn(58240.0f / 5040.0f, o2, -62832.0f / 5040.0f), o2,
+                                         15480.0f / 5040.0f),
+                               o2, -493.0f / 5040.0f);
+    const float d4 = __fmaf_rn(-28.0f / 24.0f, o2, 13.0f / 24.0f);
+    const float d6 = __fmaf_rn(__fmaf_rn(-3640.0f / 720.0f, o2, 3188.0f / 720.0f), o2, -493.0f / 720.0f);
+    const float d8 =
+        __fmaf_rn(__fmaf_rn(__fmaf_rn(-1106560.0f / 40320.0f, o2, 1417584.0f / 40320.0f), o2,
+                            -483528.0f / 40320.0f),
+                  o2, 37369.0f / 40320.0f);
+    const float ev = __fmaf_rn(__fmaf_rn(__fmaf_rn(b7, k2, b5), k2, b3), k2, 1.0f);
+    const float od = __fmul_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(d8, k2, d6), k2, d4), k2, -0.5f), k);
+    return __fmaf_rn(om, od, ev);
 }
 
 // Solve int_{wa}^{wa+d} sqrt(w^2 + D) dw = y for d in [0, dmax], on a piece

@@ -47,10 +47,24 @@ struct DevState {
     unsigned int pad2;
 };
 
+// A particle listed for the iterative push, with what the push needs, so that the
+// kernel that pushes it reads one record instead of a chain of dependent loads.
+struct HardRec {
+    int32_t slot;  // its slot in the step's input buffer
+    int32_t cell;  // c at time level n
+    float ax;      // (q/m) E gathered at the particle
+    int32_t pad;
+    float4 q;      // {offset, vx, vy, vz} at time level n (v = v^{n-1/2})
+};
+
 struct SpeciesDev {
     int32_t *cell[2];
     float4 *pv[2];
-    int32_t *hard;   // slots of this step's particles that need the iterative push
+    // this step's particles that need the iterative push: entry k < hard_recs is a
+    // record in hard[k]; a longer list (rare) continues as slots in hard_slot[k]
+    HardRec *hard;
+    int32_t *hard_slot;
+    long long hard_recs;
     long long capacity;
     float qm;        // q/m
     float v0;        // speed limit

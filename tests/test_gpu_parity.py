@@ -18,6 +18,7 @@ from oracle import oracle as orc
 from paper_1511_08225_gb300 import binding, inputs
 
 from _match import key_of, match, periodic_diff
+from _stepcheck import compare_step as _compare_step
 
 pytestmark = pytest.mark.gpu
 
@@ -111,60 +112,6 @@ def test_field_solve_matches_thomas(periodic, phi_hi):
 
 
 # ------------------------------------------------------------------ one step
-def _compare_step(prob, st, gpu, o, rel=1e-5, stats=None, lam=None):
-    """Per-particle bars of the module docstring, matched by (vy, vz).
-
-    Velocity: |v_gpu - v_orc| <= rel |v|.  Position: the move is
-    beta(|v|) v_x dt, so a velocity error of rel |v| moves x by at most
-    rel beta(|v|) |v| dt; the bar is that plus 8 ulp of the FP32 offset.
-    lam: per-cell factors of v0 (beta then takes v0 lam[start cell])."""
-    dx, N = prob["dx"], prob["n_cells"]
-    L = N * dx
-    for s in range(len(st)):
-        c0, off0, v0in = st[s]
-        x_in = (c0.astype(np.float64) + off0.astype(np.float64)) * dx
-        c, off, v = gpu.particles(s)
-        xo, vo = o.x[s], o.v[s]
-        # survivors in the oracle, in input order (no injection here)
-        ko = key_of(vo)
-        kg = key_of(v)
-        ia, ib = match(ko, kg)
-        # every oracle survivor is found on the GPU except within rounding of a wall
-        missing = np.setdiff1d(np.arange(ko.size), ia)
-        extra = np.setdiff1d(np.arange(kg.size), ib)
-        for idx, xs in ((missing, xo), ):
-            if idx.size:
-                near = np.minimum(xs[idx], L - xs[idx]) < 1e-5 * dx
-                assert near.all(), f"species {s}: {idx.size} survivors lost"
-        if extra.size:
-            xg_extra = (c[extra] + off[extra].astype(np.float64)) * dx
-            assert (np.minimum(xg_extra, L - xg_extra) < 1e-5 * dx).all()
-        xg = (c[ib].astype(np.float64) + off[ib].astype(np.float64)) * dx
-        vg = v[ib].astype(np.float64)
-        vref = vo[ia]
-        # input positions of the matched particles
-        kin = key_of(v0in)
-        ja, jb = match(ko[ia], kin)
-        assert ja.size == ia.size
-        xin = x_in[jb]
-        vnorm = np.maximum(np.linalg.norm(vref, axis=1), np.linalg.norm(v0in[jb], axis=1))
-        dv = np.linalg.norm(vg - vref, axis=1)
-        assert (dv <= rel * vnorm + 1e-30).all(), \
-            f"species {s}: worst dv/|v| {np.max(dv / np.maximum(vnorm, 1e-30)):.3e}"
-        dxp = periodic_diff(xg, xo[ia], L) if prob["periodic"] else xg - xo[ia]
-        sp = prob["species"][s]
-        r = np.linalg.norm(vref, axis=1)
-        v0p = float(sp["v0"]) if lam is None else \
-            float(sp["v0"]) * np.asarray(lam, np.float64)[st[s][0][jb]]
-        b = orc._beta_vec(int(sp["kind"]), r, v0p)
-        tol = rel * b * r * prob["dt"] + 8 * 2.0 ** -24 * dx
-        if stats is not None:
-            stats.append({"species": s, "max_dv_rel": float(np.max(dv / np.maximum(vnorm, 1e-30))),
-                          "max_dx_over_tol": float(np.max(np.abs(dxp) / tol)), "n": int(ia.size)})
-        assert (np.abs(dxp) <= tol).all(), \
-            f"species {s}: worst position error {np.max(np.abs(dxp) - tol):.3e} over tol"
-
-
 @pytest.mark.parametrize("kind", [ONE, HEAV, REL])
 @pytest.mark.parametrize("periodic", [False, True])
 def test_single_step_matches_oracle(kind, periodic):
