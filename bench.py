@@ -856,6 +856,66 @@ def unet_macs(levels, base, H, W):
     return tot
 
 
+def run_unet_net(args):
+    """The learned warm start's network alone: a tensor-core U-Net (4 levels, base
+    channels --unet-base, BF16 weights, FP32 accumulation) on --nx x --ny images,
+    batch 1, random data: W warm-up forward passes and Adam steps, then K forward
+    passes and K training steps timed with CUDA events on the network's stream.  The
+    forward's FLOPs against the measured BF16 tensor peak."""
+    import torch
+    from paper_1511_08225_gb300 import binding_unet
+    from paper_1511_08225_gb300 import build as pkg_build
+    pkg_build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    nx, ny, L, C = args.nx, args.ny, 4, args.unet_base
+    net = binding_unet.UNet(L, C, ny, nx, max_batch=1, normalise=False, seed=1,
+                            tensor_cores=not args.unet_cuda_cores)
+    net.set_stream(stream.cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(1, ny, nx, device="cuda", generator=g)
+    t = torch.randn(1, ny, nx, device="cuda", generator=g)
+    y = torch.zeros_like(x)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        net.forward(x, y)
+        net.train_step(x, t, 1e-4)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        net.forward(x, y)
+    ev[1].record(stream)
+    for _ in range(args.steps):
+        net.train_step(x, t, 1e-4)
+    ev[2].record(stream)
+    ev[2].synchronize()
+    fwd_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    train_ms = ev[1].elapsed_time(ev[2]) / args.steps
+    macs = unet_macs(L, C, ny, nx)
+    fwd_tflops = 2 * macs / (fwd_ms * 1e-3) / 1e12
+    peak, kind = bf16_peak_tflops()
+    net.close()
+    line = {
+        "metric": "U-Net forward TFLOP/s (learned warm start's network), 1xGB300",
+        "value": fwd_tflops, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": fwd_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "impl": "gb300",
+        "config": {"workload": f"U-Net {L} levels, {C}..{C * 2 ** (L - 1)} channels, "
+                               f"{nx}x{ny}, batch 1, random data", "macs": macs},
+        "train_step_ms": train_ms,
+        "train_step_tflops": 3 * 2 * macs / (train_ms * 1e-3) / 1e12,
+        "roofline": {"bound": "tensor", "achieved": fwd_tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": fwd_tflops / peak, "traffic": None,
+                     "kernel": "U-Net forward (k_conv_fwd_tc and the elementwise layers)",
+                     "peak_source": f"{kind} dense BF16 (cuBLAS burst)"},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_unet2d(args):
     """The 2D workload with the learned warm start of the CG: (rho, phi) pairs from a
     run of one seed, two U-Nets trained on them by the library (phi from rho, and the
@@ -1085,10 +1145,12 @@ def main():
     ap.add_argument("--v0-profile", default="none", choices=["none", "sine"],
                     help="sheath1d: a speed limit varying in space (per-cell factors of v0)")
     ap.add_argument("--workload", default="sheath1d",
-                    choices=["sheath1d", "plasma2d", "batch", "paper_sheath", "unet2d"],
+                    choices=["sheath1d", "plasma2d", "batch", "paper_sheath", "unet2d",
+                             "unet_net"],
                     help="sheath1d (the headline), plasma2d (2D3V + CG), batch (many "
                          "independent sheaths) or paper_sheath (the paper's SLPIC-vs-PIC "
-                         "sheath speedup) or unet2d (plasma2d with the learned CG warm start)")
+                         "sheath speedup) or unet2d (plasma2d with the learned CG warm start) "
+                         "or unet_net (the warm start's network alone)")
     ap.add_argument("--ppc-sheath", type=int, default=500)
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=1024)
@@ -1116,6 +1178,8 @@ def main():
         return run_batch(args)
     if args.workload == "paper_sheath":
         return run_paper_sheath(args)
+    if args.workload == "unet_net":
+        return run_unet_net(args)
     if args.workload == "unet2d":
         return run_unet2d(args)
     return run_gpu(args)

@@ -407,15 +407,22 @@ int slpic_set_speed_limit_profile(slpic_t *h, const double *lambda, int n_cells)
  * nodes = n_cells + 1 (Dirichlet) or n_cells (periodic).  The call waits for its
  * work on `stream` to finish before it returns.
  *
- * Its only scratch (three counters and the int64 accumulator) is a fixed array in
+ * Every input particle must have 0 <= cell < n_cells and 0 <= offset < 1; one that
+ * does not is skipped (neither deposited nor written out) and the call returns
+ * SLPIC_ERR_INVALID after completing the step for the others.  The output arrays
+ * must not overlap the input arrays (SLPIC_ERR_INVALID): survivors are packed
+ * across thread blocks, so an overlap could overwrite particles not yet read.
+ *
+ * Its only scratch (four counters and the int64 accumulator) is a fixed array in
  * device memory that every GPU loading the library holds until exit; grids of
  * more than 16384 nodes return SLPIC_ERR_CAPACITY.  The first call on a device
  * looks up that array's device address (and sets the kernel's shared-memory
- * limit); make the first call before any stream capture.  All calls share the
- * array; each call clears what it uses, so calls that overlap on the GPU
- * (concurrent streams or threads) race and must be serialised by the caller.
- * Returns SLPIC_ERR_INVALID for bad arguments or misaligned state arrays,
- * SLPIC_ERR_CFL if dt * v0 > dx, SLPIC_ERR_CUDA on a runtime error. */
+ * limit); make that first call, which does this set-up, before any stream
+ * capture.  All calls share the array; each call clears what it uses, so calls
+ * that overlap on the GPU (concurrent streams or threads) race and must be
+ * serialised by the caller.  Returns SLPIC_ERR_INVALID for bad arguments,
+ * misaligned or overlapping arrays, or skipped particles, SLPIC_ERR_CFL if
+ * dt * v0 > dx, SLPIC_ERR_CUDA on a runtime error. */
 int slpic_particle_step_noalloc(const slpic_config *cfg, int species, int64_t n,
                                 const int32_t *cell_in, const float *state_in, const float *E,
                                 int32_t *cell_out, float *state_out, int64_t *charge_out,

@@ -304,8 +304,11 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     {
         int nn_ = cfg->bc == SLPIC_BC_PERIODIC ? cfg->n_cells : cfg->n_cells + 1;
-        // the particle kernel's queue, E and deposit, plus its static shared memory
-        if (particle_kernel_smem_bytes(nn_) + 1024 > (size_t)max_smem || nn_ > field_max_nodes()) {
+        // the particle kernel's E and deposit, plus its static shared memory; the field
+        // kernel's deposits and prefixes per cluster CTA, plus its static shared memory
+        if (particle_kernel_smem_bytes(nn_) + 1024 > (size_t)max_smem ||
+            field_cluster_smem_bytes(nn_, kMaxSpecies) + 4096 > (size_t)max_smem ||
+            nn_ > field_max_nodes()) {
             g_create_err = "grid does not fit in shared memory (n_cells too large for the 1D kernel)";
             return SLPIC_ERR_INVALID;
         }

@@ -1110,6 +1110,13 @@ constexpr int kFCW = kFCT / 32;
 
 typedef unsigned __int128 u128;
 
+// 8-byte words of the field kernel's deposit copy in shared memory, rounded up to an
+// even number so that the 16-byte prefixes after it are aligned
+__host__ __device__ __forceinline__ int field_acc_words(int ns, int per_cta)
+{
+    return (ns * per_cta + 1) & ~1;
+}
+
 __device__ __forceinline__ u128 shfl_up_u128(u128 v, int o)
 {
     unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
@@ -1161,6 +1168,22 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
     const int chunk = (per_cta + kFCT - 1) / kFCT;
     const int j0 = min(c1, c0 + (int)threadIdx.x * chunk), j1 = min(c1, j0 + chunk);
+
+    // the counters CTA 0 updates at the end (thread s for species s), read now so
+    // that their loads overlap the work below rather than end the kernel
+    unsigned long long pf_ab0 = 0, pf_ab1 = 0, pf_holes = 0, pf_hard = 0;
+    long long pf_inj = 0, pf_at0 = 0, pf_at1 = 0, pf_it = 0;
+    if (mode >= 1 && rank == 0 && (int)threadIdx.x < ns) {
+        const int s = threadIdx.x;
+        pf_ab0 = st->absorbed_step[s][0];
+        pf_ab1 = st->absorbed_step[s][1];
+        pf_holes = st->holes[s][P];
+        pf_hard = st->hard_n[s];
+        pf_inj = st->injected_total[s];
+        pf_at0 = st->absorbed_total[s][0];
+        pf_at1 = st->absorbed_total[s][1];
+        pf_it = st->iterative_total[s];
+    }
 
     if (mode >= 1) {
         // ---- source injection (Sec. IV; LOSS_MATCHED / RATE readings).  Every CTA
@@ -1265,6 +1288,10 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         s_tot[threadIdx.x][1] = w2;
         s_tot[threadIdx.x][2] = t2;
     }
+    // the CTA-local inclusive prefix of rows c0.. at each of this thread's nodes, for
+    // the E pass below (which takes the nodes one per thread); 16-byte aligned after
+    // the deposits (an even number of 8-byte words)
+    u128 *s_pre = reinterpret_cast<u128 *>(s_acc + field_acc_words(ns, per_cta));  // [ns][per_cta]
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s) {
         if (s >= ns)
@@ -1273,6 +1300,12 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         for (int w = 0; w < warp; ++w)
             wp += s_warp[s][w];
         before[s] += wp;
+        u128 run = before[s];
+        for (int j = j0; j < j1; ++j) {
+            if (j >= 1 && j < N)
+                run += s_acc[s * per_cta + (j - c0)];
+            s_pre[s * per_cta + (j - c0)] = run;
+        }
     }
     cl.sync();
     // gather the CTAs' totals (distributed shared memory), one remote load per
@@ -1313,29 +1346,38 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     const double D0 = s_c[0], P_last = s_c[1], mean = s_c[2];
     const double k2 = p.k2, inv2dx = 0.5 * p.inv_dx;
 
-    // ---- E on this thread's nodes: P_{j-1} + P_j = k2 (sum_s c_s (A_s[j-1] + A_s[j])
-    //      - mean (2j - 1)), the integer pair sum converted once per species
-    u128 A[kMaxSpecies];  // A_s[j0 - 1] (prefix before the chunk's first row)
+    // ---- E at this CTA's nodes, one node per thread per pass: with A_s[j] the prefix
+    //      of rows 1..j, P_{j-1} + P_j = k2 (sum_s c_s (A_s[j-1] + A_s[j]) - mean (2j - 1))
+    //      and E_j = (P_{j-1} + P_j - 2 D0) / (2 dx); the constants are folded so that a
+    //      node costs one conversion and one FMA per species and one FMA more, its
+    //      species independent (the FP64 pipe is narrow and its latency long)
+    double cE[kMaxSpecies];
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s)
-        A[s] = (s < ns) ? s_off[s] + before[s] : (u128)0;
-    for (int j = j0; j < j1; ++j) {
+        cE[s] = s < ns ? k2 * p.sp[s].rho_unit * inv2dx : 0.0;
+    const double eK0 = -2.0 * D0 * inv2dx, eK1 = -k2 * mean * inv2dx;
+    const int ncta = c1 - c0;
+#pragma unroll 3
+    for (int t = (int)threadIdx.x; t < ncta; t += kFCT) {
+        const int j = c0 + t;
         double e;
         if (j == 0) {
             e = p.periodic ? ((P_last + 0.0) - 2.0 * D0) * inv2dx : -D0 * p.inv_dx;
         } else if (!p.periodic && j == N) {
             e = (P_last - D0) * p.inv_dx;
         } else {
-            double pair = 0.0;
+            double acc_e = fma(eK1, (double)(2 * j - 1), eK0);
 #pragma unroll
             for (int s = 0; s < kMaxSpecies; ++s) {
                 if (s >= ns)
                     break;
-                const u128 prev = A[s];
-                A[s] += s_acc[s * per_cta + (j - c0)];  // row j (1 <= j <= N-1)
-                pair = fma(p.sp[s].rho_unit, u128_to_double(prev + A[s]), pair);
+                // A_s[j] = s_off + prefix at j; A_s[j-1] likewise, or s_off at the CTA's
+                // first node
+                const u128 aj = s_off[s] + s_pre[s * per_cta + t];
+                const u128 ajm = t > 0 ? s_off[s] + s_pre[s * per_cta + t - 1] : s_off[s];
+                acc_e = fma(cE[s], u128_to_double(aj + ajm), acc_e);
             }
-            e = (k2 * (pair - mean * (double)(2 * j - 1)) - 2.0 * D0) * inv2dx;
+            e = acc_e;
         }
         if (p.wave_on)  // test-particle mode: the prescribed field at this time level
             e = wave_E(p, j, (double)(mode >= 1 ? step + 1 : step) * p.dt64);
@@ -1357,18 +1399,17 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
             const long long k = cut ? -s_ninj[s] - 1 : s_ninj[s];
             if (cut)
                 atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
-            const unsigned long long ab0 = st->absorbed_step[s][0], ab1 = st->absorbed_step[s][1];
             st->src_frac[s] = s_frac[s];
-            st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + ab0 + ab1 : 0ULL;
+            st->holes[s][P ^ 1] = mode == 1 ? pf_holes + pf_ab0 + pf_ab1 : 0ULL;
             st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + k);
-            st->injected_total[s] += k;
-            st->absorbed_total[s][0] += (long long)ab0;
-            st->absorbed_total[s][1] += (long long)ab1;
+            st->injected_total[s] = pf_inj + k;
+            st->absorbed_total[s][0] = pf_at0 + (long long)pf_ab0;
+            st->absorbed_total[s][1] = pf_at1 + (long long)pf_ab1;
             st->absorbed_step[s][0] = 0ULL;
             st->absorbed_step[s][1] = 0ULL;
             st->count[s][P] = 0ULL;
             st->holes[s][P] = 0ULL;
-            st->iterative_total[s] += (long long)st->hard_n[s];
+            st->iterative_total[s] = pf_it + (long long)pf_hard;
             st->hard_n[s] = 0ULL;
         }
         // the step index is read at the start of every CTA: advance it last
@@ -1623,7 +1664,9 @@ cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compac
 
 size_t field_cluster_smem_bytes(int nn, int ns)
 {
-    return (size_t)ns * ((nn + kFC - 1) / kFC) * sizeof(unsigned long long);
+    const int per_cta = (nn + kFC - 1) / kFC;
+    return (size_t)field_acc_words(ns, per_cta) * sizeof(unsigned long long) +
+           (size_t)ns * per_cta * sizeof(u128);
 }
 
 void launch_field(const StepParams &p, int mode, cudaStream_t st)

@@ -33,7 +33,8 @@
 namespace slpic {
 
 constexpr int kNoallocMaxNodes = 16384;
-constexpr int kNoallocCounters = 4;  // [0] survivors, [1] absorbed at x=0, [2] at x=L
+constexpr int kNoallocCounters = 4;  // [0] survivors, [1] absorbed at x=0, [2] at x=L,
+                                     // [3] particles skipped as invalid
 
 static __device__ __align__(256) unsigned long long
     g_noalloc_scratch[kNoallocCounters + kNoallocMaxNodes];
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(kNB) k_particles_noalloc(StepParams p, Species
     float *s_E = reinterpret_cast<float *>(s_hist + p.nn);
     __shared__ int s_off[kNWarps];
     __shared__ unsigned long long s_base;
-    __shared__ unsigned int s_abs[2];
+    __shared__ unsigned int s_abs[3];  // absorbed at x=0, at x=L; invalid
     unsigned long long *counters = scratch;
     unsigned long long *acc = scratch + kNoallocCounters;
 
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(kNB) k_particles_noalloc(StepParams p, Species
         s_hist[j] = 0ULL;
         s_E[j] = p.E[j];
     }
-    if (threadIdx.x < 2)
+    if (threadIdx.x < 3)
         s_abs[threadIdx.x] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -76,10 +77,17 @@ __global__ void __launch_bounds__(kNB) k_particles_noalloc(StepParams p, Species
         if (live) {
             c = cin[i];
             q = vin[i];
-            int wall = 0;
-            live = advance(p, sp, s_E, s_hist, c, q, wall);
-            if (!live)
-                atomicAdd(&s_abs[wall], 1u);
+            // the caller's data index the shared-memory grid: a cell outside the grid
+            // or an offset outside [0, 1) is skipped and counted, never used
+            if ((unsigned)c >= (unsigned)p.n_cells || !(q.x >= 0.0f && q.x < 1.0f)) {
+                live = false;
+                atomicAdd(&s_abs[2], 1u);
+            } else {
+                int wall = 0;
+                live = advance(p, sp, s_E, s_hist, c, q, wall);
+                if (!live)
+                    atomicAdd(&s_abs[wall], 1u);
+            }
         }
         unsigned mask = __ballot_sync(0xffffffffu, live);
         if (lane == 0)
@@ -112,7 +120,7 @@ __global__ void __launch_bounds__(kNB) k_particles_noalloc(StepParams p, Species
         if (v)
             atomicAdd(acc + j, v);
     }
-    if (threadIdx.x < 2 && s_abs[threadIdx.x])
+    if (threadIdx.x < 3 && s_abs[threadIdx.x])
         atomicAdd(counters + 1 + threadIdx.x, (unsigned long long)s_abs[threadIdx.x]);
 }
 
@@ -171,6 +179,18 @@ extern "C" int slpic_particle_step_noalloc(const slpic_config *cfg, int species,
         return SLPIC_ERR_CFL;
     if (((uintptr_t)state_in | (uintptr_t)state_out) & 15)
         return SLPIC_ERR_INVALID;
+    // survivors are packed across CTAs, so an output range that overlaps an input
+    // range could overwrite particles another CTA has not read yet
+    if (n > 0) {
+        auto overlap = [n](const void *a, size_t ea, const void *b, size_t eb) {
+            const uintptr_t a0 = (uintptr_t)a, a1 = a0 + (uintptr_t)n * ea;
+            const uintptr_t b0 = (uintptr_t)b, b1 = b0 + (uintptr_t)n * eb;
+            return a0 < b1 && b0 < a1;
+        };
+        if (overlap(cell_in, 4, cell_out, 4) || overlap(state_in, 16, state_out, 16) ||
+            overlap(cell_in, 4, state_out, 16) || overlap(state_in, 16, cell_out, 4))
+            return SLPIC_ERR_INVALID;
+    }
 
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -212,7 +232,7 @@ extern "C" int slpic_particle_step_noalloc(const slpic_config *cfg, int species,
     }
     e = cudaMemcpyAsync(charge_out, scratch + kNoallocCounters, sizeof(int64_t) * nn,
                         cudaMemcpyDeviceToDevice, st);
-    unsigned long long cnt[3] = {0, 0, 0};
+    unsigned long long cnt[4] = {0, 0, 0, 0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cnt, scratch, sizeof(cnt), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
@@ -222,5 +242,5 @@ extern "C" int slpic_particle_step_noalloc(const slpic_config *cfg, int species,
     *n_out = (int64_t)cnt[0];
     absorbed[0] = (int64_t)cnt[1];
     absorbed[1] = (int64_t)cnt[2];
-    return SLPIC_OK;
+    return cnt[3] ? SLPIC_ERR_INVALID : SLPIC_OK;
 }

@@ -111,13 +111,15 @@ __device__ __forceinline__ float seg_integral(float wa, float ra, float d, float
 {
     if (d <= 0.0f)
         return 0.0f;
+    // the quotients by a reciprocal approximation (__fdividef, within 2 ulp): the
+    // walk's root is then within a few ulp, far inside the push's error bar
     float S = ra + rb;
     float sum = wa + wb;
-    float t1 = 0.25f * d * (S + sum * sum / S);
+    float t1 = 0.25f * d * (S + __fdividef(sum * sum, S));
     float t2 = 0.0f;
     if (D > 0.0f) {
         float den = wb * ra + wa * rb;
-        t2 = 0.5f * D * asinhf(d * sum / den);
+        t2 = 0.5f * D * asinhf(__fdividef(d * sum, den));
     }
     return t1 + t2;
 }
@@ -178,9 +180,10 @@ __device__ __forceinline__ float solve_seg(float wa, float D, float y, float dma
     }
     for (int it = 0; it < 24; ++it) {
         float wb = wa + d;
-        float rb = sqrtf(wb * wb + D);
+        const float r2 = wb * wb + D;  // > 0: a fast piece never reaches |v| = 0
+        float rb = r2 * rsqrtf(r2);
         float f = seg_integral(wa, ra, d, wb, rb, D) - y;
-        float dn = fminf(fmaxf(d - f / rb, 0.0f), dmax);
+        float dn = fminf(fmaxf(d - __fdividef(f, rb), 0.0f), dmax);
         bool done = fabsf(dn - d) <= 4e-7f * dn;
         d = dn;
         if (done)

@@ -114,3 +114,62 @@ def test_noalloc_rejects_grids_beyond_its_scratch(torch_cuda):
             torch.zeros((1, 4), device=dev), torch.zeros(20_000, dtype=torch.int64, device=dev))
     assert ei.value.code == binding.SLPIC_ERR_CAPACITY
     del z
+
+
+def test_noalloc_rejects_overlapping_arrays(torch_cuda):
+    """Survivors are packed across thread blocks, so outputs that overlap the inputs
+    could overwrite unread particles: the call refuses them before any work."""
+    torch = torch_cuda
+    prob = _problem(False, 1, 96)
+    cfg = binding.config_from_problem(prob)
+    dev = torch.device("cuda")
+    n = 1000
+    cells = torch.zeros(2 * n, dtype=torch.int32, device=dev)
+    states = torch.zeros((2 * n, 4), dtype=torch.float32, device=dev)
+    E = torch.zeros(97, device=dev)
+    charge = torch.zeros(97, dtype=torch.int64, device=dev)
+    for cin, sin, cout, sout in ((cells[:n], states[:n], cells[:n], states[n:]),
+                                 (cells[:n], states[:n], cells[n:], states[n // 2:n // 2 + n])):
+        with pytest.raises(binding.SlpicError) as ei:
+            binding.slpic_particle_step_noalloc(cfg, 0, cin, sin, E, cout, sout, charge)
+        assert ei.value.code == binding.SLPIC_ERR_INVALID
+
+
+def test_noalloc_skips_and_reports_particles_outside_the_grid(torch_cuda):
+    """A cell outside [0, n_cells) or an offset outside [0, 1) would index the
+    kernel's shared-memory grid out of range: such particles are skipped, the others
+    stepped, and the call reports SLPIC_ERR_INVALID.  The deposit is then that of the
+    valid particles alone."""
+    torch = torch_cuda
+    N = 96
+    prob = _problem(False, 1, N)
+    cfg = binding.config_from_problem(prob)
+    dev = torch.device("cuda")
+    (c, o, v), _ = _state(N, (5000, 1), seed=9)
+    c = c.copy()
+    o = o.copy()
+    c[0::291] = -5      # below the grid
+    c[97::291] = N + 3  # beyond it
+    o[194::291] = 1.5   # offset outside [0, 1)
+    bad = (c < 0) | (c >= N) | (o >= 1.0)
+    assert bad.sum() > 10
+    st = np.concatenate([o[:, None], v], axis=1).astype(np.float32)
+    E = torch.tensor(np.linspace(-0.5, 0.5, N + 1, dtype=np.float32), device=dev)
+
+    def run(cc, ss):
+        cin = torch.tensor(cc, device=dev)
+        sin = torch.tensor(ss, device=dev)
+        cout = torch.empty_like(cin)
+        sout = torch.empty_like(sin)
+        charge = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+        return cin, sin, cout, sout, charge
+
+    cin, sin, cout, sout, charge = run(c, st)
+    with pytest.raises(binding.SlpicError) as ei:
+        binding.slpic_particle_step_noalloc(cfg, 0, cin, sin, E, cout, sout, charge)
+    assert ei.value.code == binding.SLPIC_ERR_INVALID
+    got = charge.cpu().numpy()
+    cin2, sin2, cout2, sout2, charge2 = run(c[~bad], st[~bad])
+    n_out, _ = binding.slpic_particle_step_noalloc(cfg, 0, cin2, sin2, E, cout2, sout2, charge2)
+    assert n_out > 0
+    assert np.array_equal(got, charge2.cpu().numpy())
