@@ -161,7 +161,7 @@ __device__ __forceinline__ void list_hard(bool hard, long long i, int c, const f
 
 // Bodies of the kernels take the parameters by reference (kernel parameter space
 // for one simulation, shared memory for a batch) and the CTA's share of the work.
-template <bool kProf>
+template <bool kProf, int kKind = kAny, int kPer = kAny>
 __device__ __forceinline__ void particles_compact(const StepParams &p, int s, int cta, int nctas)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -217,12 +217,14 @@ __device__ __forceinline__ void particles_compact(const StepParams &p, int s, in
             bool hard = false;
             float axh = 0.0f;
             if (live[k]) {
-                float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
+                float ax = gather_ax<kPer>(p, sp, s_E, c[k], q[k].x);
                 const float v0n = v0_at<kProf>(p, sp, c[k]);
                 float vx;
-                if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, v0n, vx)) {
+                const int kind = kKind == kAny ? sp.kind : kKind;
+                if (push_vx_easy(kind, q[k].y, q[k].z, q[k].w, ax, p.dt, v0n, vx)) {
                     int wall = 0;
-                    live[k] = move_and_deposit<kProf>(p, sp, dep, c[k], q[k], vx, wall, v0n);
+                    live[k] = move_and_deposit<kProf, kKind, kPer>(p, sp, dep, c[k], q[k], vx,
+                                                                   wall, v0n);
                     if (!live[k])
                         atomicAdd(&s_abs[wall], 1u);
                 } else {
@@ -251,7 +253,7 @@ constexpr int kWT = 32 * kWI;    // particles per warp-tile
 
 size_t particle_inplace_smem_bytes(int nn) { return (size_t)nn * 3 * sizeof(unsigned); }
 
-template <bool kProf>
+template <bool kProf, int kKind = kAny, int kPer = kAny>
 __device__ __forceinline__ void particles_inplace(const StepParams &p, int s, int cta, int nctas)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -314,12 +316,14 @@ __device__ __forceinline__ void particles_inplace(const StepParams &p, int s, in
                 if (c[k] < 0) {
                     __stcs(cout + i, -1);  // a hole stays a hole
                 } else {
-                    float ax = gather_ax(p, sp, s_E, c[k], q[k].x);
+                    float ax = gather_ax<kPer>(p, sp, s_E, c[k], q[k].x);
                     const float v0n = v0_at<kProf>(p, sp, c[k]);
                     float vx;
-                    if (push_vx_easy(sp.kind, q[k].y, q[k].z, q[k].w, ax, p.dt, v0n, vx)) {
+                    const int kind = kKind == kAny ? sp.kind : kKind;
+                    if (push_vx_easy(kind, q[k].y, q[k].z, q[k].w, ax, p.dt, v0n, vx)) {
                         int wall = 0;
-                        if (move_and_deposit<kProf>(p, sp, dep, c[k], q[k], vx, wall, v0n)) {
+                        if (move_and_deposit<kProf, kKind, kPer>(p, sp, dep, c[k], q[k], vx, wall,
+                                                                 v0n)) {
                             __stcs(cout + i, c[k]);
                             __stcs(vout + i, q[k]);
                         } else {
@@ -484,6 +488,90 @@ __device__ __forceinline__ void tma_share(long long n, int cta, int nctas, long 
     t1 = nt * (cta + 1) / nctas;
 }
 
+// One species' share of the in-place TMA step, for a consumer thread: its tiles from
+// the ring (stage counter k carried across species), each particle gathered, pushed,
+// moved, deposited into the shared histogram and written back to its slot (or listed
+// for k_hard).  kKind/kPer fix the species' beta kind and the grid's periodicity.
+template <bool kProf, int kKind, int kPer>
+__device__ __forceinline__ void tma_species(const StepParams &p, int s, int P, int &st,
+                                            unsigned &ph, int stages, uint64_t *full,
+                                            uint64_t *empty,
+                                            const float4 *s_v, const int32_t *s_c,
+                                            const float *s_E, DepositSplit32 &dep,
+                                            volatile int *fail, unsigned &nabs0, unsigned &nabs1)
+{
+    const SpeciesDev &sp = p.sp[s];
+    const int lane = threadIdx.x & 31;
+    const long long n = (long long)*(volatile unsigned long long *)&p.st->count[s][P];
+    const int32_t *__restrict__ cin = sp.cell[P];
+    int32_t *__restrict__ cout = sp.cell[P ^ 1];
+    float4 *__restrict__ vout = sp.pv[P ^ 1];
+    long long t0, t1;
+    tma_share(n, blockIdx.x, gridDim.x, t0, t1);
+    for (long long t = t0; t < t1; ++t) {
+        const bool ok = !*fail && mbar_wait(&full[st], ph, fail, &p.st->error, p.wait_cycles);
+        const long long i0 = t * kTmaTile;
+        const int cnt = (int)min((long long)kTmaTile, n - i0);
+        const int cb = cnt & ~3;
+        int c[kTmaPer];
+        float4 q[kTmaPer];
+        bool act[kTmaPer];
+#pragma unroll
+        for (int m = 0; m < kTmaPer; ++m) {
+            const int j = m * kTmaConsumers + threadIdx.x;
+            act[m] = ok && j < cnt;
+            c[m] = -1;
+            if (act[m]) {
+                q[m] = s_v[(size_t)st * kTmaTile + j];
+                c[m] = j < cb ? s_c[(size_t)st * kTmaTile + j] : __ldcs(cin + i0 + j);
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && ok)
+            mbar_arrive(&empty[st]);  // the stage is in registers: free it
+#pragma unroll
+        for (int m = 0; m < kTmaPer; ++m) {
+            const long long i = i0 + m * kTmaConsumers + threadIdx.x;
+            bool hard = false;
+            float axh = 0.0f;
+            if (act[m]) {
+                if (c[m] < 0) {
+                    __stcs(cout + i, -1);  // a hole stays a hole
+                } else {
+                    float ax = gather_ax<kPer>(p, sp, s_E, c[m], q[m].x);
+                    const float v0n = v0_at<kProf>(p, sp, c[m]);
+                    float vx;
+                    const int kind = kKind == kAny ? sp.kind : kKind;
+                    if (push_vx_easy(kind, q[m].y, q[m].z, q[m].w, ax, p.dt, v0n, vx)) {
+                        int wall = 0;
+                        if (move_and_deposit<kProf, kKind, kPer>(p, sp, dep, c[m], q[m], vx, wall,
+                                                                v0n)) {
+                            __stcs(cout + i, c[m]);
+                            __stcs(vout + i, q[m]);
+                        } else {
+                            __stcs(cout + i, -1);
+                            if (wall)
+                                ++nabs1;
+                            else
+                                ++nabs0;
+                        }
+                    } else {
+                        hard = true;  // k_hard pushes it and writes its slot
+                        axh = ax;
+                    }
+                }
+            }
+            list_hard(hard, i, c[m], q[m], axh, sp, &p.st->hard_n[s]);
+        }
+        // the next tile's stage and phase (the ring's k-th tile sits in stage k mod
+        // stages, phase (k / stages) mod 2), counted rather than divided
+        if (++st == stages) {
+            st = 0;
+            ph ^= 1u;
+        }
+    }
+}
+
 template <bool kProf>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_constant__ StepParams p,
                                                                  int stages)
@@ -554,74 +642,21 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
         }
     } else {
         // ---- consumers
-        long long k = 0;
+        int st = 0;        // stage of the next tile
+        unsigned ph = 0u;  // its phase
         for (int s = 0; s < p.ns; ++s) {
             const SpeciesDev &sp = p.sp[s];
-            const long long n = (long long)*(volatile unsigned long long *)&p.st->count[s][P];
-            const int32_t *__restrict__ cin = sp.cell[P];
-            int32_t *__restrict__ cout = sp.cell[P ^ 1];
-            float4 *__restrict__ vout = sp.pv[P ^ 1];
             DepositSplit32 dep{s_lo, s_hi};
             unsigned nabs0 = 0u, nabs1 = 0u;
-            long long t0, t1;
-            tma_share(n, blockIdx.x, gridDim.x, t0, t1);
-            for (long long t = t0; t < t1; ++t, ++k) {
-                const int st = (int)(k % stages);
-                const unsigned ph = (unsigned)((k / stages) & 1);
-                const bool ok = !*fail && mbar_wait(&full[st], ph, fail, &p.st->error,
-                                                    p.wait_cycles);
-                const long long i0 = t * kTmaTile;
-                const int cnt = (int)min((long long)kTmaTile, n - i0);
-                const int cb = cnt & ~3;
-                int c[kTmaPer];
-                float4 q[kTmaPer];
-                bool act[kTmaPer];
-#pragma unroll
-                for (int m = 0; m < kTmaPer; ++m) {
-                    const int j = m * kTmaConsumers + threadIdx.x;
-                    act[m] = ok && j < cnt;
-                    c[m] = -1;
-                    if (act[m]) {
-                        q[m] = s_v[(size_t)st * kTmaTile + j];
-                        c[m] = j < cb ? s_c[(size_t)st * kTmaTile + j] : __ldcs(cin + i0 + j);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0 && ok)
-                    mbar_arrive(&empty[st]);  // the stage is in registers: free it
-#pragma unroll
-                for (int m = 0; m < kTmaPer; ++m) {
-                    const long long i = i0 + m * kTmaConsumers + threadIdx.x;
-                    bool hard = false;
-                    float axh = 0.0f;
-                    if (act[m]) {
-                        if (c[m] < 0) {
-                            __stcs(cout + i, -1);  // a hole stays a hole
-                        } else {
-                            float ax = gather_ax(p, sp, s_E, c[m], q[m].x);
-                            const float v0n = v0_at<kProf>(p, sp, c[m]);
-                            float vx;
-                            if (push_vx_easy(sp.kind, q[m].y, q[m].z, q[m].w, ax, p.dt, v0n, vx)) {
-                                int wall = 0;
-                                if (move_and_deposit<kProf>(p, sp, dep, c[m], q[m], vx, wall, v0n)) {
-                                    __stcs(cout + i, c[m]);
-                                    __stcs(vout + i, q[m]);
-                                } else {
-                                    __stcs(cout + i, -1);
-                                    if (wall)
-                                        ++nabs1;
-                                    else
-                                        ++nabs0;
-                                }
-                            } else {
-                                hard = true;  // k_hard pushes it and writes its slot
-                                axh = ax;
-                            }
-                        }
-                    }
-                    list_hard(hard, i, c[m], q[m], axh, sp, &p.st->hard_n[s]);
-                }
-            }
+            // the species' tiles: the sheath's common shape (Heaviside beta between
+            // plates) with both fixed at compile time, every other shape read at run
+            // time (the same arithmetic either way)
+            if (sp.kind == SLPIC_BETA_HEAVISIDE && !p.periodic)
+                tma_species<kProf, SLPIC_BETA_HEAVISIDE, 0>(p, s, P, st, ph, stages, full, empty,
+                                                           s_v, s_c, s_E, dep, fail, nabs0, nabs1);
+            else
+                tma_species<kProf, kAny, kAny>(p, s, P, st, ph, stages, full, empty, s_v, s_c,
+                                               s_E, dep, fail, nabs0, nabs1);
             // species done: absorbed counts, histogram flush and clear
             const unsigned a0 = __reduce_add_sync(0xffffffffu, nabs0);
             const unsigned a1 = __reduce_add_sync(0xffffffffu, nabs1);
@@ -664,11 +699,17 @@ __device__ __forceinline__ void load_params(StepParams &dst, const StepParams *s
 }
 
 // kProf: the speed-limit profile p.lam is set
+// The body for species blockIdx.y: the sheath's common shape (Heaviside beta between
+// plates) with both fixed at compile time, every other shape read at run time (the
+// same arithmetic either way).
 template <bool kProf>
 __global__ void __launch_bounds__(kPB, 3) k_particles_compact(const __grid_constant__ StepParams p)
 {
     span_enter(p.st, 0);
-    particles_compact<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
+    if (p.sp[blockIdx.y].kind == SLPIC_BETA_HEAVISIDE && !p.periodic)
+        particles_compact<kProf, SLPIC_BETA_HEAVISIDE, 0>(p, blockIdx.y, blockIdx.x, gridDim.x);
+    else
+        particles_compact<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
     span_exit(p.st, 0);
 }
 
@@ -676,7 +717,10 @@ template <bool kProf>
 __global__ void __launch_bounds__(kPB, 4) k_particles(const __grid_constant__ StepParams p)
 {
     span_enter(p.st, 0);
-    particles_inplace<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
+    if (p.sp[blockIdx.y].kind == SLPIC_BETA_HEAVISIDE && !p.periodic)
+        particles_inplace<kProf, SLPIC_BETA_HEAVISIDE, 0>(p, blockIdx.y, blockIdx.x, gridDim.x);
+    else
+        particles_inplace<kProf>(p, blockIdx.y, blockIdx.x, gridDim.x);
     span_exit(p.st, 0);
 }
 
@@ -1110,13 +1154,6 @@ constexpr int kFCW = kFCT / 32;
 
 typedef unsigned __int128 u128;
 
-// 8-byte words of the field kernel's deposit copy in shared memory, rounded up to an
-// even number so that the 16-byte prefixes after it are aligned
-__host__ __device__ __forceinline__ int field_acc_words(int ns, int per_cta)
-{
-    return (ns * per_cta + 1) & ~1;
-}
-
 __device__ __forceinline__ u128 shfl_up_u128(u128 v, int o)
 {
     unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
@@ -1168,22 +1205,6 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
     const int chunk = (per_cta + kFCT - 1) / kFCT;
     const int j0 = min(c1, c0 + (int)threadIdx.x * chunk), j1 = min(c1, j0 + chunk);
-
-    // the counters CTA 0 updates at the end (thread s for species s), read now so
-    // that their loads overlap the work below rather than end the kernel
-    unsigned long long pf_ab0 = 0, pf_ab1 = 0, pf_holes = 0, pf_hard = 0;
-    long long pf_inj = 0, pf_at0 = 0, pf_at1 = 0, pf_it = 0;
-    if (mode >= 1 && rank == 0 && (int)threadIdx.x < ns) {
-        const int s = threadIdx.x;
-        pf_ab0 = st->absorbed_step[s][0];
-        pf_ab1 = st->absorbed_step[s][1];
-        pf_holes = st->holes[s][P];
-        pf_hard = st->hard_n[s];
-        pf_inj = st->injected_total[s];
-        pf_at0 = st->absorbed_total[s][0];
-        pf_at1 = st->absorbed_total[s][1];
-        pf_it = st->iterative_total[s];
-    }
 
     if (mode >= 1) {
         // ---- source injection (Sec. IV; LOSS_MATCHED / RATE readings).  Every CTA
@@ -1288,10 +1309,6 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         s_tot[threadIdx.x][1] = w2;
         s_tot[threadIdx.x][2] = t2;
     }
-    // the CTA-local inclusive prefix of rows c0.. at each of this thread's nodes, for
-    // the E pass below (which takes the nodes one per thread); 16-byte aligned after
-    // the deposits (an even number of 8-byte words)
-    u128 *s_pre = reinterpret_cast<u128 *>(s_acc + field_acc_words(ns, per_cta));  // [ns][per_cta]
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s) {
         if (s >= ns)
@@ -1300,12 +1317,6 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         for (int w = 0; w < warp; ++w)
             wp += s_warp[s][w];
         before[s] += wp;
-        u128 run = before[s];
-        for (int j = j0; j < j1; ++j) {
-            if (j >= 1 && j < N)
-                run += s_acc[s * per_cta + (j - c0)];
-            s_pre[s * per_cta + (j - c0)] = run;
-        }
     }
     cl.sync();
     // gather the CTAs' totals (distributed shared memory), one remote load per
@@ -1346,38 +1357,29 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     const double D0 = s_c[0], P_last = s_c[1], mean = s_c[2];
     const double k2 = p.k2, inv2dx = 0.5 * p.inv_dx;
 
-    // ---- E at this CTA's nodes, one node per thread per pass: with A_s[j] the prefix
-    //      of rows 1..j, P_{j-1} + P_j = k2 (sum_s c_s (A_s[j-1] + A_s[j]) - mean (2j - 1))
-    //      and E_j = (P_{j-1} + P_j - 2 D0) / (2 dx); the constants are folded so that a
-    //      node costs one conversion and one FMA per species and one FMA more, its
-    //      species independent (the FP64 pipe is narrow and its latency long)
-    double cE[kMaxSpecies];
+    // ---- E on this thread's nodes: P_{j-1} + P_j = k2 (sum_s c_s (A_s[j-1] + A_s[j])
+    //      - mean (2j - 1)), the integer pair sum converted once per species
+    u128 A[kMaxSpecies];  // A_s[j0 - 1] (prefix before the chunk's first row)
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s)
-        cE[s] = s < ns ? k2 * p.sp[s].rho_unit * inv2dx : 0.0;
-    const double eK0 = -2.0 * D0 * inv2dx, eK1 = -k2 * mean * inv2dx;
-    const int ncta = c1 - c0;
-#pragma unroll 3
-    for (int t = (int)threadIdx.x; t < ncta; t += kFCT) {
-        const int j = c0 + t;
+        A[s] = (s < ns) ? s_off[s] + before[s] : (u128)0;
+    for (int j = j0; j < j1; ++j) {
         double e;
         if (j == 0) {
             e = p.periodic ? ((P_last + 0.0) - 2.0 * D0) * inv2dx : -D0 * p.inv_dx;
         } else if (!p.periodic && j == N) {
             e = (P_last - D0) * p.inv_dx;
         } else {
-            double acc_e = fma(eK1, (double)(2 * j - 1), eK0);
+            double pair = 0.0;
 #pragma unroll
             for (int s = 0; s < kMaxSpecies; ++s) {
                 if (s >= ns)
                     break;
-                // A_s[j] = s_off + prefix at j; A_s[j-1] likewise, or s_off at the CTA's
-                // first node
-                const u128 aj = s_off[s] + s_pre[s * per_cta + t];
-                const u128 ajm = t > 0 ? s_off[s] + s_pre[s * per_cta + t - 1] : s_off[s];
-                acc_e = fma(cE[s], u128_to_double(aj + ajm), acc_e);
+                const u128 prev = A[s];
+                A[s] += s_acc[s * per_cta + (j - c0)];  // row j (1 <= j <= N-1)
+                pair = fma(p.sp[s].rho_unit, u128_to_double(prev + A[s]), pair);
             }
-            e = acc_e;
+            e = (k2 * (pair - mean * (double)(2 * j - 1)) - 2.0 * D0) * inv2dx;
         }
         if (p.wave_on)  // test-particle mode: the prescribed field at this time level
             e = wave_E(p, j, (double)(mode >= 1 ? step + 1 : step) * p.dt64);
@@ -1399,17 +1401,18 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
             const long long k = cut ? -s_ninj[s] - 1 : s_ninj[s];
             if (cut)
                 atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
+            const unsigned long long ab0 = st->absorbed_step[s][0], ab1 = st->absorbed_step[s][1];
             st->src_frac[s] = s_frac[s];
-            st->holes[s][P ^ 1] = mode == 1 ? pf_holes + pf_ab0 + pf_ab1 : 0ULL;
+            st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + ab0 + ab1 : 0ULL;
             st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + k);
-            st->injected_total[s] = pf_inj + k;
-            st->absorbed_total[s][0] = pf_at0 + (long long)pf_ab0;
-            st->absorbed_total[s][1] = pf_at1 + (long long)pf_ab1;
+            st->injected_total[s] += k;
+            st->absorbed_total[s][0] += (long long)ab0;
+            st->absorbed_total[s][1] += (long long)ab1;
             st->absorbed_step[s][0] = 0ULL;
             st->absorbed_step[s][1] = 0ULL;
             st->count[s][P] = 0ULL;
             st->holes[s][P] = 0ULL;
-            st->iterative_total[s] = pf_it + (long long)pf_hard;
+            st->iterative_total[s] += (long long)st->hard_n[s];
             st->hard_n[s] = 0ULL;
         }
         // the step index is read at the start of every CTA: advance it last
@@ -1420,7 +1423,8 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
+// one CTA per SM: the registers are there for the taking (64 would spill)
+__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads, 1)
     k_field(const __grid_constant__ StepParams p, int mode)
 {
     span_enter(p.st, 2);
@@ -1429,7 +1433,7 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
 }
 
 // batched: one cluster per instance
-__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads)
+__global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFieldClusterThreads, 3)
     k_field_batch(const StepParams *__restrict__ ps, int mode)
 {
     __shared__ StepParams s_p;
@@ -1664,9 +1668,7 @@ cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compac
 
 size_t field_cluster_smem_bytes(int nn, int ns)
 {
-    const int per_cta = (nn + kFC - 1) / kFC;
-    return (size_t)field_acc_words(ns, per_cta) * sizeof(unsigned long long) +
-           (size_t)ns * per_cta * sizeof(u128);
+    return (size_t)ns * ((nn + kFC - 1) / kFC) * sizeof(unsigned long long);
 }
 
 void launch_field(const StepParams &p, int mode, cudaStream_t st)

@@ -16,12 +16,20 @@ __device__ __forceinline__ void deposit_node(unsigned long long *hist, int c, in
     atomicAdd(hist + c1, qR);
 }
 
+// Compile-time shape of a particle loop: kKind the species' beta kind (SLPIC_BETA_*)
+// and kPer whether the grid is periodic (0/1), or kAny for "read at run time".  The
+// fixed forms drop the run-time tests from the hot loop; the arithmetic, and so every
+// result bit, is the same.
+constexpr int kAny = -1;
+
 // Gather (Sec. II): linear interpolation of the nodal field at the particle.
+template <int kPer = kAny>
 __device__ __forceinline__ float gather_ax(const StepParams &p, const SpeciesDev &sp,
                                            const float *sE, int c, float d)
 {
+    const bool periodic = kPer == kAny ? (p.periodic != 0) : (kPer != 0);
     int c1 = c + 1;
-    if (p.periodic && c1 == p.n_cells)
+    if (periodic && c1 == p.n_cells)
         c1 = 0;
     // explicit roundings: every kernel that inlines this gets the same bits
     float Ep = __fmaf_rn(d, sE[c1], __fmul_rn(1.0f - d, sE[c]));
@@ -51,13 +59,15 @@ __device__ __forceinline__ float v0_cell(const StepParams &p, const SpeciesDev &
 // v0n is the limit of the start cell (that of the push); with kProf the deposit
 // takes beta with the limit of the cell the particle ends in (the same beta if it
 // stayed in its cell: a warp whose particles all stay skips the second division).
-template <bool kProf = false, typename Dep>
+template <bool kProf = false, int kKind = kAny, int kPer = kAny, typename Dep>
 __device__ __forceinline__ bool move_and_deposit(const StepParams &p, const SpeciesDev &sp,
                                                  Dep &dep, int &c, float4 &q, float vx, int &wall,
                                                  float v0n)
 {
     const int N = p.n_cells;
-    float b = beta_q(sp.kind, vx, q.z, q.w, v0n);
+    const int kind = kKind == kAny ? sp.kind : kKind;
+    const bool periodic = kPer == kAny ? (p.periodic != 0) : (kPer != 0);
+    float b = beta_q(kind, vx, q.z, q.w, v0n);
     float xn = __fmaf_rn(__fmul_rn(b, vx), p.dt_dx, q.x);
     float fl = floorf(xn);
     int cn = c + (int)fl;
@@ -66,7 +76,7 @@ __device__ __forceinline__ bool move_and_deposit(const StepParams &p, const Spec
         dn = 0.0f;
         cn += 1;
     }
-    if (p.periodic) {
+    if (periodic) {
         cn %= N;
         if (cn < 0)
             cn += N;
@@ -78,10 +88,10 @@ __device__ __forceinline__ bool move_and_deposit(const StepParams &p, const Spec
         return false;
     }
     int cn1 = cn + 1;
-    if (p.periodic && cn1 == N)
+    if (periodic && cn1 == N)
         cn1 = 0;
     if (kProf && cn != c)
-        b = beta_q(sp.kind, vx, q.z, q.w, v0_at<true>(p, sp, cn));
+        b = beta_q(kind, vx, q.z, q.w, v0_at<true>(p, sp, cn));
     dep(cn, cn1, b, dn);
     c = cn;
     q.x = dn;
