@@ -444,8 +444,8 @@ def run_gpu(args):
     sim.step(args.steps if args.steps <= 4096 else 4096)
     push_ms, hard_ms_ev, field_ms_ev, nrec = binding.slpic_kernel_times(sim.h)
     binding.slpic_enable_kernel_timing(sim.h, 0)
-    replay_same = sim.diagnostics()["step"] == (dg1["step"] if args.steps <= 4096 else -1)
-    kps = binding.slpic_kernels_per_step(sim.h)
+    n_replay = min(args.steps, 4096)
+    replay_same = n_replay < args.steps or sim.diagnostics()["step"] == dg1["step"]
     iterative_per_step = (sum(dg1["iterative"]) - sum(dg0["iterative"])) / args.steps
 
     t_max, particle_steps = aggregate_ranks(ms, 0.5 * (n0 + n1) * args.steps, dist, "cuda")
@@ -475,7 +475,10 @@ def run_gpu(args):
                          "timing": "device global timer, first CTA start to last CTA end of "
                                    "each launch, over the timed steps themselves"},
             "events_ms": {"particle": push_ms, "hard": hard_ms_ev, "field": field_ms_ev,
-                          "steps": int(nrec), "replay_matches_timed_steps": bool(replay_same)},
+                          "steps": int(nrec),
+                          "replayed": ("all the timed steps" if n_replay == args.steps else
+                                       f"the first {n_replay} of the timed steps"),
+                          "replay_reached_the_same_step": bool(replay_same)},
             "iterative_pushes_per_step": iterative_per_step,
             "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP,
             "peak_source": f"{peak_kind} HBM copy bandwidth (burst)", "tuning": tuning,
@@ -532,7 +535,7 @@ def run_gpu(args):
             "particles_at_load": n_load, "particles_timed_mean": n_mean,
             "timed_state": timed_state,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_form": fp64,
-            "gpu_launches": kps * args.steps, "clocks": clk,
+            "gpu_launches": int((nl1 - nl0).sum()), "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     sim.close()

@@ -285,20 +285,21 @@ __device__ __forceinline__ bool push_vx_easy(int kind, float ux, float uy, float
     float D = Dp;
     if (kind == SLPIC_BETA_HEAVISIDE) {
         float wb = __fadd_rn(wa, rem);
+        const float sa = __fadd_rn(__fmul_rn(wa, wa), Dp);  // |v|^2 at the two ends
+        const float sb = __fadd_rn(__fmul_rn(wb, wb), Dp);
         // |v| is convex along the line: both ends in the band => beta = 1 all
         // step and the push is plain leapfrog, bit for bit
-        if (__fadd_rn(__fmul_rn(wa, wa), Dp) <= v02 && __fadd_rn(__fmul_rn(wb, wb), Dp) <= v02) {
+        if (sa <= v02 && sb <= v02) {
             vx = sg * wb;
             return true;
         }
-        if (Dp < v02) {
-            float hi = sqrtf(v02 - Dp);
-            // above the band, or below it with a budget too small to reach it:
-            // below the band 1/beta = |v|/v0 >= 1, so reaching -hi costs >= -hi - wa
-            bool ok = wa >= hi || (wa < -hi && -hi - wa >= rem);
-            if (!ok)
-                return false;
-        }
+        // Otherwise one smooth piece needs the step to stay out of the band
+        // |w| < hi = sqrt(v0^2 - Dp) (none if Dp >= v0^2): start above it (w grows), or
+        // start below it and end below it even at leapfrog speed (below the band
+        // 1/beta = |v|/v0 >= 1, so the true end lies short of wb).  Squared, no root:
+        // wa >= hi <=> wa >= 0 and sa >= v0^2;  wb <= -hi <=> wb <= 0 and sb >= v0^2.
+        if (Dp < v02 && !((wa >= 0.0f && sa >= v02) || (wb <= 0.0f && sb >= v02)))
+            return false;
     } else {
         D = Dp + v02;
     }
