@@ -1189,15 +1189,13 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     __shared__ u128 s_tot[kMaxSpecies][3];
     __shared__ u128 s_warp[kMaxSpecies][kFCW];
     __shared__ u128 s_wpart[kMaxSpecies][kFCW][2];
-    __shared__ double s_c[4];  // D0, P_{N-1}, mean, (unused)
+    __shared__ double s_dbl[kMaxSpecies][3];  // the cluster's R, W, T per species, as doubles
+    __shared__ double s_c[4];                 // D0, P_{N-1}, mean, (unused)
     __shared__ u128 s_off[kMaxSpecies];
     __shared__ long long s_ninj[kMaxSpecies], s_base[kMaxSpecies];
     __shared__ double s_frac[kMaxSpecies];
 
     DevState *st = p.st;
-    const long long step = st->step;
-    const int P = (int)(step & 1);
-    const int Q = mode ? (P ^ 1) : P;  // deposit to solve from
     const int N = p.n_cells, nn = p.nn, ns = p.ns;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this CTA's nodes [c0, c1); the thread's chunk of them
@@ -1205,6 +1203,35 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
     const int chunk = (per_cta + kFCT - 1) / kFCT;
     const int j0 = min(c1, c0 + (int)threadIdx.x * chunk), j1 = min(c1, j0 + chunk);
+
+    // ---- the step's counters, thread s for species s: every load issued at once
+    // (none depends on another, nor on the step index), used below
+    const long long step = st->step;
+    unsigned long long pf_cnt0 = 0ULL, pf_cnt1 = 0ULL, pf_holes0 = 0ULL, pf_holes1 = 0ULL;
+    unsigned long long pf_ab0 = 0ULL, pf_ab1 = 0ULL, pf_ref0 = 0ULL, pf_ref1 = 0ULL, pf_hard = 0ULL;
+    long long pf_inj = 0, pf_at0 = 0, pf_at1 = 0, pf_it = 0;
+    double pf_frac = 0.0;
+    if (mode >= 1 && (int)threadIdx.x < ns) {
+        const int s = threadIdx.x, r = p.src_ref;
+        pf_cnt0 = st->count[s][0];
+        pf_cnt1 = st->count[s][1];
+        pf_ref0 = st->absorbed_step[r][0];
+        pf_ref1 = st->absorbed_step[r][1];
+        pf_frac = st->src_frac[s];
+        if (rank == 0) {
+            pf_holes0 = st->holes[s][0];
+            pf_holes1 = st->holes[s][1];
+            pf_ab0 = st->absorbed_step[s][0];
+            pf_ab1 = st->absorbed_step[s][1];
+            pf_hard = st->hard_n[s];
+            pf_inj = st->injected_total[s];
+            pf_at0 = st->absorbed_total[s][0];
+            pf_at1 = st->absorbed_total[s][1];
+            pf_it = st->iterative_total[s];
+        }
+    }
+    const int P = (int)(step & 1);
+    const int Q = mode ? (P ^ 1) : P;  // deposit to solve from
 
     if (mode >= 1) {
         // ---- source injection (Sec. IV; LOSS_MATCHED / RATE readings).  Every CTA
@@ -1215,13 +1242,12 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         if (s < ns) {
             double S = 0.0;
             if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
-                int r = p.src_ref;
-                S = (double)(st->absorbed_step[r][0] + st->absorbed_step[r][1]) * p.sp[r].w;
+                S = (double)(pf_ref0 + pf_ref1) * p.sp[p.src_ref].w;
             } else if (p.src_mode == SLPIC_SRC_RATE) {
                 S = p.src_rate * p.dt64;
             }
             long long k = 0;
-            double f = st->src_frac[s];
+            double f = pf_frac;
             if (p.src_mode == SLPIC_SRC_WALL) {
                 if (p.sp[s].wall_rate > 0.0) {
                     f += p.sp[s].wall_rate;
@@ -1235,7 +1261,7 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
             }
             // after an in-place step the output uses the input's slots (holes
             // included); after a compacting step its count was reserved by atomics
-            long long have = (long long)(mode == 1 ? st->count[s][P] : st->count[s][P ^ 1]);
+            long long have = (long long)(mode == 1 ? (P ? pf_cnt1 : pf_cnt0) : (P ? pf_cnt0 : pf_cnt1));
             long long room = p.sp[s].capacity - have;
             s_ninj[s] = k > room ? -room - 1 : k;  // negative: truncated
             s_base[s] = have;
@@ -1252,23 +1278,27 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         cl.sync();
     }
 
-    // ---- integer sums over this thread's nodes, one species at a time: the rows'
-    // inclusive sum R (rows 1..N-1), the weighted sum W = sum (N-j) acc[j] and the
-    // total T (nodes j < N); then R's exclusive prefix over the CTA's threads.  The
-    // deposits are kept in shared memory for the E pass.
+    // ---- this CTA's deposits into shared memory, every load in flight at once
     extern __shared__ __align__(16) unsigned char fsmem[];
     unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(fsmem);  // [ns][per_cta]
+    for (int k = threadIdx.x; k < ns * per_cta; k += kFCT) {
+        const int s = k / per_cta, j = c0 + (k - s * per_cta);
+        s_acc[k] = j < c1 ? __ldcg(p.acc + ((size_t)Q * ns + s) * nn + j) : 0ULL;
+    }
+    __syncthreads();
+
+    // ---- integer sums over this thread's nodes, one species at a time: the rows'
+    // inclusive sum R (rows 1..N-1), the weighted sum W = sum (N-j) acc[j] and the
+    // total T (nodes j < N); then R's exclusive prefix over the CTA's threads
     u128 before[kMaxSpecies];
 #pragma unroll
     for (int s = 0; s < kMaxSpecies; ++s) {
         before[s] = 0;
         if (s >= ns)
             continue;
-        const unsigned long long *acc = p.acc + ((size_t)Q * ns + s) * nn;
         u128 run = 0, wsum = 0, tsum = 0;
         for (int j = j0; j < j1; ++j) {
-            const unsigned long long v = __ldcg(acc + j);
-            s_acc[s * per_cta + (j - c0)] = v;
+            const unsigned long long v = s_acc[s * per_cta + (j - c0)];
             if (j < N)
                 tsum += v;
             if (j >= 1 && j < N) {
@@ -1320,29 +1350,38 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     }
     cl.sync();
     // gather the CTAs' totals (distributed shared memory), one remote load per
-    // thread, then one thread forms the step's scalars
+    // thread; then thread (s, q) sums quantity q of species s over the cluster and
+    // converts it (and, for R, the CTAs before this one), and one thread forms the
+    // step's scalars
     __shared__ u128 s_all[kMaxSpecies][kFC][3];
     if (threadIdx.x < ns * kFC * 3) {
         const int s = threadIdx.x / (kFC * 3), r = (threadIdx.x / 3) % kFC, q = threadIdx.x % 3;
         s_all[s][r][q] = *cl.map_shared_rank(&s_tot[s][q], r);
     }
+    // this CTA's reads of the others' shared memory are done; the matching wait
+    // before exit keeps every CTA alive until all of them have read
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < ns * 3) {
+        const int s = threadIdx.x / 3, q = threadIdx.x % 3;
+        u128 tot = 0, off = 0;
+        for (int r = 0; r < kFC; ++r) {
+            tot += s_all[s][r][q];
+            if (r < rank)
+                off += s_all[s][r][q];
+        }
+        if (q == 0)
+            s_off[s] = off;
+        s_dbl[s][q] = u128_to_double(tot);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double sumW = 0.0, sumR = 0.0, sumT = 0.0;
         for (int s = 0; s < ns; ++s) {
-            u128 R = 0, W = 0, T = 0, off = 0;
-            for (int r = 0; r < kFC; ++r) {
-                R += s_all[s][r][0];
-                W += s_all[s][r][1];
-                T += s_all[s][r][2];
-                if (r < rank)
-                    off += s_all[s][r][0];
-            }
-            s_off[s] = off;
             const double cs = p.sp[s].rho_unit;
-            sumR = fma(cs, u128_to_double(R), sumR);
-            sumW = fma(cs, u128_to_double(W), sumW);
-            sumT = fma(cs, u128_to_double(T), sumT);
+            sumR = fma(cs, s_dbl[s][0], sumR);
+            sumW = fma(cs, s_dbl[s][1], sumW);
+            sumT = fma(cs, s_dbl[s][2], sumT);
         }
         const double mean = p.periodic ? sumT * p.inv_n : 0.0;
         const double sumP = p.k2 * (sumW - mean * 0.5 * (double)N * (double)(N - 1));
@@ -1350,19 +1389,24 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         s_c[1] = p.k2 * (sumR - mean * (double)(N - 1));                                // P_{N-1}
         s_c[2] = mean;
     }
-    // this CTA's reads of the others' shared memory are done; the matching wait
-    // before exit keeps every CTA alive until all of them have read
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     __syncthreads();
     const double D0 = s_c[0], P_last = s_c[1], mean = s_c[2];
     const double k2 = p.k2, inv2dx = 0.5 * p.inv_dx;
 
-    // ---- E on this thread's nodes: P_{j-1} + P_j = k2 (sum_s c_s (A_s[j-1] + A_s[j])
-    //      - mean (2j - 1)), the integer pair sum converted once per species
+    // ---- E on this thread's nodes.  With P_{j-1} + P_j = k2 (sum_s c_s X_s[j] -
+    // mean (2j - 1)), X_s[j] = A_s[j-1] + A_s[j] (the integer pair sum, converted once
+    // per species), E_j = (P_{j-1} + P_j - 2 D0) / (2 dx) is
+    //   sum_s K_s X_s[j] + (B - a j),  K_s = k2 c_s / (2 dx),
+    //   a = 2 k2 mean / (2 dx),  B = (k2 mean - 2 D0) / (2 dx)
+    // (a = 0 between plates): one multiply-add per species and node.
+    double K[kMaxSpecies];
     u128 A[kMaxSpecies];  // A_s[j0 - 1] (prefix before the chunk's first row)
 #pragma unroll
-    for (int s = 0; s < kMaxSpecies; ++s)
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        K[s] = (s < ns) ? k2 * p.sp[s].rho_unit * inv2dx : 0.0;
         A[s] = (s < ns) ? s_off[s] + before[s] : (u128)0;
+    }
+    const double a_j = 2.0 * k2 * mean * inv2dx, B = (k2 * mean - 2.0 * D0) * inv2dx;
     for (int j = j0; j < j1; ++j) {
         double e;
         if (j == 0) {
@@ -1370,16 +1414,15 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
         } else if (!p.periodic && j == N) {
             e = (P_last - D0) * p.inv_dx;
         } else {
-            double pair = 0.0;
+            e = p.periodic ? fma(-a_j, (double)j, B) : B;
 #pragma unroll
             for (int s = 0; s < kMaxSpecies; ++s) {
                 if (s >= ns)
                     break;
                 const u128 prev = A[s];
                 A[s] += s_acc[s * per_cta + (j - c0)];  // row j (1 <= j <= N-1)
-                pair = fma(p.sp[s].rho_unit, u128_to_double(prev + A[s]), pair);
+                e = fma(K[s], u128_to_double(prev + A[s]), e);
             }
-            e = (k2 * (pair - mean * (double)(2 * j - 1)) - 2.0 * D0) * inv2dx;
         }
         if (p.wave_on)  // test-particle mode: the prescribed field at this time level
             e = wave_E(p, j, (double)(mode >= 1 ? step + 1 : step) * p.dt64);
@@ -1390,29 +1433,29 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     if (mode >= 1) {
         // the deposit of rho^n is consumed: clear this CTA's nodes of it for the next
         // step's particle kernel
-        for (int s = 0; s < ns; ++s)
-            for (int j = c0 + (int)threadIdx.x; j < c1; j += kFCT)
-                p.acc[((size_t)P * ns + s) * nn + j] = 0ULL;
+        for (int k = threadIdx.x; k < ns * (c1 - c0); k += kFCT) {
+            const int s = k / (c1 - c0), j = c0 + (k - s * (c1 - c0));
+            p.acc[((size_t)P * ns + s) * nn + j] = 0ULL;
+        }
         // every CTA has read the step's state (before the exchange): CTA 0 updates it,
-        // thread s for species s
-        if (rank == 0 && threadIdx.x < ns) {
+        // thread s for species s, from the counters read at the start
+        if (rank == 0 && (int)threadIdx.x < ns) {
             const int s = threadIdx.x;
             const bool cut = s_ninj[s] < 0;
             const long long k = cut ? -s_ninj[s] - 1 : s_ninj[s];
             if (cut)
                 atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
-            const unsigned long long ab0 = st->absorbed_step[s][0], ab1 = st->absorbed_step[s][1];
             st->src_frac[s] = s_frac[s];
-            st->holes[s][P ^ 1] = mode == 1 ? st->holes[s][P] + ab0 + ab1 : 0ULL;
+            st->holes[s][P ^ 1] = mode == 1 ? (P ? pf_holes1 : pf_holes0) + pf_ab0 + pf_ab1 : 0ULL;
             st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + k);
-            st->injected_total[s] += k;
-            st->absorbed_total[s][0] += (long long)ab0;
-            st->absorbed_total[s][1] += (long long)ab1;
+            st->injected_total[s] = pf_inj + k;
+            st->absorbed_total[s][0] = pf_at0 + (long long)pf_ab0;
+            st->absorbed_total[s][1] = pf_at1 + (long long)pf_ab1;
             st->absorbed_step[s][0] = 0ULL;
             st->absorbed_step[s][1] = 0ULL;
             st->count[s][P] = 0ULL;
             st->holes[s][P] = 0ULL;
-            st->iterative_total[s] += (long long)st->hard_n[s];
+            st->iterative_total[s] = pf_it + (long long)pf_hard;
             st->hard_n[s] = 0ULL;
         }
         // the step index is read at the start of every CTA: advance it last
