@@ -952,21 +952,18 @@ __device__ double block_sum(double v, double *s_w)
     return t;
 }
 
-// Source particles of species s for this step (Sec. IV source, the readings of
-// LOSS_MATCHED / RATE): macroparticle i takes uniforms u_j = u24(SplitMix64(key, 8i+j))
-// for its position in the band (FP32, pinned operations) and a physical Maxwellian
-// velocity (Box-Muller): the g-source equals the f-source.  This CTA makes the
-// particles i = first, first + stride, ... < k, writes them to slots base + i of
-// buffer Q and adds their deposit to acc[Q].
-__device__ void inject_species(const StepParams &p, int s, long long step, long long base,
-                               long long k, int Q, int first, int stride)
+// Source particle i of species s for this step (Sec. IV source, the readings of
+// LOSS_MATCHED / RATE): it takes uniforms u_j = u24(SplitMix64(key, 8i+j)), key the
+// species' stream of the step, for its position in the band (FP32, pinned
+// operations) and a physical Maxwellian velocity (Box-Muller): the g-source equals
+// the f-source.  It goes to slot base + i of buffer Q, its deposit to acc[Q].
+__device__ __forceinline__ void inject_one(const StepParams &p, int s, unsigned long long key,
+                                           long long base, long long i, int Q)
 {
     const SpeciesDev &sp = p.sp[s];
     const int N = p.n_cells;
-    const unsigned long long key = sm64_stream(p.seed, (unsigned long long)step, (unsigned)s);
     unsigned long long *acc = p.acc + ((size_t)Q * p.ns + s) * p.nn;
-    for (long long i = first + (long long)threadIdx.x * stride; i < k;
-         i += (long long)blockDim.x * stride) {
+    {
         unsigned long long b8 = 8ULL * (unsigned long long)i;
         float u0 = u24(sm64_at(key, b8 + 0));
         float u1 = u24(sm64_at(key, b8 + 1));
@@ -1016,6 +1013,34 @@ __device__ void inject_species(const StepParams &p, int s, long long step, long 
         quantise(beta_q(sp.kind, q.y, q.z, q.w, v0_cell(p, sp, c)), off, qL, qR);
         atomicAdd(acc + c, qL);
         atomicAdd(acc + c1, qR);
+    }
+}
+
+// The step's source particles of every species (k[s] of species s, to slots base[s]
+// on): taken as one index space, so that the species' particles are made side by
+// side; this CTA makes the indices first, first + stride, ...
+__device__ void inject_all(const StepParams &p, long long step, const long long *base,
+                           const long long *k, int Q, int first, int stride)
+{
+    long long pre[kMaxSpecies + 1];  // registers: constant indices only
+    pre[0] = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s)
+        pre[s + 1] = pre[s] + (s < p.ns ? k[s] : 0);
+    const long long total = pre[kMaxSpecies];
+    for (long long t = first + (long long)threadIdx.x * stride; t < total;
+         t += (long long)blockDim.x * stride) {
+        int s = 0;
+        long long i0 = 0, b = base[0];
+#pragma unroll
+        for (int r = 1; r < kMaxSpecies; ++r)
+            if (t >= pre[r]) {
+                s = r;
+                i0 = pre[r];
+                b = base[r];
+            }
+        const unsigned long long key = sm64_stream(p.seed, (unsigned long long)step, (unsigned)s);
+        inject_one(p, s, key, b, t - i0, Q);
     }
 }
 
@@ -1170,12 +1195,24 @@ __device__ __forceinline__ u128 shfl_down_u128(u128 v, int o)
     return ((u128)hi << 64) | lo;
 }
 
+// x < 2^64 to the nearest double, built on the FP64 add pipe: a 32-bit half h is
+// exact as (2^52 + h) - 2^52, the double whose high word is that of 2^52 and whose low
+// word is h, minus 2^52; one fused multiply-add then forms hi 2^32 + lo with a single
+// rounding: the value of the conversion instruction, on the add pipe.
+__device__ __forceinline__ double u64_to_double_rn(unsigned long long x)
+{
+    const double two52 = 4503599627370496.0;
+    const double h = __hiloint2double(0x43300000, (int)(unsigned)(x >> 32)) - two52;
+    const double l = __hiloint2double(0x43300000, (int)(unsigned)x) - two52;
+    return fma(h, 4294967296.0, l);
+}
+
 __device__ __forceinline__ double u128_to_double(u128 v)
 {
     unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;
-    double d = (double)lo;
+    double d = u64_to_double_rn(lo);
     if (hi)
-        d = fma((double)hi, 18446744073709551616.0, d);  // 2^64
+        d = fma(u64_to_double_rn(hi), 18446744073709551616.0, d);  // 2^64
     return d;
 }
 
@@ -1268,10 +1305,15 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
             s_frac[s] = f;
         }
         __syncthreads();
-        for (int sp_ = 0; sp_ < ns; ++sp_) {
-            long long k = s_ninj[sp_] < 0 ? -s_ninj[sp_] - 1 : s_ninj[sp_];
-            if (k > 0)
-                inject_species(p, sp_, step, s_base[sp_], k, Q, rank, kFC);
+        {
+            long long kk[kMaxSpecies], bb[kMaxSpecies];
+#pragma unroll
+            for (int sp_ = 0; sp_ < kMaxSpecies; ++sp_) {
+                const long long k = sp_ < ns ? s_ninj[sp_] : 0;
+                kk[sp_] = k < 0 ? -k - 1 : k;
+                bb[sp_] = sp_ < ns ? s_base[sp_] : 0;
+            }
+            inject_all(p, step, bb, kk, Q, rank, kFC);
         }
         // every CTA's source deposits are in acc before any CTA reads acc
         __threadfence();
@@ -1424,10 +1466,16 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
                 e = fma(K[s], u128_to_double(prev + A[s]), e);
             }
         }
-        if (p.wave_on)  // test-particle mode: the prescribed field at this time level
-            e = wave_E(p, j, (double)(mode >= 1 ? step + 1 : step) * p.dt64);
         p.E64[j] = e;
         p.E[j] = (float)e;
+    }
+    if (p.wave_on) {  // test-particle mode: the prescribed field at this time level instead
+        const double tw = (double)(mode >= 1 ? step + 1 : step) * p.dt64;
+        for (int j = j0; j < j1; ++j) {
+            const double e = wave_E(p, j, tw);
+            p.E64[j] = e;
+            p.E[j] = (float)e;
+        }
     }
 
     if (mode >= 1) {

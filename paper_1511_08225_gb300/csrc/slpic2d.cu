@@ -2,12 +2,15 @@
 //
 // Per step (Appendix A, Eq. slpicIntegration, on an nx x ny grid, periodic in x,
 // absorbing plates in y):
-//   k_particles2d  gather E (bilinear) -> push v (the same speed-limited solve as
+//   k_particles2d_tiles (in-place steps) / k_particles2d (every kCompact2d-th step)
+//                  gather E (bilinear) -> push v (the same speed-limited solve as
 //                  1D, along the direction of a) -> move -> plates/wrap -> deposit
-//                  rho^{n+1} (quantised int64, bilinear) into the nodal arrays by
-//                  global atomics.  Absorbed particles leave holes (cell = -1); every
-//                  kCompact2d-th step the kernel writes the survivors packed instead.
-//   k_inject2d     one CTA: source particles appended and deposited; bookkeeping.
+//                  rho^{n+1} (quantised int64, bilinear) into the nodal arrays: the
+//                  tile kernel through windows of the grid in shared memory, listing
+//                  the pushes that need the piece walk for k_hard2d; the other by
+//                  global atomics, writing the survivors packed.  Absorbed particles
+//                  leave holes (cell = -1) in place.
+//   k_inject2d     source particles appended and deposited; k_book2d the bookkeeping.
 //   k_cg2d         cooperative kernel: b from the deposits, Jacobi-PCG on the
 //                  5-point system (FP64 vectors, FP64 dot products in a fixed
 //                  order), then E^{n+1}; the deposits are cleared for the next step.
@@ -15,6 +18,7 @@
 // Particle store per species, ping-pong buffers b = step & 1:
 //   cell[b][i] int32 (cy*nx + cx, -1 = hole), pv[b][i] float4 {ox, oy, vx, vy},
 //   vz[b][i] float  -- 24 bytes per macroparticle.
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -22,6 +26,7 @@
 #include <utility>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "push_math.cuh"
@@ -48,10 +53,21 @@ constexpr int kBarGroups = 64;  // first-level counters (CG grids up to 1,024 CT
 constexpr long long kBarrierSpins = 1LL << 23;  // bounded grid-barrier wait (~1 s)
 constexpr long long kMaxTimedSteps2d = 4096;    // steps recorded by the kernel timing
 
+// A particle whose push needs the piece walk, listed by the in-place tile kernel
+// for k_hard2d with what the push needs.
+struct HardRec2D {
+    int32_t slot, cell;  // its slot in the step's buffers; c at time level n
+    float ax, ay;        // (q/m) E gathered at the particle
+    float4 q;            // {ox, oy, vx, vy} at time level n (v = v^{n-1/2})
+    float vz, pad[3];
+};
+
 struct Species2D {
     int32_t *cell[2];
     float4 *pv[2];
     float *vz[2];
+    HardRec2D *hard;     // this step's listed particles (hard_cap records)
+    long long hard_cap;
     long long capacity;
     float qm, v0, vth_src;
     int kind;
@@ -67,6 +83,7 @@ struct State2D {
     long long absorbed_total[kMaxS][2];
     long long injected_total[kMaxS];
     double src_frac[kMaxS];
+    unsigned long long hard_n[kMaxS];  // particles listed for k_hard2d this step
     long long cg_total;
     double cg_res;
     int cg_iters;
@@ -77,6 +94,8 @@ struct State2D {
 
 struct Params2D {
     int nx, ny, nn, ns;
+    unsigned nx_m;  // c / nx = div_nx(c): the multiplier and shift of the round-up method
+    int nx_s;
     float dt, dt_dx;
     double dx, dt64, k2;          // k2 = dx^2 / eps0
     double phi_lo, phi_hi, rtol2;  // rtol^2
@@ -101,39 +120,84 @@ struct Params2D {
     int *hist, *cursor, *bsum;  // cell sort: counts per cell, then slots; block sums
 };
 
+// c / nx for 0 <= c < 2^32 and nx >= 2 without a division: Granlund and Montgomery's
+// method for an invariant divisor (PLDI 1994, Fig. 4.1): with l = ceil(log2 nx) and
+// m = floor(2^32 (2^l - nx) / nx) + 1 (host, make_div_nx), t = mulhi(m, c) and
+// q = (t + ((c - t) >> 1)) >> (l - 1).
+__device__ __forceinline__ int div_nx(const Params2D &p, int c)
+{
+    const unsigned n = (unsigned)c;
+    const unsigned t = __umulhi(p.nx_m, n);
+    return (int)((t + ((n - t) >> 1)) >> p.nx_s);
+}
+
+void make_div_nx(int nx, unsigned &m, int &s)
+{
+    int l = 0;
+    while ((1LL << l) < nx)
+        ++l;
+    m = (unsigned)((((unsigned long long)1 << 32) * (unsigned long long)((1LL << l) - nx)) /
+                       (unsigned long long)nx + 1ULL);
+    s = l - 1;
+}
+
 // ---------------------------------------------------------------------------------
 // Velocity push with a = (ax, ay, 0): the speed-limited solve of Appendix A,
 // Eq. slpicIntegrationV, depends only on the component w of v along a and on
 // |v_perp|, so the 1D solve (push_vx with a along +x) gives w at the end of the
 // step and v changes by (w_end - w) in the direction of a.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ void push_v2(int kind, float ux, float uy, float uz, float ax, float ay,
-                                        float dt, float v0, float &vx, float &vy)
+// kEasy: only the cases push_vx_easy solves; returns false (v untouched) for the
+// rest, which need the piece walk.  Otherwise every case; returns true.
+template <bool kEasy>
+__device__ __forceinline__ bool push_v2_impl(int kind, float ux, float uy, float uz, float ax,
+                                             float ay, float dt, float v0, float &vx, float &vy)
 {
     if (kind == SLPIC_BETA_ONE) {
         vx = __fadd_rn(ux, __fmul_rn(ax, dt));
         vy = __fadd_rn(uy, __fmul_rn(ay, dt));
-        return;
+        return true;
     }
     const float A = __fsqrt_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)));
     if (A == 0.0f) {
         vx = ux;
         vy = uy;
-        return;
+        return true;
     }
     const float hx = __fdiv_rn(ax, A), hy = __fdiv_rn(ay, A);
     const float wa = __fadd_rn(__fmul_rn(ux, hx), __fmul_rn(uy, hy));
     const float cr = __fsub_rn(__fmul_rn(ux, hy), __fmul_rn(uy, hx));
     const float vp = __fsqrt_rn(__fadd_rn(__fmul_rn(cr, cr), __fmul_rn(uz, uz)));
-    const float we = push_vx(kind, wa, vp, 0.0f, A, dt, v0);
+    float we;
+    if (kEasy) {
+        if (!push_vx_easy(kind, wa, vp, 0.0f, A, dt, v0, we))
+            return false;
+    } else {
+        we = push_vx(kind, wa, vp, 0.0f, A, dt, v0);
+    }
     const float dw = __fsub_rn(we, wa);
     vx = __fadd_rn(ux, __fmul_rn(dw, hx));
     vy = __fadd_rn(uy, __fmul_rn(dw, hy));
+    return true;
 }
 
-// the 2D quantised deposit rule stated in slpic2d.h
-__device__ __forceinline__ void deposit2d(unsigned long long *acc, int k00, int k10, int k01,
-                                          int k11, float b, float ox, float oy)
+__device__ __forceinline__ void push_v2(int kind, float ux, float uy, float uz, float ax, float ay,
+                                        float dt, float v0, float &vx, float &vy)
+{
+    push_v2_impl<false>(kind, ux, uy, uz, ax, ay, dt, v0, vx, vy);
+}
+
+__device__ __forceinline__ bool push_v2_easy(int kind, float ux, float uy, float uz, float ax,
+                                             float ay, float dt, float v0, float &vx, float &vy)
+{
+    return push_v2_impl<true>(kind, ux, uy, uz, ax, ay, dt, v0, vx, vy);
+}
+
+// the 2D quantised deposit rule stated in slpic2d.h: the charges of the cell's nodes
+// (x, y), (x+1, y), (x, y+1), (x+1, y+1)
+__device__ __forceinline__ void quantise2d(float b, float ox, float oy, unsigned long long &q00,
+                                           unsigned long long &q10, unsigned long long &q01,
+                                           unsigned long long &q11)
 {
     const float two40 = 1099511627776.0f;
     const float bx = __fmul_rn(b, ox), by = __fmul_rn(b, oy), bxy = __fmul_rn(bx, oy);
@@ -141,10 +205,21 @@ __device__ __forceinline__ void deposit2d(unsigned long long *acc, int k00, int 
     const unsigned long long qX = rint_u64(__fmul_rn(bx, two40));
     const unsigned long long qY = rint_u64(__fmul_rn(by, two40));
     const unsigned long long qXY = rint_u64(__fmul_rn(bxy, two40));
-    atomicAdd(acc + k00, qT - qX - qY + qXY);
-    atomicAdd(acc + k10, qX - qXY);
-    atomicAdd(acc + k01, qY - qXY);
-    atomicAdd(acc + k11, qXY);
+    q00 = qT - qX - qY + qXY;
+    q10 = qX - qXY;
+    q01 = qY - qXY;
+    q11 = qXY;
+}
+
+__device__ __forceinline__ void deposit2d(unsigned long long *acc, int k00, int k10, int k01,
+                                          int k11, float b, float ox, float oy)
+{
+    unsigned long long q00, q10, q01, q11;
+    quantise2d(b, ox, oy, q00, q10, q01, q11);
+    atomicAdd(acc + k00, q00);
+    atomicAdd(acc + k10, q10);
+    atomicAdd(acc + k01, q01);
+    atomicAdd(acc + k11, q11);
 }
 
 // ---------------------------------------------------------------------------------
@@ -200,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_particles2d(Params2D p)
             const bool was = live[k];
             live[k] = live[k] && c[k] >= 0;
             if (live[k]) {
-                const int cy = c[k] / nx, cx = c[k] - cy * nx;
+                const int cy = div_nx(p, c[k]), cx = c[k] - cy * nx;
                 const int cx1 = (cx + 1 == nx) ? 0 : cx + 1;
                 const int k00 = cy * nx + cx, k10 = cy * nx + cx1;
                 const float2 e00 = __ldg(p.E + k00), e10 = __ldg(p.E + k10);
@@ -231,9 +306,11 @@ __global__ void __launch_bounds__(kThreads) k_particles2d(Params2D p)
                     dyn = 0.0f;
                     ++ncy;
                 }
-                ncx %= nx;
-                if (ncx < 0)
-                    ncx += nx;
+                if ((unsigned)ncx >= (unsigned)nx) {  // the x wrap
+                    ncx %= nx;
+                    if (ncx < 0)
+                        ncx += nx;
+                }
                 if (ncy < 0) {
                     ++na0;
                     live[k] = false;
@@ -310,6 +387,417 @@ __global__ void __launch_bounds__(kThreads) k_particles2d(Params2D p)
         atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
 }
 
+// The move after the push: x^{n+1} = x^n + beta v^{n+1/2} dt in cell units from
+// cell (cx, cy) and offset (ox, oy), the x wrap and the plates.  Returns 0 or 1 if
+// the particle crossed the plate at y = 0 or y = Ly, else -1 with its new cell and
+// offset.
+__device__ __forceinline__ int move2d(const Params2D &p, int cx, int cy, float ox, float oy,
+                                      float vx, float vy, float b, int &ncx, int &ncy,
+                                      float &dxn, float &dyn)
+{
+    const int nx = p.nx;
+    const float xn = __fadd_rn(ox, __fmul_rn(__fmul_rn(b, vx), p.dt_dx));
+    const float yn = __fadd_rn(oy, __fmul_rn(__fmul_rn(b, vy), p.dt_dx));
+    const float fx = floorf(xn), fy = floorf(yn);
+    ncx = cx + (int)fx;
+    ncy = cy + (int)fy;
+    dxn = __fsub_rn(xn, fx);
+    dyn = __fsub_rn(yn, fy);
+    if (dxn >= 1.0f) {
+        dxn = 0.0f;
+        ++ncx;
+    }
+    if (dyn >= 1.0f) {
+        dyn = 0.0f;
+        ++ncy;
+    }
+    if ((unsigned)ncx >= (unsigned)nx) {  // the x wrap (at most a cell, but for beta = 1)
+        ncx %= nx;
+        if (ncx < 0)
+            ncx += nx;
+    }
+    if (ncy < 0)
+        return 0;
+    if (ncy >= p.ny)
+        return 1;
+    return -1;
+}
+
+// ---------------------------------------------------------------------------------
+// The in-place particle step with grid tiles in shared memory (the steps between
+// cell sorts).  After the sort (every kCompact2d steps) consecutive slots hold
+// particles of neighbouring cells, and each particle moves at most one cell per
+// step, so a chunk of kChunk2d consecutive slots touches a small box of the grid.
+// One CTA per chunk at a time:
+//   1. the chunk is copied into shared memory (coalesced loads), in a layout padded
+//      by one entry every 64 so that the strided reads below meet no bank conflict;
+//   2. the box of its cells, relative to the cell of a live particle near its
+//      middle (x differences taken modulo nx, so a chunk that runs over the end of a
+//      row is one box), widened by the gather's node and one cell of motion;
+//   3. the window of nodes covering the box (at most kWin2d nodes) gets E copied in
+//      and its deposit cleared;
+//   4. each particle is gathered, pushed, moved and deposited as k_particles2d does,
+//      from and into the window where its four nodes are inside it, else from E and
+//      into acc in global memory.  Thread (warp w, lane l) takes the chunk's
+//      particles 64 l + kPer2d w + k, so the lanes of a warp sit about a cell apart
+//      and their shared-memory atomics rarely meet on a node;
+//   5. the window's deposits go to acc (one atomic per nonzero node) and the chunk
+//      back to its slots.
+// The arithmetic per particle is that of k_particles2d (the same gathered values,
+// push, move and quantised deposit), so the integer deposits and every particle are
+// the same bit for bit; only where the charge is summed first differs.
+// ---------------------------------------------------------------------------------
+constexpr int kT2d = 512;                        // threads per CTA
+constexpr int kPer2d = 4;                        // particles per thread per chunk
+constexpr int kChunk2d = kT2d * kPer2d;          // 2,048 slots
+constexpr int kPad2d = kChunk2d + kChunk2d / 64; // padded shared-memory entries
+constexpr int kWin2d = 2048;                     // window nodes
+
+__device__ __forceinline__ int pad2d(int i) { return i + (i >> 6); }
+
+size_t tile2d_smem_bytes()
+{
+    return (size_t)kPad2d * (4 + 16 + 4) + (size_t)kWin2d * (8 + 4 + 4);
+}
+
+// 64-bit integer as two 32-bit words in shared memory (value = hi 2^32 + lo, modulo
+// 2^64): the carry out of lo is detected from the old value the atomic returns
+__device__ __forceinline__ void win_add(unsigned *lo, unsigned *hi, int k, unsigned long long v)
+{
+    const unsigned vl = (unsigned)v;
+    unsigned vh = (unsigned)(v >> 32);
+    const unsigned old = atomicAdd(lo + k, vl);
+    vh += (old + vl < old) ? 1u : 0u;
+    if (vh)
+        atomicAdd(hi + k, vh);
+}
+
+__global__ void __launch_bounds__(kT2d, 2) k_particles2d_tiles(Params2D p)
+{
+    extern __shared__ __align__(16) unsigned char smem2d[];
+    float4 *s_v = reinterpret_cast<float4 *>(smem2d);                  // [kPad2d]
+    float2 *s_E = reinterpret_cast<float2 *>(s_v + kPad2d);            // [kWin2d]
+    int32_t *s_c = reinterpret_cast<int32_t *>(s_E + kWin2d);          // [kPad2d]
+    float *s_z = reinterpret_cast<float *>(s_c + kPad2d);              // [kPad2d]
+    unsigned *s_lo = reinterpret_cast<unsigned *>(s_z + kPad2d);       // [kWin2d]
+    unsigned *s_hi = s_lo + kWin2d;                                    // [kWin2d]
+    __shared__ int s_ref, s_box[4];  // reference cell; min dx, -max dx, min dy, -max dy
+    __shared__ unsigned s_abs[2];
+
+    const int s = blockIdx.y;
+    const Species2D &sp = p.sp[s];
+    const long long step = *(volatile long long *)&p.st->step;
+    const int P = (int)(step & 1);
+    const long long n = (long long)p.st->count[s][P];
+    const int32_t *__restrict__ cin = sp.cell[P];
+    const float4 *__restrict__ vin = sp.pv[P];
+    const float *__restrict__ zin = sp.vz[P];
+    int32_t *__restrict__ cout = sp.cell[P ^ 1];
+    float4 *__restrict__ vout = sp.pv[P ^ 1];
+    float *__restrict__ zout = sp.vz[P ^ 1];
+    unsigned long long *acc = p.acc + (size_t)s * p.nn;
+    const int nx = p.nx, ny = p.ny;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 2)
+        s_abs[threadIdx.x] = 0u;
+    unsigned na0 = 0, na1 = 0;
+
+    const long long nchunks = (n + kChunk2d - 1) / kChunk2d;
+    for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const long long base = ch * kChunk2d;
+        const int cnt = (int)min((long long)kChunk2d, n - base);
+        // ---- 1. the chunk into shared memory
+        for (int j = threadIdx.x; j < kChunk2d; j += kT2d) {
+            const int q = pad2d(j);
+            if (j < cnt) {
+                s_c[q] = __ldcs(cin + base + j);
+                s_v[q] = __ldcs(vin + base + j);
+                s_z[q] = __ldcs(zin + base + j);
+            } else {
+                s_c[q] = -1;
+            }
+        }
+        if (threadIdx.x == 0) {
+            s_box[0] = s_box[1] = s_box[2] = s_box[3] = INT_MAX;
+            s_ref = -1;
+        }
+        __syncthreads();
+        // ---- 2. the reference cell (a live particle at or after the middle, else
+        // before it) and the box of the chunk's cells relative to it
+        if (threadIdx.x == 0) {
+            int r = -1;
+            for (int j = cnt / 2; j < cnt && r < 0; ++j)
+                r = s_c[pad2d(j)];
+            for (int j = cnt / 2 - 1; j >= 0 && r < 0; --j)
+                r = s_c[pad2d(j)];
+            s_ref = r;
+        }
+        __syncthreads();
+        const int ref = s_ref;
+        if (ref < 0) {  // nothing live: the holes stay holes
+            for (int j = threadIdx.x; j < cnt; j += kT2d)
+                __stcs(cout + base + j, -1);
+            __syncthreads();
+            continue;
+        }
+        const int ry = div_nx(p, ref), rx = ref - ry * nx;
+        {
+            int mnx = INT_MAX, mxx = INT_MAX, mny = INT_MAX, mxy = INT_MAX;  // max as -min
+            for (int k = 0; k < kPer2d; ++k) {
+                const int c = s_c[pad2d(k * kT2d + threadIdx.x)];
+                if (c >= 0) {
+                    const int cy = div_nx(p, c);
+                    int dx = c - cy * nx - rx;  // to [-nx/2, nx/2)
+                    if (dx >= nx - nx / 2)
+                        dx -= nx;
+                    else if (dx < -(nx / 2))
+                        dx += nx;
+                    const int dy = cy - ry;
+                    mnx = min(mnx, dx);
+                    mxx = min(mxx, -dx);
+                    mny = min(mny, dy);
+                    mxy = min(mxy, -dy);
+                }
+            }
+            mnx = __reduce_min_sync(0xffffffffu, mnx);
+            mxx = __reduce_min_sync(0xffffffffu, mxx);
+            mny = __reduce_min_sync(0xffffffffu, mny);
+            mxy = __reduce_min_sync(0xffffffffu, mxy);
+            if (lane == 0) {
+                atomicMin(&s_box[0], mnx);
+                atomicMin(&s_box[1], mxx);
+                atomicMin(&s_box[2], mny);
+                atomicMin(&s_box[3], mxy);
+            }
+        }
+        __syncthreads();
+        // ---- 3. the window: node columns wx0 .. wx0+ww-1 (modulo nx), rows wy0 ..
+        // wy0+wh-1, covering the box widened by the gather's node and one cell of
+        // motion each way (cut to kWin2d nodes; particles outside it go to global memory)
+        int ww = (-s_box[1]) - s_box[0] + 4;
+        int wx0 = rx + s_box[0] - 1;
+        const int wy0 = max(0, ry + s_box[2] - 1);
+        int wh = min(ny, ry - s_box[3] + 2) - wy0 + 1;
+        if (ww >= nx) {
+            ww = nx;
+            wx0 = 0;
+        }
+        wx0 %= nx;
+        if (wx0 < 0)
+            wx0 += nx;
+        if (ww > kWin2d / 2)
+            ww = kWin2d / 2;
+        if (ww * wh > kWin2d)
+            wh = kWin2d / ww;
+        // a warp per window row, a lane per column
+        for (int iy = warp; iy < wh; iy += kT2d / 32) {
+            const float2 *Er = p.E + (size_t)(wy0 + iy) * nx;
+            for (int ix = lane; ix < ww; ix += 32) {
+                const int gx = wx0 + ix < nx ? wx0 + ix : wx0 + ix - nx;
+                const int k = iy * ww + ix;
+                s_E[k] = __ldg(Er + gx);
+                s_lo[k] = 0u;
+                s_hi[k] = 0u;
+            }
+        }
+        __syncthreads();
+        // ---- 4. the particles, lanes of a warp 64 slots apart
+#pragma unroll 1
+        for (int k = 0; k < kPer2d; ++k) {
+            const int j = lane * 64 + warp * kPer2d + k;
+            const int q = pad2d(j);
+            const int c = j < cnt ? s_c[q] : -1;
+            if (c < 0)
+                continue;
+            const float4 pv = s_v[q];
+            const float z = s_z[q];
+            const int cy = div_nx(p, c), cx = c - cy * nx;
+            int ix = cx - wx0;
+            if (ix < 0)
+                ix += nx;
+            const int iy = cy - wy0;
+            float2 e00, e10, e01, e11;
+            if (ix <= ww - 2 && iy >= 0 && iy <= wh - 2) {
+                const int k00 = iy * ww + ix;
+                e00 = s_E[k00];
+                e10 = s_E[k00 + 1];
+                e01 = s_E[k00 + ww];
+                e11 = s_E[k00 + ww + 1];
+            } else {
+                const int cx1 = (cx + 1 == nx) ? 0 : cx + 1;
+                const int k00 = cy * nx + cx, k10 = cy * nx + cx1;
+                e00 = __ldg(p.E + k00);
+                e10 = __ldg(p.E + k10);
+                e01 = __ldg(p.E + k00 + nx);
+                e11 = __ldg(p.E + k10 + nx);
+            }
+            const float ox = pv.x, oy = pv.y;
+            const float wx0f = __fsub_rn(1.0f, ox), wy0f = __fsub_rn(1.0f, oy);
+            const float ex = __fadd_rn(
+                __fmul_rn(wy0f, __fadd_rn(__fmul_rn(wx0f, e00.x), __fmul_rn(ox, e10.x))),
+                __fmul_rn(oy, __fadd_rn(__fmul_rn(wx0f, e01.x), __fmul_rn(ox, e11.x))));
+            const float ey = __fadd_rn(
+                __fmul_rn(wy0f, __fadd_rn(__fmul_rn(wx0f, e00.y), __fmul_rn(ox, e10.y))),
+                __fmul_rn(oy, __fadd_rn(__fmul_rn(wx0f, e01.y), __fmul_rn(ox, e11.y))));
+            const float axp = __fmul_rn(sp.qm, ex), ayp = __fmul_rn(sp.qm, ey);
+            float vx, vy;
+            if (!push_v2_easy(sp.kind, pv.z, pv.w, z, axp, ayp, p.dt, sp.v0, vx, vy)) {
+                // the piece walk: listed for k_hard2d, which pushes it and writes its
+                // slot (pushed here once the list is full)
+                namespace cg = cooperative_groups;
+                cg::coalesced_group g = cg::coalesced_threads();
+                unsigned long long hb = 0;
+                if (g.thread_rank() == 0)
+                    hb = atomicAdd(&p.st->hard_n[s], (unsigned long long)g.size());
+                hb = g.shfl(hb, 0) + g.thread_rank();
+                if ((long long)hb < sp.hard_cap) {
+                    int4 *r = reinterpret_cast<int4 *>(sp.hard + hb);
+                    r[0] = make_int4((int)(base + j), c, __float_as_int(axp), __float_as_int(ayp));
+                    r[1] = make_int4(__float_as_int(pv.x), __float_as_int(pv.y),
+                                     __float_as_int(pv.z), __float_as_int(pv.w));
+                    r[2] = make_int4(__float_as_int(z), 0, 0, 0);
+                    s_c[q] = -2;  // its slot is k_hard2d's
+                    continue;
+                }
+                push_v2(sp.kind, pv.z, pv.w, z, axp, ayp, p.dt, sp.v0, vx, vy);
+            }
+            // x^{n+1} = x^n + beta(|v^{n+1/2}|) v^{n+1/2} dt, in cell units
+            const float b = beta_q(sp.kind, vx, vy, z, sp.v0);
+            int ncx, ncy;
+            float dxn, dyn;
+            const int wall = move2d(p, cx, cy, ox, oy, vx, vy, b, ncx, ncy, dxn, dyn);
+            if (wall == 0) {
+                ++na0;
+                s_c[q] = -1;
+            } else if (wall == 1) {
+                ++na1;
+                s_c[q] = -1;
+            } else {
+                unsigned long long q00, q10, q01, q11;
+                quantise2d(b, dxn, dyn, q00, q10, q01, q11);
+                int nix = ncx - wx0;
+                if (nix < 0)
+                    nix += nx;
+                const int niy = ncy - wy0;
+                if (nix <= ww - 2 && niy >= 0 && niy <= wh - 2) {
+                    const int k00 = niy * ww + nix;
+                    win_add(s_lo, s_hi, k00, q00);
+                    win_add(s_lo, s_hi, k00 + 1, q10);
+                    win_add(s_lo, s_hi, k00 + ww, q01);
+                    win_add(s_lo, s_hi, k00 + ww + 1, q11);
+                } else {
+                    const int ncx1 = (ncx + 1 == nx) ? 0 : ncx + 1;
+                    const int m00 = ncy * nx + ncx, m10 = ncy * nx + ncx1;
+                    atomicAdd(acc + m00, q00);
+                    atomicAdd(acc + m10, q10);
+                    atomicAdd(acc + m00 + nx, q01);
+                    atomicAdd(acc + m10 + nx, q11);
+                }
+                s_c[q] = ncy * nx + ncx;
+                s_v[q] = make_float4(dxn, dyn, vx, vy);
+            }
+        }
+        __syncthreads();
+        // ---- 5. the window's deposits to acc, the chunk to its slots
+        for (int iy = warp; iy < wh; iy += kT2d / 32) {
+            unsigned long long *ar = acc + (size_t)(wy0 + iy) * nx;
+            for (int ix = lane; ix < ww; ix += 32) {
+                const int k = iy * ww + ix;
+                const unsigned long long v = ((unsigned long long)s_hi[k] << 32) + s_lo[k];
+                if (v)
+                    atomicAdd(ar + (wx0 + ix < nx ? wx0 + ix : wx0 + ix - nx), v);
+            }
+        }
+        for (int j = threadIdx.x; j < cnt; j += kT2d) {
+            const int q = pad2d(j);
+            const int c = s_c[q];
+            if (c == -2)
+                continue;  // listed for k_hard2d
+            __stcs(cout + base + j, c);
+            if (c >= 0) {
+                __stcs(vout + base + j, s_v[q]);
+                __stcs(zout + base + j, s_z[q]);
+            }
+        }
+        __syncthreads();
+    }
+    na0 = __reduce_add_sync(0xffffffffu, na0);
+    na1 = __reduce_add_sync(0xffffffffu, na1);
+    if (lane == 0) {
+        if (na0)
+            atomicAdd(&s_abs[0], na0);
+        if (na1)
+            atomicAdd(&s_abs[1], na1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 && s_abs[threadIdx.x])
+        atomicAdd(&p.st->absorbed_step[s][threadIdx.x], (unsigned long long)s_abs[threadIdx.x]);
+}
+
+// The particles the tile kernel listed: the full push (series or piece walk, the
+// arithmetic of the inline push), the move, the plates and the deposit by global
+// atomics; each writes its own slot.  The species' lists are one index space.
+__global__ void __launch_bounds__(256) k_hard2d(Params2D p)
+{
+    __shared__ unsigned s_abs[kMaxS][2];
+    if (threadIdx.x < 2 * kMaxS)
+        s_abs[threadIdx.x >> 1][threadIdx.x & 1] = 0u;
+    __syncthreads();
+    const long long step = *(volatile long long *)&p.st->step;
+    const int P = (int)(step & 1);
+    long long pre[kMaxS + 1];  // registers: constant indices only
+    pre[0] = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxS; ++s) {
+        const long long n = s < p.ns ? (long long)*(volatile unsigned long long *)&p.st->hard_n[s] : 0;
+        pre[s + 1] = pre[s] + (s < p.ns ? min(n, p.sp[s].hard_cap) : 0);
+    }
+    const long long total = pre[kMaxS];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int s = 0;
+        long long i0 = 0;
+#pragma unroll
+        for (int r = 1; r < kMaxS; ++r)
+            if (t >= pre[r]) {
+                s = r;
+                i0 = pre[r];
+            }
+        const Species2D &sp = p.sp[s];
+        const int4 *rec = reinterpret_cast<const int4 *>(sp.hard + (t - i0));
+        const int4 r0 = __ldcs(rec), r1 = __ldcs(rec + 1), r2 = __ldcs(rec + 2);
+        const int slot = r0.x, c = r0.y;
+        const float ax = __int_as_float(r0.z), ay = __int_as_float(r0.w);
+        const float ox = __int_as_float(r1.x), oy = __int_as_float(r1.y);
+        const float ux = __int_as_float(r1.z), uy = __int_as_float(r1.w), z = __int_as_float(r2.x);
+        float vx, vy;
+        push_v2(sp.kind, ux, uy, z, ax, ay, p.dt, sp.v0, vx, vy);
+        const float b = beta_q(sp.kind, vx, vy, z, sp.v0);
+        const int cy = div_nx(p, c), cx = c - cy * p.nx;
+        int ncx, ncy;
+        float dxn, dyn;
+        const int wall = move2d(p, cx, cy, ox, oy, vx, vy, b, ncx, ncy, dxn, dyn);
+        if (wall >= 0) {
+            atomicAdd(&s_abs[s][wall], 1u);
+            sp.cell[P ^ 1][slot] = -1;
+        } else {
+            const int nx = p.nx;
+            const int ncx1 = (ncx + 1 == nx) ? 0 : ncx + 1;
+            const int m00 = ncy * nx + ncx, m10 = ncy * nx + ncx1;
+            deposit2d(p.acc + (size_t)s * p.nn, m00, m10, m00 + nx, m10 + nx, b, dxn, dyn);
+            sp.cell[P ^ 1][slot] = m00;
+            sp.pv[P ^ 1][slot] = make_float4(dxn, dyn, vx, vy);
+            sp.vz[P ^ 1][slot] = z;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kMaxS) {
+        const int s = threadIdx.x >> 1, w = threadIdx.x & 1;
+        if (s < p.ns && s_abs[s][w])
+            atomicAdd(&p.st->absorbed_step[s][w], (unsigned long long)s_abs[s][w]);
+    }
+}
+
 // rho^0 from the particles of the current buffer (after a load)
 __global__ void __launch_bounds__(kThreads) k_deposit2d(Params2D p)
 {
@@ -335,93 +823,135 @@ __global__ void __launch_bounds__(kThreads) k_deposit2d(Params2D p)
 
 // ---------------------------------------------------------------------------------
 // Source (the 1D volume source with its band across y, x uniform over the period)
-// and the step's bookkeeping; one CTA.  Particle i of species s draws
+// and the step's bookkeeping.  Particle i of species s draws
 // u_j = u24(SplitMix64(key(seed, step, s), 8i + j)): y = lo + u_0 len, x = u_5 nx (cells,
 // FP32), a physical Maxwellian velocity from u_1..u_4 (Box-Muller).
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_inject2d(Params2D p, int compact)
+// The step's source count of species s (thread s): macroparticles k to make (cut to
+// the room left; cut = true if it was), the first slot and the carried fraction.
+__device__ __forceinline__ void source_count2d(const Params2D &p, const State2D *st, int s, int P,
+                                               int compact, long long &k, long long &base,
+                                               double &frac, bool &cut)
+{
+    double S = 0.0;
+    if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
+        const int r = p.src_ref;
+        S = (double)(st->absorbed_step[r][0] + st->absorbed_step[r][1]) * p.sp[r].w;
+    } else if (p.src_mode == SLPIC_SRC_RATE) {
+        S = p.src_rate * p.dt64;
+    }
+    k = 0;
+    double f = st->src_frac[s];
+    if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
+        f = fma(S, p.sp[s].inv_w, f);
+        k = (long long)floor(f);
+        f -= (double)k;
+    }
+    // in place: the output uses the input's slots; compacted: counted by atomics
+    base = (long long)(compact ? st->count[s][P ^ 1] : st->count[s][P]);
+    const long long room = p.sp[s].capacity - base;
+    cut = k > room;
+    if (cut)
+        k = room;
+    frac = f;
+}
+
+// Every CTA derives the step's counts from the same state and makes its share of the
+// species' particles, taken as one index space; k_book2d then updates the state.
+__global__ void __launch_bounds__(256) k_inject2d(Params2D p, int compact)
 {
     __shared__ long long s_k[kMaxS], s_base[kMaxS];
-    __shared__ double s_frac[kMaxS];
-    __shared__ int s_cut[kMaxS];
-    State2D *st = p.st;
+    const State2D *st = p.st;
     const long long step = st->step;
     const int P = (int)(step & 1);
     const int ns = p.ns;
-    if (threadIdx.x < ns) {
+    if ((int)threadIdx.x < kMaxS) {
         const int s = threadIdx.x;
-        double S = 0.0;
-        if (p.src_mode == SLPIC_SRC_LOSS_MATCHED) {
-            const int r = p.src_ref;
-            S = (double)(st->absorbed_step[r][0] + st->absorbed_step[r][1]) * p.sp[r].w;
-        } else if (p.src_mode == SLPIC_SRC_RATE) {
-            S = p.src_rate * p.dt64;
-        }
-        long long k = 0;
-        double f = st->src_frac[s];
-        if (p.src_mode != SLPIC_SRC_NONE && p.sp[s].vth_src > 0.0f) {
-            f = fma(S, p.sp[s].inv_w, f);
-            k = (long long)floor(f);
-            f -= (double)k;
-        }
-        // in place: the output uses the input's slots; compacted: counted by atomics
-        const long long have = (long long)(compact ? st->count[s][P ^ 1] : st->count[s][P]);
-        const long long room = p.sp[s].capacity - have;
-        s_cut[s] = k > room;
-        s_k[s] = k > room ? room : k;
-        s_base[s] = have;
-        s_frac[s] = f;
+        long long k = 0, base = 0;
+        double f;
+        bool cut;
+        if (s < ns)
+            source_count2d(p, st, s, P, compact, k, base, f, cut);
+        s_k[s] = k;
+        s_base[s] = base;
     }
     __syncthreads();
-    for (int s = 0; s < ns; ++s) {
+    long long pre[kMaxS + 1];  // registers: constant indices only
+    pre[0] = 0;
+#pragma unroll
+    for (int s = 0; s < kMaxS; ++s)
+        pre[s + 1] = pre[s] + s_k[s];
+    const long long total = pre[kMaxS];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int s = 0;
+        long long i0 = 0;
+#pragma unroll
+        for (int r = 1; r < kMaxS; ++r)
+            if (t >= pre[r]) {
+                s = r;
+                i0 = pre[r];
+            }
+        const long long i = t - i0;
         const Species2D &sp = p.sp[s];
         const unsigned long long key = sm64_stream(p.seed, (unsigned long long)step, (unsigned)s);
         unsigned long long *acc = p.acc + (size_t)s * p.nn;
-        for (long long i = threadIdx.x; i < s_k[s]; i += blockDim.x) {
-            const unsigned long long b8 = 8ULL * (unsigned long long)i;
-            const float u0 = u24(sm64_at(key, b8 + 0)), u1 = u24(sm64_at(key, b8 + 1));
-            const float u2 = u24(sm64_at(key, b8 + 2)), u3 = u24(sm64_at(key, b8 + 3));
-            const float u4 = u24(sm64_at(key, b8 + 4)), u5 = u24(sm64_at(key, b8 + 5));
-            const float yc = __fadd_rn(p.src_lo, __fmul_rn(u0, p.src_len));
-            float xc = __fmul_rn(u5, (float)p.nx);
-            if (xc >= (float)p.nx)
-                xc = 0.0f;
-            const float fx = floorf(xc), fy = floorf(yc);
-            const int cx = (int)fx, cy = min(max((int)fy, 0), p.ny - 1);
-            const float ox = __fsub_rn(xc, fx), oy = __fsub_rn(yc, fy);
-            const float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
-            float s2, c2;
-            sincospif(2.0f * u2, &s2, &c2);
-            const float vx = sp.vth_src * r1 * c2, vy = sp.vth_src * r1 * s2;
-            const float vz = sp.vth_src * r2 * cospif(2.0f * u4);
-            const long long o = s_base[s] + i;
-            const int c = cy * p.nx + cx;
-            sp.cell[P ^ 1][o] = c;
-            sp.pv[P ^ 1][o] = make_float4(ox, oy, vx, vy);
-            sp.vz[P ^ 1][o] = vz;
-            const int cx1 = (cx + 1 == p.nx) ? 0 : cx + 1;
-            deposit2d(acc, c, cy * p.nx + cx1, c + p.nx, cy * p.nx + cx1 + p.nx,
-                      beta_q(sp.kind, vx, vy, vz, sp.v0), ox, oy);
-        }
+        const unsigned long long b8 = 8ULL * (unsigned long long)i;
+        const float u0 = u24(sm64_at(key, b8 + 0)), u1 = u24(sm64_at(key, b8 + 1));
+        const float u2 = u24(sm64_at(key, b8 + 2)), u3 = u24(sm64_at(key, b8 + 3));
+        const float u4 = u24(sm64_at(key, b8 + 4)), u5 = u24(sm64_at(key, b8 + 5));
+        const float yc = __fadd_rn(p.src_lo, __fmul_rn(u0, p.src_len));
+        float xc = __fmul_rn(u5, (float)p.nx);
+        if (xc >= (float)p.nx)
+            xc = 0.0f;
+        const float fx = floorf(xc), fy = floorf(yc);
+        const int cx = (int)fx, cy = min(max((int)fy, 0), p.ny - 1);
+        const float ox = __fsub_rn(xc, fx), oy = __fsub_rn(yc, fy);
+        const float r1 = sqrtf(-2.0f * logf(u1)), r2 = sqrtf(-2.0f * logf(u3));
+        float s2, c2;
+        sincospif(2.0f * u2, &s2, &c2);
+        const float vx = sp.vth_src * r1 * c2, vy = sp.vth_src * r1 * s2;
+        const float vz = sp.vth_src * r2 * cospif(2.0f * u4);
+        const long long o = s_base[s] + i;
+        const int c = cy * p.nx + cx;
+        sp.cell[P ^ 1][o] = c;
+        sp.pv[P ^ 1][o] = make_float4(ox, oy, vx, vy);
+        sp.vz[P ^ 1][o] = vz;
+        const int cx1 = (cx + 1 == p.nx) ? 0 : cx + 1;
+        deposit2d(acc, c, cy * p.nx + cx1, c + p.nx, cy * p.nx + cx1 + p.nx,
+                  beta_q(sp.kind, vx, vy, vz, sp.v0), ox, oy);
     }
-    __syncthreads();
-    if (threadIdx.x < ns) {
+}
+
+// The step's bookkeeping, after the source (one warp; thread s for species s, from
+// the same counts as k_inject2d); the step index last.
+__global__ void k_book2d(Params2D p, int compact)
+{
+    State2D *st = p.st;
+    const long long step = st->step;
+    const int P = (int)(step & 1);
+    if ((int)threadIdx.x < p.ns) {
         const int s = threadIdx.x;
-        if (s_cut[s])
+        long long k, base;
+        double f;
+        bool cut;
+        source_count2d(p, st, s, P, compact, k, base, f, cut);
+        if (cut)
             atomicCAS(&st->error, 0, SLPIC_ERR_CAPACITY);
         const unsigned long long a0 = st->absorbed_step[s][0], a1 = st->absorbed_step[s][1];
-        st->src_frac[s] = s_frac[s];
+        st->src_frac[s] = f;
         st->holes[s][P ^ 1] = compact ? 0ULL : st->holes[s][P] + a0 + a1;
-        st->count[s][P ^ 1] = (unsigned long long)(s_base[s] + s_k[s]);
-        st->injected_total[s] += s_k[s];
+        st->count[s][P ^ 1] = (unsigned long long)(base + k);
+        st->injected_total[s] += k;
         st->absorbed_total[s][0] += (long long)a0;
         st->absorbed_total[s][1] += (long long)a1;
         st->absorbed_step[s][0] = 0ULL;
         st->absorbed_step[s][1] = 0ULL;
         st->count[s][P] = 0ULL;
         st->holes[s][P] = 0ULL;
+        st->hard_n[s] = 0ULL;
     }
-    __syncthreads();
+    __syncwarp();
     if (threadIdx.x == 0)
         st->step = step + 1;
 }
@@ -1169,6 +1699,8 @@ struct slpic2d_sim {
     cudaStream_t stream = nullptr, own_stream = nullptr;
     Params2D p{};
     int ctas = 1;     // particle-kernel CTAs per species
+    int tile_ctas = 0;  // k_particles2d_tiles CTAs per species (0: not resident)
+    int small_ctas = 1; // k_hard2d and k_inject2d: 2 CTAs of 256 threads per SM
     int cg_ctas = 1;  // cooperative CG grid
     bool prepared = false;
     bool timing = false;               // record events around the kernels of each step
@@ -1404,6 +1936,7 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
     h->stream = h->own_stream;
     Params2D &p = h->p;
     p.nx = c->nx;
+    make_div_nx(p.nx, p.nx_m, p.nx_s);
     p.ny = c->ny;
     p.nn = c->nx * (c->ny + 1);
     p.ns = c->n_species;
@@ -1437,6 +1970,13 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
             ok = alloc((void **)&d.cell[b], sizeof(int32_t) * sp.capacity) &&
                  alloc((void **)&d.pv[b], sizeof(float4) * sp.capacity) &&
                  alloc((void **)&d.vz[b], sizeof(float) * sp.capacity);
+        // the step's list of walked pushes: an eighth of the capacity, at least 64k
+        // (slot indices are int32; beyond the list the tile kernel pushes inline)
+        d.hard_cap = sp.capacity <= INT_MAX
+                         ? std::min<long long>(sp.capacity, std::max<long long>(sp.capacity / 8, 65536))
+                         : 0;
+        if (ok && d.hard_cap)
+            ok = alloc((void **)&d.hard, sizeof(HardRec2D) * d.hard_cap);
         d.capacity = sp.capacity;
         d.qm = (float)(sp.q / sp.m);
         d.v0 = (float)sp.v0;
@@ -1457,6 +1997,18 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
         return bail(SLPIC_ERR_CUDA, "CG kernel occupancy query failed");
     h->cg_ctas = std::min(sms * std::min(occ, 2), kBarGroup * kBarGroups);
     h->ctas = sms * 4;
+    h->small_ctas = sms * 2;
+    {
+        // the tile kernel: every CTA of both species resident at once
+        int occ_t = 0;
+        if (cudaFuncSetAttribute(k_particles2d_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile2d_smem_bytes()) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, k_particles2d_tiles, kT2d,
+                                                          tile2d_smem_bytes()) == cudaSuccess &&
+            occ_t > 0)
+            h->tile_ctas = std::max(1, sms * occ_t / p.ns);
+        cudaGetLastError();
+    }
     if (!alloc((void **)&p.part, sizeof(double) * 3 * h->cg_ctas))
         return bail(SLPIC_ERR_OOM, "device allocation failed");
     if (!alloc((void **)&p.hist, sizeof(int) * nn) || !alloc((void **)&p.cursor, sizeof(int) * nn) ||
@@ -1644,11 +2196,16 @@ extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
             CK2(h, cudaEventRecord(ev[0], h->stream));
         if (compact)
             k_particles2d<true><<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
-        else
+        else if (h->tile_ctas) {
+            k_particles2d_tiles<<<dim3(h->tile_ctas, p.ns), kT2d, tile2d_smem_bytes(), h->stream>>>(p);
+            k_hard2d<<<h->small_ctas, 256, 0, h->stream>>>(p);
+        } else {
             k_particles2d<false><<<dim3(h->ctas, p.ns), kThreads, 0, h->stream>>>(p);
+        }
         if (ev)
             CK2(h, cudaEventRecord(ev[1], h->stream));
-        k_inject2d<<<1, 1024, 0, h->stream>>>(p, compact ? 1 : 0);
+        k_inject2d<<<h->small_ctas, 256, 0, h->stream>>>(p, compact ? 1 : 0);
+        k_book2d<<<1, 32, 0, h->stream>>>(p, compact ? 1 : 0);
         CK2(h, cudaGetLastError());
         // after the compacting step (holes dropped, sources appended): particles by cell
         if (compact && (rc = sort_particles(h, (int)((step + 1) & 1))))

@@ -354,12 +354,14 @@ def test_particles_are_sorted_by_cell_after_load_and_compaction():
     g.close()
 
 
-def test_warp_summed_deposit_is_the_per_particle_deposit():
-    """The step's deposit adds the lanes of a warp that share a cell before its
-    atomics.  With the direct solver (exact to roundoff), the potential each step
-    leaves equals the direct solve of the charge recomputed particle by particle
-    (slpic2d_fields) at the same positions: a lost, doubled or misplaced sum would
-    show at once.  Sorted particles (after the load) make the groups long."""
+def test_tile_summed_deposit_is_the_per_particle_deposit():
+    """The in-place step sums a chunk's charge in a window of nodes in shared memory
+    (global atomics for what falls outside it) before adding it to the grid.  With
+    the direct solver (exact to roundoff), the potential each step leaves equals the
+    direct solve of the charge recomputed particle by particle (slpic2d_fields) at the
+    same positions: a lost, doubled or misplaced sum would show at once.  On this
+    narrow grid a chunk spans whole rows, so the windows are whole rows and the last
+    column's cells take the global path."""
     prob = _prob(nx=64, ny=40, ppc=16, v0=0.3, dt=1.5, phi_hi=0.5)
     prob["solver"] = "fft"
     st = inputs.load_state2d(prob, seed=61)
@@ -389,4 +391,24 @@ def test_sort_drops_holes_when_particles_are_added_later():
         c, _, _ = g.particles(s)
         assert c.size == before[s] + extra[s][0].size
         assert np.all(c >= 0) and np.all(np.diff(c) >= 0)
+    g.close()
+
+
+def test_tile_windows_over_in_place_steps_match_per_particle_deposit():
+    """The same bar on a wide grid, where a sorted chunk covers part of a row and its
+    window a small box: over the in-place steps between two sorts (particles drift
+    and the boxes grow), in a strong non-uniform field with absorbing plates and a
+    biased plate, the step's summed deposit gives the potential of the charge
+    recomputed particle by particle."""
+    prob = _prob(nx=256, ny=48, ppc=20, v0=0.3, dt=1.5, phi_hi=0.5)
+    prob["solver"] = "fft"
+    st = _nonneutral(inputs.load_state2d(prob, seed=81), frac=0.5, seed=3)
+    g = _sim(prob, st)
+    for n in (1, 6, 8):  # after 1, 7 and 15 steps, all in place (the 16th compacts)
+        g.step(n)
+        rho, phi, _, _ = g.fields()
+        ref = orc.poisson2d_direct(rho, prob["dx"], prob["phi_lo"], prob["phi_hi"])
+        assert np.abs(phi - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), n
+    d = g.diagnostics()
+    assert sum(d["absorbed"][0]) > 0
     g.close()
