@@ -805,8 +805,13 @@ def run_2d(args):
                    "l2": "state larger than L2"},
         "particles_at_load": int(n_load), "particles_timed_mean": n_mean,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_particles2d",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": ("k_particles2d_tiles + k_hard2d (in-place steps; k_particles2d "
+                                "every 16th)"),
                      "kernel_ms": pk, "inject_kernel_ms": ik, "field_kernel_ms": fk,
+                     "inject_note": "source and bookkeeping, and the cell sort after the "
+                                    "compacting step",
+                     "iterative_pushes_last_step": d1["iterative_last"],
                      "bytes_per_particle_step": bpp,
                      "peak_source": f"{peak_kind} HBM copy bandwidth"},
         "field_solve": {"cg_iterations_per_step": cg_per_step,

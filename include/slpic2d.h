@@ -84,7 +84,8 @@ typedef struct {
     int64_t absorbed[SLPIC_MAX_SPECIES][2]; /* cumulative, at y = 0 / y = Ly            */
     int64_t injected[SLPIC_MAX_SPECIES];    /* cumulative                               */
     int32_t cg_iterations;                  /* iterations of the last solve             */
-    int32_t reserved;
+    int32_t iterative_last;                 /* pushes of the last step that took the
+                                               piece walk (all species)                 */
     int64_t cg_iterations_total;            /* over every solve since creation          */
     double cg_rel_residual;                 /* ||b - A phi|| / ||b|| after the last solve */
 } slpic2d_diag;

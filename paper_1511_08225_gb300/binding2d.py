@@ -45,7 +45,7 @@ class slpic2d_diag(ctypes.Structure):
                 ("count", ctypes.c_int64 * SLPIC_MAX_SPECIES),
                 ("absorbed", (ctypes.c_int64 * 2) * SLPIC_MAX_SPECIES),
                 ("injected", ctypes.c_int64 * SLPIC_MAX_SPECIES),
-                ("cg_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cg_iterations", ctypes.c_int32), ("iterative_last", ctypes.c_int32),
                 ("cg_iterations_total", ctypes.c_int64), ("cg_rel_residual", ctypes.c_double)]
 
 
@@ -200,7 +200,8 @@ def slpic2d_diagnostics(h) -> dict:
     _check(h, load_library().slpic2d_diagnostics(h, ctypes.byref(d)), "slpic2d_diagnostics")
     return {"step": d.step, "time": d.time, "count": list(d.count),
             "absorbed": [list(a) for a in d.absorbed], "injected": list(d.injected),
-            "cg_iterations": d.cg_iterations, "cg_iterations_total": d.cg_iterations_total,
+            "cg_iterations": d.cg_iterations, "iterative_last": d.iterative_last,
+            "cg_iterations_total": d.cg_iterations_total,
             "cg_rel_residual": d.cg_rel_residual}
 
 

@@ -84,6 +84,7 @@ struct State2D {
     long long injected_total[kMaxS];
     double src_frac[kMaxS];
     unsigned long long hard_n[kMaxS];  // particles listed for k_hard2d this step
+    unsigned long long iter_last;      // walked pushes of the last step, all species
     long long cg_total;
     double cg_res;
     int cg_iters;
@@ -949,9 +950,17 @@ __global__ void k_book2d(Params2D p, int compact)
         st->absorbed_step[s][1] = 0ULL;
         st->count[s][P] = 0ULL;
         st->holes[s][P] = 0ULL;
-        st->hard_n[s] = 0ULL;
     }
     __syncwarp();
+    if (threadIdx.x == 0) {
+        unsigned long long it = 0;
+        for (int s = 0; s < p.ns; ++s)
+            it += st->hard_n[s];
+        st->iter_last = it;
+    }
+    __syncwarp();
+    if ((int)threadIdx.x < p.ns)
+        st->hard_n[threadIdx.x] = 0ULL;
     if (threadIdx.x == 0)
         st->step = step + 1;
 }
@@ -2397,6 +2406,7 @@ extern "C" int slpic2d_diagnostics(slpic2d_t *h, slpic2d_diag *out)
         out->injected[s] = st.injected_total[s];
     }
     out->cg_iterations = st.cg_iters;
+    out->iterative_last = (int32_t)std::min<unsigned long long>(st.iter_last, 0x7fffffffULL);
     out->cg_iterations_total = st.cg_total;
     out->cg_rel_residual = st.cg_res;
     return SLPIC_OK;
