@@ -117,6 +117,7 @@ struct Params2D {
     double2 *tw;              // [nx/2] (cos, sin)(2 pi m / nx)
     double2 *spec;            // [nn] Fourier coefficients along x, row by row
     double *inv_m;            // [nn] Thomas multipliers 1/m_j per (row j, mode k)
+    double *seg_f, *seg_b;    // [nn] their products within a segment, up to / from row j
     double *rpart;            // [2 (ny+1)] per-row sums of r^2 and b^2
     int *hist, *cursor, *bsum;  // cell sort: counts per cell, then slots; block sums
 };
@@ -290,8 +291,15 @@ __global__ void __launch_bounds__(kThreads) k_particles2d(Params2D p)
                     __fmul_rn(wy0, __fadd_rn(__fmul_rn(wx0, e00.y), __fmul_rn(ox, e10.y))),
                     __fmul_rn(oy, __fadd_rn(__fmul_rn(wx0, e01.y), __fmul_rn(ox, e11.y))));
                 float vx, vy;
-                push_v2(sp.kind, q[k].z, q[k].w, z[k], __fmul_rn(sp.qm, ex), __fmul_rn(sp.qm, ey),
-                        p.dt, sp.v0, vx, vy);
+                const float axp = __fmul_rn(sp.qm, ex), ayp = __fmul_rn(sp.qm, ey);
+                if (!push_v2_easy(sp.kind, q[k].z, q[k].w, z[k], axp, ayp, p.dt, sp.v0, vx, vy)) {
+                    // the piece walk, here inline; counted for the diagnostics
+                    namespace cg = cooperative_groups;
+                    cg::coalesced_group g = cg::coalesced_threads();
+                    if (g.thread_rank() == 0)
+                        atomicAdd(&p.st->hard_n[s], (unsigned long long)g.size());
+                    push_v2(sp.kind, q[k].z, q[k].w, z[k], axp, ayp, p.dt, sp.v0, vx, vy);
+                }
                 // x^{n+1} = x^n + beta(|v^{n+1/2}|) v^{n+1/2} dt, in cell units
                 const float b = beta_q(sp.kind, vx, vy, z[k], sp.v0);
                 const float xn = __fadd_rn(ox, __fmul_rn(__fmul_rn(b, vx), p.dt_dx));
@@ -1359,68 +1367,97 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_rows(Params2D p, int mode)
         p.spec[(size_t)j * nx + k] = sx[k];
 }
 
-// Thomas per mode k: forward u'_j = (b^_j + u'_{j-1}) / m_j, back u_j = u'_j + u_{j+1} / m_j.
-// One thread per mode; rows are taken kTriRows at a time, their loads issued together
-// before the dependent chain runs through them, so a block costs one memory latency.
-// Launched as one warp per CTA, so that the nx chains spread over as many SMs as
-// they can fill.
-constexpr int kTriRows = 16;
-constexpr int kTriThreads = 32;
+// Thomas per mode k: forward u'_j = (b^_j + u'_{j-1}) / m_j, back u_j = u'_j + u_{j+1} / m_j
+// (rows 1..ny-1), the multipliers 1/m_j tabulated.  Both are first-order linear
+// recurrences, so each is solved in segments of L rows side by side: every segment
+// from a zero start (x~), then the value entering each segment by a short sequential
+// pass over the segments' ends, then x = x~ + P x_in with P the product of the
+// segment's multipliers up to the row (tabulated: seg_f forward, seg_b backward).
+// A CTA takes kTriModes modes (consecutive k: coalesced rows) times kTriSegs segments.
+constexpr int kTriModes = 8;
+constexpr int kTriSegs = 32;
 
-__global__ void __launch_bounds__(kTriThreads) k_tridiag_modes(Params2D p)
+__host__ __device__ __forceinline__ int tri_seg_len(int ny)
 {
+    return (ny - 1 + kTriSegs - 1) / kTriSegs;
+}
+
+__global__ void __launch_bounds__(kTriModes * kTriSegs) k_tridiag_modes(Params2D p)
+{
+    __shared__ double2 s_end[kTriSegs][kTriModes], s_in[kTriSegs][kTriModes];
     const int nx = p.nx, ny = p.ny;
-    const int k = blockIdx.x * kTriThreads + threadIdx.x;
-    if (k >= nx)
-        return;
+    const int kk = threadIdx.x % kTriModes, sg = threadIdx.x / kTriModes;
+    const int k = blockIdx.x * kTriModes + kk;
+    const bool act = k < nx;
+    const int L = tri_seg_len(ny);
+    const int j0 = 1 + sg * L, j1 = min(ny, j0 + L);  // this segment's rows [j0, j1)
     double2 *__restrict__ spec = p.spec;
     const double *__restrict__ invm = p.inv_m;
-    double2 d = make_double2(0.0, 0.0);
-    for (int j0 = 1; j0 < ny; j0 += kTriRows) {
-        double2 v[kTriRows];
-        double m[kTriRows];
-#pragma unroll
-        for (int r = 0; r < kTriRows; ++r)
-            if (j0 + r < ny) {
-                const size_t o = (size_t)(j0 + r) * nx + k;
-                v[r] = spec[o];
-                m[r] = __ldg(invm + o);
+    const double *__restrict__ pf = p.seg_f;
+    const double *__restrict__ pb = p.seg_b;
+    // 1. forward, from zero
+    double2 x = make_double2(0.0, 0.0);
+    if (act)
+        for (int j = j0; j < j1; ++j) {
+            const size_t o = (size_t)j * nx + k;
+            const double2 v = spec[o];
+            const double m = __ldg(invm + o);
+            x = make_double2((v.x + x.x) * m, (v.y + x.y) * m);
+            spec[o] = x;
+        }
+    s_end[sg][kk] = x;
+    __syncthreads();
+    // 2. the forward value entering each segment (a thread per mode)
+    if (sg == 0 && act) {
+        double2 c = make_double2(0.0, 0.0);
+        for (int t = 0; t < kTriSegs; ++t) {
+            s_in[t][kk] = c;
+            const int e = min(ny, 1 + (t + 1) * L) - 1;  // the segment's last row
+            if (1 + t * L <= e) {
+                const double f = __ldg(pf + (size_t)e * nx + k);
+                c = make_double2(fma(f, c.x, s_end[t][kk].x), fma(f, c.y, s_end[t][kk].y));
             }
-#pragma unroll
-        for (int r = 0; r < kTriRows; ++r)
-            if (j0 + r < ny) {
-                d = make_double2((v[r].x + d.x) * m[r], (v[r].y + d.y) * m[r]);
-                v[r] = d;
-            }
-#pragma unroll
-        for (int r = 0; r < kTriRows; ++r)
-            if (j0 + r < ny)
-                spec[(size_t)(j0 + r) * nx + k] = v[r];
+        }
     }
+    __syncthreads();
+    // 3. the forward values completed, then the backward recurrence from zero, top down
+    const double2 cf = s_in[sg][kk];
     double2 u = make_double2(0.0, 0.0);
-    const int nb = (ny - 1 + kTriRows - 1) / kTriRows;  // blocks of rows 1..ny-1
-    for (int b = nb - 1; b >= 0; --b) {
-        const int j0 = 1 + b * kTriRows;
-        double2 v[kTriRows];
-        double m[kTriRows];
-#pragma unroll
-        for (int r = 0; r < kTriRows; ++r)
-            if (j0 + r < ny) {
-                const size_t o = (size_t)(j0 + r) * nx + k;
-                v[r] = spec[o];
-                m[r] = __ldg(invm + o);
+    if (act)
+        for (int j = j1 - 1; j >= j0; --j) {
+            const size_t o = (size_t)j * nx + k;
+            const double f = __ldg(pf + o);
+            const double2 v = spec[o];
+            const double2 d = make_double2(fma(f, cf.x, v.x), fma(f, cf.y, v.y));
+            const double m = __ldg(invm + o);
+            u = make_double2(fma(u.x, m, d.x), fma(u.y, m, d.y));
+            spec[o] = u;
+        }
+    __syncthreads();  // every thread has read s_in
+    s_end[sg][kk] = u;
+    __syncthreads();
+    // 4. the backward value entering each segment from above
+    if (sg == 0 && act) {
+        double2 c = make_double2(0.0, 0.0);
+        for (int t = kTriSegs - 1; t >= 0; --t) {
+            s_in[t][kk] = c;
+            const int b0 = 1 + t * L;  // the segment's first row
+            if (b0 <= min(ny, b0 + L) - 1) {
+                const double g = __ldg(pb + (size_t)b0 * nx + k);
+                c = make_double2(fma(g, c.x, s_end[t][kk].x), fma(g, c.y, s_end[t][kk].y));
             }
-#pragma unroll
-        for (int r = kTriRows - 1; r >= 0; --r)
-            if (j0 + r < ny) {
-                u = make_double2(fma(u.x, m[r], v[r].x), fma(u.y, m[r], v[r].y));
-                v[r] = u;
-            }
-#pragma unroll
-        for (int r = 0; r < kTriRows; ++r)
-            if (j0 + r < ny)
-                spec[(size_t)(j0 + r) * nx + k] = v[r];
+        }
     }
+    __syncthreads();
+    // 5. the backward values completed
+    const double2 cb = s_in[sg][kk];
+    if (act)
+        for (int j = j0; j < j1; ++j) {
+            const size_t o = (size_t)j * nx + k;
+            const double g = __ldg(pb + o);
+            const double2 w = spec[o];
+            spec[o] = make_double2(fma(g, cb.x, w.x), fma(g, cb.y, w.y));
+        }
 }
 
 // inverse: phi of row j from its coefficients
@@ -1864,7 +1901,7 @@ static int launch_solve(slpic2d_t *h, int mode)
     const Params2D &p = h->p;
     const size_t smem = (size_t)16 * p.nx;
     k_fft_rows<<<p.ny - 1, kFftThreads, smem, h->stream>>>(p, mode);
-    k_tridiag_modes<<<(p.nx + kTriThreads - 1) / kTriThreads, kTriThreads, 0, h->stream>>>(p);
+    k_tridiag_modes<<<(p.nx + kTriModes - 1) / kTriModes, kTriModes * kTriSegs, 0, h->stream>>>(p);
     k_ifft_rows<<<p.ny - 1, kFftThreads, smem, h->stream>>>(p);
     k_fft_finish<<<p.ny + 1, kFftThreads, 0, h->stream>>>(p, mode);
     k_fft_report<<<1, kFftThreads, 0, h->stream>>>(p);
@@ -2032,6 +2069,8 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
         if (!alloc((void **)&p.tw, sizeof(double2) * std::max(1, p.nx / 2)) ||
             !alloc((void **)&p.spec, sizeof(double2) * nn) ||
             !alloc((void **)&p.inv_m, sizeof(double) * nn) ||
+            !alloc((void **)&p.seg_f, sizeof(double) * nn) ||
+            !alloc((void **)&p.seg_b, sizeof(double) * nn) ||
             !alloc((void **)&p.rpart, sizeof(double) * 2 * (p.ny + 1)))
             return bail(SLPIC_ERR_OOM, "device allocation failed");
         const double two_pi = 6.283185307179586;
@@ -2047,9 +2086,29 @@ extern "C" int slpic2d_create(const slpic2d_config *c, slpic2d_t **out)
                 inv_m[(size_t)j * p.nx + k] = prev;
             }
         }
+        // products of the multipliers within each segment of rows (k_tridiag_modes)
+        std::vector<double> seg_f(nn, 0.0), seg_b(nn, 0.0);
+        const int L = tri_seg_len(p.ny);
+        for (int k = 0; k < p.nx; ++k)
+            for (int j0 = 1; j0 < p.ny; j0 += L) {
+                const int j1 = std::min(p.ny, j0 + L);
+                double f = 1.0, g = 1.0;
+                for (int j = j0; j < j1; ++j) {
+                    f *= inv_m[(size_t)j * p.nx + k];
+                    seg_f[(size_t)j * p.nx + k] = f;
+                }
+                for (int j = j1 - 1; j >= j0; --j) {
+                    g *= inv_m[(size_t)j * p.nx + k];
+                    seg_b[(size_t)j * p.nx + k] = g;
+                }
+            }
         cudaError_t e2 = cudaMemcpy(p.tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice);
         if (e2 == cudaSuccess)
             e2 = cudaMemcpy(p.inv_m, inv_m.data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpy(p.seg_f, seg_f.data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpy(p.seg_b, seg_b.data(), sizeof(double) * nn, cudaMemcpyHostToDevice);
         const int smem = 16 * p.nx;
         if (e2 == cudaSuccess && smem > 48 * 1024)
             e2 = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
