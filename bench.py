@@ -941,16 +941,30 @@ def run_unet2d(args):
     # the pairs from a run of the direct solver (the same potential, 30x cheaper to make
     # when nx is a power of two); the timed runs below use the CG
     gen = dict(prob, solver="fft") if nx & (nx - 1) == 0 else prob
-    pairs = warmstart.collect_pairs(gen, seeds=(inputs.SEED + 1,), pairs_per_seed=args.unet_pairs,
-                                    every=2, skip=10, keep_prev=True)
+    # a large set (more than 512 pairs) is made on the device, change images only: the
+    # network of the change mode alone is trained on it
+    big = args.unet_pairs > 512
+    if big:
+        sets = [("delta", warmstart.collect_delta_images(gen, inputs.SEED + 1, args.unet_pairs,
+                                                         every=2, skip=10))]
+    else:
+        pairs = warmstart.collect_pairs(gen, seeds=(inputs.SEED + 1,),
+                                        pairs_per_seed=args.unet_pairs, every=2, skip=10,
+                                        keep_prev=True)
+        sets = [("direct", warmstart.images(pairs)), ("delta", warmstart.delta_images(pairs))]
+        del pairs
     collect_s = time.perf_counter() - t0
     L, C = 4, args.unet_base
     nets, train_info = {}, {}
-    for name, (x, t) in (("direct", warmstart.images(pairs)), ("delta", warmstart.delta_images(pairs))):
+    for name, (x, t) in sets:
+        if big:
+            xd, td = x, t
+            scale = warmstart.output_scale(x[:512].cpu().numpy(), t[:512].cpu().numpy())
+        else:
+            xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+            scale = warmstart.output_scale(x, t)
         net = binding_unet.UNet(L, C, ny, nx, max_batch=args.unet_batch, normalise=True,
-                                out_scale=warmstart.output_scale(x, t), seed=1,
-                                tensor_cores=not args.unet_cuda_cores)
-        xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+                                out_scale=scale, seed=1, tensor_cores=not args.unet_cuda_cores)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         losses = warmstart.fit(net, xd, td, steps=args.unet_train_steps, batch=args.unet_batch,
@@ -959,17 +973,18 @@ def run_unet2d(args):
         train_info[name] = {"seconds": time.perf_counter() - t1, "loss_first": losses[0][1],
                             "loss_last": losses[-1][1]}
         nets[name] = net
-        del xd, td
-    del pairs
+        del xd, td, x, t
+    sets = None
+    fwd_net = nets.get("direct", nets["delta"])
     # the network's forward pass alone, CUDA events on its stream
     xin = torch.randn(1, ny, nx, device="cuda")
     yout = torch.zeros_like(xin)
     for _ in range(3):
-        nets["direct"].forward(xin, yout)
+        fwd_net.forward(xin, yout)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(10):
-        nets["direct"].forward(xin, yout)
+        fwd_net.forward(xin, yout)
     e1.record()
     e1.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 10
@@ -983,9 +998,10 @@ def run_unet2d(args):
         bound, kern = "tensor", "U-Net forward (k_conv_fwd_tc, tcgen05)"
 
     state = inputs.load_state2d(prob)
-    modes = (("prev", binding2d.SLPIC2D_WARM_PREV, None), ("zero", binding2d.SLPIC2D_WARM_ZERO, None),
-             ("unet", binding2d.SLPIC2D_WARM_UNET, nets["direct"]),
-             ("unet_delta", binding2d.SLPIC2D_WARM_UNET_DELTA, nets["delta"]))
+    modes = (("prev", binding2d.SLPIC2D_WARM_PREV, None), ("zero", binding2d.SLPIC2D_WARM_ZERO, None))
+    if "direct" in nets:
+        modes += (("unet", binding2d.SLPIC2D_WARM_UNET, nets["direct"]),)
+    modes += (("unet_delta", binding2d.SLPIC2D_WARM_UNET_DELTA, nets["delta"]),)
     clocks = ClockSampler(0)
     clocks.start()
     res = {}
@@ -1040,7 +1056,8 @@ def run_unet2d(args):
         "cg_iterations_saved_vs_zero": 1 - best["cg_iterations_per_step"] / res["zero"]["cg_iterations_per_step"],
         "cg_iterations_saved_vs_prev": 1 - best["cg_iterations_per_step"] / res["prev"]["cg_iterations_per_step"],
         "unet": {"forward_ms": fwd_ms, "forward_tflops": fwd_tflops, "training": train_info,
-                 "pair_collection_s": collect_s},
+                 "pair_collection_s": collect_s, "networks": sorted(nets),
+                 "pairs": args.unet_pairs},
         "roofline": {"bound": bound, "achieved": fwd_tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": fwd_tflops / peak, "traffic": None, "kernel": kern,
                      "peak_source": peak_src},

@@ -324,8 +324,11 @@ int slpic_kernels_per_step(slpic_t *h, int *n);
  * few steps to capture the graphs and then steps_per_trial steps (rounded up to
  * whole intervals) timed with CUDA events on the handle's stream, and keeps the
  * fastest.  The trials are real steps: the simulation advances by all of them.
- * An interval is tried only if the free capacity exceeds twice the holes and
- * source particles it may gather, so a trial never truncates the source.
+ * An interval of v steps is tried only if the free slots of every species exceed
+ * 4 v (2 r + 64), r the larger of its mean source rate per step since the start and
+ * its rate over the tuner's first trial (a loss-matched source can still be growing):
+ * eight times the holes and source particles the interval may gather.  A source that
+ * later grows past that is truncated and reported (SLPIC_ERR_CAPACITY).
  * *chosen (may be NULL) receives the settings kept, *ms_per_step (may be NULL)
  * their time per step.  Synchronises. */
 typedef struct {

@@ -307,7 +307,7 @@ extern "C" int slpic_create(const slpic_config *cfg, slpic_t **out)
         // the particle kernel's E and deposit, plus its static shared memory; the field
         // kernel's deposits and prefixes per cluster CTA, plus its static shared memory
         if (particle_kernel_smem_bytes(nn_) + 1024 > (size_t)max_smem ||
-            field_cluster_smem_bytes(nn_, kMaxSpecies) + 4096 > (size_t)max_smem ||
+            field_cluster_smem_bytes(nn_, kMaxSpecies, kFieldClusterCtas) + 4096 > (size_t)max_smem ||
             nn_ > field_max_nodes()) {
             g_create_err = "grid does not fit in shared memory (n_cells too large for the 1D kernel)";
             return SLPIC_ERR_INVALID;
@@ -1551,11 +1551,40 @@ extern "C" int slpic_set_tuning(slpic_t *h, const slpic_tuning *t)
 // a step adds the source's particles (twice the mean rate so far, plus a margin),
 // and holes stay until the next compacting step, so an interval of `every` steps
 // is safe while this is well above `every`.
-static int slots_headroom(slpic_t *h, long long *ratio)
+// Per member and species, the injected total and step index at a point of the run, so
+// that the rate of the steps since then can be taken (slots_headroom).
+struct InjectionMark {
+    std::vector<std::vector<long long>> injected;  // [member][species]
+    std::vector<long long> step;                   // [member]
+};
+
+static int mark_injection(slpic_t *h, InjectionMark *mk)
+{
+    std::vector<slpic_t *> sims = is_batch(h) ? h->members : std::vector<slpic_t *>{h};
+    mk->injected.assign(sims.size(), {});
+    mk->step.assign(sims.size(), 0);
+    for (size_t i = 0; i < sims.size(); ++i) {
+        DevState a;
+        int rc = read_state(sims[i], &a);
+        if (rc)
+            return rc;
+        mk->step[i] = sims[i]->step;
+        for (int s = 0; s < sims[i]->ns; ++s)
+            mk->injected[i].push_back(a.injected_total[s]);
+    }
+    return SLPIC_OK;
+}
+
+// How many steps of source injection the slots left free can take, at the worst of each
+// species' mean rate since the start and its rate since `mk` (a sheath's losses, and so
+// a loss-matched source, can still be growing), over every member: an interval of v
+// in-place steps between compactions leaves holes of up to v steps' worth of particles.
+static int slots_headroom(slpic_t *h, const InjectionMark &mk, long long *ratio)
 {
     std::vector<slpic_t *> sims = is_batch(h) ? h->members : std::vector<slpic_t *>{h};
     long long best = 1LL << 40;
-    for (slpic_t *m : sims) {
+    for (size_t i = 0; i < sims.size(); ++i) {
+        slpic_t *m = sims[i];
         DevState a;
         int rc = read_state(m, &a);
         if (rc)
@@ -1564,7 +1593,10 @@ static int slots_headroom(slpic_t *h, long long *ratio)
         for (int s = 0; s < m->ns; ++s) {
             const long long used = (long long)a.count[s][P];
             const long long cap = m->cfg.species[s].capacity;
-            const long long inj = m->step > 0 ? a.injected_total[s] / std::max(1LL, m->step) : 0;
+            long long inj = m->step > 0 ? a.injected_total[s] / std::max(1LL, m->step) : 0;
+            const long long dn = m->step - mk.step[i];
+            if (dn > 0 && s < (int)mk.injected[i].size())
+                inj = std::max(inj, (a.injected_total[s] - mk.injected[i][s] + dn - 1) / dn);
             best = std::min(best, (cap - used) / (2 * inj + 64));
         }
     }
@@ -1618,7 +1650,8 @@ extern "C" int slpic_autotune(slpic_t *h, int32_t steps_per_trial, slpic_tuning 
     slpic_tuning best{};
     slpic_get_tuning(h, &best);
     double best_ms = 0.0;
-    if ((rc = trial(best, &best_ms)))
+    InjectionMark mark;
+    if ((rc = mark_injection(h, &mark)) || (rc = trial(best, &best_ms)))
         return rc;
     // coordinate search: each setting in turn over its candidates, the others held
     // at their best so far
@@ -1646,9 +1679,9 @@ extern "C" int slpic_autotune(slpic_t *h, int32_t steps_per_trial, slpic_tuning 
                 continue;  // measured already
             if (which == kEvery) {
                 long long ratio = 0;
-                if ((rc = slots_headroom(h, &ratio)))
+                if ((rc = slots_headroom(h, mark, &ratio)))
                     return rc;
-                if (ratio < 2LL * v)
+                if (ratio < 4LL * v)
                     continue;  // its holes might not fit: never risk a truncated source
             }
             double ms = 0.0;

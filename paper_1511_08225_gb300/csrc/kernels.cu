@@ -1216,6 +1216,8 @@ __device__ __forceinline__ double u128_to_double(u128 v)
     return d;
 }
 
+// kC: the CTAs of the cluster
+template <int kC>
 __device__ __forceinline__ void field_body(const StepParams &p, int mode)
 {
     namespace cg = cooperative_groups;
@@ -1236,7 +1238,7 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     const int N = p.n_cells, nn = p.nn, ns = p.ns;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // this CTA's nodes [c0, c1); the thread's chunk of them
-    const int per_cta = (nn + kFC - 1) / kFC;
+    const int per_cta = (nn + kC - 1) / kC;
     const int c0 = min(nn, rank * per_cta), c1 = min(nn, c0 + per_cta);
     const int chunk = (per_cta + kFCT - 1) / kFCT;
     const int j0 = min(c1, c0 + (int)threadIdx.x * chunk), j1 = min(c1, j0 + chunk);
@@ -1273,7 +1275,7 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     if (mode >= 1) {
         // ---- source injection (Sec. IV; LOSS_MATCHED / RATE readings).  Every CTA
         // derives the same counts from the same state (thread s for species s) and
-        // makes every kFC-th particle; CTA 0 writes the bookkeeping after the
+        // makes every kC-th particle; CTA 0 writes the bookkeeping after the
         // exchange below, when every CTA has read the state.
         const int s = threadIdx.x;
         if (s < ns) {
@@ -1313,7 +1315,7 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
                 kk[sp_] = k < 0 ? -k - 1 : k;
                 bb[sp_] = sp_ < ns ? s_base[sp_] : 0;
             }
-            inject_all(p, step, bb, kk, Q, rank, kFC);
+            inject_all(p, step, bb, kk, Q, rank, kC);
         }
         // every CTA's source deposits are in acc before any CTA reads acc
         __threadfence();
@@ -1395,9 +1397,9 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     // thread; then thread (s, q) sums quantity q of species s over the cluster and
     // converts it (and, for R, the CTAs before this one), and one thread forms the
     // step's scalars
-    __shared__ u128 s_all[kMaxSpecies][kFC][3];
-    if (threadIdx.x < ns * kFC * 3) {
-        const int s = threadIdx.x / (kFC * 3), r = (threadIdx.x / 3) % kFC, q = threadIdx.x % 3;
+    __shared__ u128 s_all[kMaxSpecies][kC][3];
+    if (threadIdx.x < ns * kC * 3) {
+        const int s = threadIdx.x / (kC * 3), r = (threadIdx.x / 3) % kC, q = threadIdx.x % 3;
         s_all[s][r][q] = *cl.map_shared_rank(&s_tot[s][q], r);
     }
     // this CTA's reads of the others' shared memory are done; the matching wait
@@ -1407,7 +1409,7 @@ __device__ __forceinline__ void field_body(const StepParams &p, int mode)
     if (threadIdx.x < ns * 3) {
         const int s = threadIdx.x / 3, q = threadIdx.x % 3;
         u128 tot = 0, off = 0;
-        for (int r = 0; r < kFC; ++r) {
+        for (int r = 0; r < kC; ++r) {
             tot += s_all[s][r][q];
             if (r < rank)
                 off += s_all[s][r][q];
@@ -1519,7 +1521,18 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
     k_field(const __grid_constant__ StepParams p, int mode)
 {
     span_enter(p.st, 2);
-    field_body(p, mode);
+    field_body<kFieldClusterCtas>(p, mode);
+    span_exit(p.st, 2);
+}
+
+// the same on a cluster of kFieldClusterCtasWide CTAs (a non-portable cluster size, used
+// where the GPU can schedule it): half the nodes, and half the FP64 work, per SM
+__global__ void __cluster_dims__(kFieldClusterCtasWide, 1, 1)
+    __launch_bounds__(kFieldClusterThreads, 1) k_field_wide(const __grid_constant__ StepParams p,
+                                                            int mode)
+{
+    span_enter(p.st, 2);
+    field_body<kFieldClusterCtasWide>(p, mode);
     span_exit(p.st, 2);
 }
 
@@ -1529,7 +1542,7 @@ __global__ void __cluster_dims__(kFieldClusterCtas, 1, 1) __launch_bounds__(kFie
 {
     __shared__ StepParams s_p;
     load_params(s_p, ps + blockIdx.x / kFC);
-    field_body(s_p, mode);
+    field_body<kFieldClusterCtas>(s_p, mode);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1625,6 +1638,10 @@ size_t particle_smem_bytes(int nn) { return (size_t)nn * (sizeof(unsigned long l
 size_t field_smem_bytes(int nn) { return (size_t)nn * sizeof(double); }
 int field_max_nodes() { return 1 << 16; }
 
+// k_field_wide where a cluster of its size fits on this GPU (set by configure_kernels),
+// else k_field
+static bool g_field_wide = false;
+
 cudaError_t configure_kernels(int nn)
 {
     // the attributes only ever grow: simulations of several sizes share the kernels
@@ -1652,9 +1669,27 @@ cudaError_t configure_kernels(int nn)
     if (e != cudaSuccess)
         return e;
     e = cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)field_cluster_smem_bytes(nn, kMaxSpecies));
+                             (int)field_cluster_smem_bytes(nn, kMaxSpecies, kFC));
     if (e != cudaSuccess)
         return e;
+    // the wide field kernel if a cluster of its size can be resident here (else the
+    // portable 8-CTA kernel; a refusal is not an error)
+    {
+        const size_t wsmem = field_cluster_smem_bytes(nn, kMaxSpecies, kFieldClusterCtasWide);
+        int nclusters = 0;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kFieldClusterCtasWide, 1, 1);
+        cfg.blockDim = dim3(kFCT, 1, 1);
+        cfg.dynamicSmemBytes = wsmem;
+        g_field_wide =
+            cudaFuncSetAttribute(k_field_wide, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_field_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wsmem) == cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&nclusters, k_field_wide, &cfg) == cudaSuccess &&
+            nclusters >= 1;
+        cudaGetLastError();
+    }
     return cudaFuncSetAttribute(k_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)field_smem_bytes(nn));
 }
@@ -1734,7 +1769,7 @@ void launch_hard_batch(const StepParams *d_params, int m, int ctas_per_instance,
 void launch_field_batch(const StepParams *d_params, int m, int max_nn, int max_ns, int mode,
                         cudaStream_t st)
 {
-    k_field_batch<<<m * kFC, kFCT, field_cluster_smem_bytes(max_nn, max_ns), st>>>(d_params, mode);
+    k_field_batch<<<m * kFC, kFCT, field_cluster_smem_bytes(max_nn, max_ns, kFC), st>>>(d_params, mode);
 }
 
 cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compact_per_sm)
@@ -1747,7 +1782,7 @@ cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compac
                                  (int)particle_kernel_smem_bytes(max_nn));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_field_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)field_cluster_smem_bytes(max_nn, kMaxSpecies));
+                                 (int)field_cluster_smem_bytes(max_nn, kMaxSpecies, kFC));
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(inplace_per_sm, k_particles_batch, kPB,
                                                           particle_inplace_smem_bytes(max_nn));
@@ -1757,14 +1792,18 @@ cudaError_t configure_batch_kernels(int max_nn, int *inplace_per_sm, int *compac
     return e;
 }
 
-size_t field_cluster_smem_bytes(int nn, int ns)
+size_t field_cluster_smem_bytes(int nn, int ns, int ctas)
 {
-    return (size_t)ns * ((nn + kFC - 1) / kFC) * sizeof(unsigned long long);
+    return (size_t)ns * ((nn + ctas - 1) / ctas) * sizeof(unsigned long long);
 }
 
 void launch_field(const StepParams &p, int mode, cudaStream_t st)
 {
-    k_field<<<kFC, kFCT, field_cluster_smem_bytes(p.nn, p.ns), st>>>(p, mode);
+    if (g_field_wide)
+        k_field_wide<<<kFieldClusterCtasWide, kFCT,
+                       field_cluster_smem_bytes(p.nn, p.ns, kFieldClusterCtasWide), st>>>(p, mode);
+    else
+        k_field<<<kFC, kFCT, field_cluster_smem_bytes(p.nn, p.ns, kFC), st>>>(p, mode);
 }
 
 // the latest deposit ([species][nn]) and E copied for a read-back that runs beside

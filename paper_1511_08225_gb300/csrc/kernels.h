@@ -12,6 +12,7 @@ namespace slpic {
 constexpr int kParticleThreads = 256;
 constexpr int kFieldThreads = 1024;        // k_potential (one CTA)
 constexpr int kFieldClusterCtas = 8;       // k_field: one cluster of 8 CTAs
+constexpr int kFieldClusterCtasWide = 16;  // k_field_wide: 16 (non-portable cluster size)
 constexpr int kFieldClusterThreads = 256;
 
 size_t particle_smem_bytes(int nn);         // E + one int64 per node (allocation-free kernel)
@@ -19,7 +20,7 @@ size_t particle_kernel_smem_bytes(int nn);  // k_particles_compact: E + split de
 size_t particle_inplace_smem_bytes(int nn); // k_particles: E + split deposit
 constexpr int kCompactEvery = 16;           // one compacting particle step per this many
 size_t field_smem_bytes(int nn);
-size_t field_cluster_smem_bytes(int nn, int ns);
+size_t field_cluster_smem_bytes(int nn, int ns, int ctas);
 int field_max_nodes();
 cudaError_t configure_kernels(int nn);
 cudaError_t particle_ctas_per_sm(int nn, int *inplace, int *compacting);

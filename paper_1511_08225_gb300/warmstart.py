@@ -73,6 +73,33 @@ def collect_pairs(prob: dict, seeds, pairs_per_seed: int, every: int, skip: int,
     return out
 
 
+def collect_delta_images(prob: dict, seed: int, n_pairs: int, every: int, skip: int):
+    """delta_images of collect_pairs(prob, (seed,), n_pairs, every, skip,
+    keep_prev=True), made pair by pair into float32 device tensors (N, ny, nx), so
+    that a large set (10k pairs of a 1024 x 1024 grid: 80 GB) never sits in host
+    memory.  Returns (x, t)."""
+    import torch
+
+    ny, nx = int(prob["ny"]), int(prob["nx"])
+    x = torch.empty((n_pairs, ny, nx), dtype=torch.float32, device="cuda")
+    t = torch.empty_like(x)
+    p = dict(prob, seed=int(seed))
+    sim = binding2d.Simulation2D(p)
+    sim.load_state(inputs.load_state2d(p, seed=int(seed)))
+    sim.prepare()
+    sim.step(skip)
+    for i in range(n_pairs):
+        if every > 1:
+            sim.step(every - 1)
+        r0, f0, _, _ = sim.fields()
+        sim.step(1)
+        r, f, _, _ = sim.fields()
+        x[i].copy_(torch.from_numpy(rho_image(r - r0)))
+        t[i].copy_(torch.from_numpy(phi_image(f - f0)))
+    sim.close()
+    return x, t
+
+
 def images(pairs: dict, phi_lo: float = 0.0, phi_hi: float = 0.0):
     """(x, t): the network's input and target images, (N, ny, nx) FP32."""
     x = np.stack([rho_image(r) for r in pairs["rho"]])
