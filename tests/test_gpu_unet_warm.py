@@ -138,3 +138,18 @@ def test_warm_start_rejects_a_network_of_the_wrong_grid():
     g.set_warm_start(binding2d.SLPIC2D_WARM_ZERO)
     net.close()
     g.close()
+
+
+def test_device_made_change_images_equal_the_host_made_ones():
+    """collect_delta_images (pairs made one by one into device tensors, for sets too
+    large for host memory) gives exactly delta_images of collect_pairs with keep_prev
+    on the same run."""
+    import torch
+    prob = inputs.plasma2d_problem(nx=64, ny=32, ppc=8, v0=0.2, solver="fft")
+    pairs = warmstart.collect_pairs(prob, seeds=(7,), pairs_per_seed=5, every=2, skip=3,
+                                    keep_prev=True)
+    x_h, t_h = warmstart.delta_images(pairs)
+    x_d, t_d = warmstart.collect_delta_images(prob, 7, 5, every=2, skip=3)
+    torch.cuda.synchronize()
+    assert x_d.dtype == torch.float32 and tuple(x_d.shape) == x_h.shape
+    assert np.array_equal(x_d.cpu().numpy(), x_h) and np.array_equal(t_d.cpu().numpy(), t_h)
