@@ -477,7 +477,8 @@ __device__ __forceinline__ void consumers_sync()
 
 size_t particle_tma_smem_bytes(int nn, int stages)
 {
-    return (size_t)16 * stages + (size_t)stages * kTmaTile * 20 + (size_t)nn * 3 * sizeof(unsigned);
+    // the ring, the histogram's two words, E and the speed-limit profile per node
+    return (size_t)16 * stages + (size_t)stages * kTmaTile * 20 + (size_t)nn * 4 * sizeof(unsigned);
 }
 
 // tiles [t0, t1) of species s for CTA `cta` of `nctas`
@@ -497,8 +498,9 @@ __device__ __forceinline__ void tma_species(const StepParams &p, int s, int P, i
                                             unsigned &ph, int stages, uint64_t *full,
                                             uint64_t *empty,
                                             const float4 *s_v, const int32_t *s_c,
-                                            const float *s_E, DepositSplit32 &dep,
-                                            volatile int *fail, unsigned &nabs0, unsigned &nabs1)
+                                            const float *s_E, const float *s_lam,
+                                            DepositSplit32 &dep, volatile int *fail,
+                                            unsigned &nabs0, unsigned &nabs1)
 {
     const SpeciesDev &sp = p.sp[s];
     const int lane = threadIdx.x & 31;
@@ -539,13 +541,13 @@ __device__ __forceinline__ void tma_species(const StepParams &p, int s, int P, i
                     __stcs(cout + i, -1);  // a hole stays a hole
                 } else {
                     float ax = gather_ax<kPer>(p, sp, s_E, c[m], q[m].x);
-                    const float v0n = v0_at<kProf>(p, sp, c[m]);
+                    const float v0n = v0_at<kProf>(p, sp, c[m], s_lam);
                     float vx;
                     const int kind = kKind == kAny ? sp.kind : kKind;
                     if (push_vx_easy(kind, q[m].y, q[m].z, q[m].w, ax, p.dt, v0n, vx)) {
                         int wall = 0;
                         if (move_and_deposit<kProf, kKind, kPer>(p, sp, dep, c[m], q[m], vx, wall,
-                                                                v0n)) {
+                                                                v0n, s_lam)) {
                             __stcs(cout + i, c[m]);
                             __stcs(vout + i, q[m]);
                         } else {
@@ -584,6 +586,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
     unsigned *s_lo = reinterpret_cast<unsigned *>(s_c + (size_t)stages * kTmaTile);
     unsigned *s_hi = s_lo + p.nn;
     float *s_E = reinterpret_cast<float *>(s_hi + p.nn);
+    float *s_lam = s_E + p.nn;  // the speed-limit profile (kProf)
     __shared__ unsigned s_abs[2];
     __shared__ int s_fail;
 
@@ -604,8 +607,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
     span_enter(p.st, 0);
     const long long step = *(volatile long long *)&p.st->step;
     const int P = (int)(step & 1);
-    for (int j = threadIdx.x; j < p.nn; j += kTmaThreads)
+    for (int j = threadIdx.x; j < p.nn; j += kTmaThreads) {
         s_E[j] = p.E[j];
+        if (kProf)
+            s_lam[j] = __ldg(p.lam + j);
+    }
     __syncthreads();
     volatile int *fail = &s_fail;
 
@@ -653,10 +659,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
             // time (the same arithmetic either way)
             if (sp.kind == SLPIC_BETA_HEAVISIDE && !p.periodic)
                 tma_species<kProf, SLPIC_BETA_HEAVISIDE, 0>(p, s, P, st, ph, stages, full, empty,
-                                                           s_v, s_c, s_E, dep, fail, nabs0, nabs1);
+                                                           s_v, s_c, s_E, s_lam, dep, fail, nabs0,
+                                                           nabs1);
             else
                 tma_species<kProf, kAny, kAny>(p, s, P, st, ph, stages, full, empty, s_v, s_c,
-                                               s_E, dep, fail, nabs0, nabs1);
+                                               s_E, s_lam, dep, fail, nabs0, nabs1);
             // species done: absorbed counts, histogram flush and clear
             const unsigned a0 = __reduce_add_sync(0xffffffffu, nabs0);
             const unsigned a1 = __reduce_add_sync(0xffffffffu, nabs1);

@@ -38,13 +38,15 @@ __device__ __forceinline__ float gather_ax(const StepParams &p, const SpeciesDev
 
 // The speed limit of species sp in cell c (Sec. II: v0 may vary with position).
 // kProf: a per-cell profile is set (p.lam), and the limit is the FP32 product
-// v0 * lam[c] rounded to nearest; otherwise the species' uniform v0.
+// v0 * lam[c] rounded to nearest; otherwise the species' uniform v0.  lam: a copy of
+// the profile (in shared memory) to read instead of p.lam, or null.
 template <bool kProf>
-__device__ __forceinline__ float v0_at(const StepParams &p, const SpeciesDev &sp, int c)
+__device__ __forceinline__ float v0_at(const StepParams &p, const SpeciesDev &sp, int c,
+                                       const float *lam = nullptr)
 {
     if (!kProf)
         return sp.v0;
-    return __fmul_rn(sp.v0, __ldg(p.lam + c));
+    return __fmul_rn(sp.v0, lam ? lam[c] : __ldg(p.lam + c));
 }
 
 // The same where a kernel serves both cases at run time (p.lam may be null).
@@ -62,7 +64,7 @@ __device__ __forceinline__ float v0_cell(const StepParams &p, const SpeciesDev &
 template <bool kProf = false, int kKind = kAny, int kPer = kAny, typename Dep>
 __device__ __forceinline__ bool move_and_deposit(const StepParams &p, const SpeciesDev &sp,
                                                  Dep &dep, int &c, float4 &q, float vx, int &wall,
-                                                 float v0n)
+                                                 float v0n, const float *lam = nullptr)
 {
     const int N = p.n_cells;
     const int kind = kKind == kAny ? sp.kind : kKind;
@@ -91,7 +93,7 @@ __device__ __forceinline__ bool move_and_deposit(const StepParams &p, const Spec
     if (periodic && cn1 == N)
         cn1 = 0;
     if (kProf && cn != c)
-        b = beta_q(kind, vx, q.z, q.w, v0_at<true>(p, sp, cn));
+        b = beta_q(kind, vx, q.z, q.w, v0_at<true>(p, sp, cn, lam));
     dep(cn, cn1, b, dn);
     c = cn;
     q.x = dn;
