@@ -2,14 +2,15 @@
 //
 // Per step (Appendix A, Eq. slpicIntegration, on an nx x ny grid, periodic in x,
 // absorbing plates in y):
-//   k_particles2d_tiles (in-place steps) / k_particles2d (every kCompact2d-th step)
+//   k_particles2d_tiles (+ k_hard2d), or k_particles2d where its windows do not fit
 //                  gather E (bilinear) -> push v (the same speed-limited solve as
 //                  1D, along the direction of a) -> move -> plates/wrap -> deposit
 //                  rho^{n+1} (quantised int64, bilinear) into the nodal arrays: the
 //                  tile kernel through windows of the grid in shared memory, listing
 //                  the pushes that need the piece walk for k_hard2d; the other by
-//                  global atomics, writing the survivors packed.  Absorbed particles
-//                  leave holes (cell = -1) in place.
+//                  global atomics.  Absorbed particles leave holes (cell = -1) in
+//                  place; every kCompact2d-th step the counting sort by cell drops
+//                  them (k_particles2d packs the survivors itself on that step).
 //   k_inject2d     source particles appended and deposited; k_book2d the bookkeeping.
 //   k_cg2d         cooperative kernel: b from the deposits, Jacobi-PCG on the
 //                  5-point system (FP64 vectors, FP64 dot products in a fixed
@@ -2250,7 +2251,11 @@ extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
     long long step = st.step;
     Params2D &p = h->p;
     for (int64_t k = 0; k < nsteps; ++k, ++step) {
-        const bool compact = (step % kCompact2d) == kCompact2d - 1;
+        // every kCompact2d-th step the particles are sorted by cell again; with the tile
+        // kernel that step is in place too (the sort drops the holes), else the global
+        // kernel packs the survivors first
+        const bool sort = (step % kCompact2d) == kCompact2d - 1;
+        const bool compact = sort && !h->tile_ctas;
         cudaEvent_t *ev = nullptr;
         if (h->timing && h->t_steps < kMaxTimedSteps2d) {
             while ((long long)h->events.size() < 4 * (h->t_steps + 1)) {
@@ -2275,8 +2280,8 @@ extern "C" int slpic2d_step(slpic2d_t *h, int64_t nsteps)
         k_inject2d<<<h->small_ctas, 256, 0, h->stream>>>(p, compact ? 1 : 0);
         k_book2d<<<1, 32, 0, h->stream>>>(p, compact ? 1 : 0);
         CK2(h, cudaGetLastError());
-        // after the compacting step (holes dropped, sources appended): particles by cell
-        if (compact && (rc = sort_particles(h, (int)((step + 1) & 1))))
+        // particles by cell (sources appended; holes dropped)
+        if (sort && (rc = sort_particles(h, (int)((step + 1) & 1))))
             return rc;
         if (ev)
             CK2(h, cudaEventRecord(ev[2], h->stream));
