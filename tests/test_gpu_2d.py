@@ -412,3 +412,30 @@ def test_tile_windows_over_in_place_steps_match_per_particle_deposit():
     d = g.diagnostics()
     assert sum(d["absorbed"][0]) > 0
     g.close()
+
+
+def test_2d_empty_species_and_a_single_particle():
+    """Edge cases of the tile kernel and the sort: no electrons at all, and a single ion
+    (one ragged chunk of one slot, its window a single cell's box), stepped across the
+    sort step with the direct solver: the potential each step leaves is the direct solve
+    of the charge recomputed from the particles, the counts are consistent and the ion
+    stays the one particle."""
+    prob = _prob(nx=32, ny=24, ppc=1, v0=0.3, dt=1.5)
+    prob["solver"] = "fft"
+    g = binding2d.Simulation2D(prob)
+    g.load(0, np.zeros(0, np.int32), np.zeros((0, 2), np.float32), np.zeros((0, 3), np.float32))
+    g.load(1, np.array([12 * 32 + 7], np.int32), np.array([[0.25, 0.5]], np.float32),
+           np.array([[0.01, -0.02, 0.005]], np.float32))
+    g.prepare()
+    for n in (1, 15, 2):  # steps 1, 16 (the 16th sorts), 18
+        g.step(n)
+        rho, phi, _, _ = g.fields()
+        ref = orc.poisson2d_direct(rho, prob["dx"], prob["phi_lo"], prob["phi_hi"])
+        assert np.abs(phi - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max()), n
+        d = g.diagnostics()
+        assert d["count"][0] == 0
+        c, o, v = g.particles(1)
+        live = c >= 0
+        assert live.sum() + sum(d["absorbed"][1]) == 1
+        assert d["count"][1] == live.sum()
+    g.close()
