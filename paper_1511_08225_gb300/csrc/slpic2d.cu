@@ -161,16 +161,22 @@ __device__ __forceinline__ bool push_v2_impl(int kind, float ux, float uy, float
         vy = __fadd_rn(uy, __fmul_rn(ay, dt));
         return true;
     }
-    const float A = __fsqrt_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)));
-    if (A == 0.0f) {
+    // |a|, the direction of a and |v_perp| from reciprocal square roots (within a few
+    // ulp; the push's bar is 1e-5 of |v|): one approximation instead of a correctly
+    // rounded square root and two divisions
+    const float a2 = __fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay));
+    if (a2 == 0.0f) {
         vx = ux;
         vy = uy;
         return true;
     }
-    const float hx = __fdiv_rn(ax, A), hy = __fdiv_rn(ay, A);
+    const float ra = rsqrtf(a2);
+    const float A = __fmul_rn(a2, ra);
+    const float hx = __fmul_rn(ax, ra), hy = __fmul_rn(ay, ra);
     const float wa = __fadd_rn(__fmul_rn(ux, hx), __fmul_rn(uy, hy));
     const float cr = __fsub_rn(__fmul_rn(ux, hy), __fmul_rn(uy, hx));
-    const float vp = __fsqrt_rn(__fadd_rn(__fmul_rn(cr, cr), __fmul_rn(uz, uz)));
+    const float vp2 = __fadd_rn(__fmul_rn(cr, cr), __fmul_rn(uz, uz));
+    const float vp = vp2 > 0.0f ? __fmul_rn(vp2, rsqrtf(vp2)) : 0.0f;
     float we;
     if (kEasy) {
         if (!push_vx_easy(kind, wa, vp, 0.0f, A, dt, v0, we))
