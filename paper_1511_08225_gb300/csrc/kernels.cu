@@ -481,12 +481,14 @@ size_t particle_tma_smem_bytes(int nn, int stages)
     return (size_t)16 * stages + (size_t)stages * kTmaTile * 20 + (size_t)nn * 4 * sizeof(unsigned);
 }
 
-// tiles [t0, t1) of species s for CTA `cta` of `nctas`
-__device__ __forceinline__ void tma_share(long long n, int cta, int nctas, long long &t0, long long &t1)
+// slots [r0, r1) of a species of n particles for CTA `cta` of `nctas`: equal shares to
+// within 4 slots (a multiple of 4 at every boundary, so that each tile's cells start on
+// a 16-byte boundary), walked in tiles of kTmaTile from r0 (the last one partial).  A
+// share of whole tiles would leave some CTAs a tile more than others.
+__device__ __forceinline__ void tma_share(long long n, int cta, int nctas, long long &r0, long long &r1)
 {
-    const long long nt = (n + kTmaTile - 1) / kTmaTile;
-    t0 = nt * cta / nctas;
-    t1 = nt * (cta + 1) / nctas;
+    r0 = (n * cta / nctas) & ~3LL;
+    r1 = cta + 1 == nctas ? n : (n * (cta + 1) / nctas) & ~3LL;
 }
 
 // One species' share of the in-place TMA step, for a consumer thread: its tiles from
@@ -508,12 +510,11 @@ __device__ __forceinline__ void tma_species(const StepParams &p, int s, int P, i
     const int32_t *__restrict__ cin = sp.cell[P];
     int32_t *__restrict__ cout = sp.cell[P ^ 1];
     float4 *__restrict__ vout = sp.pv[P ^ 1];
-    long long t0, t1;
-    tma_share(n, blockIdx.x, gridDim.x, t0, t1);
-    for (long long t = t0; t < t1; ++t) {
+    long long r0, r1;
+    tma_share(n, blockIdx.x, gridDim.x, r0, r1);
+    for (long long i0 = r0; i0 < r1; i0 += kTmaTile) {
         const bool ok = !*fail && mbar_wait(&full[st], ph, fail, &p.st->error, p.wait_cycles);
-        const long long i0 = t * kTmaTile;
-        const int cnt = (int)min((long long)kTmaTile, n - i0);
+        const int cnt = (int)min((long long)kTmaTile, r1 - i0);
         const int cb = cnt & ~3;
         int c[kTmaPer];
         float4 q[kTmaPer];
@@ -622,16 +623,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_particles_tma(const __grid_c
             for (int s = 0; s < p.ns && !*fail; ++s) {
                 const SpeciesDev &sp = p.sp[s];
                 const long long n = (long long)*(volatile unsigned long long *)&p.st->count[s][P];
-                long long t0, t1;
-                tma_share(n, blockIdx.x, gridDim.x, t0, t1);
-                for (long long t = t0; t < t1; ++t, ++k) {
+                long long r0, r1;
+                tma_share(n, blockIdx.x, gridDim.x, r0, r1);
+                for (long long i0 = r0; i0 < r1; i0 += kTmaTile, ++k) {
                     const int st = (int)(k % stages);
                     const unsigned ph = (unsigned)((k / stages) & 1);
                     if (k >= stages &&
                         !mbar_wait(&empty[st], ph ^ 1u, fail, &p.st->error, p.wait_cycles))
                         break;
-                    const long long i0 = t * kTmaTile;
-                    const int cnt = (int)min((long long)kTmaTile, n - i0);
+                    const int cnt = (int)min((long long)kTmaTile, r1 - i0);
                     const int cb = cnt & ~3;  // cells by bulk copy (16-byte multiple)
                     mbar_expect_tx(&full[st], (unsigned)(cnt * 16 + cb * 4));
                     bulk_load(s_v + (size_t)st * kTmaTile, sp.pv[P] + i0, (unsigned)cnt * 16, &full[st]);

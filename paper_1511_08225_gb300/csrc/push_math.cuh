@@ -14,7 +14,7 @@
 //     F(w) = (w sqrt(w^2+D') + D' asinh(w / sqrt(D'))) / 2.
 //
 // Most particles need no iteration (push_vx_easy): plain leapfrog inside the
-// band, or the 8th-order series reversion of (*) when the step is small
+// band, or the 6th-order series reversion of (*) when the step is small
 // against the speed.  The rest walk the pieces the line crosses (fast w < 0,
 // slow band, fast w > 0), spending the budget |a| dt of (*), and solve the
 // last piece for w_end (push_vx_walk): by the series, or by Newton from a
@@ -126,9 +126,13 @@ __device__ __forceinline__ float seg_integral(float wa, float ra, float d, float
 
 // Series reversion of int_{wa}^{wa+d} sqrt(w^2 + D) dw = y about wa.  With
 // ra = sqrt(wa^2 + D), om = wa/ra and k = y/ra^2 (so D/ra^2 = 1 - om^2),
-//   d / ra = k (1 + b2 k + b3 k^2 + ... + b8 k^7) + O(k^9),
-// the b_i below (derived symbolically; b2..b4 by hand).  The truncation error is
-// below 6 k^9 ra for every om in [-1, 1], i.e. < 3e-8 ra for k <= 0.12.  The
+//   d / ra = k (1 + b2 k + b3 k^2 + ... + b6 k^5) + O(k^7),
+// the b_i below (derived symbolically; b2..b4 by hand).  Against the exact root
+// (40-digit arithmetic, om in [-1, 1]) the truncation error is below 9.2e-7 ra at
+// k = 0.12 and falls as k^7: a tenth of the push's 1e-5 |v| bar at the largest k,
+// and about 2e-21 ra at the median k of the sheath's particles (about 1e-3).  The
+// terms b7, b8 would take it to 3.6e-8 ra for eight more fused multiply-adds per
+// particle, on the path nearly every particle takes.  The
 // integrand is analytic within |w - wa| < ra, so the series holds across w = 0
 // when D > 0; it must not be used across the Heaviside band edge.
 constexpr float kSeriesMax = 0.12f;
@@ -138,23 +142,16 @@ __device__ __forceinline__ float series_poly(float om, float k)
     // b_n is even in om for odd n and om times an even polynomial for even n, so the
     // sum splits into two polynomials in k^2 whose coefficients are polynomials in
     // om^2 (the divisors folded into them):
-    //   1 + b3 k^2 + b5 k^4 + b7 k^6  +  om k (d2 + d4 k^2 + d6 k^4 + d8 k^6),  b_n = om d_n.
+    //   1 + b3 k^2 + b5 k^4  +  om k (d2 + d4 k^2 + d6 k^4),  b_n = om d_n.
     // Explicit fused multiply-adds: every kernel that inlines this gets the same bits.
     const float o2 = __fmul_rn(om, om);
     const float k2 = __fmul_rn(k, k);
     const float b3 = __fmaf_rn(4.0f / 6.0f, o2, -1.0f / 6.0f);
     const float b5 = __fmaf_rn(__fmaf_rn(280.0f / 120.0f, o2, -188.0f / 120.0f), o2, 13.0f / 120.0f);
-    const float b7 = __fmaf_rn(__fmaf_rn(__fmaf_rn(58240.0f / 5040.0f, o2, -62832.0f / 5040.0f), o2,
-                                         15480.0f / 5040.0f),
-                               o2, -493.0f / 5040.0f);
     const float d4 = __fmaf_rn(-28.0f / 24.0f, o2, 13.0f / 24.0f);
     const float d6 = __fmaf_rn(__fmaf_rn(-3640.0f / 720.0f, o2, 3188.0f / 720.0f), o2, -493.0f / 720.0f);
-    const float d8 =
-        __fmaf_rn(__fmaf_rn(__fmaf_rn(-1106560.0f / 40320.0f, o2, 1417584.0f / 40320.0f), o2,
-                            -483528.0f / 40320.0f),
-                  o2, 37369.0f / 40320.0f);
-    const float ev = __fmaf_rn(__fmaf_rn(__fmaf_rn(b7, k2, b5), k2, b3), k2, 1.0f);
-    const float od = __fmul_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(d8, k2, d6), k2, d4), k2, -0.5f), k);
+    const float ev = __fmaf_rn(__fmaf_rn(b5, k2, b3), k2, 1.0f);
+    const float od = __fmul_rn(__fmaf_rn(__fmaf_rn(d6, k2, d4), k2, -0.5f), k);
     return __fmaf_rn(om, od, ev);
 }
 
@@ -306,8 +303,11 @@ __device__ __forceinline__ bool push_vx_easy(int kind, float ux, float uy, float
     float y = __fmul_rn(rem, v0);
     float ra2 = __fmaf_rn(wa, wa, D);
     // one reciprocal square root gives 1/ra, wa/ra and y/ra^2 (its ~2 ulp error
-    // moves d, already a small correction to wa, by ~1e-7 of itself)
-    float rs = rsqrtf(ra2);
+    // moves d, already a small correction to wa, by ~1e-7 of itself).  Here ra2 is
+    // about v0^2 or more, so the flush-to-zero form needs no subnormal fix-up; a
+    // subnormal ra2 would give an infinite or NaN kap, and the hard path.
+    float rs;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(ra2));
     float yr = __fmul_rn(y, rs);       // y / ra
     float kap = __fmul_rn(yr, rs);     // y / ra^2
     if (!(kap <= kSeriesMax))
