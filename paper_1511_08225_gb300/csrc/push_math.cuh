@@ -50,23 +50,22 @@ __device__ __forceinline__ float beta_q(int kind, float vx, float vy, float vz, 
 }
 
 // rint(x) (round to nearest, ties to even) for 0 <= x < 2^41 as two 32-bit words,
-// value = hi 2^32 + lo, with 32-bit integer operations only (a float -> int64
-// conversion would run on the FP64 pipe, which is narrow on this GPU, and a 64-bit
-// variable shift takes several instructions):
-//   x < 2^23:  x + 2^23 lies in [2^23, 2^24], where the float spacing is 1, so the
-//              sum is rounded to an integer exactly as rint rounds x, and its bits
-//              minus those of 2^23 are that integer (2^24 - 2^23 = 2^23 included);
-//   x >= 2^23: x is an integer already: its 24-bit significand shifted left by
-//              exponent - 23 (0..17), the words split off by a funnel shift.
+// value = hi 2^32 + lo, in FP32 and 32-bit operations (a float -> int64 conversion
+// would run on the FP64 pipe, which is narrow on this GPU):
+//   hf = floor(x 2^-32): the scaling by a power of two is exact, and hf is an integer
+//        below 2^9; the bits of hf + 2^23 (exact: the float spacing there is 1) minus
+//        those of 2^23 are hi;
+//   x - hf 2^32 is exact in FP32 (below 2^32 it is x; above, x and hf 2^32 are both
+//        multiples of the ulp of x and the difference is below 2^32, so it has at most
+//        24 significant bits) and lies in [0, 2^32); converted to an unsigned integer
+//        with ties to even it is lo, because rint(a + n) = rint(a) + n for an even
+//        integer n = hf 2^32.
+// Checked against llrintf for every float in [0, 2^41) on the CPU.
 __device__ __forceinline__ void rint_split(float x, unsigned &lo, unsigned &hi)
 {
-    const unsigned bits = __float_as_uint(x);
-    const bool big = x >= 8388608.0f;
-    const unsigned sh = big ? (bits >> 23) - 150u : 0u;  // exponent - 23
-    const unsigned m = (bits & 0x7FFFFFu) | 0x800000u;
-    const unsigned small = __float_as_uint(__fadd_rn(x, 8388608.0f)) - 0x4B000000u;
-    lo = big ? (m << sh) : small;
-    hi = big ? __funnelshift_l(m, 0u, sh) : 0u;
+    const float hf = floorf(__fmul_rn(x, 0x1p-32f));
+    hi = __float_as_uint(__fadd_rn(hf, 8388608.0f)) - 0x4B000000u;
+    lo = __float2uint_rn(__fmaf_rn(-hf, 4294967296.0f, x));
 }
 
 // The same value as one unsigned 64-bit integer.
