@@ -419,9 +419,8 @@ int slpic_set_speed_limit_profile(slpic_t *h, const double *lambda, int n_cells)
  * Its only scratch (four counters and the int64 accumulator) is a fixed array in
  * device memory that every GPU loading the library holds until exit; grids of
  * more than 16384 nodes return SLPIC_ERR_CAPACITY.  The first call on a device
- * looks up that array's device address (and sets the kernel's shared-memory
- * limit); make that first call, which does this set-up, before any stream
- * capture.  All calls share the array; each call clears what it uses, so calls
+ * also looks up that array's device address and sets the kernel's shared-memory
+ * limit.  All calls share the array; each call clears what it uses, so calls
  * that overlap on the GPU (concurrent streams or threads) race and must be
  * serialised by the caller.  Returns SLPIC_ERR_INVALID for bad arguments,
  * misaligned or overlapping arrays, or skipped particles, SLPIC_ERR_CFL if

@@ -7,7 +7,9 @@ It keeps its scratch in a fixed device array shared by all calls, so this test
 calls it twice in a row and checks that each call's output equals what the
 simulation handle (slpic_step, which allocates its own scratch) computes for
 the same particles and field: the deposit bit for bit (the bar of the deposit
-parity tests) and the surviving particles bit for bit.
+parity tests) and the surviving particles bit for bit.  The deposit is also held,
+bit for bit, to the oracle's quantised deposit rule applied to the survivors the
+call returns, so the check does not rest on the handle path alone.
 
 This file is collected last on purpose, and passes both alone in a fresh
 process and after the other tests.
@@ -15,6 +17,7 @@ process and after the other tests.
 import numpy as np
 import pytest
 
+from oracle import oracle as orc
 from paper_1511_08225_gb300 import binding, inputs
 
 from _match import key_of, match
@@ -94,6 +97,10 @@ def test_noalloc_step_matches_handle_step_twice(torch_cuda, periodic, kind, N):
             assert np.array_equal(charge.cpu().numpy(), acc_ref), f"call {call} species {s}"
             c2 = cout[:n_out].cpu().numpy()
             st2 = sout[:n_out].cpu().numpy()
+            sp = prob["species"][s]
+            acc_orc = orc.deposit_q40(N, periodic, c2, st2[:, 0], st2[:, 1:], sp["kind"],
+                                      np.float32(sp["v0"]))
+            assert np.array_equal(charge.cpu().numpy(), acc_orc), f"call {call} species {s}"
             ia, ib = match(key_of(st2[:, 1:]), key_of(vg))
             assert ia.size == n_out
             assert np.array_equal(c2[ia], cg[ib])
