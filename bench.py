@@ -381,6 +381,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     sim = binding.Simulation(prob)
     binding.slpic_set_stream(sim.h, stream.cuda_stream)
+    binding.slpic_set_tuning(sim.h, compact_every=args.compact_every)
     sim.load_state(state)
     sim.prepare()
 
@@ -597,6 +598,7 @@ def run_e2e(prob, settled, args, binding, torch, stream):
     steps = max(1, min(args.steps, args.e2e_steps))
     sim = binding.Simulation(prob)
     binding.slpic_set_stream(sim.h, stream.cuda_stream)
+    binding.slpic_set_tuning(sim.h, compact_every=args.compact_every)
     torch.cuda.synchronize()
     h2d = sum(a.nbytes + b.nbytes + c.nbytes for a, b, c in pinned)
     t0 = time.perf_counter()
@@ -1187,6 +1189,10 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="sheath1d / batch: pick the compaction interval, particle kernel and "
                          "batch work split with slpic_autotune after the warm-up")
+    ap.add_argument("--compact-every", type=int, default=32,
+                    help="sheath1d: the compaction interval (slpic_set_tuning), set before the "
+                         "load; 32 measured about 1%% faster per step than the library's "
+                         "default 16 on the saturated sheath, whose holes are few")
     ap.add_argument("--unet-pairs", type=int, default=96)
     ap.add_argument("--unet-train-steps", type=int, default=1500)
     ap.add_argument("--unet-batch", type=int, default=4)
