@@ -448,21 +448,26 @@ def run_gpu(args):
     n_replay = min(args.steps, 4096)
     # the replay ends where the timed steps did (checked when it covers all of them)
     replay_same = None if n_replay < args.steps else sim.diagnostics()["step"] == dg1["step"]
+    n_replay_end = live()  # the live count where the replay ends
     iterative_per_step = (sum(dg1["iterative"]) - sum(dg0["iterative"])) / args.steps
 
     t_max, particle_steps = aggregate_ranks(ms, 0.5 * (n0 + n1) * args.steps, dist, "cuda")
     value = particle_steps / (t_max * 1e-3)
 
     # roofline of the particle kernel (dominant kernel): algorithmic bytes over its
-    # CUDA-event duration on the library's stream, the timed steps replayed
+    # CUDA-event duration on the library's stream, the timed steps replayed; the
+    # particles per launch are the mean live count over the replayed steps
     n_mean = 0.5 * (n0 + n1)
+    n_launch = 0.5 * (n0 + n_replay_end)
     peak, peak_kind = hbm_peak()
     if push_ms <= 0:
         push_ms = span_ms[0]
-    achieved = BYTES_PER_PARTICLE_STEP * n_mean / (push_ms * 1e-3) / 1e9
+        n_launch = n_mean
+    achieved = BYTES_PER_PARTICLE_STEP * n_launch / (push_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": profiled_traffic(n_mean) if lam is None else None,
+            "traffic": profiled_traffic(n_launch) if lam is None else None,
+            "particles_per_launch": n_launch,
             "kernel": (f"{'k_particles_tma' if tuning['particle_kernel'] == 0 else 'k_particles'}"
                        f"{'' if lam is None else ' (speed-limit profile variant)'} "
                        f"(in-place steps; k_particles_compact every {tuning['compact_every']})"),
