@@ -136,6 +136,32 @@ def test_single_step_matches_oracle(kind, periodic):
     gpu.close()
 
 
+@pytest.mark.parametrize("n_per", [(1, 3), (7, 0), (151 * 4 + 3, 2), (4_099, 5),
+                                   (1984 * 151 + 13, 1)])
+def test_single_step_with_ragged_counts_matches_oracle(n_per):
+    """The in-place particle kernel splits each species' slots over its CTAs in shares
+    whose boundaries are multiples of 4, walked in tiles of 1,984: counts that leave most
+    CTAs no slot, a CTA with fewer than 4 slots (no bulk copy of cells), tails of 1 to 3
+    cells read one by one, and shares just over one whole tile.  Each is stepped once
+    against the oracle (strong field, both beta regimes, a biased plate), and the deposit
+    of the stepped particles is the oracle's rule on them, bit for bit."""
+    v0 = 0.3
+    prob = _problem(N=96, periodic=False, kind=HEAV, v0=v0, dx=0.5, dt=0.5 / v0, phi_hi=2.0,
+                    capacity=max(n_per) + 64)
+    st = _state(prob, n_per, seed=sum(n_per) + 17, vscale=1.0, nonneutral=True)
+    gpu = _sim(prob, st)
+    o = _oracle(prob, st)
+    gpu.step(1)
+    gpu.synchronize()
+    o.step(1)
+    _compare_step(prob, st, gpu, o)
+    for s in range(2):
+        c, off, v = gpu.particles(s)
+        ref = orc.deposit_q40(96, False, c, off, v, HEAV, np.float32(v0))
+        assert np.array_equal(gpu.charge_raw(s), ref), f"species {s}"
+    gpu.close()
+
+
 def test_slow_particles_are_plain_leapfrog_bitwise():
     """Heaviside beta with v0 above every speed: the GPU push is the beta = 1
     push bit for bit (Sec. II: SLPIC identical to PIC)."""
